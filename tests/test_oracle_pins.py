@@ -1,0 +1,392 @@
+"""Pins of the CPU oracle against the mathematics (no GPU).
+
+Each test checks the oracle against something other than itself: closed-form
+Fourier symbols, textbook special cases, exact invariants (conservation,
+linearity, projector identities), order of accuracy, the Parareal exactness
+property K = N, and a dense brute-force restatement of Alg. 2 on tiny grids.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests import symbols as S
+
+
+def _prob(nx=16, ny=8, N=4, **kw):
+    p = W.make_problem(nx, ny, N, **kw)
+    return p
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+# ---------------------------------------------------------------- fine propagator
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("UV", [(0.1, 0.0), (-0.3, 0.2)])
+def test_fine_plane_wave_matches_closed_form(order, UV):
+    """RK-3 + flux-form stencils on a plane wave equal R(dt A)^n qhat (Sec. 3, fine F)."""
+    U, V = UV
+    p = dataclasses.replace(_prob(16, 8, U=U, V=V), adv_order_f=order)
+    rng = np.random.default_rng(order)
+    for kx, ky in [(1, 0), (0, 1), (3, 2), (-5, 3), (8, 4), (7, -3)]:
+        qhat = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+        q0 = S.plane_wave(p.nx, p.ny, kx, ky, qhat)
+        n = 3
+        got = oracle.fine_steps(p, q0.ravel(), n).reshape(3, p.ny, p.nx)
+        want = S.plane_wave(p.nx, p.ny, kx, ky, S.fine_amplification(p, kx, ky, n) @ qhat)
+        assert _rel(got, want) < 1e-13, (order, kx, ky, _rel(got, want))
+
+
+def test_fine_rhs_symbol_single_mode():
+    """L_f on a plane wave equals A(k) qhat (one evaluation, no time stepping)."""
+    p = _prob(32, 16)
+    qhat = np.array([0.3 + 0.1j, -0.2 + 0.5j, 0.7 - 0.4j])
+    for kx, ky in [(2, 1), (11, 5), (16, 8)]:
+        q0 = S.plane_wave(p.nx, p.ny, kx, ky, qhat)
+        got = oracle.fine_rhs(p, q0.ravel()).reshape(3, p.ny, p.nx)
+        want = S.plane_wave(p.nx, p.ny, kx, ky, S.fine_symbol(p, kx, ky) @ qhat)
+        assert np.max(np.abs(got - want)) < 1e-11 * max(1.0, np.max(np.abs(want)))
+
+
+@pytest.mark.parametrize("order,p_expect", [(2, 2), (4, 4), (6, 6), (1, 1), (3, 3), (5, 5)])
+def test_modified_wavenumber_order(order, p_expect):
+    """The advective symbol approximates i*theta with error O(theta^(p+1))."""
+    errs = []
+    for th in [0.2, 0.1]:
+        c, e = S.flux_symbol(order, th)
+        errs.append(abs(c + e - 1j * th))
+    rate = math.log(errs[0] / errs[1]) / math.log(2.0)
+    assert abs(rate - (p_expect + 1)) < 0.3, rate
+
+
+def test_rk3_undamped_scalar_amplification():
+    """Pure advection (c_s = 0, nu = 0, 6th order): |R(iy)|^2 = 1 - y^4/12 + y^6/36."""
+    p = dataclasses.replace(_prob(32, 8, U=0.7, c_s=0.0), nu_f=0.0)
+    for kx in [1, 4, 9, 15]:
+        q0 = S.plane_wave(p.nx, p.ny, kx, 0, np.array([1.0 + 0j, 0.0, 0.0]))
+        q1 = oracle.fine_steps(p, q0.ravel(), 1).reshape(3, p.ny, p.nx)
+        # complex amplitude from the projection on the mode
+        i = np.arange(p.nx)
+        ph = np.exp(1j * 2 * np.pi * kx / p.nx * i)
+        amp = 2.0 * np.mean(q1[0] * np.conj(ph)[None, :])
+        th = 2 * np.pi * kx / p.nx
+        kappa = (45 * np.sin(th) - 9 * np.sin(2 * th) + np.sin(3 * th)) / 30.0
+        y = -p.U * kappa * p.dt_f / (p.lx / p.nx)
+        assert abs(abs(amp) ** 2 - (1 - y ** 4 / 12 + y ** 6 / 36)) < 1e-13
+
+
+def _exact_plane_wave(p, n, kx, ky, qhat, T):
+    """Exact solution of Eq. acousticAd (no damping) for one Fourier mode."""
+    k1, k2 = 2 * np.pi * kx, 2 * np.pi * ky
+    A = -1j * (p.U * k1 + p.V * k2) * np.eye(3, dtype=complex)
+    A[0, 2] += -1j * p.c_s * k1
+    A[1, 2] += -1j * p.c_s * k2
+    A[2, 0] += -1j * p.c_s * k1
+    A[2, 1] += -1j * p.c_s * k2
+    w, Vv = np.linalg.eig(A)
+    E = Vv @ np.diag(np.exp(w * T)) @ np.linalg.inv(Vv)
+    return S.plane_wave(n, n, kx, ky, E @ qhat)
+
+
+@pytest.mark.parametrize("cs,rate", [(0.0, 3.0), (1.0, 2.0)])
+def test_fine_convergence_order(cs, rate):
+    """With nu_f = 0 and a fixed CFL number, F converges to the exact plane-wave
+    solution of Eq. acousticAd.  Pure advection (6th-order flux) is limited by
+    the 3rd-order RK-3 time error; with sound waves the 2nd-order centred
+    acoustic fluxes (Sec. 3) dominate."""
+    errs = []
+    for n in [32, 64, 128]:
+        p = W.Problem(nx=n, ny=n, U=0.4, V=0.3, c_s=cs, nu_f=0.0, dt_f=0.4 / n, n_f=1)
+        kx, ky = 1, 2
+        qhat = np.array([0.5, -0.2 + 0.3j, 1.0])
+        T = 0.4
+        nsteps = int(round(T / p.dt_f))
+        got = oracle.fine_steps(p, S.plane_wave(n, n, kx, ky, qhat).ravel(), nsteps)
+        errs.append(_rel(got, _exact_plane_wave(p, n, kx, ky, qhat, T)))
+    r1 = math.log(errs[0] / errs[1]) / math.log(2)
+    r2 = math.log(errs[1] / errs[2]) / math.log(2)
+    assert abs(r2 - rate) < 0.25 and abs(r1 - rate) < 0.4, (errs, r1, r2)
+
+
+# ---------------------------------------------------------------- coarse propagator
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_coarse_plane_wave_matches_closed_form(order):
+    """Split FE / forward-backward coarse step equals the product of substep symbols."""
+    p = dataclasses.replace(_prob(16, 8, U=0.15, V=-0.05), adv_order_c=order)
+    rng = np.random.default_rng(7)
+    for kx, ky in [(1, 0), (0, 1), (3, 2), (-5, 3), (8, 4)]:
+        qhat = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+        q0 = S.plane_wave(p.nx, p.ny, kx, ky, qhat)
+        got = oracle.coarse_steps(p, q0.ravel(), 2).reshape(3, p.ny, p.nx)
+        want = S.plane_wave(p.nx, p.ny, kx, ky, S.coarse_amplification(p, kx, ky, 2) @ qhat)
+        assert _rel(got, want) < 1e-13, (kx, ky, _rel(got, want))
+
+
+def test_coarse_reduces_to_upwind_forward_euler():
+    """c_s = 0, nu_c = 0: n_sound substeps with a frozen slow tendency are one
+    forward-Euler upwind step of length Delta t (textbook FTBS)."""
+    p = dataclasses.replace(_prob(16, 8, U=0.3, V=0.2, c_s=0.0), nu_c=0.0)
+    q0 = W.ic_random(p.nx, p.ny, seed=3)
+    got = oracle.coarse_steps(p, q0.ravel(), 1).reshape(q0.shape)
+    cx = p.U * p.dt_g * p.nx
+    cy = p.V * p.dt_g * p.ny
+    want = q0 - cx * (q0 - np.roll(q0, 1, axis=2)) - cy * (q0 - np.roll(q0, 1, axis=1))
+    assert np.max(np.abs(got - want)) < 1e-14
+
+
+def test_coarse_reduces_to_forward_backward_wave():
+    """U = V = 0, nu_c = 0: textbook forward-backward scheme for the wave system."""
+    p = dataclasses.replace(_prob(16, 8, U=0.0), nu_c=0.0)
+    q = W.ic_random(p.nx, p.ny, seed=4)
+    got = oracle.coarse_steps(p, q.ravel(), 1).reshape(q.shape)
+    tau = p.dt_g / p.n_sound
+    dx, dy = 1.0 / p.nx, 1.0 / p.ny
+    u, w, pr = q.copy()
+    ddx = lambda f: (np.roll(f, -1, 1) - np.roll(f, 1, 1)) / (2 * dx)
+    ddy = lambda f: (np.roll(f, -1, 0) - np.roll(f, 1, 0)) / (2 * dy)
+    for _ in range(p.n_sound):
+        u, w = u - tau * p.c_s * ddx(pr), w - tau * p.c_s * ddy(pr)
+        pr = pr - tau * p.c_s * (ddx(u) + ddy(w))
+    assert np.max(np.abs(got - np.stack([u, w, pr]))) < 1e-14
+
+
+def _coarse_worst(p, step=1):
+    worst = 0.0
+    for kx in range(-p.nx // 2 + 1, p.nx // 2 + 1, step):
+        for ky in range(-p.ny // 2 + 1, p.ny // 2 + 1, step):
+            worst = max(worst, np.max(np.abs(np.linalg.eigvals(S.coarse_amplification(p, kx, ky, 1)))))
+    return worst
+
+
+def test_coarse_stability_at_workload_parameters():
+    """Spectral radius of the coarse-step symbol at C_c = 4, N_sound = 4, nu_c = 0.1.
+
+    Without advection (U = 0) the forward-backward substeps with divergence
+    damping are stable (radius <= 1).  With U/c_s = 0.1 the partially split
+    forward Euler step is weakly unstable for a band of modes around
+    k dx ~ 0.7 (radius 1.0927 per coarse step): the semi-discrete instability
+    of partially split forward Euler that Sec. 3.2 mentions, which damping
+    reduces but does not remove at these parameters."""
+    p = W.make_problem(64, 32, 8)
+    assert _coarse_worst(dataclasses.replace(p, U=0.0)) <= 1.0 + 1e-12
+    w = _coarse_worst(p)
+    assert 1.09 < w < 1.095, w
+    assert _coarse_worst(dataclasses.replace(p, nu_c=0.2)) < w  # more damping helps
+    assert 1.09 < _coarse_worst(W.make_problem(256, 128, 32), step=2) < 1.095
+
+
+def test_fine_is_stable_at_workload_parameters():
+    for p in [W.make_problem(64, 32, 8), W.make_problem(512, 256, 64)]:
+        worst = 0.0
+        for kx in range(-p.nx // 2 + 1, p.nx // 2 + 1, max(1, p.nx // 64)):
+            for ky in range(-p.ny // 2 + 1, p.ny // 2 + 1, max(1, p.ny // 32)):
+                R = S.rk3_matrix(S.fine_symbol(p, kx, ky), p.dt_f)
+                worst = max(worst, np.max(np.abs(np.linalg.eigvals(R))))
+        assert worst <= 1.0 + 1e-12, worst
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("which", ["fine", "coarse"])
+def test_conservation_of_field_sums(which):
+    """Flux form + periodicity conserve sum(u), sum(w), sum(p) exactly (to rounding)."""
+    p = _prob(32, 16, U=0.2, V=0.1)
+    q0 = W.ic_random(p.nx, p.ny, seed=5) + 0.3
+    f = oracle.fine_prop if which == "fine" else oracle.coarse_prop
+    q1 = f(p, q0.ravel()).reshape(q0.shape)
+    for k in range(3):
+        assert abs(q1[k].sum() - q0[k].sum()) < 1e-12 * np.abs(q0[k]).sum()
+
+
+@pytest.mark.parametrize("which", ["fine", "coarse"])
+def test_linearity(which):
+    p = _prob(32, 16)
+    x = W.ic_random(p.nx, p.ny, seed=1).ravel()
+    y = W.ic_random(p.nx, p.ny, seed=2).ravel()
+    f = oracle.fine_prop if which == "fine" else oracle.coarse_prop
+    lhs = f(p, 2.5 * x - 0.75 * y)
+    rhs = 2.5 * f(p, x) - 0.75 * f(p, y)
+    assert _rel(lhs, rhs) < 1e-13
+
+
+def test_damping_removes_only_divergence():
+    """A divergence-free mode (u depends on y only, w = p = 0) is untouched by the
+    damping term; a divergent one is damped (Sec. 3.2)."""
+    p = dataclasses.replace(_prob(16, 16), U=0.0, c_s=0.0, nu_f=0.01)
+    L = oracle.fine_rhs(p, S.plane_wave(16, 16, 0, 3, np.array([1.0, 0, 0])).ravel())
+    assert np.max(np.abs(L)) < 1e-12
+    L = oracle.fine_rhs(p, S.plane_wave(16, 16, 3, 0, np.array([1.0, 0, 0])).ravel())
+    assert np.max(np.abs(L)) > 1e-3
+
+
+# ---------------------------------------------------------------- subspace / projector
+
+def test_basis_projector_identities():
+    p = _prob(16, 8)
+    d = p.d
+    rng = np.random.default_rng(11)
+    B = oracle.Basis(d, 40)
+    cols = []
+    for j in range(12):
+        a = rng.standard_normal(d)
+        kept, ratio = B.add(a, oracle.fine_prop(p, a))
+        assert kept and ratio > 0.1
+        cols.append(a)
+    # a dependent column (combination of kept ones) and an exact duplicate are dropped
+    comb = sum((0.3 * (j + 1)) * c for j, c in enumerate(cols[:5]))
+    kept, ratio = B.add(comb, oracle.fine_prop(p, comb))
+    assert not kept and ratio < 1e-13
+    kept, ratio = B.add(cols[3], oracle.fine_prop(p, cols[3]))
+    assert not kept and ratio < 1e-13
+    Q = B.Q()
+    assert Q.shape == (d, 12)
+    assert np.max(np.abs(Q.T @ Q - np.eye(12))) < 1e-13
+    P = Q @ Q.T
+    assert np.max(np.abs(P @ P - P)) < 1e-13
+    for c in cols:
+        assert _rel(P @ c, c) < 1e-13
+    # F(P q) from stored images (Eq. Genhance) equals F applied to P q
+    q = rng.standard_normal(d)
+    Pq, FPq = B.project(q)
+    assert _rel(Pq, P @ q) < 1e-13
+    assert _rel(FPq, oracle.fine_prop(p, Pq)) < 1e-12
+    # images of the basis vectors are F(Q)
+    FQ = B.FQ()
+    assert _rel(FQ[:, 5], oracle.fine_prop(p, Q[:, 5])) < 1e-12
+
+
+def test_basis_cap_freezes():
+    d = 50
+    B = oracle.Basis(d, 3)
+    rng = np.random.default_rng(0)
+    kept = [B.add(rng.standard_normal(d), rng.standard_normal(d))[0] for _ in range(5)]
+    assert kept == [True, True, True, False, False] and B.rank == 3
+
+
+# ---------------------------------------------------------------- Parareal
+
+def test_parareal_K_equals_N_reproduces_serial_fine_bitwise():
+    """After N iterations Parareal returns the sequential fine solution (Sec. 2.1),
+    and q_i^k = q_seq(t_i) for i <= k, bit for bit (Alg. 2 correction evaluated
+    as q~ + (K_new - K_old))."""
+    p = _prob(16, 8, N=5)
+    q0 = W.ic_gaussian(p.nx, p.ny, seed=0).ravel()
+    qs = oracle.serial_fine(p, q0)
+    for K in range(1, 6):
+        r = oracle.parareal(p, q0, K)
+        assert np.array_equal(r["q"][: K + 1], qs[: K + 1])
+    assert np.array_equal(oracle.parareal(p, q0, 5)["q"], qs)
+    assert np.array_equal(oracle.parareal(p, q0, 5, variant="original")["q"], qs)
+
+
+def test_parareal_K0_is_serial_coarse():
+    p = _prob(16, 8, N=4)
+    q0 = W.ic_gaussian(p.nx, p.ny, seed=0).ravel()
+    r = oracle.parareal(p, q0, 0)
+    q = q0.copy()
+    for n in range(p.n_slices):
+        q = oracle.coarse_prop(p, q)
+        assert np.array_equal(r["q"][n + 1], q)
+
+
+def test_parareal_invariant_subspace_gives_fine_after_one_iteration():
+    """Once S^k contains every iterate (the span stops growing), P q = q on the
+    iterates, K acts as F on them and the next iterate is the serial fine
+    solution (Sec. 2.2).  On a 2x2 periodic grid the coarse chain of a random
+    q0 spans a 7-dimensional subspace that both propagators map into itself."""
+    p = W.Problem(nx=2, ny=2, U=0.13, V=0.07, c_s=1.0, n_slices=16, n_f=20, n_g=2,
+                  dt_f=1.0 / 320, dt_g=1.0 / 32, T=1.0)
+    q0 = W.ic_random(2, 2, seed=9).ravel()
+    r = oracle.parareal(p, q0, 2, cap=64)
+    assert list(r["rank"]) == [7, 7]
+    qs = oracle.serial_fine(p, q0)
+    assert _rel(r["q"], qs) < 1e-11
+    r1 = oracle.parareal(p, q0, 1, cap=64)
+    assert _rel(r1["q"], qs) < 1e-11
+    # original Parareal has no such shortcut
+    assert _rel(oracle.parareal(p, q0, 1, variant="original")["q"], qs) > 1e-6
+
+
+def _dense_operator(fn, p, d):
+    M = np.empty((d, d))
+    for j in range(d):
+        e = np.zeros(d)
+        e[j] = 1.0
+        M[:, j] = fn(p, e)
+    return M
+
+
+def _dense_parareal(F, G, q0, N, K, eta, variant="kse"):
+    """Alg. 2 / Alg. 1 with dense matrices and an SVD-based projector."""
+    d = q0.size
+    q = [q0]
+    for i in range(N):
+        q.append(G @ q[i])
+    cols, ranks, rs = [], [], []
+    for k in range(K):
+        qt = [F @ q[i] for i in range(N)]
+        if variant == "kse":
+            for i in range(N):
+                a = q[i]
+                if cols:
+                    Uu = np.linalg.svd(np.stack(cols, 1), full_matrices=False)[0]
+                    res = np.linalg.norm(a - Uu @ (Uu.T @ a))
+                else:
+                    res = np.linalg.norm(a)
+                if res > eta * np.linalg.norm(a):
+                    cols.append(a)
+            Uu = np.linalg.svd(np.stack(cols, 1), full_matrices=False)[0]
+            P = Uu @ Uu.T
+            Kop = lambda x: G @ (x - P @ x) + F @ (P @ x)
+        else:
+            Kop = lambda x: G @ x
+        qn = [q0]
+        for i in range(N):
+            qn.append(qt[i] + (Kop(qn[i]) - Kop(q[i])))
+        rs.append(max(np.linalg.norm(qn[i] - q[i]) for i in range(1, N + 1)))
+        ranks.append(len(cols))
+        q = qn
+    return np.stack(q), np.array(rs), np.array(ranks)
+
+
+@pytest.mark.parametrize("variant", ["kse", "original"])
+@pytest.mark.parametrize("N,K", [(4, 2), (6, 3)])
+def test_parareal_matches_dense_brute_force(variant, N, K):
+    """Alg. 2 in the oracle (Householder basis, images by linearity) equals a
+    dense restatement (explicit F and G matrices, SVD projector, F applied to
+    P q directly) on an 8x4 grid (d = 96)."""
+    p = _prob(8, 4, N=N)
+    d = p.d
+    F = _dense_operator(oracle.fine_prop, p, d)
+    G = _dense_operator(oracle.coarse_prop, p, d)
+    q0 = W.ic_gaussian(p.nx, p.ny, seed=0).ravel()
+    want_q, want_r, want_rank = _dense_parareal(F, G, q0, N, K, 1e-10, variant)
+    got = oracle.parareal(p, q0, K, variant=variant)
+    assert _rel(got["q"], want_q) < 1e-12
+    assert np.allclose(got["r"], want_r, rtol=1e-10, atol=0)
+    if variant == "kse":
+        assert np.array_equal(got["rank"], want_rank)
+
+
+def test_kse_error_decreases_on_small_workload():
+    """The iteration error falls with k and reaches zero at K = N (64x32, N = 8)."""
+    wl = W.workload_small()
+    p = wl.problem
+    q0 = wl.ics[0][1]().ravel()
+    qs = oracle.serial_fine(p, q0)
+    r = oracle.parareal(p, q0, 4)
+    errs = []
+    for K in range(0, 5):
+        rr = oracle.parareal(p, q0, K)
+        errs.append(oracle.rel_error(rr["q"][-1], qs[-1]))
+    assert all(errs[i + 1] < errs[i] for i in range(4)), errs
+    assert list(r["rank"]) == [8, 15, 21, 26]
