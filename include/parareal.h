@@ -1,0 +1,164 @@
+/*
+ * parareal.h -- C ABI of the GB300 (sm_103a) KSE-Parareal library for the
+ * linear 2D acoustic-advection system (Ruprecht & Krause, "Explicit
+ * Parallel-in-time Integration of a Linear Acoustic-Advection System",
+ * arXiv 1510.02237).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - A state q holds d = 3*nx*ny doubles laid out [field][y][x] with x
+ *    contiguous; fields are (u, w, p) = the paper's (u, v, pi) of
+ *    Eq. acousticAd.  The domain is periodic, [0,lx) x [0,ly), cells of size
+ *    dx = lx/nx, dy = ly/ny (Sec. 3, flux form on equal rectangular cells).
+ *  - A batch of n states is n*d contiguous doubles.
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *    library never frees or retains them beyond the call.  Host pointers are
+ *    ordinary (pageable or pinned) host memory, also owned by the caller.
+ *  - All device work is enqueued on the handle's stream (pr_options.stream,
+ *    a cudaStream_t; NULL means the legacy default stream).  Calls return
+ *    after enqueueing unless stated otherwise; results are valid once the
+ *    stream has reached that point.
+ *  - Every call returns a pr_status; no exception crosses the ABI.  On an
+ *    error the handle keeps a message readable with parareal_last_error().
+ *    PR_EINVAL leaves the handle unchanged.  After PR_ECUDA the handle's
+ *    device state is unspecified and it should be destroyed.
+ *  - One handle per host thread; handles are independent.
+ */
+#ifndef PARAREAL_H
+#define PARAREAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pr_solver pr_solver; /* opaque: owns iterates, fine images, basis Q and D = F(Q) - G(Q) */
+
+typedef enum {
+    PR_OK = 0,
+    PR_EINVAL = -1,     /* bad argument (sizes, NaN, unsupported option)      */
+    PR_ENOMEM = -2,     /* device or host allocation failed                   */
+    PR_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed        */
+    PR_ETIMEOUT = -4,   /* a bounded device wait gave up                      */
+    PR_ESTATE = -5,     /* call not valid in the handle's current state       */
+    PR_ECANCELLED = -6  /* request cancelled                                  */
+} pr_status;
+
+enum { PR_FP64 = 0, PR_FP32 = 1 };                 /* arithmetic of the fine sweep   */
+enum { PR_KSE = 0, PR_ORIGINAL = 1 };              /* Alg. 2 / Alg. 1                */
+#define PR_MAX_ITERS 128
+
+typedef struct {
+    int32_t nx, ny;   /* cells in x and y; nx, ny >= 4                          */
+    double lx, ly;    /* domain lengths; <= 0 means 1.0                         */
+} pr_grid;
+
+typedef struct {
+    double T;              /* end time of the single parallel step (default 1.0) */
+    double nu_f;           /* fine divergence damping factor, Eq. dampingCoeff (0.005) */
+    double nu_c;           /* coarse divergence damping factor (0.1)             */
+    int32_t n_sound;       /* acoustic substeps per coarse step, Sec. 3.2 (4)    */
+    int32_t adv_order_f;   /* advective flux order of F: 6 (centred)             */
+    int32_t adv_order_c;   /* advective flux order of G: 1 (upwind)              */
+    double V;              /* y component of the advection velocity (0.0)        */
+    int32_t K_max;         /* largest K passed to parareal_solve (default N)     */
+    int32_t krylov_cap;    /* max dim of S^k; 0 = sum_{k<K_max} (N - k)          */
+    double drop_tol;       /* eta: drop a column whose residual after projection
+                              is <= eta * its norm (1e-10)                       */
+    int32_t fine_prec;     /* PR_FP64 or PR_FP32 arithmetic inside F             */
+    int32_t variant;       /* PR_KSE (Alg. 2) or PR_ORIGINAL (Alg. 1)            */
+    void* stream;          /* cudaStream_t, or NULL                              */
+} pr_options;
+
+typedef struct {
+    int32_t K;                   /* iterations performed                          */
+    int32_t rank[PR_MAX_ITERS];  /* dim S^k after the update of iteration k      */
+    double r[PR_MAX_ITERS];      /* r^k = max_i ||q_i^{k+1} - q_i^k||_2 (Sec. 2.1) */
+    float ms_total;              /* device time of the whole solve (CUDA events)  */
+} pr_report;
+
+/* Fill *opt with the defaults listed above (the paper's values, Sec. 3.2). */
+pr_status parareal_default_options(pr_options* opt);
+
+/* Create a solver for  q_t = f(q)  (Eq. ODE) from the spatial discretisation
+ * of Eq. acousticAd with constant advection velocity (U, opt->V) and sound
+ * speed c_s.  The interval [0, T] is split into N_slices time slices of
+ * length T/N_slices (Sec. 2.1); the fine propagator F uses dt_f (RK-3) and
+ * the coarse propagator G uses dt_g (partially split forward Euler with
+ * forward-backward acoustic substeps, Sec. 3.2).  T/N_slices must be an
+ * integer multiple of dt_f and of dt_g within 1e-9 relative (PR_EINVAL
+ * otherwise).  Allocates every device buffer the solve needs; later calls
+ * do not allocate.  *out receives the handle (NULL on failure). */
+pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, double dt_g,
+                          int32_t N_slices, const pr_options* opt, pr_solver** out);
+
+/* Release the handle and its device memory (synchronises its stream). */
+pr_status parareal_destroy(pr_solver* h);
+
+/* Message of the last error on h ("" if none).  Valid until the next call on h.
+ * h == NULL returns the message of the last failed parareal_create. */
+const char* parareal_last_error(const pr_solver* h);
+
+/* Bytes of device memory a handle with these parameters holds. */
+size_t parareal_footprint_bytes(const pr_grid* g, int32_t N_slices, const pr_options* opt);
+
+/* KSE-Parareal, Alg. 2 (or Alg. 1 with variant = PR_ORIGINAL):
+ * initialise q_{i+1}^0 = G(q_i^0) serially, then K_iters iterations of
+ * parallel fine predictor, subspace update (Eq. subspaceUpdate) and serial
+ * correction q_{i+1}^{k+1} = q~_{i+1}^k + (K(q_i^{k+1}) - K(q_i^k)) with the
+ * modified coarse propagator K of Eq. modifiedCoarse.
+ *   u0_dev : device, d doubles, the initial value q_0.
+ *   K_iters: 0 <= K_iters <= opt.K_max.
+ *   q_out_dev: device, (N+1)*d doubles receiving q_n^K, n = 0..N; may be NULL.
+ *   qT_dev : device, d doubles receiving q_N^K; may be NULL.
+ *   rep    : host; if non-NULL the call synchronises the stream and fills it.
+ * The subspace S^K remains in the handle for krylov_project(). */
+pr_status parareal_solve(pr_solver* h, const double* u0_dev, int32_t K_iters, double* q_out_dev,
+                         double* qT_dev, pr_report* rep);
+
+/* parareal_solve with host buffers: copies u0_host (d doubles) to the device,
+ * solves, and copies q_N^K back to qT_host (d doubles).  Synchronous. */
+pr_status parareal_solve_host(pr_solver* h, const double* u0_host, int32_t K_iters, double* qT_host,
+                              pr_report* rep);
+
+/* Fine propagator F over one slice (N_f = (T/N)/dt_f RK-3 steps, Sec. 3.2)
+ * applied independently to n states: q_out[i] = F(q_in[i]), the parallel
+ * predictor of Alg. 2.  q_in_dev / q_out_dev: device, n*d doubles each,
+ * must not overlap.  1 <= n <= N_slices. */
+pr_status parareal_fine_sweep(pr_solver* h, const double* q_in_dev, double* q_out_dev, int32_t n);
+
+/* Serial coarse sweep (initialisation of Alg. 2): q_out[i] = G^{i+1}(q0),
+ * i = 0..N-1.  q0_dev: d doubles; q_out_dev: N*d doubles (device). */
+pr_status parareal_coarse_sweep(pr_solver* h, const double* q0_dev, double* q_out_dev);
+
+/* Coarse propagator G over one slice applied independently to n states. */
+pr_status parareal_coarse_apply(pr_solver* h, const double* q_in_dev, double* q_out_dev, int32_t n);
+
+/* Empty the handle's subspace (S = {}). */
+pr_status krylov_reset(pr_solver* h);
+
+/* Subspace update S -> S + span{V_j} (Sec. 2.2, Eq. subspaceUpdate) with the
+ * fine images FV_j = F(V_j): the columns are orthogonalised in order against
+ * the current basis (block classical Gram-Schmidt, applied twice) and then
+ * against each other; column j is dropped when its residual is <= drop_tol
+ * times its norm or the basis is full.  The same transformation applied to
+ * F(V_j) - G(V_j) keeps D = F(Q) - G(Q) exact by linearity.
+ *   V_dev, FV_dev: device, m*d doubles each.  kept_host: optional host array
+ *   of m flags (synchronises when non-NULL).  1 <= m <= N_slices. */
+pr_status krylov_update(pr_solver* h, const double* V_dev, const double* FV_dev, int32_t m,
+                        int32_t* kept_host);
+
+/* Current dim S (synchronises). */
+pr_status krylov_rank(pr_solver* h, int32_t* rank);
+
+/* Projection onto the current subspace (Sec. 2.2): Pq = Q Q^T q and, by
+ * linearity (Eq. Genhance), FPq = F(P q) = D (Q^T q) + G(P q).  q_dev, Pq_dev,
+ * FPq_dev: device, d doubles each; Pq_dev or FPq_dev may be NULL. */
+pr_status krylov_project(pr_solver* h, const double* q_dev, double* Pq_dev, double* FPq_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PARAREAL_H */

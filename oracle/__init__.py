@@ -24,7 +24,7 @@ import os
 
 import numpy as np
 
-from ._build import build as _build
+from ._build import build as _build_lib
 
 _lib = None
 
@@ -45,7 +45,7 @@ _I = C.POINTER(C.c_int)
 def lib():
     global _lib
     if _lib is None:
-        path = _build()
+        path = _build_lib()
         L = C.CDLL(path)
         pp = C.POINTER(_Problem)
         for name in ("orc_fine_rhs",):

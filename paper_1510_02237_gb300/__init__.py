@@ -1,0 +1,224 @@
+"""Python binding of the GB300 KSE-Parareal library (``libparareal.so``).
+
+Thin ctypes marshalling over the C ABI declared in ``include/parareal.h``;
+every step of the computation runs in the library's CUDA kernels.  PyTorch
+is used only for device memory (tensors passed by pointer) and streams.
+Importing this module loads the in-tree library and raises if it has not
+been built -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libparareal.so")
+
+PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ETIMEOUT, PR_ESTATE, PR_ECANCELLED = 0, -1, -2, -3, -4, -5, -6
+PR_FP64, PR_FP32 = 0, 1
+PR_KSE, PR_ORIGINAL = 0, 1
+PR_MAX_ITERS = 128
+_STATUS = {0: "PR_OK", -1: "PR_EINVAL", -2: "PR_ENOMEM", -3: "PR_ECUDA", -4: "PR_ETIMEOUT",
+           -5: "PR_ESTATE", -6: "PR_ECANCELLED"}
+
+
+class pr_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("lx", C.c_double), ("ly", C.c_double)]
+
+
+class pr_options(C.Structure):
+    _fields_ = [("T", C.c_double), ("nu_f", C.c_double), ("nu_c", C.c_double), ("n_sound", C.c_int32),
+                ("adv_order_f", C.c_int32), ("adv_order_c", C.c_int32), ("V", C.c_double),
+                ("K_max", C.c_int32), ("krylov_cap", C.c_int32), ("drop_tol", C.c_double),
+                ("fine_prec", C.c_int32), ("variant", C.c_int32), ("stream", C.c_void_p)]
+
+
+class pr_report(C.Structure):
+    _fields_ = [("K", C.c_int32), ("rank", C.c_int32 * PR_MAX_ITERS), ("r", C.c_double * PR_MAX_ITERS),
+                ("ms_total", C.c_float)]
+
+
+class PararealError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+EXPORTS = ["parareal_default_options", "parareal_create", "parareal_destroy", "parareal_last_error",
+           "parareal_footprint_bytes", "parareal_solve", "parareal_solve_host", "parareal_fine_sweep",
+           "parareal_coarse_sweep", "parareal_coarse_apply", "krylov_reset", "krylov_update", "krylov_rank",
+           "krylov_project"]
+
+_lib = None
+
+
+def lib():
+    """Load ``libparareal.so`` (raises if missing: build it with ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not built; run python -c 'import __graft_entry__ as g; g.build()'")
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    st = C.c_int
+    L.parareal_default_options.argtypes = [C.POINTER(pr_options)]
+    L.parareal_default_options.restype = st
+    L.parareal_create.argtypes = [C.POINTER(pr_grid), C.c_double, C.c_double, C.c_double, C.c_double,
+                                  C.c_int32, C.POINTER(pr_options), C.POINTER(P)]
+    L.parareal_create.restype = st
+    L.parareal_destroy.argtypes = [P]
+    L.parareal_destroy.restype = st
+    L.parareal_last_error.argtypes = [P]
+    L.parareal_last_error.restype = C.c_char_p
+    L.parareal_footprint_bytes.argtypes = [C.POINTER(pr_grid), C.c_int32, C.POINTER(pr_options)]
+    L.parareal_footprint_bytes.restype = C.c_size_t
+    L.parareal_solve.argtypes = [P, P, C.c_int32, P, P, C.POINTER(pr_report)]
+    L.parareal_solve.restype = st
+    L.parareal_solve_host.argtypes = [P, P, C.c_int32, P, C.POINTER(pr_report)]
+    L.parareal_solve_host.restype = st
+    L.parareal_fine_sweep.argtypes = [P, P, P, C.c_int32]
+    L.parareal_fine_sweep.restype = st
+    L.parareal_coarse_sweep.argtypes = [P, P, P]
+    L.parareal_coarse_sweep.restype = st
+    L.parareal_coarse_apply.argtypes = [P, P, P, C.c_int32]
+    L.parareal_coarse_apply.restype = st
+    L.krylov_reset.argtypes = [P]
+    L.krylov_reset.restype = st
+    L.krylov_update.argtypes = [P, P, P, C.c_int32, C.POINTER(C.c_int32)]
+    L.krylov_update.restype = st
+    L.krylov_rank.argtypes = [P, C.POINTER(C.c_int32)]
+    L.krylov_rank.restype = st
+    L.krylov_project.argtypes = [P, P, P, P]
+    L.krylov_project.restype = st
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    """Device (or host) address of a tensor / array, or None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return C.c_void_p(t.data_ptr())
+    if hasattr(t, "ctypes"):
+        return C.c_void_p(t.ctypes.data)
+    return C.c_void_p(int(t))
+
+
+def _check(h, status):
+    if status != PR_OK:
+        msg = lib().parareal_last_error(h)
+        raise PararealError(status, msg.decode() if msg else "")
+
+
+def parareal_default_options(**over) -> pr_options:
+    o = pr_options()
+    lib().parareal_default_options(C.byref(o))
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+def parareal_footprint_bytes(nx, ny, N, **opt) -> int:
+    return int(lib().parareal_footprint_bytes(C.byref(pr_grid(nx, ny, 1.0, 1.0)), int(N),
+                                              C.byref(parareal_default_options(**opt))))
+
+
+def parareal_create(nx, ny, U, c_s, dt_f, dt_g, N_slices, *, stream=None, **opt):
+    """Returns an opaque handle (int).  ``stream``: a ``torch.cuda.Stream``/raw handle or None."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    o = parareal_default_options(**opt)
+    o.stream = C.c_void_p(stream) if stream else None
+    h = C.c_void_p()
+    _check(None, lib().parareal_create(C.byref(pr_grid(nx, ny, 1.0, 1.0)), float(U), float(c_s), float(dt_f),
+                                       float(dt_g), int(N_slices), C.byref(o), C.byref(h)))
+    return h
+
+
+def parareal_destroy(h):
+    _check(h, lib().parareal_destroy(h))
+
+
+def parareal_last_error(h) -> str:
+    m = lib().parareal_last_error(h)
+    return m.decode() if m else ""
+
+
+def parareal_solve(h, u0, K, q_out=None, qT=None, report=True):
+    rep = pr_report() if report else None
+    _check(h, lib().parareal_solve(h, _ptr(u0), int(K), _ptr(q_out), _ptr(qT),
+                                   C.byref(rep) if rep is not None else None))
+    return rep
+
+
+def parareal_solve_host(h, u0_host, K, qT_host, report=True):
+    rep = pr_report() if report else None
+    _check(h, lib().parareal_solve_host(h, _ptr(u0_host), int(K), _ptr(qT_host),
+                                        C.byref(rep) if rep is not None else None))
+    return rep
+
+
+def parareal_fine_sweep(h, q_in, q_out, n):
+    _check(h, lib().parareal_fine_sweep(h, _ptr(q_in), _ptr(q_out), int(n)))
+
+
+def parareal_coarse_sweep(h, q0, q_out):
+    _check(h, lib().parareal_coarse_sweep(h, _ptr(q0), _ptr(q_out)))
+
+
+def parareal_coarse_apply(h, q_in, q_out, n):
+    _check(h, lib().parareal_coarse_apply(h, _ptr(q_in), _ptr(q_out), int(n)))
+
+
+def krylov_reset(h):
+    _check(h, lib().krylov_reset(h))
+
+
+def krylov_update(h, V, FV, m, want_kept=True):
+    kept = (C.c_int32 * int(m))() if want_kept else None
+    _check(h, lib().krylov_update(h, _ptr(V), _ptr(FV), int(m), kept))
+    return list(kept) if want_kept else None
+
+
+def krylov_rank(h) -> int:
+    r = C.c_int32()
+    _check(h, lib().krylov_rank(h, C.byref(r)))
+    return r.value
+
+
+def krylov_project(h, q, Pq=None, FPq=None):
+    _check(h, lib().krylov_project(h, _ptr(q), _ptr(Pq), _ptr(FPq)))
+
+
+class Solver:
+    """Convenience owner of a handle for a ``workloads.Problem``-like object."""
+
+    def __init__(self, p, *, stream=None, **opt):
+        opt.setdefault("T", p.T)
+        opt.setdefault("nu_f", p.nu_f)
+        opt.setdefault("nu_c", p.nu_c)
+        opt.setdefault("n_sound", p.n_sound)
+        opt.setdefault("adv_order_f", p.adv_order_f)
+        opt.setdefault("adv_order_c", p.adv_order_c)
+        opt.setdefault("V", p.V)
+        self.p = p
+        self.h = parareal_create(p.nx, p.ny, p.U, p.c_s, p.dt_f, p.dt_g, p.n_slices, stream=stream, **opt)
+
+    def close(self):
+        if self.h:
+            parareal_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,96 @@
+// common.cuh -- internal definitions shared by the CUDA translation units of
+// the KSE-Parareal library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pr {
+
+// Periodic index for offsets that may exceed one period (tiny grids).
+__host__ __device__ __forceinline__ int pwrap(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// Coefficients of the fine tendency L_f (Sec. 3 flux form, 6th-order
+// centred advection, 2nd-order centred acoustics, compact grad-div damping).
+template <typename T>
+struct FineCoef {
+    T ax6;    // U / (60 dx): multiplies the 6-point x advective difference
+    T ay6;    // V / (60 dy)
+    T csx;    // c_s / (2 dx)
+    T csy;    // c_s / (2 dy)
+    T dxx;    // alpha1 / dx^2
+    T dxy1;   // alpha1 / (4 dx dy)
+    T dyy;    // alpha2 / dy^2
+    T dxy2;   // alpha2 / (4 dx dy)
+    T c1, c2, c3;   // RK-3 stage lengths dt/3, dt/2, dt
+};
+
+// Coefficients of one partially split coarse step (Sec. 3.2).
+struct CoarseCoef {
+    double U, V;        // advection velocity (upwind direction from the sign)
+    double inv_dx, inv_dy;
+    double tau;         // acoustic substep Delta t / n_sound
+    double csx, csy;    // c_s / (2 dx), c_s / (2 dy)
+    double dxx, dxy1;   // alpha1 / dx^2, alpha1 / (4 dx dy); alpha = nu_c dx^2 / tau
+    double dyy, dxy2;   // alpha2 / dy^2, alpha2 / (4 dx dy)
+    int n_sound;
+    int order;          // 1 or 3 (upwind-biased advective flux)
+};
+
+// ------------------------------------------------------------ launchers
+// Each returns a cudaError_t from the launch.
+
+// One RK-3 step on n states.  in/out element types select FP64 or FP32
+// arithmetic (T) with conversion at the boundary.  instride/outstride are
+// element strides between consecutive states.
+template <typename T, typename Tin, typename Tout>
+cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outstride, int n, int nx,
+                             int ny, bool has_v, const FineCoef<T>& c, cudaStream_t s);
+
+// One coarse step (slow tendency + n_sound forward-backward substeps) on n states.
+cudaError_t launch_coarse_step(const double* in, double* out, long stride, int n, int nx, int ny,
+                               const CoarseCoef& c, cudaStream_t s);
+int coarse_halo(const CoarseCoef& c);
+
+// -------- tall-skinny FP64 linear algebra over d-long columns (column-major)
+// Column ranges are read from device memory ([*c0_dev, *c1_dev), c0_dev may be
+// NULL for 0) so a whole solve can be enqueued without host synchronisation;
+// ccap is the host-side upper bound used to size grids.
+struct TsWork {
+    double* partial;   // scratch for per-chunk partial sums
+    long elems;        // its capacity in doubles (>= tswork_elems(...))
+};
+long tswork_elems(long nrows, int ccap, int mmax);
+
+// C[c, j] = sum_rows A[row, c0 + c] * X[row, j]   (C column-major with leading dim ldc)
+cudaError_t gemm_tn(const double* A, long lda, const int* c0_dev, const int* c1_dev, int ccap,
+                    const double* X, long ldx, int m, long nrows, double* C, int ldc, const TsWork& w,
+                    cudaStream_t s);
+// Y[:, j] = B[:, j] + sgn * sum_c A[:, c0 + c] C[c, j]   (B may alias Y; B == NULL means 0)
+cudaError_t gemm_nn(const double* A, long lda, const int* c0_dev, const int* c1_dev, int ccap,
+                    const double* C, int ldc, const double* B, long ldb, double* Y, long ldy, int m,
+                    long nrows, double sgn, cudaStream_t s);
+// out[j] = sum_rows X[row, j]^2
+cudaError_t colnorm2(const double* X, long ldx, int m, long nrows, double* out, const TsWork& w,
+                     cudaStream_t s);
+// Append v / ||v|| and z / ||v|| as column *r of Q and D if ||v|| > eta ||a|| and *r < cap;
+// *kept receives the decision and *r is incremented when kept.
+cudaError_t krylov_append(const double* v, const double* z, const double* res2, const double* a2,
+                          double eta, int cap, int* r, double* Q, double* D, long ld, long nrows,
+                          int* kept, cudaStream_t s);
+// Serial correction of Alg. 2 for one slice: q <- qt + ((g + D c) - kold),
+// *res2_slot = ||q_new - q_old||^2.
+cudaError_t chain_update(const double* qt, const double* g, const double* D, long ldd, const int* c1_dev,
+                         int ccap, const double* c, const double* kold, double* q, long nrows,
+                         double* res2_slot, const TsWork& w, cudaStream_t s);
+// dst <- src with *res2 = ||src - dst_old||^2
+cudaError_t copy_resid(const double* src, double* dst, long n, double* res2, const TsWork& w, cudaStream_t s);
+// *out = max_i sqrt(res2[i])
+cudaError_t max_sqrt(const double* res2, int n, double* out, cudaStream_t s);
+cudaError_t sub(const double* a, const double* b, double* out, long n, cudaStream_t s);
+cudaError_t fill_int(int* p, int v, int n, cudaStream_t s);
+
+}  // namespace pr

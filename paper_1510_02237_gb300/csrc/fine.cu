@@ -1,0 +1,185 @@
+// fine.cu -- fine propagator F: one RK-3 step of the flux-form
+// acoustic-advection tendency (Sec. 3; fine scheme of Sec. 3.2) per launch,
+// with the three stages fused in shared memory.
+//
+// Tendency per cell (x contiguous, periodic):
+//   adv   = -U/(60 dx) [(f[i+3]-f[i-3]) - 9(f[i+2]-f[i-2]) + 45(f[i+1]-f[i-1])]  (+ same in y with V)
+//           i.e. the difference of 6th-order centred interface fluxes;
+//   u_t  += -c_s (p[i+1]-p[i-1])/(2dx) + alpha1 [ (u[i+1]-2u+u[i-1])/dx^2
+//           + ((w[i+1,j+1]-w[i+1,j-1]) - (w[i-1,j+1]-w[i-1,j-1]))/(4 dx dy) ]
+//   w_t  += -c_s (p[j+1]-p[j-1])/(2dy) + alpha2 [ (w[j+1]-2w+w[j-1])/dy^2 + (same cross term of u) ]
+//   p_t  += -c_s [ (u[i+1]-u[i-1])/(2dx) + (w[j+1]-w[j-1])/(2dy) ]
+// with alpha = nu_f dx^2 / delta t (Eq. dampingCoeff).
+// RK-3: q* = q + dt/3 L(q), q** = q + dt/2 L(q*), q' = q + dt L(q**).
+//
+// Each CTA owns a TX x TY output tile of one state and loads a halo of
+// 3 cells per stage in x (9 in total) and RYH per stage in y (RYH = 1 when
+// V = 0, else 3).  Stage 1 is computed on the tile shrunk by one stage
+// radius, stage 2 by two, stage 3 on the tile itself, so each step reads the
+// state from memory once and writes it once.
+#include "common.cuh"
+
+namespace pr {
+namespace {
+
+template <typename T, int RYH>
+__device__ __forceinline__ void fine_tend(const T* __restrict__ u, const T* __restrict__ w,
+                                          const T* __restrict__ p, int i, int RX,
+                                          const FineCoef<T>& c, T& Lu, T& Lw, T& Lp) {
+    const int S1 = RX;
+    T du = (u[i + 3] - u[i - 3]) - T(9) * (u[i + 2] - u[i - 2]) + T(45) * (u[i + 1] - u[i - 1]);
+    T dw = (w[i + 3] - w[i - 3]) - T(9) * (w[i + 2] - w[i - 2]) + T(45) * (w[i + 1] - w[i - 1]);
+    T dp = (p[i + 3] - p[i - 3]) - T(9) * (p[i + 2] - p[i - 2]) + T(45) * (p[i + 1] - p[i - 1]);
+    Lu = -c.ax6 * du;
+    Lw = -c.ax6 * dw;
+    Lp = -c.ax6 * dp;
+    if (RYH == 3) {
+        const int S2 = 2 * RX, S3 = 3 * RX;
+        T eu = (u[i + S3] - u[i - S3]) - T(9) * (u[i + S2] - u[i - S2]) + T(45) * (u[i + S1] - u[i - S1]);
+        T ew = (w[i + S3] - w[i - S3]) - T(9) * (w[i + S2] - w[i - S2]) + T(45) * (w[i + S1] - w[i - S1]);
+        T ep = (p[i + S3] - p[i - S3]) - T(9) * (p[i + S2] - p[i - S2]) + T(45) * (p[i + S1] - p[i - S1]);
+        Lu -= c.ay6 * eu;
+        Lw -= c.ay6 * ew;
+        Lp -= c.ay6 * ep;
+    }
+    Lu -= c.csx * (p[i + 1] - p[i - 1]);
+    Lw -= c.csy * (p[i + S1] - p[i - S1]);
+    Lp -= c.csx * (u[i + 1] - u[i - 1]) + c.csy * (w[i + S1] - w[i - S1]);
+    Lu += c.dxx * (u[i + 1] - T(2) * u[i] + u[i - 1]) +
+          c.dxy1 * ((w[i + 1 + S1] - w[i + 1 - S1]) - (w[i - 1 + S1] - w[i - 1 - S1]));
+    Lw += c.dyy * (w[i + S1] - T(2) * w[i] + w[i - S1]) +
+          c.dxy2 * ((u[i + 1 + S1] - u[i - 1 + S1]) - (u[i + 1 - S1] - u[i - 1 - S1]));
+}
+
+template <typename T, typename Tin, typename Tout, int RYH, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_fine_step(const Tin* __restrict__ in, long instride,
+                                                   Tout* __restrict__ out, long outstride, int nx,
+                                                   int ny, FineCoef<T> c) {
+    constexpr int HX = 9, HY = 3 * RYH;
+    constexpr int RX = TX + 2 * HX, RY = TY + 2 * HY, NR = RX * RY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* q = reinterpret_cast<T*>(smem_raw);
+    T* s = q + 3 * NR;
+    const long ncell = (long)nx * ny;
+    const Tin* src = in + (long)blockIdx.z * instride;
+    Tout* dst = out + (long)blockIdx.z * outstride;
+    const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
+
+    // load the haloed region (periodic wrap)
+    for (int idx = threadIdx.x; idx < NR; idx += NT) {
+        int ly = idx / RX, lx = idx - ly * RX;
+        long g = (long)pwrap(ty0 - HY + ly, ny) * nx + pwrap(tx0 - HX + lx, nx);
+        q[idx] = (T)src[g];
+        q[NR + idx] = (T)src[ncell + g];
+        q[2 * NR + idx] = (T)src[2 * ncell + g];
+    }
+    __syncthreads();
+
+    // stage 1: s = q + dt/3 L(q) on the region shrunk by (3, RYH)
+    {
+        constexpr int W1 = RX - 6, H1 = RY - 2 * RYH, N1 = W1 * H1;
+        for (int t = threadIdx.x; t < N1; t += NT) {
+            int r = t / W1;
+            int i = (r + RYH) * RX + (t - r * W1) + 3;
+            T Lu, Lw, Lp;
+            fine_tend<T, RYH>(q, q + NR, q + 2 * NR, i, RX, c, Lu, Lw, Lp);
+            s[i] = q[i] + c.c1 * Lu;
+            s[NR + i] = q[NR + i] + c.c1 * Lw;
+            s[2 * NR + i] = q[2 * NR + i] + c.c1 * Lp;
+        }
+    }
+    __syncthreads();
+
+    // stage 2: s <- q + dt/2 L(s) on the region shrunk by (6, 2 RYH); staged in registers
+    {
+        constexpr int W2 = RX - 12, H2 = RY - 4 * RYH, N2 = W2 * H2, NPT = (N2 + NT - 1) / NT;
+        T ru[NPT], rw[NPT], rp[NPT];
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            int t = threadIdx.x + k * NT;
+            if (t < N2) {
+                int r = t / W2;
+                int i = (r + 2 * RYH) * RX + (t - r * W2) + 6;
+                T Lu, Lw, Lp;
+                fine_tend<T, RYH>(s, s + NR, s + 2 * NR, i, RX, c, Lu, Lw, Lp);
+                ru[k] = q[i] + c.c2 * Lu;
+                rw[k] = q[NR + i] + c.c2 * Lw;
+                rp[k] = q[2 * NR + i] + c.c2 * Lp;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            int t = threadIdx.x + k * NT;
+            if (t < N2) {
+                int r = t / W2;
+                int i = (r + 2 * RYH) * RX + (t - r * W2) + 6;
+                s[i] = ru[k];
+                s[NR + i] = rw[k];
+                s[2 * NR + i] = rp[k];
+            }
+        }
+    }
+    __syncthreads();
+
+    // stage 3: q' = q + dt L(s) on the tile, written to global memory
+    for (int t = threadIdx.x; t < TX * TY; t += NT) {
+        int r = t / TX, cx = t - r * TX;
+        int gx = tx0 + cx, gy = ty0 + r;
+        if (gx < nx && gy < ny) {
+            int i = (r + HY) * RX + cx + HX;
+            T Lu, Lw, Lp;
+            fine_tend<T, RYH>(s, s + NR, s + 2 * NR, i, RX, c, Lu, Lw, Lp);
+            long g = (long)gy * nx + gx;
+            dst[g] = (Tout)(q[i] + c.c3 * Lu);
+            dst[ncell + g] = (Tout)(q[NR + i] + c.c3 * Lw);
+            dst[2 * ncell + g] = (Tout)(q[2 * NR + i] + c.c3 * Lp);
+        }
+    }
+}
+
+template <typename T, typename Tin, typename Tout, int RYH, int TX, int TY, int NT>
+cudaError_t launch_tile(const Tin* in, long instride, Tout* out, long outstride, int n, int nx, int ny,
+                        const FineCoef<T>& c, cudaStream_t s) {
+    constexpr int RX = TX + 18, RY = TY + 6 * RYH;
+    constexpr size_t smem = sizeof(T) * 6 * RX * RY;
+    auto kern = k_fine_step<T, Tin, Tout, RYH, TX, TY, NT>;
+    // idempotent; set on every launch so it holds on whichever device is current
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, n);
+    kern<<<grid, NT, smem, s>>>(in, instride, out, outstride, nx, ny, c);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T, typename Tin, typename Tout>
+cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outstride, int n, int nx,
+                             int ny, bool has_v, const FineCoef<T>& c, cudaStream_t s) {
+    const bool big = nx >= 64 && ny >= 16;
+    if (has_v) {
+        if (big) return launch_tile<T, Tin, Tout, 3, 64, 16, 256>(in, instride, out, outstride, n, nx, ny, c, s);
+        return launch_tile<T, Tin, Tout, 3, 32, 8, 256>(in, instride, out, outstride, n, nx, ny, c, s);
+    }
+    if (big) return launch_tile<T, Tin, Tout, 1, 64, 16, 256>(in, instride, out, outstride, n, nx, ny, c, s);
+    return launch_tile<T, Tin, Tout, 1, 32, 8, 256>(in, instride, out, outstride, n, nx, ny, c, s);
+}
+
+template cudaError_t launch_fine_step<double, double, double>(const double*, long, double*, long, int,
+                                                              int, int, bool, const FineCoef<double>&,
+                                                              cudaStream_t);
+template cudaError_t launch_fine_step<float, double, float>(const double*, long, float*, long, int, int,
+                                                            int, bool, const FineCoef<float>&,
+                                                            cudaStream_t);
+template cudaError_t launch_fine_step<float, float, float>(const float*, long, float*, long, int, int,
+                                                           int, bool, const FineCoef<float>&,
+                                                           cudaStream_t);
+template cudaError_t launch_fine_step<float, float, double>(const float*, long, double*, long, int, int,
+                                                            int, bool, const FineCoef<float>&,
+                                                            cudaStream_t);
+template cudaError_t launch_fine_step<float, double, double>(const double*, long, double*, long, int,
+                                                             int, int, bool, const FineCoef<float>&,
+                                                             cudaStream_t);
+
+}  // namespace pr

@@ -1,0 +1,387 @@
+// krylov.cu -- FP64 tall-skinny linear algebra of the subspace update and
+// the modified coarse propagator (Sec. 2.2: Eq. subspaceUpdate,
+// Eq. modifiedCoarse, Eq. Genhance) and the serial Parareal correction
+// (Alg. 2).
+//
+// All matrices are column-major with d-long columns (one state per column).
+// Reductions over the d rows are split into fixed row chunks; every chunk
+// writes a partial result and a second kernel sums the chunks in a fixed
+// order, so results are bitwise reproducible run to run and independent of
+// what else runs on the GPU (no atomics in any reduction).
+#include "common.cuh"
+
+namespace pr {
+namespace {
+
+constexpr int TN_CB = 32;     // columns of A per CTA (gemm_tn)
+constexpr int TN_JB = 16;     // columns of X per CTA (gemm_tn)
+constexpr int TN_KT = 32;     // rows per shared-memory tile
+constexpr int GV_CB = 64;     // columns of A per CTA (gemv_tn)
+constexpr int NN_JB = 16;     // output columns per thread (gemm_nn)
+
+__device__ __forceinline__ int cols_avail(const int* c0_dev, const int* c1_dev) {
+    int c0 = c0_dev ? *c0_dev : 0;
+    return *c1_dev - c0;
+}
+
+// partial[chunk][c * m + j] = sum over the chunk's rows of A[row, c0 + c] * X[row, j]
+__global__ void __launch_bounds__(256) k_gemm_tn_partial(const double* __restrict__ A, long lda,
+                                                         const int* c0_dev, const int* c1_dev,
+                                                         const double* __restrict__ X, long ldx,
+                                                         int m, long nrows, int rpc, int ccap,
+                                                         double* __restrict__ partial) {
+    __shared__ double As[TN_KT][TN_CB + 1];
+    __shared__ double Xs[TN_KT][TN_JB + 1];
+    const int ncols = cols_avail(c0_dev, c1_dev);
+    const int c0 = c0_dev ? *c0_dev : 0;
+    const int cb = blockIdx.y * TN_CB, jb = blockIdx.z * TN_JB;
+    if (cb >= ncols) return;
+    const long r0 = (long)blockIdx.x * rpc;
+    const long r1 = min(nrows, r0 + rpc);
+    const int tx = threadIdx.x & 31;      // column of A within the block
+    const int ty = threadIdx.x >> 5;      // 8 groups of output columns j
+    double acc[TN_JB / 8] = {0.0, 0.0};
+    for (long rt = r0; rt < r1; rt += TN_KT) {
+        // load A tile: rows rt..rt+31, columns cb..cb+31 (coalesced along rows)
+        for (int e = threadIdx.x; e < TN_KT * TN_CB; e += 256) {
+            int cc = e / TN_KT, rr = e - cc * TN_KT;
+            long row = rt + rr;
+            int col = cb + cc;
+            As[rr][cc] = (row < r1 && col < ncols) ? A[row + (long)(c0 + col) * lda] : 0.0;
+        }
+        for (int e = threadIdx.x; e < TN_KT * TN_JB; e += 256) {
+            int jj = e / TN_KT, rr = e - jj * TN_KT;
+            long row = rt + rr;
+            int j = jb + jj;
+            Xs[rr][jj] = (row < r1 && j < m) ? X[row + (long)j * ldx] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int rr = 0; rr < TN_KT; ++rr) {
+            double a = As[rr][tx];
+#pragma unroll
+            for (int k = 0; k < TN_JB / 8; ++k) acc[k] += a * Xs[rr][ty + 8 * k];
+        }
+        __syncthreads();
+    }
+    double* P = partial + (long)blockIdx.x * ccap * m;
+    const int col = cb + tx;
+    if (col < ncols) {
+#pragma unroll
+        for (int k = 0; k < TN_JB / 8; ++k) {
+            int j = jb + ty + 8 * k;
+            if (j < m) P[(long)col * m + j] = acc[k];
+        }
+    }
+}
+
+// m == 1: warp per column, lanes over rows (coalesced), x chunk in shared memory
+__global__ void __launch_bounds__(256) k_gemv_tn_partial(const double* __restrict__ A, long lda,
+                                                         const int* c0_dev, const int* c1_dev,
+                                                         const double* __restrict__ x, long nrows,
+                                                         int rpc, int ccap, double* __restrict__ partial) {
+    extern __shared__ double xs[];
+    const int ncols = cols_avail(c0_dev, c1_dev);
+    const int c0 = c0_dev ? *c0_dev : 0;
+    const int cb = blockIdx.y * GV_CB;
+    if (cb >= ncols) return;
+    const long r0 = (long)blockIdx.x * rpc;
+    const int nr = (int)min((long)rpc, nrows - r0);
+    for (int e = threadIdx.x; e < nr; e += 256) xs[e] = x[r0 + e];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int cend = min(ncols, cb + GV_CB);
+    double* P = partial + (long)blockIdx.x * ccap;
+    for (int col = cb + wid; col < cend; col += 8) {
+        const double* a = A + r0 + (long)(c0 + col) * lda;
+        double s = 0.0;
+        for (int e = lane; e < nr; e += 32) s += a[e] * xs[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) P[col] = s;
+    }
+}
+
+// out[idx] = sum_chunk partial[chunk][idx], idx < n_dev_cols * m (fixed chunk order)
+__global__ void k_reduce_chunks(const double* __restrict__ partial, int nchunk, long pstride,
+                                const int* c0_dev, const int* c1_dev, int m, double* __restrict__ out,
+                                int ldo) {
+    const int ncols = c1_dev ? cols_avail(c0_dev, c1_dev) : 1;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ncols * m) return;
+    double s = 0.0;
+    for (int k = 0; k < nchunk; ++k) s += partial[(long)k * pstride + idx];
+    const int c = idx / m, j = idx - c * m;
+    out[c + (long)j * ldo] = s;
+}
+
+// Y[:, j] = B[:, j] + sgn * sum_{c < ncols} A[:, c0 + c] C[c, j]
+__global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ A, long lda,
+                                                 const int* c0_dev, const int* c1_dev,
+                                                 const double* __restrict__ C, int ldc,
+                                                 const double* B, long ldb, double* Y, long ldy,
+                                                 int m, long nrows, double sgn) {
+    extern __shared__ double Cs[];   // ncap x NN_JB
+    const int ncols = cols_avail(c0_dev, c1_dev);
+    const int c0 = c0_dev ? *c0_dev : 0;
+    const int jb = blockIdx.y * NN_JB;
+    const int nj = min(NN_JB, m - jb);
+    for (int e = threadIdx.x; e < ncols * NN_JB; e += 256) {
+        int c = e / NN_JB, jj = e - c * NN_JB;
+        Cs[e] = (jj < nj) ? sgn * C[c + (long)(jb + jj) * ldc] : 0.0;
+    }
+    __syncthreads();
+    const long row = (long)blockIdx.x * 256 + threadIdx.x;
+    if (row >= nrows) return;
+    double acc[NN_JB];
+#pragma unroll
+    for (int k = 0; k < NN_JB; ++k) acc[k] = 0.0;
+    for (int c = 0; c < ncols; ++c) {
+        double a = A[row + (long)(c0 + c) * lda];
+#pragma unroll
+        for (int k = 0; k < NN_JB; ++k) acc[k] += a * Cs[c * NN_JB + k];
+    }
+#pragma unroll
+    for (int k = 0; k < NN_JB; ++k)
+        if (k < nj) Y[row + (long)(jb + k) * ldy] = (B ? B[row + (long)(jb + k) * ldb] : 0.0) + acc[k];
+}
+
+// block-level fixed-order sum of 256 values
+__device__ __forceinline__ double block_sum256(double v, double* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 8; ++k) s += red[k];
+    }
+    return s;   // valid in thread 0
+}
+
+// partial[chunk * m + j] = sum over the chunk's rows of X[row, j]^2  (grid.y = j)
+__global__ void __launch_bounds__(256) k_colnorm2_partial(const double* __restrict__ X, long ldx, int m,
+                                                          long nrows, int rpc, double* __restrict__ partial) {
+    __shared__ double red[8];
+    const int j = blockIdx.y;
+    const long r0 = (long)blockIdx.x * rpc;
+    const long r1 = min(nrows, r0 + rpc);
+    double s = 0.0;
+    for (long r = r0 + threadIdx.x; r < r1; r += 256) {
+        double v = X[r + (long)j * ldx];
+        s += v * v;
+    }
+    s = block_sum256(s, red);
+    if (threadIdx.x == 0) partial[(long)blockIdx.x * m + j] = s;
+}
+
+__global__ void k_krylov_append(const double* __restrict__ v, const double* __restrict__ z,
+                                const double* res2, const double* a2, double eta, int cap, const int* r,
+                                double* Q, double* D, long ld, long nrows, int* kept) {
+    const double res = sqrt(*res2), an = sqrt(*a2);
+    const int slot = *r;
+    const bool keep = (res > eta * an) && (an > 0.0) && (slot < cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && kept) *kept = keep ? 1 : 0;
+    if (!keep) return;
+    const double inv = 1.0 / res;
+    for (long row = (long)blockIdx.x * blockDim.x + threadIdx.x; row < nrows; row += (long)gridDim.x * blockDim.x) {
+        Q[row + (long)slot * ld] = v[row] * inv;
+        D[row + (long)slot * ld] = z[row] * inv;
+    }
+}
+
+__global__ void k_bump_rank(int* r, const int* kept) {
+    if (*kept) *r += 1;
+}
+
+// q_new = qt + ((g + D c) - kold); partial res2 over the chunk
+__global__ void __launch_bounds__(256) k_chain_update(const double* __restrict__ qt, const double* __restrict__ g,
+                                                      const double* __restrict__ D, long ldd,
+                                                      const int* c1_dev, const double* __restrict__ cvec,
+                                                      const double* __restrict__ kold, double* q, long nrows,
+                                                      double* __restrict__ partial) {
+    extern __shared__ double cs[];
+    __shared__ double red[8];
+    const int ncols = c1_dev ? *c1_dev : 0;
+    for (int e = threadIdx.x; e < ncols; e += 256) cs[e] = cvec[e];
+    __syncthreads();
+    const long row = (long)blockIdx.x * 256 + threadIdx.x;
+    double s = 0.0;
+    if (row < nrows) {
+        double acc = 0.0;
+        for (int c = 0; c < ncols; ++c) acc += D[row + (long)c * ldd] * cs[c];
+        double knew = g[row] + acc;
+        double y = qt[row] + (knew - kold[row]);
+        double e = y - q[row];
+        s = e * e;
+        q[row] = y;
+    }
+    s = block_sum256(s, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_copy_resid(const double* __restrict__ src, double* __restrict__ dst, long n,
+                             double* __restrict__ partial) {
+    __shared__ double red[8];
+    const long row = (long)blockIdx.x * 256 + threadIdx.x;
+    double s = 0.0;
+    if (row < n) {
+        double y = src[row];
+        double e = y - dst[row];
+        s = e * e;
+        dst[row] = y;
+    }
+    s = block_sum256(s, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int n, double* out) {
+    __shared__ double red[8];
+    double s = 0.0;
+    // fixed assignment of partials to threads and fixed combination order
+    for (int k = threadIdx.x; k < n; k += 256) s += partial[k];
+    s = block_sum256(s, red);
+    if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_max_sqrt(const double* res2, int n, double* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < n; ++i) m = fmax(m, sqrt(res2[i]));
+        *out = m;
+    }
+}
+
+__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ o, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        o[i] = a[i] - b[i];
+}
+
+__global__ void k_fill_int(int* p, int v, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+}  // namespace
+
+constexpr int TN_RPC = 2048;  // rows per chunk, gemm_tn
+constexpr int GV_RPC = 1024;  // rows per chunk, gemv_tn
+constexpr int NRM_RPC = 4096; // rows per chunk, column norms
+
+static inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
+
+long tswork_elems(long nrows, int ccap, int mmax) {
+    long a = (long)cdiv(nrows, TN_RPC) * ccap * (mmax > 1 ? mmax : 1);
+    long b = (long)cdiv(nrows, GV_RPC) * ccap;
+    long c = (long)cdiv(nrows, NRM_RPC) * (mmax > 1 ? mmax : 1);
+    long d = (long)cdiv(nrows, 256);
+    long m = a > b ? a : b;
+    m = m > c ? m : c;
+    return m > d ? m : d;
+}
+
+cudaError_t gemm_tn(const double* A, long lda, const int* c0_dev, const int* c1_dev, int ccap,
+                    const double* X, long ldx, int m, long nrows, double* C, int ldc, const TsWork& w,
+                    cudaStream_t s) {
+    if (m <= 0 || ccap <= 0) return cudaSuccess;
+    if (m == 1) {
+        const int nchunk = cdiv(nrows, GV_RPC);
+        if ((long)nchunk * ccap > w.elems) return cudaErrorInvalidValue;
+        dim3 grid(nchunk, cdiv(ccap, GV_CB));
+        k_gemv_tn_partial<<<grid, 256, GV_RPC * sizeof(double), s>>>(A, lda, c0_dev, c1_dev, X, nrows,
+                                                                    GV_RPC, ccap, w.partial);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_reduce_chunks<<<cdiv(ccap, 256), 256, 0, s>>>(w.partial, nchunk, ccap, c0_dev, c1_dev, 1, C, ldc);
+        return cudaGetLastError();
+    }
+    const int nchunk = cdiv(nrows, TN_RPC);
+    if ((long)nchunk * ccap * m > w.elems) return cudaErrorInvalidValue;
+    dim3 grid(nchunk, cdiv(ccap, TN_CB), cdiv(m, TN_JB));
+    k_gemm_tn_partial<<<grid, 256, 0, s>>>(A, lda, c0_dev, c1_dev, X, ldx, m, nrows, TN_RPC, ccap, w.partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_chunks<<<cdiv((long)ccap * m, 256), 256, 0, s>>>(w.partial, nchunk, (long)ccap * m, c0_dev,
+                                                            c1_dev, m, C, ldc);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm_nn(const double* A, long lda, const int* c0_dev, const int* c1_dev, int ccap,
+                    const double* C, int ldc, const double* B, long ldb, double* Y, long ldy, int m,
+                    long nrows, double sgn, cudaStream_t s) {
+    if (m <= 0 || ccap <= 0) return cudaSuccess;
+    const size_t smem = sizeof(double) * (size_t)ccap * NN_JB;
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(cdiv(nrows, 256), cdiv(m, NN_JB));
+    k_gemm_nn<<<grid, 256, smem, s>>>(A, lda, c0_dev, c1_dev, C, ldc, B, ldb, Y, ldy, m, nrows, sgn);
+    return cudaGetLastError();
+}
+
+cudaError_t colnorm2(const double* X, long ldx, int m, long nrows, double* out, const TsWork& w,
+                     cudaStream_t s) {
+    const int nchunk = cdiv(nrows, NRM_RPC);
+    if ((long)nchunk * m > w.elems) return cudaErrorInvalidValue;
+    k_colnorm2_partial<<<dim3(nchunk, m), 256, 0, s>>>(X, ldx, m, nrows, NRM_RPC, w.partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_chunks<<<cdiv(m, 256), 256, 0, s>>>(w.partial, nchunk, m, nullptr, nullptr, m, out, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t krylov_append(const double* v, const double* z, const double* res2, const double* a2,
+                          double eta, int cap, int* r, double* Q, double* D, long ld, long nrows,
+                          int* kept, cudaStream_t s) {
+    int nb = cdiv(nrows, 256);
+    if (nb > 1024) nb = 1024;
+    k_krylov_append<<<nb, 256, 0, s>>>(v, z, res2, a2, eta, cap, r, Q, D, ld, nrows, kept);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_bump_rank<<<1, 1, 0, s>>>(r, kept);
+    return cudaGetLastError();
+}
+
+cudaError_t chain_update(const double* qt, const double* g, const double* D, long ldd, const int* c1_dev,
+                         int ccap, const double* c, const double* kold, double* q, long nrows,
+                         double* res2_slot, const TsWork& w, cudaStream_t s) {
+    const int nb = cdiv(nrows, 256);
+    if (nb > w.elems) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double) * (size_t)(ccap > 0 ? ccap : 1);
+    cudaError_t e = cudaFuncSetAttribute(k_chain_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_chain_update<<<nb, 256, smem, s>>>(qt, g, D, ldd, c1_dev, c, kold, q, nrows, w.partial);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sum_partials<<<1, 256, 0, s>>>(w.partial, nb, res2_slot);
+    return cudaGetLastError();
+}
+
+cudaError_t copy_resid(const double* src, double* dst, long n, double* res2, const TsWork& w, cudaStream_t s) {
+    const int nb = cdiv(n, 256);
+    if (nb > w.elems) return cudaErrorInvalidValue;
+    k_copy_resid<<<nb, 256, 0, s>>>(src, dst, n, w.partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sum_partials<<<1, 256, 0, s>>>(w.partial, nb, res2);
+    return cudaGetLastError();
+}
+
+cudaError_t max_sqrt(const double* res2, int n, double* out, cudaStream_t s) {
+    k_max_sqrt<<<1, 32, 0, s>>>(res2, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t sub(const double* a, const double* b, double* out, long n, cudaStream_t s) {
+    int nb = cdiv(n, 256);
+    if (nb > 4096) nb = 4096;
+    k_sub<<<nb, 256, 0, s>>>(a, b, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t fill_int(int* p, int v, int n, cudaStream_t s) {
+    k_fill_int<<<cdiv(n, 256), 256, 0, s>>>(p, v, n);
+    return cudaGetLastError();
+}
+
+}  // namespace pr

@@ -1,0 +1,564 @@
+// solver.cu -- the solver handle, the KSE-Parareal driver (Alg. 2 / Alg. 1)
+// and the extern "C" entry points declared in include/parareal.h.
+//
+// Device data layout (all FP64 unless noted, column = one state of d values):
+//   q    (N+1) x d   iterates q_n^k, updated in place by the serial correction
+//   qt   N x d       fine images q~_{i+1}^k = F(q_i^k)   (slot i)
+//   gv   N x d       coarse images G(q_i^k)              (slot i)
+//   kold N x d       K(q_i^k) with the current subspace   (slot i)
+//   Q, D d x cap     orthonormal basis of S^k and D = F(Q) - G(Q); by linearity
+//                    K(q) = G(q - Q Q^T q) + F(Q) Q^T q = G(q) + D (Q^T q)
+//   wv, wz N x d     Gram-Schmidt work columns and their D-images
+//   fine/coarse ping-pong buffers (FP64, and FP32 when the fine sweep runs in FP32)
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+#include "parareal.h"
+
+using namespace pr;
+
+struct pr_solver {
+    int nx = 0, ny = 0, N = 0, n_f = 0, n_g = 0, K_max = 0, cap = 0;
+    long d = 0;
+    double U = 0, V = 0, cs = 0, dt_f = 0, dt_g = 0, lx = 1, ly = 1;
+    pr_options opt{};
+    cudaStream_t stream = nullptr;
+    FineCoef<double> fc64{};
+    FineCoef<float> fc32{};
+    CoarseCoef cc{};
+    double *q = nullptr, *qt = nullptr, *gv = nullptr, *kold = nullptr;
+    double *Q = nullptr, *D = nullptr, *wv = nullptr, *wz = nullptr;
+    double *fb0 = nullptr, *fb1 = nullptr, *cb0 = nullptr, *cb1 = nullptr, *gtmp = nullptr;
+    float *f32a = nullptr, *f32b = nullptr;
+    double *C = nullptr, *cvec = nullptr, *partial = nullptr;
+    double *anorm2 = nullptr, *res2 = nullptr, *rhist = nullptr, *nres2 = nullptr;
+    int *r = nullptr, *r_old = nullptr, *kept = nullptr, *ranks = nullptr, *zero = nullptr;
+    long partial_elems = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+};
+
+static std::string g_create_err;
+
+static pr_status set_err(pr_solver* h, pr_status st, const std::string& msg) {
+    if (h) h->err = msg; else g_create_err = msg;
+    return st;
+}
+
+#define CKC(call)                                                                                   \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return set_err(h, PR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+#define CKS(call)                                                                                   \
+    do {                                                                                            \
+        pr_status s_ = (call);                                                                      \
+        if (s_ != PR_OK) return s_;                                                                 \
+    } while (0)
+
+// ------------------------------------------------------------------ sizes
+
+static int default_cap(int N, int K_max) {
+    long c = 0;
+    for (int k = 0; k < K_max; ++k) c += N - k;
+    return (int)(c > 0 ? c : 1);
+}
+
+struct Sizes {
+    long d;
+    int cap;
+    long partial;
+    size_t bytes;
+};
+
+static Sizes compute_sizes(int nx, int ny, int N, int K_max, const pr_options& o) {
+    Sizes s{};
+    s.d = 3L * nx * ny;
+    int cap = o.krylov_cap > 0 ? o.krylov_cap : default_cap(N, K_max);
+    if (cap > s.d) cap = (int)s.d;
+    s.cap = cap < 1 ? 1 : cap;
+    s.partial = tswork_elems(s.d, s.cap, N);
+    size_t dd = sizeof(double);
+    size_t b = 0;
+    b += dd * (size_t)(N + 1) * s.d;           // q
+    b += dd * (size_t)N * s.d * 4;             // qt, gv, kold, wv
+    b += dd * (size_t)N * s.d;                 // wz
+    b += dd * (size_t)s.cap * s.d * 2;         // Q, D
+    b += dd * (size_t)N * s.d * 2;             // coarse ping-pong
+    if (o.fine_prec == PR_FP32)
+        b += sizeof(float) * (size_t)N * s.d * 2;
+    else
+        b += dd * (size_t)N * s.d * 2;         // fine ping-pong
+    b += dd * (size_t)s.d;                     // gtmp
+    b += dd * ((size_t)s.cap * N + s.cap);     // C, cvec
+    b += dd * (size_t)s.partial;
+    b += dd * (size_t)(N + (N + 1) + PR_MAX_ITERS + 1);
+    b += sizeof(int) * (size_t)(3 + N + PR_MAX_ITERS);
+    s.bytes = b;
+    return s;
+}
+
+// ------------------------------------------------------------------ propagators
+
+static pr_status fine_apply(pr_solver* h, const double* in, double* out, int n) {
+    const long d = h->d;
+    const bool hv = h->V != 0.0;
+    cudaStream_t s = h->stream;
+    const int nf = h->n_f;
+    if (h->opt.fine_prec == PR_FP32) {
+        if (nf == 1) {
+            CKC((launch_fine_step<float, double, double>(in, d, out, d, n, h->nx, h->ny, hv, h->fc32, s)));
+            return PR_OK;
+        }
+        CKC((launch_fine_step<float, double, float>(in, d, h->f32a, d, n, h->nx, h->ny, hv, h->fc32, s)));
+        float* a = h->f32a;
+        float* b = h->f32b;
+        for (int st = 1; st < nf - 1; ++st) {
+            CKC((launch_fine_step<float, float, float>(a, d, b, d, n, h->nx, h->ny, hv, h->fc32, s)));
+            float* t = a; a = b; b = t;
+        }
+        CKC((launch_fine_step<float, float, double>(a, d, out, d, n, h->nx, h->ny, hv, h->fc32, s)));
+        return PR_OK;
+    }
+    if (nf == 1) {
+        CKC((launch_fine_step<double, double, double>(in, d, out, d, n, h->nx, h->ny, hv, h->fc64, s)));
+        return PR_OK;
+    }
+    CKC((launch_fine_step<double, double, double>(in, d, h->fb0, d, n, h->nx, h->ny, hv, h->fc64, s)));
+    double* a = h->fb0;
+    double* b = h->fb1;
+    for (int st = 1; st < nf - 1; ++st) {
+        CKC((launch_fine_step<double, double, double>(a, d, b, d, n, h->nx, h->ny, hv, h->fc64, s)));
+        double* t = a; a = b; b = t;
+    }
+    CKC((launch_fine_step<double, double, double>(a, d, out, d, n, h->nx, h->ny, hv, h->fc64, s)));
+    return PR_OK;
+}
+
+static pr_status coarse_apply(pr_solver* h, const double* in, double* out, int n) {
+    const long d = h->d;
+    cudaStream_t s = h->stream;
+    if (h->n_g == 1) {
+        CKC(launch_coarse_step(in, out, d, n, h->nx, h->ny, h->cc, s));
+        return PR_OK;
+    }
+    CKC(launch_coarse_step(in, h->cb0, d, n, h->nx, h->ny, h->cc, s));
+    double* a = h->cb0;
+    double* b = h->cb1;
+    for (int st = 1; st < h->n_g - 1; ++st) {
+        CKC(launch_coarse_step(a, b, d, n, h->nx, h->ny, h->cc, s));
+        double* t = a; a = b; b = t;
+    }
+    CKC(launch_coarse_step(a, out, d, n, h->nx, h->ny, h->cc, s));
+    return PR_OK;
+}
+
+// ------------------------------------------------------------------ subspace update
+
+// Append the m columns V (with fine images FV and coarse images GV) to the
+// subspace, in order (Eq. subspaceUpdate): two passes of block classical
+// Gram-Schmidt against the basis present at entry, then two passes against
+// the columns kept earlier in this block, then the drop rule.  The D-images
+// Z = FV - GV receive exactly the same coefficients, so D = F(Q) - G(Q).
+static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, const double* GV, int m) {
+    const long d = h->d;
+    const int cap = h->cap;
+    cudaStream_t s = h->stream;
+    TsWork w{h->partial, h->partial_elems};
+    CKC(cudaMemcpyAsync(h->wv, V, sizeof(double) * m * d, cudaMemcpyDeviceToDevice, s));
+    CKC(sub(FV, GV, h->wz, (long)m * d, s));
+    CKC(colnorm2(h->wv, d, m, d, h->anorm2, w, s));
+    CKC(cudaMemcpyAsync(h->r_old, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    for (int pass = 0; pass < 2; ++pass) {
+        CKC(gemm_tn(h->Q, d, nullptr, h->r_old, cap, h->wv, d, m, d, h->C, cap, w, s));
+        CKC(gemm_nn(h->Q, d, nullptr, h->r_old, cap, h->C, cap, h->wv, d, h->wv, d, m, d, -1.0, s));
+        CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->C, cap, h->wz, d, h->wz, d, m, d, -1.0, s));
+    }
+    for (int j = 0; j < m; ++j) {
+        double* v = h->wv + (long)j * d;
+        double* z = h->wz + (long)j * d;
+        if (j > 0) {
+            for (int pass = 0; pass < 2; ++pass) {
+                CKC(gemm_tn(h->Q, d, h->r_old, h->r, cap, v, d, 1, d, h->cvec, cap, w, s));
+                CKC(gemm_nn(h->Q, d, h->r_old, h->r, cap, h->cvec, cap, v, d, v, d, 1, d, -1.0, s));
+                CKC(gemm_nn(h->D, d, h->r_old, h->r, cap, h->cvec, cap, z, d, z, d, 1, d, -1.0, s));
+            }
+        }
+        CKC(colnorm2(v, d, 1, d, h->nres2, w, s));
+        CKC(krylov_append(v, z, h->nres2, h->anorm2 + j, h->opt.drop_tol, cap, h->r, h->Q, h->D, d, d,
+                          h->kept + j, s));
+    }
+    return PR_OK;
+}
+
+// ------------------------------------------------------------------ the solve
+
+static pr_status solve_impl(pr_solver* h, int K, pr_report* rep) {
+    const long d = h->d;
+    const int N = h->N, cap = h->cap;
+    cudaStream_t s = h->stream;
+    TsWork w{h->partial, h->partial_elems};
+    const bool kse = h->opt.variant == PR_KSE;
+
+    // initialisation: q_{i+1}^0 = G(q_i^0), serially (q[0] already holds u0)
+    for (int i = 0; i < N; ++i) CKS(coarse_apply(h, h->q + (long)i * d, h->q + (long)(i + 1) * d, 1));
+    CKC(fill_int(h->r, 0, 1, s));
+
+    for (int k = 0; k < K; ++k) {
+        // Slices i < k satisfy q_i^{k} = q_i^{k-1} bit for bit (the correction
+        // of a converged slice is K(q) - K(q) = 0), so their fine images, their
+        // columns (already in S) and their corrections are skipped.
+        const int a = k, M = N - k;
+        double* qa = h->q + (long)a * d;
+        // parallel predictor: q~_{i+1}^k = F(q_i^k)
+        CKS(fine_apply(h, qa, h->qt + (long)a * d, M));
+        // coarse images G(q_i^k) (subspace images and K(q_i^k))
+        CKS(coarse_apply(h, qa, h->gv + (long)a * d, M));
+        if (kse) {
+            CKS(krylov_block(h, qa, h->qt + (long)a * d, h->gv + (long)a * d, M));
+            // K(q_i^k) = G(q_i^k) + D Q^T q_i^k for i = k+1..N-1 with the updated S^k
+            if (M > 1) {
+                CKC(gemm_tn(h->Q, d, nullptr, h->r, cap, h->q + (long)(a + 1) * d, d, M - 1, d, h->C, cap, w, s));
+                CKC(gemm_nn(h->D, d, nullptr, h->r, cap, h->C, cap, h->gv + (long)(a + 1) * d, d,
+                            h->kold + (long)(a + 1) * d, d, M - 1, d, 1.0, s));
+            }
+            CKC(cudaMemcpyAsync(h->ranks + k, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
+        }
+        // serial correction
+        CKC(cudaMemsetAsync(h->res2, 0, sizeof(double) * (N + 1), s));
+        CKC(copy_resid(h->qt + (long)a * d, h->q + (long)(a + 1) * d, d, h->res2 + a + 1, w, s));
+        for (int i = a + 1; i < N; ++i) {
+            double* qi = h->q + (long)i * d;
+            if (kse) CKC(gemm_tn(h->Q, d, nullptr, h->r, cap, qi, d, 1, d, h->cvec, cap, w, s));
+            CKS(coarse_apply(h, qi, h->gtmp, 1));
+            CKC(chain_update(h->qt + (long)i * d, h->gtmp, h->D, d, kse ? h->r : h->zero, cap, h->cvec,
+                             kse ? h->kold + (long)i * d : h->gv + (long)i * d, h->q + (long)(i + 1) * d, d,
+                             h->res2 + i + 1, w, s));
+        }
+        CKC(max_sqrt(h->res2 + 1, N, h->rhist + k, s));
+    }
+    (void)rep;
+    return PR_OK;
+}
+
+static pr_status fill_report(pr_solver* h, int K, pr_report* rep) {
+    CKC(cudaStreamSynchronize(h->stream));
+    std::memset(rep, 0, sizeof(*rep));
+    rep->K = K;
+    if (K > 0) {
+        CKC(cudaMemcpy(rep->r, h->rhist, sizeof(double) * K, cudaMemcpyDeviceToHost));
+        if (h->opt.variant == PR_KSE) CKC(cudaMemcpy(rep->rank, h->ranks, sizeof(int) * K, cudaMemcpyDeviceToHost));
+    }
+    float ms = 0.f;
+    CKC(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    rep->ms_total = ms;
+    return PR_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+
+static bool is_fin(double x) { return std::isfinite(x); }
+
+template <typename T>
+static FineCoef<T> make_fine_coef(double U, double V, double cs, double dx, double dy, double nu, double dt) {
+    const double a1 = nu * dx * dx / dt, a2 = nu * dy * dy / dt;
+    FineCoef<T> c;
+    c.ax6 = (T)(U / (60.0 * dx));
+    c.ay6 = (T)(V / (60.0 * dy));
+    c.csx = (T)(cs / (2.0 * dx));
+    c.csy = (T)(cs / (2.0 * dy));
+    c.dxx = (T)(a1 / (dx * dx));
+    c.dxy1 = (T)(a1 / (4.0 * dx * dy));
+    c.dyy = (T)(a2 / (dy * dy));
+    c.dxy2 = (T)(a2 / (4.0 * dx * dy));
+    c.c1 = (T)(dt / 3.0);
+    c.c2 = (T)(dt / 2.0);
+    c.c3 = (T)dt;
+    return c;
+}
+
+extern "C" {
+
+pr_status parareal_default_options(pr_options* o) {
+    if (!o) return PR_EINVAL;
+    std::memset(o, 0, sizeof(*o));
+    o->T = 1.0;
+    o->nu_f = 0.005;
+    o->nu_c = 0.1;
+    o->n_sound = 4;
+    o->adv_order_f = 6;
+    o->adv_order_c = 1;
+    o->V = 0.0;
+    o->K_max = 0;
+    o->krylov_cap = 0;
+    o->drop_tol = 1e-10;
+    o->fine_prec = PR_FP64;
+    o->variant = PR_KSE;
+    o->stream = nullptr;
+    return PR_OK;
+}
+
+static pr_status validate(const pr_grid* g, double U, double c_s, double dt_f, double dt_g, int N,
+                          const pr_options& o, int* n_f, int* n_g) {
+    pr_solver* h = nullptr;
+    if (!g) return set_err(h, PR_EINVAL, "grid is NULL");
+    if (g->nx < 4 || g->ny < 4) return set_err(h, PR_EINVAL, "nx and ny must be >= 4");
+    if ((long)g->nx * g->ny > (1L << 28)) return set_err(h, PR_EINVAL, "grid too large");
+    if (N < 1 || N > 4096) return set_err(h, PR_EINVAL, "N_slices must be in [1, 4096]");
+    if (!is_fin(U) || !is_fin(c_s) || !is_fin(o.V) || c_s < 0) return set_err(h, PR_EINVAL, "U, V, c_s must be finite, c_s >= 0");
+    if (!(dt_f > 0) || !(dt_g > 0) || !is_fin(dt_f) || !is_fin(dt_g)) return set_err(h, PR_EINVAL, "dt_f, dt_g must be > 0");
+    if (!(o.T > 0) || !is_fin(o.T)) return set_err(h, PR_EINVAL, "T must be > 0");
+    if (!is_fin(o.nu_f) || !is_fin(o.nu_c) || o.nu_f < 0 || o.nu_c < 0) return set_err(h, PR_EINVAL, "nu_f, nu_c must be >= 0");
+    if (o.adv_order_f != 6) return set_err(h, PR_EINVAL, "adv_order_f must be 6");
+    if (o.adv_order_c != 1 && o.adv_order_c != 3) return set_err(h, PR_EINVAL, "adv_order_c must be 1 or 3");
+    if (o.n_sound < 1) return set_err(h, PR_EINVAL, "n_sound must be >= 1");
+    if ((o.adv_order_c == 1 ? 1 : 2) + 2 * o.n_sound - 1 > 12) return set_err(h, PR_EINVAL, "n_sound too large for the fused coarse step (halo > 12)");
+    if (o.fine_prec != PR_FP64 && o.fine_prec != PR_FP32) return set_err(h, PR_EINVAL, "fine_prec must be PR_FP64 or PR_FP32");
+    if (o.variant != PR_KSE && o.variant != PR_ORIGINAL) return set_err(h, PR_EINVAL, "variant must be PR_KSE or PR_ORIGINAL");
+    if (!(o.drop_tol >= 0) || !is_fin(o.drop_tol)) return set_err(h, PR_EINVAL, "drop_tol must be >= 0");
+    if (o.K_max < 0 || o.K_max > PR_MAX_ITERS || o.K_max > N) return set_err(h, PR_EINVAL, "K_max must be in [0, min(N, 128)]");
+    if (o.krylov_cap < 0 || o.krylov_cap > 1600) return set_err(h, PR_EINVAL, "krylov_cap must be in [0, 1600]");
+    const double DT = o.T / N;
+    double nf = DT / dt_f, ng = DT / dt_g;
+    long inf = std::lround(nf), ing = std::lround(ng);
+    if (inf < 1 || std::fabs(inf * dt_f - DT) > 1e-9 * DT) return set_err(h, PR_EINVAL, "T/N is not an integer multiple of dt_f");
+    if (ing < 1 || std::fabs(ing * dt_g - DT) > 1e-9 * DT) return set_err(h, PR_EINVAL, "T/N is not an integer multiple of dt_g");
+    if (inf > 100000 || ing > 100000) return set_err(h, PR_EINVAL, "too many steps per slice");
+    *n_f = (int)inf;
+    *n_g = (int)ing;
+    return PR_OK;
+}
+
+size_t parareal_footprint_bytes(const pr_grid* g, int32_t N_slices, const pr_options* opt) {
+    pr_options o;
+    if (opt) o = *opt; else parareal_default_options(&o);
+    if (!g || g->nx < 1 || g->ny < 1 || N_slices < 1) return 0;
+    int K_max = o.K_max > 0 ? o.K_max : N_slices;
+    return compute_sizes(g->nx, g->ny, N_slices, K_max, o).bytes;
+}
+
+pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, double dt_g, int32_t N_slices,
+                          const pr_options* opt, pr_solver** out) {
+    if (!out) return set_err(nullptr, PR_EINVAL, "out is NULL");
+    *out = nullptr;
+    pr_options o;
+    if (opt) o = *opt; else parareal_default_options(&o);
+    int n_f = 0, n_g = 0;
+    CKS(validate(g, U, c_s, dt_f, dt_g, N_slices, o, &n_f, &n_g));
+    pr_solver* h = new (std::nothrow) pr_solver();
+    if (!h) return set_err(nullptr, PR_ENOMEM, "host allocation failed");
+    h->nx = g->nx;
+    h->ny = g->ny;
+    h->lx = g->lx > 0 ? g->lx : 1.0;
+    h->ly = g->ly > 0 ? g->ly : 1.0;
+    h->N = N_slices;
+    h->n_f = n_f;
+    h->n_g = n_g;
+    h->K_max = o.K_max > 0 ? o.K_max : N_slices;
+    h->U = U;
+    h->V = o.V;
+    h->cs = c_s;
+    h->dt_f = dt_f;
+    h->dt_g = dt_g;
+    h->opt = o;
+    h->stream = (cudaStream_t)o.stream;
+    Sizes sz = compute_sizes(h->nx, h->ny, h->N, h->K_max, o);
+    h->d = sz.d;
+    h->cap = sz.cap;
+    h->partial_elems = sz.partial;
+    const double dx = h->lx / h->nx, dy = h->ly / h->ny;
+    h->fc64 = make_fine_coef<double>(U, o.V, c_s, dx, dy, o.nu_f, dt_f);
+    h->fc32 = make_fine_coef<float>(U, o.V, c_s, dx, dy, o.nu_f, dt_f);
+    const double tau = dt_g / o.n_sound;
+    const double a1 = o.nu_c * dx * dx / tau, a2 = o.nu_c * dy * dy / tau;
+    h->cc.U = U;
+    h->cc.V = o.V;
+    h->cc.inv_dx = 1.0 / dx;
+    h->cc.inv_dy = 1.0 / dy;
+    h->cc.tau = tau;
+    h->cc.csx = c_s / (2.0 * dx);
+    h->cc.csy = c_s / (2.0 * dy);
+    h->cc.dxx = a1 / (dx * dx);
+    h->cc.dxy1 = a1 / (4.0 * dx * dy);
+    h->cc.dyy = a2 / (dy * dy);
+    h->cc.dxy2 = a2 / (4.0 * dx * dy);
+    h->cc.n_sound = o.n_sound;
+    h->cc.order = o.adv_order_c;
+
+    const long d = h->d;
+    const int N = h->N;
+    auto dalloc = [&](double** p, size_t n) { return cudaMalloc((void**)p, sizeof(double) * (n ? n : 1)); };
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chk(dalloc(&h->q, (size_t)(N + 1) * d));
+    chk(dalloc(&h->qt, (size_t)N * d));
+    chk(dalloc(&h->gv, (size_t)N * d));
+    chk(dalloc(&h->kold, (size_t)N * d));
+    chk(dalloc(&h->wv, (size_t)N * d));
+    chk(dalloc(&h->wz, (size_t)N * d));
+    chk(dalloc(&h->Q, (size_t)h->cap * d));
+    chk(dalloc(&h->D, (size_t)h->cap * d));
+    chk(dalloc(&h->cb0, (size_t)N * d));
+    chk(dalloc(&h->cb1, (size_t)N * d));
+    if (o.fine_prec == PR_FP32) {
+        chk(cudaMalloc((void**)&h->f32a, sizeof(float) * (size_t)N * d));
+        chk(cudaMalloc((void**)&h->f32b, sizeof(float) * (size_t)N * d));
+    } else {
+        chk(dalloc(&h->fb0, (size_t)N * d));
+        chk(dalloc(&h->fb1, (size_t)N * d));
+    }
+    chk(dalloc(&h->gtmp, (size_t)d));
+    chk(dalloc(&h->C, (size_t)h->cap * N));
+    chk(dalloc(&h->cvec, (size_t)h->cap));
+    chk(dalloc(&h->partial, (size_t)h->partial_elems));
+    chk(dalloc(&h->anorm2, (size_t)N));
+    chk(dalloc(&h->res2, (size_t)N + 1));
+    chk(dalloc(&h->rhist, (size_t)PR_MAX_ITERS));
+    chk(dalloc(&h->nres2, 1));
+    chk(cudaMalloc((void**)&h->r, sizeof(int) * 3));
+    chk(cudaMalloc((void**)&h->kept, sizeof(int) * N));
+    chk(cudaMalloc((void**)&h->ranks, sizeof(int) * PR_MAX_ITERS));
+    if (e == cudaSuccess) {
+        h->r_old = h->r + 1;
+        h->zero = h->r + 2;
+        chk(cudaMemset(h->r, 0, sizeof(int) * 3));
+        chk(cudaMemset(h->ranks, 0, sizeof(int) * PR_MAX_ITERS));
+        chk(cudaMemset(h->rhist, 0, sizeof(double) * PR_MAX_ITERS));
+        chk(cudaEventCreate(&h->ev0));
+        chk(cudaEventCreate(&h->ev1));
+    }
+    if (e != cudaSuccess) {
+        std::string msg = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        parareal_destroy(h);
+        return set_err(nullptr, e == cudaErrorMemoryAllocation ? PR_ENOMEM : PR_ECUDA, msg);
+    }
+    *out = h;
+    return PR_OK;
+}
+
+pr_status parareal_destroy(pr_solver* h) {
+    if (!h) return PR_EINVAL;
+    if (h->stream || h->q) cudaStreamSynchronize(h->stream);
+    double* ds[] = {h->q, h->qt, h->gv, h->kold, h->Q, h->D, h->wv, h->wz, h->fb0, h->fb1, h->cb0, h->cb1,
+                    h->gtmp, h->C, h->cvec, h->partial, h->anorm2, h->res2, h->rhist, h->nres2};
+    for (double* p : ds) if (p) cudaFree(p);
+    if (h->f32a) cudaFree(h->f32a);
+    if (h->f32b) cudaFree(h->f32b);
+    if (h->r) cudaFree(h->r);
+    if (h->kept) cudaFree(h->kept);
+    if (h->ranks) cudaFree(h->ranks);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+    return PR_OK;
+}
+
+const char* parareal_last_error(const pr_solver* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+pr_status parareal_solve(pr_solver* h, const double* u0_dev, int32_t K, double* q_out_dev, double* qT_dev,
+                         pr_report* rep) {
+    if (!h) return PR_EINVAL;
+    if (!u0_dev) return set_err(h, PR_EINVAL, "u0 is NULL");
+    if (K < 0 || K > h->K_max) return set_err(h, PR_EINVAL, "K_iters out of [0, K_max]");
+    const long d = h->d;
+    CKC(cudaEventRecord(h->ev0, h->stream));
+    CKC(cudaMemcpyAsync(h->q, u0_dev, sizeof(double) * d, cudaMemcpyDeviceToDevice, h->stream));
+    CKS(solve_impl(h, K, rep));
+    CKC(cudaEventRecord(h->ev1, h->stream));
+    if (q_out_dev)
+        CKC(cudaMemcpyAsync(q_out_dev, h->q, sizeof(double) * (h->N + 1) * d, cudaMemcpyDeviceToDevice, h->stream));
+    if (qT_dev)
+        CKC(cudaMemcpyAsync(qT_dev, h->q + (long)h->N * d, sizeof(double) * d, cudaMemcpyDeviceToDevice, h->stream));
+    if (rep) CKS(fill_report(h, K, rep));
+    return PR_OK;
+}
+
+pr_status parareal_solve_host(pr_solver* h, const double* u0_host, int32_t K, double* qT_host, pr_report* rep) {
+    if (!h) return PR_EINVAL;
+    if (!u0_host || !qT_host) return set_err(h, PR_EINVAL, "host buffers must be non-NULL");
+    if (K < 0 || K > h->K_max) return set_err(h, PR_EINVAL, "K_iters out of [0, K_max]");
+    const long d = h->d;
+    CKC(cudaEventRecord(h->ev0, h->stream));
+    CKC(cudaMemcpyAsync(h->q, u0_host, sizeof(double) * d, cudaMemcpyHostToDevice, h->stream));
+    CKS(solve_impl(h, K, rep));
+    CKC(cudaMemcpyAsync(qT_host, h->q + (long)h->N * d, sizeof(double) * d, cudaMemcpyDeviceToHost, h->stream));
+    CKC(cudaEventRecord(h->ev1, h->stream));
+    CKC(cudaStreamSynchronize(h->stream));
+    if (rep) CKS(fill_report(h, K, rep));
+    return PR_OK;
+}
+
+pr_status parareal_fine_sweep(pr_solver* h, const double* q_in_dev, double* q_out_dev, int32_t n) {
+    if (!h) return PR_EINVAL;
+    if (!q_in_dev || !q_out_dev) return set_err(h, PR_EINVAL, "NULL buffer");
+    if (n < 1 || n > h->N) return set_err(h, PR_EINVAL, "n must be in [1, N_slices]");
+    return fine_apply(h, q_in_dev, q_out_dev, n);
+}
+
+pr_status parareal_coarse_apply(pr_solver* h, const double* q_in_dev, double* q_out_dev, int32_t n) {
+    if (!h) return PR_EINVAL;
+    if (!q_in_dev || !q_out_dev) return set_err(h, PR_EINVAL, "NULL buffer");
+    if (n < 1 || n > h->N) return set_err(h, PR_EINVAL, "n must be in [1, N_slices]");
+    return coarse_apply(h, q_in_dev, q_out_dev, n);
+}
+
+pr_status parareal_coarse_sweep(pr_solver* h, const double* q0_dev, double* q_out_dev) {
+    if (!h) return PR_EINVAL;
+    if (!q0_dev || !q_out_dev) return set_err(h, PR_EINVAL, "NULL buffer");
+    const long d = h->d;
+    CKS(coarse_apply(h, q0_dev, q_out_dev, 1));
+    for (int i = 1; i < h->N; ++i)
+        CKS(coarse_apply(h, q_out_dev + (long)(i - 1) * d, q_out_dev + (long)i * d, 1));
+    return PR_OK;
+}
+
+pr_status krylov_reset(pr_solver* h) {
+    if (!h) return PR_EINVAL;
+    CKC(fill_int(h->r, 0, 1, h->stream));
+    return PR_OK;
+}
+
+pr_status krylov_update(pr_solver* h, const double* V_dev, const double* FV_dev, int32_t m, int32_t* kept_host) {
+    if (!h) return PR_EINVAL;
+    if (!V_dev || !FV_dev) return set_err(h, PR_EINVAL, "NULL buffer");
+    if (m < 1 || m > h->N) return set_err(h, PR_EINVAL, "m must be in [1, N_slices]");
+    CKS(coarse_apply(h, V_dev, h->gv, m));
+    CKS(krylov_block(h, V_dev, FV_dev, h->gv, m));
+    if (kept_host) {
+        CKC(cudaMemcpyAsync(kept_host, h->kept, sizeof(int) * m, cudaMemcpyDeviceToHost, h->stream));
+        CKC(cudaStreamSynchronize(h->stream));
+    }
+    return PR_OK;
+}
+
+pr_status krylov_rank(pr_solver* h, int32_t* rank) {
+    if (!h || !rank) return PR_EINVAL;
+    CKC(cudaMemcpyAsync(rank, h->r, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CKC(cudaStreamSynchronize(h->stream));
+    return PR_OK;
+}
+
+pr_status krylov_project(pr_solver* h, const double* q_dev, double* Pq_dev, double* FPq_dev) {
+    if (!h) return PR_EINVAL;
+    if (!q_dev) return set_err(h, PR_EINVAL, "q is NULL");
+    const long d = h->d;
+    cudaStream_t s = h->stream;
+    TsWork w{h->partial, h->partial_elems};
+    double* pq = Pq_dev ? Pq_dev : h->wv;
+    CKC(gemm_tn(h->Q, d, nullptr, h->r, h->cap, q_dev, d, 1, d, h->cvec, h->cap, w, s));
+    CKC(gemm_nn(h->Q, d, nullptr, h->r, h->cap, h->cvec, h->cap, nullptr, d, pq, d, 1, d, 1.0, s));
+    if (FPq_dev) {
+        CKS(coarse_apply(h, pq, h->gtmp, 1));
+        CKC(gemm_nn(h->D, d, nullptr, h->r, h->cap, h->cvec, h->cap, h->gtmp, d, FPq_dev, d, 1, d, 1.0, s));
+    }
+    return PR_OK;
+}
+
+}  // extern "C"

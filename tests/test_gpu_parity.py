@@ -1,0 +1,329 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (written from the arithmetic): FP64 paths agree with the oracle to
+<= 1e-12 relative (l2 over the compared states) -- both evaluate the same
+formulas in IEEE double, differing only in summation order and fused
+multiply-adds; the FP32 fine sweep agrees to <= 1e-5 relative.
+Integer results (ranks, drop decisions) must agree exactly.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_1510_02237_gb300")
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    torch.cuda.set_device(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    a = np.ravel(a)
+    b = np.ravel(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def solver(p, **opt):
+    return P.Solver(p, stream=torch.cuda.current_stream(), **opt)
+
+
+def states(p, n, seed):
+    return np.stack([W.ic_random(p.nx, p.ny, seed=seed + i).ravel() for i in range(n)])
+
+
+GRIDS = [
+    ("64x32", dict(nx=64, ny=32, N=8)),
+    ("ragged40x24", dict(nx=40, ny=24, N=4)),
+    ("tiny8x4", dict(nx=8, ny=4, N=4)),
+    ("128x64_V", dict(nx=128, ny=64, N=4, V=0.05)),
+    ("96x20_negU", dict(nx=96, ny=20, N=3, U=-0.15)),
+]
+
+
+def _prob(spec):
+    spec = dict(spec)
+    nx, ny, N = spec.pop("nx"), spec.pop("ny"), spec.pop("N")
+    return W.make_problem(nx, ny, N, **spec)
+
+
+# ------------------------------------------------------------------ propagators
+
+@pytest.mark.parametrize("name,spec", GRIDS, ids=[g[0] for g in GRIDS])
+def test_fine_sweep_fp64(name, spec):
+    p = _prob(spec)
+    X = states(p, p.n_slices, 10)
+    with solver(p) as s:
+        out = torch.empty(p.n_slices * p.d, dtype=torch.float64, device="cuda")
+        P.parareal_fine_sweep(s.h, dev(X), out, p.n_slices)
+        got = host(out).reshape(p.n_slices, p.d)
+    for i in range(p.n_slices):
+        assert rel(got[i], oracle.fine_prop(p, X[i])) < TOL64
+
+
+@pytest.mark.parametrize("name,spec", GRIDS[:4], ids=[g[0] for g in GRIDS[:4]])
+def test_fine_sweep_fp32(name, spec):
+    p = _prob(spec)
+    X = states(p, p.n_slices, 20)
+    with solver(p, fine_prec=P.PR_FP32) as s:
+        out = torch.empty(p.n_slices * p.d, dtype=torch.float64, device="cuda")
+        P.parareal_fine_sweep(s.h, dev(X), out, p.n_slices)
+        got = host(out).reshape(p.n_slices, p.d)
+    for i in range(p.n_slices):
+        assert rel(got[i], oracle.fine_prop(p, X[i])) < TOL32
+
+
+def test_fine_single_step_slices():
+    """N_f = 1 (one RK-3 step per slice) uses the direct in->out launch."""
+    p = W.Problem(nx=64, ny=32, n_slices=4, n_f=1, n_g=1, dt_f=1.0 / 160, dt_g=1.0 / 160, T=4.0 / 160)
+    X = states(p, 4, 3)
+    for prec, tol in [(P.PR_FP64, TOL64), (P.PR_FP32, TOL32)]:
+        with solver(p, fine_prec=prec) as s:
+            out = torch.empty(4 * p.d, dtype=torch.float64, device="cuda")
+            P.parareal_fine_sweep(s.h, dev(X), out, 4)
+            got = host(out).reshape(4, p.d)
+        for i in range(4):
+            assert rel(got[i], oracle.fine_prop(p, X[i])) < tol
+
+
+@pytest.mark.parametrize("order", [1, 3])
+@pytest.mark.parametrize("name,spec", GRIDS, ids=[g[0] for g in GRIDS])
+def test_coarse_apply(name, spec, order):
+    p = dataclasses.replace(_prob(spec), adv_order_c=order)
+    X = states(p, p.n_slices, 30)
+    with solver(p) as s:
+        out = torch.empty(p.n_slices * p.d, dtype=torch.float64, device="cuda")
+        P.parareal_coarse_apply(s.h, dev(X), out, p.n_slices)
+        got = host(out).reshape(p.n_slices, p.d)
+    for i in range(p.n_slices):
+        assert rel(got[i], oracle.coarse_prop(p, X[i])) < TOL64
+
+
+def test_coarse_sweep_is_serial_chain():
+    p = W.make_problem(64, 32, 8)
+    q0 = W.ic_gaussian(64, 32, seed=0).ravel()
+    with solver(p) as s:
+        out = torch.empty(p.n_slices * p.d, dtype=torch.float64, device="cuda")
+        P.parareal_coarse_sweep(s.h, dev(q0), out)
+        got = host(out).reshape(p.n_slices, p.d)
+    q = q0
+    for i in range(p.n_slices):
+        q = oracle.coarse_prop(p, q)
+        assert rel(got[i], q) < TOL64
+
+
+# ------------------------------------------------------------------ subspace
+
+def test_krylov_update_and_project_match_oracle():
+    p = W.make_problem(64, 32, 8)
+    rng = np.random.default_rng(5)
+    X = states(p, 6, 40)
+    X[3] = 0.5 * X[0] - 2.0 * X[2]          # dependent on earlier columns -> dropped
+    X[5] = X[1]                             # duplicate -> dropped
+    FX = np.stack([oracle.fine_prop(p, x) for x in X])
+    B = oracle.Basis(p.d, 16)
+    want_kept = [B.add(X[j], FX[j])[0] for j in range(6)]
+    with solver(p) as s:
+        kept = P.krylov_update(s.h, dev(X[:4]), dev(FX[:4]), 4)
+        kept += P.krylov_update(s.h, dev(X[4:]), dev(FX[4:]), 2)
+        assert kept == [int(k) for k in want_kept] == [1, 1, 1, 0, 1, 0]
+        assert P.krylov_rank(s.h) == B.rank == 4
+        for trial in range(3):
+            q = rng.standard_normal(p.d)
+            Pq = torch.empty(p.d, dtype=torch.float64, device="cuda")
+            FPq = torch.empty_like(Pq)
+            P.krylov_project(s.h, dev(q), Pq, FPq)
+            wPq, wFPq = B.project(q)
+            assert rel(host(Pq), wPq) < TOL64
+            assert rel(host(FPq), wFPq) < 1e-11
+            # and F(P q) is F applied to P q (Eq. Genhance)
+            assert rel(host(FPq), oracle.fine_prop(p, host(Pq))) < 1e-11
+
+
+def test_krylov_cap_freezes_basis():
+    p = W.make_problem(64, 32, 8)
+    X = states(p, 5, 50)
+    FX = np.stack([oracle.fine_prop(p, x) for x in X])
+    with solver(p, krylov_cap=3) as s:
+        kept = P.krylov_update(s.h, dev(X), dev(FX), 5)
+        assert kept == [1, 1, 1, 0, 0] and P.krylov_rank(s.h) == 3
+        P.krylov_reset(s.h)
+        assert P.krylov_rank(s.h) == 0
+
+
+# ------------------------------------------------------------------ whole solve
+
+def _solve(p, q0, K, **opt):
+    opt.setdefault("K_max", max(K, 1))
+    with solver(p, **opt) as s:
+        qall = torch.empty((p.n_slices + 1) * p.d, dtype=torch.float64, device="cuda")
+        rep = P.parareal_solve(s.h, dev(q0), K, q_out=qall)
+        return host(qall).reshape(p.n_slices + 1, p.d), rep
+
+
+@pytest.mark.parametrize("K", [0, 1, 2, 3, 5, 8])
+def test_solve_matches_oracle_64x32(K):
+    wl = W.workload_small()
+    p = wl.problem
+    q0 = wl.ics[0][1]().ravel()
+    got, rep = _solve(p, q0, K)
+    want = oracle.parareal(p, q0, K)
+    assert rel(got, want["q"]) < TOL64
+    assert list(rep.rank[:K]) == list(want["rank"])
+    assert np.allclose(np.array(rep.r[:K]), want["r"], rtol=1e-9, atol=0)
+
+
+def test_solve_original_parareal_matches_oracle():
+    p = W.make_problem(64, 32, 8)
+    q0 = W.ic_gaussian(64, 32, seed=0).ravel()
+    got, rep = _solve(p, q0, 3, variant=P.PR_ORIGINAL)
+    want = oracle.parareal(p, q0, 3, variant="original")
+    assert rel(got, want["q"]) < TOL64
+    assert np.allclose(np.array(rep.r[:3]), want["r"], rtol=1e-9)
+
+
+@pytest.mark.parametrize("name,spec", GRIDS[1:], ids=[g[0] for g in GRIDS[1:]])
+def test_solve_edge_grids(name, spec):
+    p = _prob(spec)
+    q0 = W.ic_fourier(p.nx, p.ny, seed=3, n_modes=4, kmax=3.0).ravel()
+    K = min(2, p.n_slices)
+    got, rep = _solve(p, q0, K)
+    want = oracle.parareal(p, q0, K)
+    assert rel(got, want["q"]) < TOL64
+    assert list(rep.rank[:K]) == list(want["rank"])
+
+
+def test_single_slice_one_iteration_is_fine():
+    p = W.make_problem(64, 32, 1)
+    q0 = W.ic_gaussian(64, 32, seed=1).ravel()
+    got, _ = _solve(p, q0, 1)
+    assert rel(got[1], oracle.fine_prop(p, q0)) < TOL64
+
+
+def test_K_equals_N_is_serial_fine_bitwise():
+    """Converged slices are exact: q_N^N equals N serial fine sweeps bit for bit."""
+    p = W.make_problem(64, 32, 8)
+    q0 = W.ic_gaussian(64, 32, seed=0).ravel()
+    got, _ = _solve(p, q0, 8)
+    with solver(p) as s:
+        q = dev(q0)
+        for i in range(p.n_slices):
+            nxt = torch.empty_like(q)
+            P.parareal_fine_sweep(s.h, q, nxt, 1)
+            q = nxt
+            assert np.array_equal(host(q), got[i + 1])
+    assert rel(got, oracle.serial_fine(p, q0)) < TOL64
+
+
+def test_solve_is_deterministic():
+    p = W.make_problem(64, 32, 8)
+    q0 = W.ic_gaussian(64, 32, seed=0).ravel()
+    a, _ = _solve(p, q0, 3)
+    b, _ = _solve(p, q0, 3)
+    assert np.array_equal(a, b)
+
+
+def test_solve_fp32_fine_accuracy():
+    """Mixed precision (FP32 fine sweep): the error against the serial fine
+    solution moves by at most 1e-5 relative."""
+    wl = W.workload_small()
+    p = wl.problem
+    q0 = wl.ics[0][1]().ravel()
+    qs = oracle.serial_fine(p, q0)
+    for K in (1, 3):
+        g32, _ = _solve(p, q0, K, fine_prec=P.PR_FP32)
+        want = oracle.parareal(p, q0, K)
+        e32 = oracle.rel_error(g32[-1], qs[-1])
+        e64 = oracle.rel_error(want["q"][-1], qs[-1])
+        assert abs(e32 - e64) <= 1e-5
+        assert rel(g32, want["q"]) < 1e-5
+
+
+def test_solve_host_matches_device():
+    p = W.make_problem(64, 32, 8)
+    q0 = W.ic_gaussian(64, 32, seed=0).ravel()
+    a, _ = _solve(p, q0, 2)
+    with solver(p, K_max=2) as s:
+        out = np.empty(p.d)
+        rep = P.parareal_solve_host(s.h, np.ascontiguousarray(q0), 2, out)
+    assert np.array_equal(out, a[-1])
+    assert rep.K == 2 and rep.ms_total > 0
+
+
+def test_invalid_calls_fail_cleanly():
+    p = W.make_problem(64, 32, 8)
+    with solver(p, K_max=2) as s:
+        x = torch.zeros(p.d * 9, dtype=torch.float64, device="cuda")
+        with pytest.raises(P.PararealError) as ei:
+            P.parareal_solve(s.h, x, 3)
+        assert ei.value.status == P.PR_EINVAL
+        with pytest.raises(P.PararealError):
+            P.parareal_fine_sweep(s.h, x, x, 9)
+        with pytest.raises(P.PararealError):
+            P.krylov_update(s.h, x, x, 0)
+        # the handle still works after rejected calls
+        P.parareal_solve(s.h, x, 1)
+
+
+# ------------------------------------------------------------------ full size (256x128, N = 32, K = 6)
+
+def test_full_size_sampled():
+    """The benchmark's configuration: sampled outputs checked one by one
+    against the oracle, plus properties that hold at any size."""
+    wl = W.workload_medium()
+    p = wl.problem
+    K = wl.K
+    q0 = wl.ics[0][1]().ravel()
+    with solver(p, K_max=K, krylov_cap=wl.krylov_cap) as s:
+        qall = torch.empty((p.n_slices + 1) * p.d, dtype=torch.float64, device="cuda")
+        rep = P.parareal_solve(s.h, dev(q0), K, q_out=qall)
+        got = host(qall).reshape(p.n_slices + 1, p.d)
+        ranks = list(rep.rank[:K])
+        assert all(0 < ranks[k] <= W.krylov_bound(p.n_slices, k + 1) for k in range(K)), ranks
+        assert all(np.diff(ranks) > 0), ranks
+        # converged slices i <= K are the serial fine solution
+        qs = q0
+        for i in range(1, K + 1):
+            qs = oracle.fine_prop(p, qs)
+            assert rel(got[i], qs) < TOL64
+        # sampled fine and coarse images of final iterates
+        for i in (K + 3, p.n_slices - 1):
+            out = torch.empty(p.d, dtype=torch.float64, device="cuda")
+            P.parareal_fine_sweep(s.h, dev(got[i]), out, 1)
+            assert rel(host(out), oracle.fine_prop(p, got[i])) < TOL64
+            P.parareal_coarse_apply(s.h, dev(got[i]), out, 1)
+            assert rel(host(out), oracle.coarse_prop(p, got[i])) < TOL64
+        # projector properties of S^K and F(P q) by linearity
+        q = got[p.n_slices]
+        Pq = torch.empty(p.d, dtype=torch.float64, device="cuda")
+        FPq = torch.empty_like(Pq)
+        P.krylov_project(s.h, dev(q), Pq, FPq)
+        pq = host(Pq)
+        PPq = torch.empty_like(Pq)
+        P.krylov_project(s.h, Pq, PPq, None)
+        assert rel(host(PPq), pq) < 1e-12
+        assert abs(np.dot(q - pq, pq)) < 1e-12 * np.dot(q, q)
+        assert rel(host(FPq), oracle.fine_prop(p, pq)) < 1e-11
