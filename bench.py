@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark: KSE-Parareal solves/s on GB300.
+
+Workload (one "step"): the plain-FP64 256x128 problem with N = 32 time
+slices, K = 6 iterations and a Krylov cap of 192, solved for each of its
+three seeded initial conditions (Gaussian bump + noise, 8 random-phase
+Fourier modes, filtered noise) -- 3 solves per step.  Inputs are resident in
+HBM when the timed region starts; each solve's working set (basis Q and D,
+302 MB, plus ~1.1 GB of buffers) is larger than the 129 MB L2, so no
+explicit L2 flush is used between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own copy of the batch (replicas; the
+method has no data-path exchange between independent solves), rank 0 prints
+one JSON line with the whole-job throughput.  ``--impl reference`` times the
+CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "Parareal solves/s & fine cell-steps/s vs plain FP64 on GB300; p50/p99 latency"
+
+# Floating-point operations of one fine cell-step (three RK-3 stages) as the
+# fine kernel evaluates them with V = 0, counting an FMA as 2: per stage and
+# cell the 6th-order x-advection difference of three fields (3 x 7), its
+# scaling (3), the acoustic terms (12), the divergence damping (18) and the
+# stage update (6) = 60.
+FINE_FLOPS_PER_CELL_STEP = 180.0
+# One fine cell-step reads and writes the three FP64 fields once (M1 model).
+FINE_BYTES_PER_CELL_STEP_F64 = 48.0
+
+
+def _sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
+
+
+# DRAM traffic of one fine RK-3 step launch from an ncu capture of the same
+# kernel source (profiles/fine_step_fp64_256x128_N32.md: 25.2 MB read + 0.04 MB
+# written for 32 x 32768 cells); reported as null once fine.cu changes.
+FINE_TRAFFIC = {"source_sha": "ba315e77be3c", "bytes_per_cell_step": 24.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["fine", "solve"], default=None,
+                    help="small isolated case for profiler captures: 'fine' = three fine sweeps over all "
+                         "32 slices of the 256x128 workload; 'solve' = two solves of its first IC")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+
+def oracle_sample(budget_s: float, wl):
+    """Time the oracle on a bounded sample of the workload on the host cores.
+
+    Sample: one KSE-Parareal iteration (K = 1) of the first IC -- the serial
+    coarse initialisation, the fine predictor on all N slices, the Householder
+    subspace update and the serial correction.  A K-iteration solve repeats
+    the iteration K times (the oracle propagates every slice in every
+    iteration), so K * t(sample) is a lower bound of the oracle's solve time
+    (the update and the correction grow with the basis); the throughput
+    reported is therefore an upper bound for the oracle.  If the budget is
+    below one sample, the sample shrinks to fine propagations of single slices
+    and is scaled by the fine share of the work (K * N slice propagations).
+    """
+    import oracle
+    p = wl.problem
+    q0 = wl.ics[0][1]().ravel()
+    t0 = time.perf_counter()
+    oracle.fine_prop(p, q0)
+    t_slice = time.perf_counter() - t0
+    est_iter = t_slice * p.n_slices * 1.5
+    if budget_s >= est_iter:
+        t0 = time.perf_counter()
+        oracle.parareal(p, q0, 1)
+        t = time.perf_counter() - t0
+        return {"value": 1.0 / (wl.K * t), "sample": f"one K=1 iteration of the {wl.name} solve (IC 0) = "
+                f"{t:.2f} s; solve time estimated as K={wl.K} x that (lower bound)", "seconds": t}
+    n = max(1, int(budget_s / max(t_slice, 1e-3)))
+    t0 = time.perf_counter()
+    for _ in range(n):
+        oracle.fine_prop(p, q0)
+    t = (time.perf_counter() - t0) / n
+    return {"value": 1.0 / (wl.K * p.n_slices * t), "sample": f"{n} fine slice propagations of {wl.name} "
+            f"({t:.3f} s each); solve time estimated as K*N of them (fine work only, lower bound)",
+            "seconds": t * n}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = W.workload_medium()
+    # warm-up steps: one fine slice each (untimed); timed steps share a ~150 s budget
+    import oracle
+    p = wl.problem
+    q0 = wl.ics[0][1]().ravel()
+    for _ in range(args.warmup):
+        oracle.fine_prop(p, q0)
+    per_step = 150.0 / max(1, args.steps)
+    vals, secs, samples = [], 0.0, None
+    for _ in range(args.steps):
+        r = oracle_sample(per_step, wl)
+        vals.append(r["value"])
+        secs += r["seconds"]
+        samples = r["sample"]
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "grid": f"{p.nx}x{p.ny}", "N_slices": p.n_slices, "K": wl.K,
+                   "krylov_cap": wl.krylov_cap, "ics": [n for n, _ in wl.ics]},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": samples},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1510_02237_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    P.lib()
+
+    wl = W.workload_medium()
+    p, K = wl.problem, wl.K
+    ics = [f().ravel() for _, f in wl.ics]
+    nsol = len(ics)
+    stream = torch.cuda.current_stream()
+    u0s = [torch.from_numpy(q).cuda() for q in ics]
+    outs = [torch.empty(p.d, dtype=torch.float64, device="cuda") for _ in ics]
+    s = P.Solver(p, stream=stream, K_max=K, krylov_cap=wl.krylov_cap)
+
+    def step(evs=None):
+        for j, (u0, out) in enumerate(zip(u0s, outs)):
+            if evs is not None:
+                evs[j][0].record(stream)
+            P.parareal_solve(s.h, u0, K, qT=out, report=False)
+            if evs is not None:
+                evs[j][1].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs)
+    P.parareal_timing_enable(s.h, args.steps * nsol)
+    lat_events = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(nsol)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = P.parareal_kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(lat_events[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = P.parareal_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    tm = P.parareal_timing_read(s.h)
+    lat = sorted(a.elapsed_time(b) for row in lat_events for a, b in row)
+
+    solves = args.steps * nsol * world
+    value = solves / (ms / 1e3)
+    fine_cell_steps = tm["fine_cell_steps"] * world
+    n = tm["n_solves"]
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    hin = [torch.from_numpy(q).pin_memory() for q in ics]
+    hout = [torch.empty(p.d, dtype=torch.float64).pin_memory() for _ in ics]
+    for j in range(nsol):
+        P.parareal_solve_host(s.h, hin[j], K, hout[j], report=False)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for j in range(nsol):
+            P.parareal_solve_host(s.h, hin[j], K, hout[j], report=False)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": solves / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": nsol * p.d * 8,
+           "d2h_bytes_per_step": nsol * p.d * 8}
+
+    line = None
+    if rank == 0:
+        # ---- roofline of the dominant phase's kernel
+        phases = {k: tm[k] / n for k in ("ms_init", "ms_fine", "ms_coarse", "ms_krylov", "ms_chain")}
+        fp64_peak = P.parareal_alu_probe(P.PR_FP64, 4096)
+        fine_flops = tm["fine_cell_steps"] * FINE_FLOPS_PER_CELL_STEP
+        achieved = fine_flops / (tm["ms_fine"] / 1e3) / 1e12
+        peak = fp64_peak / 1e12
+        src = os.path.join(ROOT, "paper_1510_02237_gb300", "csrc", "fine.cu")
+        traffic = None
+        if FINE_TRAFFIC["source_sha"] == _sha(src) and FINE_TRAFFIC["bytes_per_cell_step"]:
+            cells_per_launch = tm["fine_cell_steps"] / tm["fine_launches"]
+            traffic = FINE_TRAFFIC["bytes_per_cell_step"] * cells_per_launch
+        roof = {"kernel": "k_fine_step<double> (one RK-3 step, stages fused)", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": "measured FP64 FMA probe (parareal_alu_probe), same run",
+                "algorithmic_flops_per_cell_step": FINE_FLOPS_PER_CELL_STEP,
+                "avg_launch_ms": tm["ms_fine"] / tm["fine_launches"],
+                "achieved_algorithmic_GBps": tm["fine_cell_steps"] * FINE_BYTES_PER_CELL_STEP_F64
+                / (tm["ms_fine"] / 1e3) / 1e9}
+        cpu = None
+        if not args.no_cpu_baseline:
+            cb = oracle_sample(25.0, wl)
+            cpu = {"value": cb["value"], "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": cb["sample"]}
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "grid": f"{p.nx}x{p.ny}", "N_slices": p.n_slices, "K": K,
+                       "krylov_cap": wl.krylov_cap, "n_f": p.n_f, "n_g": p.n_g, "ics": [nm for nm, _ in wl.ics],
+                       "solves_per_step": nsol, "fine_prec": "f64",
+                       "l2": "no flush: per-solve working set (Q, D 302 MB + buffers) > 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "fine_cell_steps_per_s": fine_cell_steps / (ms / 1e3),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "what": "device time of one solve, CUDA events"},
+            "phases_ms_per_solve": phases,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "fp64_fma_tflops": peak,
+        }
+        print(json.dumps(line))
+    s.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_case(args):
+    """Minimal launches of one kernel family for ncu (no timing, no JSON)."""
+    import torch
+
+    import paper_1510_02237_gb300 as P
+    torch.cuda.set_device(0)
+    wl = W.workload_medium()
+    p = wl.problem
+    s = P.Solver(p, stream=torch.cuda.current_stream(), K_max=wl.K, krylov_cap=wl.krylov_cap)
+    q0 = torch.from_numpy(wl.ics[0][1]().ravel()).cuda()
+    if args.case == "fine":
+        X = q0.repeat(p.n_slices)
+        Y = torch.empty_like(X)
+        for _ in range(3):
+            P.parareal_fine_sweep(s.h, X, Y, p.n_slices)
+    else:
+        out = torch.empty_like(q0)
+        for _ in range(2):
+            P.parareal_solve(s.h, q0, wl.K, qT=out, report=False)
+    torch.cuda.synchronize()
+    s.close()
+    print(f"case {args.case} done")
+    return 0
+
+
+def main():
+    args = parse()
+    if args.case:
+        return run_case(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

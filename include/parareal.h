@@ -79,6 +79,23 @@ typedef struct {
     float ms_total;              /* device time of the whole solve (CUDA events)  */
 } pr_report;
 
+/* Phase timing of solves, measured with CUDA events on the handle's stream
+ * (no synchronisation while solving).  Phases follow Alg. 2: the serial
+ * coarse initialisation, then per iteration the parallel fine predictor, the
+ * coarse images G(q_i^k), the subspace update with K(q_i^k), and the serial
+ * correction. */
+typedef struct {
+    int32_t n_solves;        /* solves accumulated since the last reset           */
+    double ms_init;          /* serial coarse initialisation                      */
+    double ms_fine;          /* fine predictor F (all RK-3 step launches)         */
+    double ms_coarse;        /* coarse images G(q_i^k)                            */
+    double ms_krylov;        /* subspace update and K(q_i^k)                      */
+    double ms_chain;         /* serial correction                                 */
+    double ms_total;         /* sum of the solves' device time                    */
+    double fine_cell_steps;  /* cells x RK-3 steps computed by the fine predictor */
+    int64_t fine_launches;   /* RK-3 step kernel launches of the fine predictor   */
+} pr_timing;
+
 /* Fill *opt with the defaults listed above (the paper's values, Sec. 3.2). */
 pr_status parareal_default_options(pr_options* opt);
 
@@ -157,6 +174,24 @@ pr_status krylov_rank(pr_solver* h, int32_t* rank);
  * linearity (Eq. Genhance), FPq = F(P q) = D (Q^T q) + G(P q).  q_dev, Pq_dev,
  * FPq_dev: device, d doubles each; Pq_dev or FPq_dev may be NULL. */
 pr_status krylov_project(pr_solver* h, const double* q_dev, double* Pq_dev, double* FPq_dev);
+
+/* Record phase events for up to max_solves subsequent solves (allocates the
+ * events; max_solves = 0 disables and frees them).  Resets the accumulators. */
+pr_status parareal_timing_enable(pr_solver* h, int32_t max_solves);
+
+/* Synchronise the stream and return the phase times accumulated over the
+ * solves recorded since the last reset; reset != 0 starts a new accumulation. */
+pr_status parareal_timing_read(pr_solver* h, pr_timing* t, int32_t reset);
+
+/* Measurement utility with no counterpart in the paper: fused multiply-add
+ * throughput of the current device in FLOP/s for prec = PR_FP64 or PR_FP32
+ * (8 independent FMA chains per thread, 8 CTAs of 256 threads per SM, iters
+ * x 32 FMAs per thread), the denominator of the ALU roofline.  Allocates a
+ * small device buffer, synchronises the legacy default stream. */
+pr_status parareal_alu_probe(int32_t prec, int32_t iters, double* flops_per_s);
+
+/* Process-wide number of CUDA kernels this library has launched. */
+uint64_t parareal_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -38,6 +38,15 @@ class pr_report(C.Structure):
                 ("ms_total", C.c_float)]
 
 
+class pr_timing(C.Structure):
+    _fields_ = [("n_solves", C.c_int32), ("ms_init", C.c_double), ("ms_fine", C.c_double),
+                ("ms_coarse", C.c_double), ("ms_krylov", C.c_double), ("ms_chain", C.c_double),
+                ("ms_total", C.c_double), ("fine_cell_steps", C.c_double), ("fine_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class PararealError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -47,7 +56,8 @@ class PararealError(RuntimeError):
 EXPORTS = ["parareal_default_options", "parareal_create", "parareal_destroy", "parareal_last_error",
            "parareal_footprint_bytes", "parareal_solve", "parareal_solve_host", "parareal_fine_sweep",
            "parareal_coarse_sweep", "parareal_coarse_apply", "krylov_reset", "krylov_update", "krylov_rank",
-           "krylov_project"]
+           "krylov_project", "parareal_timing_enable", "parareal_timing_read", "parareal_kernel_launches",
+           "parareal_alu_probe"]
 
 _lib = None
 
@@ -91,6 +101,14 @@ def lib():
     L.krylov_rank.restype = st
     L.krylov_project.argtypes = [P, P, P, P]
     L.krylov_project.restype = st
+    L.parareal_timing_enable.argtypes = [P, C.c_int32]
+    L.parareal_timing_enable.restype = st
+    L.parareal_timing_read.argtypes = [P, C.POINTER(pr_timing), C.c_int32]
+    L.parareal_timing_read.restype = st
+    L.parareal_kernel_launches.argtypes = []
+    L.parareal_kernel_launches.restype = C.c_uint64
+    L.parareal_alu_probe.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_double)]
+    L.parareal_alu_probe.restype = st
     _lib = L
     return L
 
@@ -190,6 +208,26 @@ def krylov_rank(h) -> int:
 
 def krylov_project(h, q, Pq=None, FPq=None):
     _check(h, lib().krylov_project(h, _ptr(q), _ptr(Pq), _ptr(FPq)))
+
+
+def parareal_timing_enable(h, max_solves):
+    _check(h, lib().parareal_timing_enable(h, int(max_solves)))
+
+
+def parareal_timing_read(h, reset=True) -> dict:
+    t = pr_timing()
+    _check(h, lib().parareal_timing_read(h, C.byref(t), 1 if reset else 0))
+    return t.as_dict()
+
+
+def parareal_kernel_launches() -> int:
+    return int(lib().parareal_kernel_launches())
+
+
+def parareal_alu_probe(prec=PR_FP64, iters=4096) -> float:
+    v = C.c_double()
+    _check(None, lib().parareal_alu_probe(int(prec), int(iters), C.byref(v)))
+    return v.value
 
 
 class Solver:

@@ -145,6 +145,7 @@ cudaError_t launch_coarse_step(const double* in, double* out, long stride, int n
     if (e != cudaSuccess) return e;
     dim3 grid((nx + CTX - 1) / CTX, (ny + CTY - 1) / CTY, n);
     k_coarse_step<<<grid, CNT, smem, s>>>(in, out, stride, nx, ny, c, H);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,9 @@
 
 namespace pr {
 
+// Count n kernel launches (process-wide, reported by parareal_kernel_launches).
+void count_launches(int n);
+
 // Periodic index for offsets that may exceed one period (tiny grids).
 __host__ __device__ __forceinline__ int pwrap(int i, int n) {
     i %= n;

@@ -149,6 +149,7 @@ cudaError_t launch_tile(const Tin* in, long instride, Tout* out, long outstride,
     if (e != cudaSuccess) return e;
     dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, n);
     kern<<<grid, NT, smem, s>>>(in, instride, out, outstride, nx, ny, c);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -291,19 +291,23 @@ cudaError_t gemm_tn(const double* A, long lda, const int* c0_dev, const int* c1_
         dim3 grid(nchunk, cdiv(ccap, GV_CB));
         k_gemv_tn_partial<<<grid, 256, GV_RPC * sizeof(double), s>>>(A, lda, c0_dev, c1_dev, X, nrows,
                                                                     GV_RPC, ccap, w.partial);
+        count_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         k_reduce_chunks<<<cdiv(ccap, 256), 256, 0, s>>>(w.partial, nchunk, ccap, c0_dev, c1_dev, 1, C, ldc);
+        count_launches(1);
         return cudaGetLastError();
     }
     const int nchunk = cdiv(nrows, TN_RPC);
     if ((long)nchunk * ccap * m > w.elems) return cudaErrorInvalidValue;
     dim3 grid(nchunk, cdiv(ccap, TN_CB), cdiv(m, TN_JB));
     k_gemm_tn_partial<<<grid, 256, 0, s>>>(A, lda, c0_dev, c1_dev, X, ldx, m, nrows, TN_RPC, ccap, w.partial);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_chunks<<<cdiv((long)ccap * m, 256), 256, 0, s>>>(w.partial, nchunk, (long)ccap * m, c0_dev,
                                                             c1_dev, m, C, ldc);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -316,6 +320,7 @@ cudaError_t gemm_nn(const double* A, long lda, const int* c0_dev, const int* c1_
     if (e != cudaSuccess) return e;
     dim3 grid(cdiv(nrows, 256), cdiv(m, NN_JB));
     k_gemm_nn<<<grid, 256, smem, s>>>(A, lda, c0_dev, c1_dev, C, ldc, B, ldb, Y, ldy, m, nrows, sgn);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -324,9 +329,11 @@ cudaError_t colnorm2(const double* X, long ldx, int m, long nrows, double* out, 
     const int nchunk = cdiv(nrows, NRM_RPC);
     if ((long)nchunk * m > w.elems) return cudaErrorInvalidValue;
     k_colnorm2_partial<<<dim3(nchunk, m), 256, 0, s>>>(X, ldx, m, nrows, NRM_RPC, w.partial);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_chunks<<<cdiv(m, 256), 256, 0, s>>>(w.partial, nchunk, m, nullptr, nullptr, m, out, 1);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -336,9 +343,11 @@ cudaError_t krylov_append(const double* v, const double* z, const double* res2, 
     int nb = cdiv(nrows, 256);
     if (nb > 1024) nb = 1024;
     k_krylov_append<<<nb, 256, 0, s>>>(v, z, res2, a2, eta, cap, r, Q, D, ld, nrows, kept);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_bump_rank<<<1, 1, 0, s>>>(r, kept);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -351,9 +360,11 @@ cudaError_t chain_update(const double* qt, const double* g, const double* D, lon
     cudaError_t e = cudaFuncSetAttribute(k_chain_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_chain_update<<<nb, 256, smem, s>>>(qt, g, D, ldd, c1_dev, c, kold, q, nrows, w.partial);
+    count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sum_partials<<<1, 256, 0, s>>>(w.partial, nb, res2_slot);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -361,14 +372,17 @@ cudaError_t copy_resid(const double* src, double* dst, long n, double* res2, con
     const int nb = cdiv(n, 256);
     if (nb > w.elems) return cudaErrorInvalidValue;
     k_copy_resid<<<nb, 256, 0, s>>>(src, dst, n, w.partial);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sum_partials<<<1, 256, 0, s>>>(w.partial, nb, res2);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t max_sqrt(const double* res2, int n, double* out, cudaStream_t s) {
     k_max_sqrt<<<1, 32, 0, s>>>(res2, n, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -376,11 +390,13 @@ cudaError_t sub(const double* a, const double* b, double* out, long n, cudaStrea
     int nb = cdiv(n, 256);
     if (nb > 4096) nb = 4096;
     k_sub<<<nb, 256, 0, s>>>(a, b, out, n);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t fill_int(int* p, int v, int n, cudaStream_t s) {
     k_fill_int<<<cdiv(n, 256), 256, 0, s>>>(p, v, n);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -13,13 +13,26 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "parareal.h"
 
 using namespace pr;
+
+static std::atomic<uint64_t> g_launches{0};
+void pr::count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// Ring of CUDA events recording the phase boundaries of up to max_solves solves:
+// [start, init end, then per iteration: fine end, coarse end, krylov end, chain end].
+struct TimingRing {
+    int max_solves = 0, per_solve = 0, n = 0;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> K;
+};
 
 struct pr_solver {
     int nx = 0, ny = 0, N = 0, n_f = 0, n_g = 0, K_max = 0, cap = 0;
@@ -39,6 +52,7 @@ struct pr_solver {
     int *r = nullptr, *r_old = nullptr, *kept = nullptr, *ranks = nullptr, *zero = nullptr;
     long partial_elems = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    TimingRing tr;
     std::string err;
 };
 
@@ -205,10 +219,20 @@ static pr_status solve_impl(pr_solver* h, int K, pr_report* rep) {
     cudaStream_t s = h->stream;
     TsWork w{h->partial, h->partial_elems};
     const bool kse = h->opt.variant == PR_KSE;
+    cudaEvent_t* ev = nullptr;
+    if (h->tr.n < h->tr.max_solves) {
+        ev = h->tr.ev.data() + (size_t)h->tr.n * h->tr.per_solve;
+        h->tr.K[h->tr.n] = K;
+        h->tr.n += 1;
+    }
+    int evi = 0;
+    auto mark = [&]() -> cudaError_t { return ev ? cudaEventRecord(ev[evi++], s) : cudaSuccess; };
+    CKC(mark());
 
     // initialisation: q_{i+1}^0 = G(q_i^0), serially (q[0] already holds u0)
     for (int i = 0; i < N; ++i) CKS(coarse_apply(h, h->q + (long)i * d, h->q + (long)(i + 1) * d, 1));
     CKC(fill_int(h->r, 0, 1, s));
+    CKC(mark());
 
     for (int k = 0; k < K; ++k) {
         // Slices i < k satisfy q_i^{k} = q_i^{k-1} bit for bit (the correction
@@ -218,8 +242,10 @@ static pr_status solve_impl(pr_solver* h, int K, pr_report* rep) {
         double* qa = h->q + (long)a * d;
         // parallel predictor: q~_{i+1}^k = F(q_i^k)
         CKS(fine_apply(h, qa, h->qt + (long)a * d, M));
+        CKC(mark());
         // coarse images G(q_i^k) (subspace images and K(q_i^k))
         CKS(coarse_apply(h, qa, h->gv + (long)a * d, M));
+        CKC(mark());
         if (kse) {
             CKS(krylov_block(h, qa, h->qt + (long)a * d, h->gv + (long)a * d, M));
             // K(q_i^k) = G(q_i^k) + D Q^T q_i^k for i = k+1..N-1 with the updated S^k
@@ -230,6 +256,7 @@ static pr_status solve_impl(pr_solver* h, int K, pr_report* rep) {
             }
             CKC(cudaMemcpyAsync(h->ranks + k, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
         }
+        CKC(mark());
         // serial correction
         CKC(cudaMemsetAsync(h->res2, 0, sizeof(double) * (N + 1), s));
         CKC(copy_resid(h->qt + (long)a * d, h->q + (long)(a + 1) * d, d, h->res2 + a + 1, w, s));
@@ -242,9 +269,15 @@ static pr_status solve_impl(pr_solver* h, int K, pr_report* rep) {
                              h->res2 + i + 1, w, s));
         }
         CKC(max_sqrt(h->res2 + 1, N, h->rhist + k, s));
+        CKC(mark());
     }
     (void)rep;
     return PR_OK;
+}
+
+static void timing_free(pr_solver* h) {
+    for (cudaEvent_t e : h->tr.ev) cudaEventDestroy(e);
+    h->tr = TimingRing();
 }
 
 static pr_status fill_report(pr_solver* h, int K, pr_report* rep) {
@@ -456,6 +489,7 @@ pr_status parareal_destroy(pr_solver* h) {
     if (h->ranks) cudaFree(h->ranks);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    timing_free(h);
     delete h;
     return PR_OK;
 }
@@ -560,5 +594,55 @@ pr_status krylov_project(pr_solver* h, const double* q_dev, double* Pq_dev, doub
     }
     return PR_OK;
 }
+
+pr_status parareal_timing_enable(pr_solver* h, int32_t max_solves) {
+    if (!h) return PR_EINVAL;
+    if (max_solves < 0 || max_solves > 100000) return set_err(h, PR_EINVAL, "max_solves out of range");
+    CKC(cudaStreamSynchronize(h->stream));
+    timing_free(h);
+    if (max_solves == 0) return PR_OK;
+    h->tr.max_solves = max_solves;
+    h->tr.per_solve = 2 + 4 * h->K_max;
+    h->tr.ev.assign((size_t)max_solves * h->tr.per_solve, nullptr);
+    h->tr.K.assign((size_t)max_solves, 0);
+    for (auto& e : h->tr.ev) {
+        cudaError_t x = cudaEventCreate(&e);
+        if (x != cudaSuccess) {
+            timing_free(h);
+            return set_err(h, PR_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(x));
+        }
+    }
+    return PR_OK;
+}
+
+pr_status parareal_timing_read(pr_solver* h, pr_timing* t, int32_t reset) {
+    if (!h || !t) return PR_EINVAL;
+    CKC(cudaStreamSynchronize(h->stream));
+    std::memset(t, 0, sizeof(*t));
+    const long ncell = (long)h->nx * h->ny;
+    for (int sidx = 0; sidx < h->tr.n; ++sidx) {
+        cudaEvent_t* ev = h->tr.ev.data() + (size_t)sidx * h->tr.per_solve;
+        const int K = h->tr.K[sidx];
+        float ms = 0.f;
+        CKC(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        t->ms_init += ms;
+        t->ms_total += ms;
+        for (int k = 0; k < K; ++k) {
+            double* acc[4] = {&t->ms_fine, &t->ms_coarse, &t->ms_krylov, &t->ms_chain};
+            for (int ph = 0; ph < 4; ++ph) {
+                CKC(cudaEventElapsedTime(&ms, ev[1 + 4 * k + ph], ev[2 + 4 * k + ph]));
+                *acc[ph] += ms;
+                t->ms_total += ms;
+            }
+            t->fine_cell_steps += (double)(h->N - k) * h->n_f * ncell;
+            t->fine_launches += h->n_f;
+        }
+        t->n_solves += 1;
+    }
+    if (reset) h->tr.n = 0;
+    return PR_OK;
+}
+
+uint64_t parareal_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

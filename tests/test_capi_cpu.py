@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared_symbols():
     src = open(os.path.join(ROOT, "include", "parareal.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:pr_status|size_t|const char\s*\*)\s+([a-z_]+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:pr_status|size_t|uint64_t|const char\s*\*)\s+([a-z_0-9]+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
