@@ -190,6 +190,31 @@ pr_status parareal_timing_read(pr_solver* h, pr_timing* t, int32_t reset);
  * small device buffer, synchronises the legacy default stream. */
 pr_status parareal_alu_probe(int32_t prec, int32_t iters, double* flops_per_s);
 
+/* Allocation-free fine sweep, for callers that cannot allocate device memory
+ * where they need F: code running while a stream is captured into a CUDA
+ * graph (cudaMalloc is not permitted there), runtimes that route every
+ * device allocation through their own pool, and hosts that may not allocate
+ * after start-up.  The paper has no counterpart; it computes exactly what
+ * parareal_fine_sweep computes (n_steps RK-3 steps of the fine tendency on n
+ * independent states) without a handle: every input and output comes from
+ * the caller and the RK-3 intermediates live in a file-scope device array of
+ * 32 MiB (two 16 MiB halves) that every GPU loading the library holds until
+ * the process exits.
+ *   g, U, V, c_s, nu_f, dt_f: as for parareal_create (nx, ny >= 4).
+ *   n_steps: RK-3 steps (>= 1); fine_prec: PR_FP64 or PR_FP32.
+ *   q_in_dev / q_out_dev: device, n*d doubles each, not overlapping.
+ *   n: 1..65535 states with n*d*(8 for FP64, 4 for FP32) <= 16 MiB, i.e.
+ *      n*d <= 2097152 (FP64) or 4194304 (FP32); larger sizes return
+ *      PR_EINVAL and print the limit to stderr.
+ *   stream: cudaStream_t or NULL.  Returns after enqueueing.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and must come before any stream capture.  Calls share
+ * the array: calls whose work overlaps on the GPU race and must be
+ * serialised by the caller.  No allocation of any kind is made. */
+pr_status parareal_fine_sweep_static(const pr_grid* g, double U, double V, double c_s, double nu_f,
+                                     double dt_f, int32_t n_steps, int32_t fine_prec,
+                                     const double* q_in_dev, double* q_out_dev, int32_t n, void* stream);
+
 /* Process-wide number of CUDA kernels this library has launched. */
 uint64_t parareal_kernel_launches(void);
 

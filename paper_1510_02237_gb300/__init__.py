@@ -57,7 +57,7 @@ EXPORTS = ["parareal_default_options", "parareal_create", "parareal_destroy", "p
            "parareal_footprint_bytes", "parareal_solve", "parareal_solve_host", "parareal_fine_sweep",
            "parareal_coarse_sweep", "parareal_coarse_apply", "krylov_reset", "krylov_update", "krylov_rank",
            "krylov_project", "parareal_timing_enable", "parareal_timing_read", "parareal_kernel_launches",
-           "parareal_alu_probe"]
+           "parareal_alu_probe", "parareal_fine_sweep_static"]
 
 _lib = None
 
@@ -109,6 +109,9 @@ def lib():
     L.parareal_kernel_launches.restype = C.c_uint64
     L.parareal_alu_probe.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_double)]
     L.parareal_alu_probe.restype = st
+    L.parareal_fine_sweep_static.argtypes = [C.POINTER(pr_grid), C.c_double, C.c_double, C.c_double, C.c_double,
+                                             C.c_double, C.c_int32, C.c_int32, P, P, C.c_int32, P]
+    L.parareal_fine_sweep_static.restype = st
     _lib = L
     return L
 
@@ -228,6 +231,16 @@ def parareal_alu_probe(prec=PR_FP64, iters=4096) -> float:
     v = C.c_double()
     _check(None, lib().parareal_alu_probe(int(prec), int(iters), C.byref(v)))
     return v.value
+
+
+def parareal_fine_sweep_static(nx, ny, U, V, c_s, nu_f, dt_f, n_steps, fine_prec, q_in, q_out, n, stream=None):
+    """Allocation-free fine sweep (no handle); see include/parareal.h for its limits."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(None, lib().parareal_fine_sweep_static(C.byref(pr_grid(nx, ny, 1.0, 1.0)), float(U), float(V),
+                                                  float(c_s), float(nu_f), float(dt_f), int(n_steps),
+                                                  int(fine_prec), _ptr(q_in), _ptr(q_out), int(n),
+                                                  C.c_void_p(stream) if stream else None))
 
 
 class Solver:
