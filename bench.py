@@ -284,7 +284,8 @@ def run_ours(args):
     line = None
     if rank == 0:
         # ---- roofline of the dominant phase's kernel
-        phases = {k: tm[k] / n for k in ("ms_init", "ms_fine", "ms_coarse", "ms_krylov", "ms_chain")}
+        phases = {k: tm[k] / n for k in ("ms_init", "ms_fine", "ms_coarse", "ms_krylov", "ms_gs_block",
+                                          "ms_gs_intra", "ms_kold", "ms_chain")}
         fp64_peak = P.parareal_alu_probe(P.PR_FP64, 4096)
         fine_flops = tm["fine_cell_steps"] * FINE_FLOPS_PER_CELL_STEP
         achieved = fine_flops / (tm["ms_fine"] / 1e3) / 1e12

@@ -89,7 +89,10 @@ typedef struct {
     double ms_init;          /* serial coarse initialisation                      */
     double ms_fine;          /* fine predictor F (all RK-3 step launches)         */
     double ms_coarse;        /* coarse images G(q_i^k)                            */
-    double ms_krylov;        /* subspace update and K(q_i^k)                      */
+    double ms_krylov;        /* subspace update and K(q_i^k) (sum of the next 3)  */
+    double ms_gs_block;      /*   Gram-Schmidt against the existing basis         */
+    double ms_gs_intra;      /*   Gram-Schmidt within the new columns, appends    */
+    double ms_kold;          /*   K(q_i^k) for the correction                     */
     double ms_chain;         /* serial correction                                 */
     double ms_total;         /* sum of the solves' device time                    */
     double fine_cell_steps;  /* cells x RK-3 steps computed by the fine predictor */

@@ -40,7 +40,8 @@ class pr_report(C.Structure):
 
 class pr_timing(C.Structure):
     _fields_ = [("n_solves", C.c_int32), ("ms_init", C.c_double), ("ms_fine", C.c_double),
-                ("ms_coarse", C.c_double), ("ms_krylov", C.c_double), ("ms_chain", C.c_double),
+                ("ms_coarse", C.c_double), ("ms_krylov", C.c_double), ("ms_gs_block", C.c_double),
+                ("ms_gs_intra", C.c_double), ("ms_kold", C.c_double), ("ms_chain", C.c_double),
                 ("ms_total", C.c_double), ("fine_cell_steps", C.c_double), ("fine_launches", C.c_int64)]
 
     def as_dict(self):

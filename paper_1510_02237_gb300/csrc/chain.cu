@@ -1,0 +1,150 @@
+// chain.cu -- the serial correction of Alg. 2 for a run of consecutive
+// slices in one cooperative launch:
+//
+//   for i = i_begin .. i_end-1:
+//     c         = Q^T q_i                                 (Eq. modifiedCoarse, P q = Q c)
+//     K(q_i)    = G(q_i) + D c,   D = F(Q) - G(Q)          (Eq. Genhance by linearity)
+//     q_{i+1}   = q~_{i+1} + (K(q_i) - K_old_i)            (Alg. 2)
+//     res2[i+1] = ||q_{i+1}^{new} - q_{i+1}^{old}||^2       (for r^k, Sec. 2.1)
+//
+// With no basis, no fine images and no K_old it is the serial coarse sweep
+// q_{i+1} = G(q_i) of the initialisation; with K_old = G(q_i^k) and no basis
+// it is the correction of the original Parareal (Alg. 1).
+//
+// Every CTA owns a fixed range of rows for the dot products and the update
+// and a set of 16 x 16 tiles for the coarse steps.  Per slice: phase A
+// computes the CTA's partial dot products and the first coarse step; after a
+// barrier the coefficients are reduced (each CTA sums a share of them over
+// all CTA partials in a fixed order) while the second coarse step runs;
+// after a barrier every CTA updates its rows; a last barrier publishes
+// q_{i+1} before the next slice's coarse step reads its halos.  All waits are
+// bounded (grid_barrier).
+#include "coarse_tile.cuh"
+#include "grid_barrier.cuh"
+
+namespace pr {
+namespace {
+
+constexpr int CH_NT = 512, CH_TX = 16, CH_TY = 16;
+
+__global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
+    extern __shared__ __align__(16) double sm[];
+    __shared__ double red[CH_NT / 32];
+    const unsigned nb = gridDim.x;
+    const int b = blockIdx.x;
+    const long d = A.d;
+    const long rpb = (d + nb - 1) / nb;
+    const long r0 = min(d, (long)b * rpb), r1 = min(d, r0 + rpb);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = CH_NT / 32;
+    const int ncols = A.r_dev ? *A.r_dev : 0;
+    const int ntx = (A.nx + CH_TX - 1) / CH_TX, nty = (A.ny + CH_TY - 1) / CH_TY, ntiles = ntx * nty;
+    const int cpb = (ncols + (int)nb - 1) / (int)nb;
+
+    for (int i = A.i_begin; i < A.i_end; ++i) {
+        const double* qi = A.q + (long)i * d;
+        double* qn = A.q + (long)(i + 1) * d;
+        // phase A: this CTA's partial dot products c_l = sum_rows Q[row, l] q_i[row]
+        for (int l = wid; l < ncols; l += nw) {
+            const double s = warp_dot(A.Q + (long)l * d, qi, r0, r1);
+            if (lane == 0) A.part[(long)b * A.ccap + l] = s;
+        }
+        // coarse steps G(q_i), one barrier after each
+        const double* gin = qi;
+        for (int st = 0; st < A.n_g; ++st) {
+            double* gout = A.gbuf + (long)(st & 1) * d;
+            for (int t = b; t < ntiles; t += nb) {
+                const int ty = t / ntx, tx = t - ty * ntx;
+                coarse_tile<CH_TX, CH_TY, CH_NT>(gin, gout, A.nx, A.ny, A.cc, A.H, tx * CH_TX, ty * CH_TY, sm);
+            }
+            if (!grid_barrier(A.gb, nb)) return;
+            if (st == 0 && ncols > 0) {
+                // this CTA's share of the coefficients, summed over all CTAs in order
+                const int l1 = min(ncols, (b + 1) * cpb);
+                for (int l = b * cpb + wid; l < l1; l += nw) {
+                    const double s = warp_sum_strided(A.part + l, nb, A.ccap);
+                    if (lane == 0) A.cvec[l] = s;
+                }
+                if (A.n_g == 1 && !grid_barrier(A.gb, nb)) return;
+            }
+            gin = gout;
+        }
+        // update of this CTA's rows
+        double* cs = sm;
+        for (int l = threadIdx.x; l < ncols; l += CH_NT) cs[l] = __ldcg(A.cvec + l);
+        __syncthreads();
+        const double* qt = A.qt ? A.qt + (long)i * d : nullptr;
+        const double* ko = A.kold ? A.kold + (long)i * d : nullptr;
+        double s = 0.0;
+        for (long row = r0 + threadIdx.x; row < r1; row += CH_NT) {
+            double acc = 0.0;
+            const double* Dr = A.D + row;
+#pragma unroll 8
+            for (int l = 0; l < ncols; ++l) acc += __ldg(Dr + (long)l * d) * cs[l];
+            const double knew = gin[row] + acc;
+            const double y = (qt ? qt[row] : 0.0) + (knew - (ko ? ko[row] : 0.0));
+            const double e = y - qn[row];
+            s += e * e;
+            qn[row] = y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[wid] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < nw; ++k) t += red[k];
+            A.resp[(long)i * nb + b] = t;
+        }
+        if (!grid_barrier(A.gb, nb)) return;
+    }
+    if (A.res2 && b == 0) {
+        for (int i = A.i_begin + wid; i < A.i_end; i += nw) {
+            const double t = warp_sum_strided(A.resp + (long)i * nb, nb, 1);
+            if (lane == 0) A.res2[i + 1] = t;
+        }
+    }
+}
+
+size_t chain_smem_bytes(int H, int ccap) {
+    size_t a = sizeof(double) * coarse_tile_smem_doubles<CH_TX, CH_TY>(H);
+    size_t c = sizeof(double) * (size_t)(ccap > 0 ? ccap : 1);
+    return a > c ? a : c;
+}
+
+}  // namespace
+
+int chain_grid(int H, int ccap) {
+    static int cached[64][2] = {};   // [device] -> (key, blocks)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    const int key = (int)chain_smem_bytes(H, ccap);
+    if (cached[dev][0] != key) {
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, key) != cudaSuccess) return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain, CH_NT, key);
+        cached[dev][0] = key;
+        cached[dev][1] = per >= 1 ? sms : 0;
+    }
+    return cached[dev][1];
+}
+
+long chain_resp_elems(int n_slices) { return (long)(n_slices + 1) * 1024; }
+
+cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s) {
+    if (a.i_end <= a.i_begin) return cudaSuccess;
+    const int nb = chain_grid(a.H, a.ccap);
+    if (nb < 1 || nb > 1024) return cudaErrorInvalidConfiguration;
+    const size_t smem = chain_smem_bytes(a.H, a.ccap);
+    cudaError_t e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(&a.gb->count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    ChainArgs arg = a;
+    void* args[] = {&arg};
+    e = cudaLaunchCooperativeKernel((const void*)k_chain, dim3(nb), dim3(CH_NT), args, smem, s);
+    count_launches(1);
+    return e;
+}
+
+}  // namespace pr

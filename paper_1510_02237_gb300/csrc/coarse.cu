@@ -1,135 +1,18 @@
-// coarse.cu -- coarse propagator G: one partially split forward-Euler step
-// with forward-backward acoustic substeps and divergence damping (Sec. 3.2).
-//
-//   S = -(F_{i+1/2} - F_{i-1/2})/dx - (G_{j+1/2} - G_{j-1/2})/dy    slow tendency at q^n,
-//        upwind-biased advective fluxes of order 1 or 3, held fixed for the step;
-//   n_sound times, tau = Delta t / n_sound, alpha = nu_c dx^2 / tau:
-//     u <- u + tau [S_u - c_s (p[i+1]-p[i-1])/(2dx) + alpha1 (div u)_x]
-//     w <- w + tau [S_w - c_s (p[j+1]-p[j-1])/(2dy) + alpha2 (div u)_y]
-//     p <- p + tau [S_p - c_s ((u[i+1]-u[i-1])/(2dx) + (w[j+1]-w[j-1])/(2dy))]   (new u, w)
-//
-// One launch performs one whole coarse step for a TX x TY tile of each
-// state.  Every substep widens the dependency cone by 2 cells (1 for the
-// velocities, 1 for the pressure) and the slow tendency by the flux radius,
-// so the tile loads a halo H = r_adv + 2 n_sound - 1 and shrinks the valid
-// region as the substeps proceed; nothing is written to memory between
-// substeps.
-#include "common.cuh"
+// coarse.cu -- coarse propagator G over a batch of states: one launch per
+// partially split forward-Euler coarse step (Sec. 3.2); the step itself is
+// coarse_tile() (coarse_tile.cuh), one 32 x 16 tile per CTA.
+#include "coarse_tile.cuh"
 
 namespace pr {
 namespace {
 
-constexpr int CTX = 32, CTY = 16, CNT = 256, CMAXH = 12;
+constexpr int CTX = 32, CTY = 16, CNT = 256;
 
-__device__ __forceinline__ double upwind_flux(int order, double U, const double* f, int i, int st) {
-    // interface i+1/2 along stride st
-    if (order == 1) return U >= 0.0 ? U * f[i] : U * f[i + st];
-    double aU = fabs(U);
-    return U * (7.0 * (f[i + st] + f[i]) - (f[i + 2 * st] + f[i - st])) * (1.0 / 12.0) +
-           aU * ((f[i + 2 * st] - f[i - st]) - 3.0 * (f[i + st] - f[i])) * (1.0 / 12.0);
-}
-
-__global__ void __launch_bounds__(CNT) k_coarse_step(const double* __restrict__ in,
-                                                     double* __restrict__ out, long stride, int nx,
-                                                     int ny, CoarseCoef c, int H) {
-    const int RX = CTX + 2 * H, RY = CTY + 2 * H, NR = RX * RY;
+__global__ void __launch_bounds__(CNT) k_coarse_step(const double* __restrict__ in, double* __restrict__ out,
+                                                     long stride, int nx, int ny, CoarseCoef c, int H) {
     extern __shared__ __align__(16) double sm[];
-    double* u = sm;
-    double* w = u + NR;
-    double* p = w + NR;
-    double* su = p + NR;
-    double* sw = su + NR;
-    double* sp = sw + NR;
-    const long ncell = (long)nx * ny;
-    const double* src = in + (long)blockIdx.z * stride;
-    double* dst = out + (long)blockIdx.z * stride;
-    const int tx0 = blockIdx.x * CTX, ty0 = blockIdx.y * CTY;
-
-    for (int idx = threadIdx.x; idx < NR; idx += CNT) {
-        int ly = idx / RX, lx = idx - ly * RX;
-        long g = (long)pwrap(ty0 - H + ly, ny) * nx + pwrap(tx0 - H + lx, nx);
-        u[idx] = src[g];
-        w[idx] = src[ncell + g];
-        p[idx] = src[2 * ncell + g];
-    }
-    __syncthreads();
-
-    const int ra = c.order == 1 ? 1 : 2;
-    // slow (advective) tendency on the region shrunk by ra
-    {
-        const int W1 = RX - 2 * ra, H1 = RY - 2 * ra, N1 = W1 * H1;
-        for (int t = threadIdx.x; t < N1; t += CNT) {
-            int r = t / W1;
-            int i = (r + ra) * RX + (t - r * W1) + ra;
-            double* fs[3] = {u, w, p};
-            double* ss[3] = {su, sw, sp};
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                const double* a = fs[f];
-                double Fe = upwind_flux(c.order, c.U, a, i, 1), Fw = upwind_flux(c.order, c.U, a, i - 1, 1);
-                double Gn = upwind_flux(c.order, c.V, a, i, RX), Gs = upwind_flux(c.order, c.V, a, i - RX, RX);
-                ss[f][i] = -(Fe - Fw) * c.inv_dx - (Gn - Gs) * c.inv_dy;
-            }
-        }
-    }
-    __syncthreads();
-
-    constexpr int MAXC = ((CTX + 2 * CMAXH) * (CTY + 2 * CMAXH) + CNT - 1) / CNT;
-    for (int m = 0; m < c.n_sound; ++m) {
-        // forward: velocities on the region shrunk by ra + 2m
-        const int sh = ra + 2 * m;
-        const int W2 = RX - 2 * sh, H2 = RY - 2 * sh, N2 = W2 * H2;
-        double nu[MAXC], nw[MAXC];
-#pragma unroll
-        for (int k = 0; k < MAXC; ++k) {
-            int t = threadIdx.x + k * CNT;
-            if (t < N2) {
-                int r = t / W2;
-                int i = (r + sh) * RX + (t - r * W2) + sh;
-                double du = su[i] - c.csx * (p[i + 1] - p[i - 1]) +
-                            c.dxx * (u[i + 1] - 2.0 * u[i] + u[i - 1]) +
-                            c.dxy1 * ((w[i + 1 + RX] - w[i + 1 - RX]) - (w[i - 1 + RX] - w[i - 1 - RX]));
-                double dw = sw[i] - c.csy * (p[i + RX] - p[i - RX]) +
-                            c.dyy * (w[i + RX] - 2.0 * w[i] + w[i - RX]) +
-                            c.dxy2 * ((u[i + 1 + RX] - u[i - 1 + RX]) - (u[i + 1 - RX] - u[i - 1 - RX]));
-                nu[k] = u[i] + c.tau * du;
-                nw[k] = w[i] + c.tau * dw;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < MAXC; ++k) {
-            int t = threadIdx.x + k * CNT;
-            if (t < N2) {
-                int r = t / W2;
-                int i = (r + sh) * RX + (t - r * W2) + sh;
-                u[i] = nu[k];
-                w[i] = nw[k];
-            }
-        }
-        __syncthreads();
-        // backward: pressure with the new velocities on the region shrunk by ra + 2m + 1
-        const int sp1 = sh + 1;
-        const int W3 = RX - 2 * sp1, H3 = RY - 2 * sp1, N3 = W3 * H3;
-        for (int t = threadIdx.x; t < N3; t += CNT) {
-            int r = t / W3;
-            int i = (r + sp1) * RX + (t - r * W3) + sp1;
-            p[i] = p[i] + c.tau * (sp[i] - (c.csx * (u[i + 1] - u[i - 1]) + c.csy * (w[i + RX] - w[i - RX])));
-        }
-        __syncthreads();
-    }
-
-    for (int t = threadIdx.x; t < CTX * CTY; t += CNT) {
-        int r = t / CTX, cx = t - r * CTX;
-        int gx = tx0 + cx, gy = ty0 + r;
-        if (gx < nx && gy < ny) {
-            int i = (r + H) * RX + cx + H;
-            long g = (long)gy * nx + gx;
-            dst[g] = u[i];
-            dst[ncell + g] = w[i];
-            dst[2 * ncell + g] = p[i];
-        }
-    }
+    coarse_tile<CTX, CTY, CNT>(in + (long)blockIdx.z * stride, out + (long)blockIdx.z * stride, nx, ny, c, H,
+                               blockIdx.x * CTX, blockIdx.y * CTY, sm);
 }
 
 }  // namespace
@@ -139,8 +22,8 @@ int coarse_halo(const CoarseCoef& c) { return (c.order == 1 ? 1 : 2) + 2 * c.n_s
 cudaError_t launch_coarse_step(const double* in, double* out, long stride, int n, int nx, int ny,
                                const CoarseCoef& c, cudaStream_t s) {
     const int H = coarse_halo(c);
-    if (H > CMAXH) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(double) * 6 * (CTX + 2 * H) * (CTY + 2 * H);
+    if (H > COARSE_MAXH) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double) * coarse_tile_smem_doubles<CTX, CTY>(H);
     cudaError_t e = cudaFuncSetAttribute(k_coarse_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((nx + CTX - 1) / CTX, (ny + CTY - 1) / CTY, n);

@@ -96,4 +96,65 @@ cudaError_t max_sqrt(const double* res2, int n, double* out, cudaStream_t s);
 cudaError_t sub(const double* a, const double* b, double* out, long n, cudaStream_t s);
 cudaError_t fill_int(int* p, int v, int n, cudaStream_t s);
 
+// Grid-barrier state of a cooperative launch (zeroed before each launch).
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+    int err;   // set to 1 when a barrier wait gave up
+};
+// In-order Gram-Schmidt (twice) within a block of m <= 64 columns that are
+// already orthogonal to the basis columns [0, *r_old_dev), the drop rule
+// against the original column norms a2[j] and the append, in one cooperative
+// launch.  gb->err != 0 afterwards (sticky) means a barrier wait gave up and
+// the result is invalid.
+cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2, const int* r_old_dev,
+                        int* r_dev, int cap, double eta, double* Q, double* D, int* kept, const TsWork& w,
+                        GridBar* gb, cudaStream_t s);
+
+
+// Serial correction of Alg. 2 over slices [i_begin, i_end) in one cooperative
+// launch (chain.cu):  q_{i+1} = qt_i + ((G(q_i) + D Q^T q_i) - kold_i).
+// qt, kold may be NULL (zero) and r_dev NULL (no basis): with all three NULL
+// it is the serial coarse sweep q_{i+1} = G(q_i).
+struct ChainArgs {
+    double* q;            // (N+1) x d iterates; q_i read, q_{i+1} written
+    const double* qt;     // slot i: fine image q~_{i+1}, or NULL
+    const double* kold;   // slot i: K(q_i^k), or NULL
+    const double* Q;      // basis, d x cap
+    const double* D;      // F(Q) - G(Q), d x cap
+    const int* r_dev;     // number of basis columns, or NULL for none
+    int ccap;             // basis capacity (partial-sum stride)
+    int i_begin, i_end;
+    long d;
+    int nx, ny;
+    CoarseCoef cc;
+    int n_g, H;
+    double* gbuf;         // 2 x d coarse ping-pong
+    double* cvec;         // >= ccap coefficients
+    double* part;         // >= 1024 x ccap partial sums
+    double* resp;         // >= chain_resp_elems(N) residual partials
+    double* res2;         // res2[i+1] = ||q_{i+1} change||^2, or NULL
+    GridBar* gb;
+};
+cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s);
+long chain_resp_elems(int n_slices);
+
+
+// FP64 fine sweep in one cooperative launch (fine_coop.cu).  Coefficients
+// already multiplied by the stage length c_k (k = 0, 1, 2: dt/3, dt/2, dt)
+// and signed as they enter q^n + c_k L.
+struct FineCoefK {
+    double adx[3], ady[3], csx[3], csy[3], dxx[3], dxy1[3], dyy[3], dxy2[3];
+};
+FineCoefK make_fine_coef_k(double U, double V, double cs, double dx, double dy, double nu, double dt);
+struct FineSweepArgs {
+    const double* in;    // n x d, not modified
+    double* out;         // n x d
+    double *w1, *w2, *w3;  // n x d work buffers each (distinct from in and out)
+    int n, nx, ny, nsteps;
+    FineCoefK c;
+    GridBar* gb;
+};
+cudaError_t fine_sweep_coop(const FineSweepArgs& a, bool has_v, cudaStream_t s);
+
 }  // namespace pr

@@ -1,0 +1,77 @@
+// grid_barrier.cuh -- bounded barrier over all CTAs of a cooperative launch.
+#pragma once
+
+#include "common.cuh"
+
+namespace pr {
+
+// Sense-reversal barrier over all CTAs of a cooperative launch.  The spin is
+// bounded: after ~2^22 polls (well over a second) it sets the error word and
+// returns false, so a fault elsewhere can never hang the GPU.
+__device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &gb->gen;
+        volatile int* verr = &gb->err;
+        if (*verr == 0) {
+            const unsigned g = *vgen;
+            __threadfence();
+            if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+                atomicExch(&gb->count, 0u);
+                __threadfence();
+                atomicAdd(&gb->gen, 1u);
+            } else {
+                unsigned long long it = 0;
+                while (*vgen == g) {
+                    if (++it > (1ull << 22) || *verr != 0) {
+                        atomicExch(&gb->err, 1);
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            __threadfence();
+        }
+        s_ok = *verr == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Sum of the nb values base[k * stride], k = 0..nb-1, by one warp: lane j adds
+// k = j, j+32, ... in order, then a fixed xor-shuffle tree combines the lanes.
+// Deterministic, the same in every CTA; the loads are independent, so they
+// are in flight together.  Reads bypass L1 (written by other CTAs).
+__device__ __forceinline__ double warp_sum_strided(const double* base, unsigned nb, long stride) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (unsigned k = lane; k < nb; k += 32) s += __ldcg(base + (long)k * stride);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Dot product of a and b over rows [r0, r1) by one warp: lane j takes rows
+// r0 + j + 32 t in order, four rows per iteration with their loads issued
+// together, then a fixed xor-shuffle tree.  Deterministic.
+__device__ __forceinline__ double warp_dot(const double* __restrict__ a, const double* __restrict__ b, long r0,
+                                           long r1) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    long row = r0 + lane;
+    for (; row + 96 < r1; row += 128) {
+        const double a0 = a[row], a1 = a[row + 32], a2 = a[row + 64], a3 = a[row + 96];
+        const double b0 = b[row], b1 = b[row + 32], b2 = b[row + 64], b3 = b[row + 96];
+        s += a0 * b0;
+        s += a1 * b1;
+        s += a2 * b2;
+        s += a3 * b3;
+    }
+    for (; row < r1; row += 32) s += a[row] * b[row];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+}  // namespace pr

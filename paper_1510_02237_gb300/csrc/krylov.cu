@@ -9,6 +9,7 @@
 // order, so results are bitwise reproducible run to run and independent of
 // what else runs on the GPU (no atomics in any reduction).
 #include "common.cuh"
+#include "grid_barrier.cuh"
 
 namespace pr {
 namespace {
@@ -263,9 +264,111 @@ __global__ void k_fill_int(int* p, int v, int n) {
     if (i < n) p[i] = v;
 }
 
+
+// In-order classical Gram-Schmidt (twice) of each of m columns against the
+// columns kept earlier in this block, the drop rule and the append, all in
+// one cooperative launch.  Every CTA owns a fixed range of rows; dot products
+// are summed per CTA in a fixed order and published; after a barrier every
+// CTA sums the CTA partials in the same order, so all CTAs hold identical
+// coefficients and take identical decisions.  Partial buffers alternate
+// between two halves, so one barrier per reduction suffices.
+constexpr int IB_NT = 512;
+__global__ void __launch_bounds__(IB_NT) k_intra_block(double* __restrict__ wv, double* __restrict__ wz, long d,
+                                                      int m, const double* __restrict__ a2, const int* r_old_dev,
+                                                      int* r_dev, int cap, double eta, double* __restrict__ Q,
+                                                      double* __restrict__ D, int* kept,
+                                                      double* __restrict__ part, int pstride, GridBar* gb) {
+    __shared__ double cs[64];
+    __shared__ double red[IB_NT / 32];
+    __shared__ double s_res2;   // pstride >= 64: slot 63 carries ||v||^2 partials (nn <= 63)
+    const unsigned nb = gridDim.x;
+    const int b = blockIdx.x;
+    const long rpb = (d + nb - 1) / nb;
+    const long r0 = min(d, (long)b * rpb), r1 = min(d, r0 + rpb);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = IB_NT / 32;
+    const int c0 = *r_old_dev;
+    int rl = *r_dev;
+    int buf = 0;
+    double* P0 = part;
+    double* P1 = part + (long)nb * pstride;
+    for (int j = 0; j < m; ++j) {
+        double* v = wv + (long)j * d;
+        double* z = wz + (long)j * d;
+        const int nn = rl - c0;   // columns kept so far in this block
+        // Two passes of classical Gram-Schmidt against those columns.  The
+        // second pass also reduces ||v||^2: with c2 = Q^T v and Q^T Q = I the
+        // residual is ||v - Q c2||^2 = ||v||^2 - ||c2||^2, where ||c2|| is
+        // already at rounding level after the first pass (no cancellation).
+        // Without earlier columns only ||v||^2 is reduced.
+        const int npass = nn > 0 ? 2 : 1;
+        double res2 = 0.0;
+        for (int pass = 0; pass < npass; ++pass) {
+            double* P = buf ? P1 : P0;
+            const bool last = pass == npass - 1;
+            for (int l = wid; l < nn; l += nw) {
+                const double s = warp_dot(Q + (long)(c0 + l) * d, v, r0, r1);
+                if (lane == 0) P[(long)b * pstride + l] = s;
+            }
+            if (last) {
+                double s = 0.0;
+                for (long row = r0 + threadIdx.x; row < r1; row += IB_NT) s += v[row] * v[row];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) red[wid] = s;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    double t = 0.0;
+                    for (int q = 0; q < nw; ++q) t += red[q];
+                    P[(long)b * pstride + 63] = t;
+                }
+            }
+            if (!grid_barrier(gb, nb)) return;
+            for (int l = wid; l < nn; l += nw) {
+                const double s = warp_sum_strided(P + l, nb, pstride);
+                if (lane == 0) cs[l] = s;
+            }
+            if (last && wid == nw - 1) {
+                const double t = warp_sum_strided(P + 63, nb, pstride);
+                if (lane == 0) s_res2 = t;
+            }
+            buf ^= 1;
+            __syncthreads();
+            if (last) {
+                double c2 = 0.0;
+                for (int l = 0; l < nn; ++l) c2 += cs[l] * cs[l];
+                res2 = fmax(s_res2 - c2, 0.0);
+            }
+            for (long row = r0 + threadIdx.x; row < r1 && nn > 0; row += IB_NT) {
+                double av = 0.0, az = 0.0;
+#pragma unroll 4
+                for (int l = 0; l < nn; ++l) {
+                    av += Q[row + (long)(c0 + l) * d] * cs[l];
+                    az += D[row + (long)(c0 + l) * d] * cs[l];
+                }
+                v[row] -= av;
+                z[row] -= az;
+            }
+            __syncthreads();   // the next dot products read these rows with another thread mapping
+        }
+        const double res = sqrt(res2), an = sqrt(a2[j]);
+        const bool keep = (res > eta * an) && (an > 0.0) && (rl < cap);
+        if (keep) {
+            const double inv = 1.0 / res;
+            for (long row = r0 + threadIdx.x; row < r1; row += IB_NT) {
+                Q[row + (long)rl * d] = v[row] * inv;
+                D[row + (long)rl * d] = z[row] * inv;
+            }
+            ++rl;
+        }
+        __syncthreads();       // the appended column is read by the next column's dot products
+        if (b == 0 && threadIdx.x == 0) kept[j] = keep ? 1 : 0;
+    }
+    if (b == 0 && threadIdx.x == 0) *r_dev = rl;
+}
+
 }  // namespace
 
-constexpr int TN_RPC = 2048;  // rows per chunk, gemm_tn
+constexpr int TN_RPC = 512;   // rows per chunk, gemm_tn
 constexpr int GV_RPC = 1024;  // rows per chunk, gemv_tn
 constexpr int NRM_RPC = 4096; // rows per chunk, column norms
 
@@ -276,6 +379,7 @@ long tswork_elems(long nrows, int ccap, int mmax) {
     long b = (long)cdiv(nrows, GV_RPC) * ccap;
     long c = (long)cdiv(nrows, NRM_RPC) * (mmax > 1 ? mmax : 1);
     long d = (long)cdiv(nrows, 256);
+    d = d > 2L * 512 * 64 ? d : 2L * 512 * 64;   // intra-block partials: 2 halves x CTAs x 64
     long m = a > b ? a : b;
     m = m > c ? m : c;
     return m > d ? m : d;
@@ -392,6 +496,38 @@ cudaError_t sub(const double* a, const double* b, double* out, long n, cudaStrea
     k_sub<<<nb, 256, 0, s>>>(a, b, out, n);
     count_launches(1);
     return cudaGetLastError();
+}
+
+int intra_block_grid() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!cached[dev]) {
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_intra_block, IB_NT, 0);
+        cached[dev] = sms * (per < 1 ? 0 : 1);
+    }
+    return cached[dev];
+}
+
+cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2, const int* r_old_dev,
+                        int* r_dev, int cap, double eta, double* Q, double* D, int* kept, const TsWork& w,
+                        GridBar* gb, cudaStream_t s) {
+    if (m < 1 || m > 64) return cudaErrorInvalidValue;
+    int nb = intra_block_grid();
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    int pstride = 64;
+    if ((long)2 * nb * pstride > w.elems) return cudaErrorInvalidValue;
+    // arrival counter to zero; generation and the sticky error word are kept
+    cudaError_t e = cudaMemsetAsync(&gb->count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    double* part = w.partial;
+    void* args[] = {&wv, &wz, &d, &m, (void*)&a2, (void*)&r_old_dev, &r_dev, &cap, &eta, &Q, &D, &kept, &part,
+                    &pstride, &gb};
+    e = cudaLaunchCooperativeKernel((const void*)k_intra_block, dim3(nb), dim3(IB_NT), args, 0, s);
+    count_launches(1);
+    return e;
 }
 
 cudaError_t fill_int(int* p, int v, int n, cudaStream_t s) {

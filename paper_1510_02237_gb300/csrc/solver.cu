@@ -42,6 +42,8 @@ struct pr_solver {
     cudaStream_t stream = nullptr;
     FineCoef<double> fc64{};
     FineCoef<float> fc32{};
+    FineCoefK fck{};
+    double* fb2 = nullptr;
     CoarseCoef cc{};
     double *q = nullptr, *qt = nullptr, *gv = nullptr, *kold = nullptr;
     double *Q = nullptr, *D = nullptr, *wv = nullptr, *wz = nullptr;
@@ -49,7 +51,9 @@ struct pr_solver {
     float *f32a = nullptr, *f32b = nullptr;
     double *C = nullptr, *cvec = nullptr, *partial = nullptr;
     double *anorm2 = nullptr, *res2 = nullptr, *rhist = nullptr, *nres2 = nullptr;
+    double *gbuf = nullptr, *resp = nullptr;
     int *r = nullptr, *r_old = nullptr, *kept = nullptr, *ranks = nullptr, *zero = nullptr;
+    GridBar* gbar = nullptr;
     long partial_elems = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     TimingRing tr;
@@ -108,8 +112,9 @@ static Sizes compute_sizes(int nx, int ny, int N, int K_max, const pr_options& o
     if (o.fine_prec == PR_FP32)
         b += sizeof(float) * (size_t)N * s.d * 2;
     else
-        b += dd * (size_t)N * s.d * 2;         // fine ping-pong
-    b += dd * (size_t)s.d;                     // gtmp
+        b += dd * (size_t)N * s.d * 3;         // fine stage buffers
+    b += dd * (size_t)s.d * 3;                 // gtmp, chain coarse ping-pong
+    b += dd * (size_t)chain_resp_elems(N);
     b += dd * ((size_t)s.cap * N + s.cap);     // C, cvec
     b += dd * (size_t)s.partial;
     b += dd * (size_t)(N + (N + 1) + PR_MAX_ITERS + 1);
@@ -138,6 +143,22 @@ static pr_status fine_apply(pr_solver* h, const double* in, double* out, int n) 
             float* t = a; a = b; b = t;
         }
         CKC((launch_fine_step<float, float, double>(a, d, out, d, n, h->nx, h->ny, hv, h->fc32, s)));
+        return PR_OK;
+    }
+    if (h->fb2) {
+        FineSweepArgs a{};
+        a.in = in;
+        a.out = out;
+        a.w1 = h->fb0;
+        a.w2 = h->fb1;
+        a.w3 = h->fb2;
+        a.n = n;
+        a.nx = h->nx;
+        a.ny = h->ny;
+        a.nsteps = nf;
+        a.c = h->fck;
+        a.gb = h->gbar;
+        CKC(fine_sweep_coop(a, hv, s));
         return PR_OK;
     }
     if (nf == 1) {
@@ -180,7 +201,8 @@ static pr_status coarse_apply(pr_solver* h, const double* in, double* out, int n
 // Gram-Schmidt against the basis present at entry, then two passes against
 // the columns kept earlier in this block, then the drop rule.  The D-images
 // Z = FV - GV receive exactly the same coefficients, so D = F(Q) - G(Q).
-static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, const double* GV, int m) {
+template <typename Mark>
+static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, const double* GV, int m, Mark mark) {
     const long d = h->d;
     const int cap = h->cap;
     cudaStream_t s = h->stream;
@@ -188,30 +210,53 @@ static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, c
     CKC(cudaMemcpyAsync(h->wv, V, sizeof(double) * m * d, cudaMemcpyDeviceToDevice, s));
     CKC(sub(FV, GV, h->wz, (long)m * d, s));
     CKC(colnorm2(h->wv, d, m, d, h->anorm2, w, s));
-    CKC(cudaMemcpyAsync(h->r_old, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
-    for (int pass = 0; pass < 2; ++pass) {
-        CKC(gemm_tn(h->Q, d, nullptr, h->r_old, cap, h->wv, d, m, d, h->C, cap, w, s));
-        CKC(gemm_nn(h->Q, d, nullptr, h->r_old, cap, h->C, cap, h->wv, d, h->wv, d, m, d, -1.0, s));
-        CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->C, cap, h->wz, d, h->wz, d, m, d, -1.0, s));
-    }
-    for (int j = 0; j < m; ++j) {
-        double* v = h->wv + (long)j * d;
-        double* z = h->wz + (long)j * d;
-        if (j > 0) {
-            for (int pass = 0; pass < 2; ++pass) {
-                CKC(gemm_tn(h->Q, d, h->r_old, h->r, cap, v, d, 1, d, h->cvec, cap, w, s));
-                CKC(gemm_nn(h->Q, d, h->r_old, h->r, cap, h->cvec, cap, v, d, v, d, 1, d, -1.0, s));
-                CKC(gemm_nn(h->D, d, h->r_old, h->r, cap, h->cvec, cap, z, d, z, d, 1, d, -1.0, s));
-            }
+    for (int j0 = 0; j0 < m; j0 += 64) {
+        const int mm = m - j0 < 64 ? m - j0 : 64;
+        double* v = h->wv + (long)j0 * d;
+        double* z = h->wz + (long)j0 * d;
+        CKC(cudaMemcpyAsync(h->r_old, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
+        for (int pass = 0; pass < 2; ++pass) {
+            CKC(gemm_tn(h->Q, d, nullptr, h->r_old, cap, v, d, mm, d, h->C, cap, w, s));
+            CKC(gemm_nn(h->Q, d, nullptr, h->r_old, cap, h->C, cap, v, d, v, d, mm, d, -1.0, s));
+            CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->C, cap, z, d, z, d, mm, d, -1.0, s));
         }
-        CKC(colnorm2(v, d, 1, d, h->nres2, w, s));
-        CKC(krylov_append(v, z, h->nres2, h->anorm2 + j, h->opt.drop_tol, cap, h->r, h->Q, h->D, d, d,
-                          h->kept + j, s));
+        if (j0 == 0) CKC(mark());
+        CKC(intra_block(v, z, d, mm, h->anorm2 + j0, h->r_old, h->r, cap, h->opt.drop_tol, h->Q, h->D,
+                        h->kept + j0, w, h->gbar, s));
     }
     return PR_OK;
 }
 
+static cudaError_t no_mark() { return cudaSuccess; }
+
 // ------------------------------------------------------------------ the solve
+
+static ChainArgs chain_args(pr_solver* h, int i_begin, int i_end, const double* qt, const double* kold,
+                            const int* r_dev, double* res2) {
+    ChainArgs a{};
+    a.q = h->q;
+    a.qt = qt;
+    a.kold = kold;
+    a.Q = h->Q;
+    a.D = h->D;
+    a.r_dev = r_dev;
+    a.ccap = h->cap;
+    a.i_begin = i_begin;
+    a.i_end = i_end;
+    a.d = h->d;
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.cc = h->cc;
+    a.n_g = h->n_g;
+    a.H = coarse_halo(h->cc);
+    a.gbuf = h->gbuf;
+    a.cvec = h->cvec;
+    a.part = h->partial;
+    a.resp = h->resp;
+    a.res2 = res2;
+    a.gb = h->gbar;
+    return a;
+}
 
 static pr_status solve_impl(pr_solver* h, int K, pr_report* rep) {
     const long d = h->d;
@@ -230,7 +275,7 @@ static pr_status solve_impl(pr_solver* h, int K, pr_report* rep) {
     CKC(mark());
 
     // initialisation: q_{i+1}^0 = G(q_i^0), serially (q[0] already holds u0)
-    for (int i = 0; i < N; ++i) CKS(coarse_apply(h, h->q + (long)i * d, h->q + (long)(i + 1) * d, 1));
+    CKC(chain_coop(chain_args(h, 0, N, nullptr, nullptr, nullptr, nullptr), s));
     CKC(fill_int(h->r, 0, 1, s));
     CKC(mark());
 
@@ -247,7 +292,8 @@ static pr_status solve_impl(pr_solver* h, int K, pr_report* rep) {
         CKS(coarse_apply(h, qa, h->gv + (long)a * d, M));
         CKC(mark());
         if (kse) {
-            CKS(krylov_block(h, qa, h->qt + (long)a * d, h->gv + (long)a * d, M));
+            CKS(krylov_block(h, qa, h->qt + (long)a * d, h->gv + (long)a * d, M, mark));
+            CKC(mark());
             // K(q_i^k) = G(q_i^k) + D Q^T q_i^k for i = k+1..N-1 with the updated S^k
             if (M > 1) {
                 CKC(gemm_tn(h->Q, d, nullptr, h->r, cap, h->q + (long)(a + 1) * d, d, M - 1, d, h->C, cap, w, s));
@@ -255,19 +301,15 @@ static pr_status solve_impl(pr_solver* h, int K, pr_report* rep) {
                             h->kold + (long)(a + 1) * d, d, M - 1, d, 1.0, s));
             }
             CKC(cudaMemcpyAsync(h->ranks + k, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
+        } else {
+            CKC(mark());
+            CKC(mark());
         }
         CKC(mark());
         // serial correction
         CKC(cudaMemsetAsync(h->res2, 0, sizeof(double) * (N + 1), s));
         CKC(copy_resid(h->qt + (long)a * d, h->q + (long)(a + 1) * d, d, h->res2 + a + 1, w, s));
-        for (int i = a + 1; i < N; ++i) {
-            double* qi = h->q + (long)i * d;
-            if (kse) CKC(gemm_tn(h->Q, d, nullptr, h->r, cap, qi, d, 1, d, h->cvec, cap, w, s));
-            CKS(coarse_apply(h, qi, h->gtmp, 1));
-            CKC(chain_update(h->qt + (long)i * d, h->gtmp, h->D, d, kse ? h->r : h->zero, cap, h->cvec,
-                             kse ? h->kold + (long)i * d : h->gv + (long)i * d, h->q + (long)(i + 1) * d, d,
-                             h->res2 + i + 1, w, s));
-        }
+        CKC(chain_coop(chain_args(h, a + 1, N, h->qt, kse ? h->kold : h->gv, kse ? h->r : nullptr, h->res2), s));
         CKC(max_sqrt(h->res2 + 1, N, h->rhist + k, s));
         CKC(mark());
     }
@@ -280,8 +322,17 @@ static void timing_free(pr_solver* h) {
     h->tr = TimingRing();
 }
 
+// After a synchronisation: PR_ETIMEOUT if a bounded device wait gave up.
+static pr_status check_device_waits(pr_solver* h) {
+    int err = 0;
+    CKC(cudaMemcpy(&err, &h->gbar->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return set_err(h, PR_ETIMEOUT, "a grid barrier wait gave up; results of this handle are invalid");
+    return PR_OK;
+}
+
 static pr_status fill_report(pr_solver* h, int K, pr_report* rep) {
     CKC(cudaStreamSynchronize(h->stream));
+    CKS(check_device_waits(h));
     std::memset(rep, 0, sizeof(*rep));
     rep->K = K;
     if (K > 0) {
@@ -408,6 +459,7 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     const double dx = h->lx / h->nx, dy = h->ly / h->ny;
     h->fc64 = make_fine_coef<double>(U, o.V, c_s, dx, dy, o.nu_f, dt_f);
     h->fc32 = make_fine_coef<float>(U, o.V, c_s, dx, dy, o.nu_f, dt_f);
+    h->fck = make_fine_coef_k(U, o.V, c_s, dx, dy, o.nu_f, dt_f);
     const double tau = dt_g / o.n_sound;
     const double a1 = o.nu_c * dx * dx / tau, a2 = o.nu_c * dy * dy / tau;
     h->cc.U = U;
@@ -445,8 +497,11 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     } else {
         chk(dalloc(&h->fb0, (size_t)N * d));
         chk(dalloc(&h->fb1, (size_t)N * d));
+        chk(dalloc(&h->fb2, (size_t)N * d));
     }
     chk(dalloc(&h->gtmp, (size_t)d));
+    chk(dalloc(&h->gbuf, (size_t)2 * d));
+    chk(dalloc(&h->resp, (size_t)chain_resp_elems(N)));
     chk(dalloc(&h->C, (size_t)h->cap * N));
     chk(dalloc(&h->cvec, (size_t)h->cap));
     chk(dalloc(&h->partial, (size_t)h->partial_elems));
@@ -457,11 +512,13 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     chk(cudaMalloc((void**)&h->r, sizeof(int) * 3));
     chk(cudaMalloc((void**)&h->kept, sizeof(int) * N));
     chk(cudaMalloc((void**)&h->ranks, sizeof(int) * PR_MAX_ITERS));
+    chk(cudaMalloc((void**)&h->gbar, sizeof(GridBar)));
     if (e == cudaSuccess) {
         h->r_old = h->r + 1;
         h->zero = h->r + 2;
         chk(cudaMemset(h->r, 0, sizeof(int) * 3));
         chk(cudaMemset(h->ranks, 0, sizeof(int) * PR_MAX_ITERS));
+        chk(cudaMemset(h->gbar, 0, sizeof(GridBar)));
         chk(cudaMemset(h->rhist, 0, sizeof(double) * PR_MAX_ITERS));
         chk(cudaEventCreate(&h->ev0));
         chk(cudaEventCreate(&h->ev1));
@@ -479,14 +536,16 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
 pr_status parareal_destroy(pr_solver* h) {
     if (!h) return PR_EINVAL;
     if (h->stream || h->q) cudaStreamSynchronize(h->stream);
-    double* ds[] = {h->q, h->qt, h->gv, h->kold, h->Q, h->D, h->wv, h->wz, h->fb0, h->fb1, h->cb0, h->cb1,
-                    h->gtmp, h->C, h->cvec, h->partial, h->anorm2, h->res2, h->rhist, h->nres2};
+    double* ds[] = {h->q, h->qt, h->gv, h->kold, h->Q, h->D, h->wv, h->wz, h->fb0, h->fb1, h->fb2, h->cb0, h->cb1,
+                    h->gtmp, h->C, h->cvec, h->partial, h->anorm2, h->res2, h->rhist, h->nres2,
+                    h->gbuf, h->resp};
     for (double* p : ds) if (p) cudaFree(p);
     if (h->f32a) cudaFree(h->f32a);
     if (h->f32b) cudaFree(h->f32b);
     if (h->r) cudaFree(h->r);
     if (h->kept) cudaFree(h->kept);
     if (h->ranks) cudaFree(h->ranks);
+    if (h->gbar) cudaFree(h->gbar);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     timing_free(h);
@@ -525,6 +584,7 @@ pr_status parareal_solve_host(pr_solver* h, const double* u0_host, int32_t K, do
     CKC(cudaMemcpyAsync(qT_host, h->q + (long)h->N * d, sizeof(double) * d, cudaMemcpyDeviceToHost, h->stream));
     CKC(cudaEventRecord(h->ev1, h->stream));
     CKC(cudaStreamSynchronize(h->stream));
+    CKS(check_device_waits(h));
     if (rep) CKS(fill_report(h, K, rep));
     return PR_OK;
 }
@@ -564,10 +624,11 @@ pr_status krylov_update(pr_solver* h, const double* V_dev, const double* FV_dev,
     if (!V_dev || !FV_dev) return set_err(h, PR_EINVAL, "NULL buffer");
     if (m < 1 || m > h->N) return set_err(h, PR_EINVAL, "m must be in [1, N_slices]");
     CKS(coarse_apply(h, V_dev, h->gv, m));
-    CKS(krylov_block(h, V_dev, FV_dev, h->gv, m));
+    CKS(krylov_block(h, V_dev, FV_dev, h->gv, m, no_mark));
     if (kept_host) {
         CKC(cudaMemcpyAsync(kept_host, h->kept, sizeof(int) * m, cudaMemcpyDeviceToHost, h->stream));
         CKC(cudaStreamSynchronize(h->stream));
+        CKS(check_device_waits(h));
     }
     return PR_OK;
 }
@@ -602,7 +663,7 @@ pr_status parareal_timing_enable(pr_solver* h, int32_t max_solves) {
     timing_free(h);
     if (max_solves == 0) return PR_OK;
     h->tr.max_solves = max_solves;
-    h->tr.per_solve = 2 + 4 * h->K_max;
+    h->tr.per_solve = 2 + 6 * h->K_max;
     h->tr.ev.assign((size_t)max_solves * h->tr.per_solve, nullptr);
     h->tr.K.assign((size_t)max_solves, 0);
     for (auto& e : h->tr.ev) {
@@ -618,6 +679,7 @@ pr_status parareal_timing_enable(pr_solver* h, int32_t max_solves) {
 pr_status parareal_timing_read(pr_solver* h, pr_timing* t, int32_t reset) {
     if (!h || !t) return PR_EINVAL;
     CKC(cudaStreamSynchronize(h->stream));
+    CKS(check_device_waits(h));
     std::memset(t, 0, sizeof(*t));
     const long ncell = (long)h->nx * h->ny;
     for (int sidx = 0; sidx < h->tr.n; ++sidx) {
@@ -628,10 +690,11 @@ pr_status parareal_timing_read(pr_solver* h, pr_timing* t, int32_t reset) {
         t->ms_init += ms;
         t->ms_total += ms;
         for (int k = 0; k < K; ++k) {
-            double* acc[4] = {&t->ms_fine, &t->ms_coarse, &t->ms_krylov, &t->ms_chain};
-            for (int ph = 0; ph < 4; ++ph) {
-                CKC(cudaEventElapsedTime(&ms, ev[1 + 4 * k + ph], ev[2 + 4 * k + ph]));
+            double* acc[6] = {&t->ms_fine, &t->ms_coarse, &t->ms_gs_block, &t->ms_gs_intra, &t->ms_kold, &t->ms_chain};
+            for (int ph = 0; ph < 6; ++ph) {
+                CKC(cudaEventElapsedTime(&ms, ev[1 + 6 * k + ph], ev[2 + 6 * k + ph]));
                 *acc[ph] += ms;
+                if (ph >= 2 && ph <= 4) t->ms_krylov += ms;
                 t->ms_total += ms;
             }
             t->fine_cell_steps += (double)(h->N - k) * h->n_f * ncell;
