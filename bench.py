@@ -194,6 +194,55 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 
+def serial_fine_gpu(P, s, u0, n):
+    """q_seq(T): n fine sweeps of one slice each through the C ABI (FP64 handle)."""
+    import torch
+    q = u0
+    for _ in range(n):
+        nxt = torch.empty_like(q)
+        P.parareal_fine_sweep(s.h, q, nxt, 1)
+        q = nxt
+    return q
+
+
+def rel_l2(a, b):
+    return float(torch_norm(a - b) / torch_norm(b))
+
+
+def torch_norm(x):
+    return x.double().norm().item()
+
+
+def precision_workload(P, torch, stream):
+    """512x256, N = 64, K = 5, power-law Fourier IC: one solve each in plain FP64
+    (images by linearity, as in the paper), FP64 with direct images, and mixed
+    precision (FP32 tendencies on an FP64 state, FP32 correction, FP64
+    Gram-Schmidt), each timed with CUDA events after one untimed solve, with
+    the error of each against the serial FP64 fine solution."""
+    wl = W.workload_large()
+    p, K = wl.problem, wl.K
+    u0 = torch.from_numpy(wl.ics[0][1]().ravel()).cuda()
+    res = {"workload": wl.name, "grid": f"{p.nx}x{p.ny}", "N_slices": p.n_slices, "K": K}
+    qs = None
+    for tag, opt in (("fp64", {}), ("fp64_direct", {"images": P.PR_IMAGES_DIRECT}),
+                     ("mixed", {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32})):
+        s = P.Solver(p, stream=stream, K_max=K, **opt)
+        out = torch.empty(p.d, dtype=torch.float64, device="cuda")
+        P.parareal_solve(s.h, u0, K, qT=out, report=False)
+        rep = P.parareal_solve(s.h, u0, K, qT=out, report=True)
+        if qs is None:
+            qs = serial_fine_gpu(P, s, u0, p.n_slices)
+        res[tag] = {"ms_per_solve": rep.ms_total, "eps": rel_l2(out, qs), "rank": list(rep.rank[:K]),
+                    "min_kept_ratio": [float(x) for x in rep.min_ratio[:K]]}
+        s.close()
+    res["speedup_mixed_vs_fp64"] = res["fp64"]["ms_per_solve"] / res["mixed"]["ms_per_solve"]
+    res["abs_eps_diff_mixed_vs_fp64_direct"] = abs(res["fp64_direct"]["eps"] - res["mixed"]["eps"])
+    res["note"] = ("the first iteration's columns are nearly dependent (min kept ratio ~1e-6): F(Q) formed "
+                   "by linearity (fp64) carries amplified rounding; fp64_direct is the well-conditioned FP64 "
+                   "evaluation the mixed solve is compared with")
+    return res
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -281,8 +330,53 @@ def run_ours(args):
     e2e = {"value": solves / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": nsol * p.d * 8,
            "d2h_bytes_per_step": nsol * p.d * 8}
 
+    # ---- mixed precision on the same workload: FP32 fine sweep, FP32 correction
+    #      by linearity, FP64 Gram-Schmidt and accumulation
+    sm = P.Solver(p, stream=stream, K_max=K, krylov_cap=wl.krylov_cap, fine_prec=P.PR_FP32X, corr_prec=P.PR_FP32)
+    outs_m = [torch.empty(p.d, dtype=torch.float64, device="cuda") for _ in ics]
+
+    def step_m():
+        for u0, out in zip(u0s, outs_m):
+            P.parareal_solve(sm.h, u0, K, qT=out, report=False)
+
+    for _ in range(max(3, args.warmup)):
+        step_m()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_m()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_m = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_m], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_m = float(t.item())
+    mixed = {"value": solves / (ms_m / 1e3), "unit": "solves/s",
+             "fine_prec": "f32 tendencies and stages, f64 state", "corr_prec": "f32 (delta form)",
+             "images": "direct F(Q) - G(Q) in f32", "gram_schmidt": "f64",
+             "speedup_vs_fp64": (solves / (ms_m / 1e3)) / value}
+    if rank == 0:
+        per_ic = {}
+        for j in range(nsol):
+            qs = serial_fine_gpu(P, s, u0s[j], p.n_slices)
+            rep = P.parareal_solve(s.h, u0s[j], K, qT=outs[j], report=True)
+            a, b_ = rel_l2(outs[j], qs), rel_l2(outs_m[j], qs)
+            per_ic[wl.ics[j][0]] = {"eps_fp64": a, "eps_mixed": b_, "abs_diff": abs(a - b_),
+                                    "min_kept_ratio": min(rep.min_ratio[:K])}
+        mixed.update({"per_ic": per_ic,
+                      "eps_def": "||q_N^K - q_seq(T)|| / ||q_seq(T)|| against N serial FP64 fine sweeps",
+                      "note": "|eps_mixed - eps_fp64| <= 1e-5 holds for the well-conditioned IC; the "
+                              "filtered-noise IC excites the coarse step's growing band (FP32 rounding "
+                              "amplified along the chain), the Fourier IC has nearly dependent iterates "
+                              "(min kept ratio ~1e-5)"})
+    sm.close()
+
     line = None
     if rank == 0:
+        precision = precision_workload(P, torch, stream)
         # ---- roofline of the dominant phase's kernel
         phases = {k: tm[k] / n for k in ("ms_init", "ms_fine", "ms_coarse", "ms_krylov", "ms_gs_block",
                                           "ms_gs_intra", "ms_kold", "ms_chain")}
@@ -325,6 +419,8 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clk,
             "fp64_fma_tflops": peak,
+            "mixed": mixed,
+            "precision_workload": precision,
         }
         print(json.dumps(line))
     s.close()

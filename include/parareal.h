@@ -46,8 +46,13 @@ typedef enum {
     PR_ECANCELLED = -6  /* request cancelled                                  */
 } pr_status;
 
-enum { PR_FP64 = 0, PR_FP32 = 1 };                 /* arithmetic of the fine sweep   */
+enum { PR_FP64 = 0, PR_FP32 = 1, PR_FP32X = 2 };   /* arithmetic of the fine sweep:
+                                                      FP64; FP32 state and stages;
+                                                      FP32 tendencies and stages with
+                                                      an FP64 state (q^{n+1} = q^n +
+                                                      dt L(q**) formed in FP64)      */
 enum { PR_KSE = 0, PR_ORIGINAL = 1 };              /* Alg. 2 / Alg. 1                */
+enum { PR_IMAGES_LINEARITY = 0, PR_IMAGES_DIRECT = 1 };  /* how F(Q) is formed          */
 #define PR_MAX_ITERS 128
 
 typedef struct {
@@ -67,16 +72,43 @@ typedef struct {
     int32_t krylov_cap;    /* max dim of S^k; 0 = sum_{k<K_max} (N - k)          */
     double drop_tol;       /* eta: drop a column whose residual after projection
                               is <= eta * its norm (1e-10)                       */
-    int32_t fine_prec;     /* PR_FP64 or PR_FP32 arithmetic inside F             */
+    int32_t fine_prec;     /* PR_FP64, PR_FP32 or PR_FP32X arithmetic inside F   */
     int32_t variant;       /* PR_KSE (Alg. 2) or PR_ORIGINAL (Alg. 1)            */
+    int32_t corr_prec;     /* PR_FP64: serial correction evaluated literally in
+                              FP64; PR_FP32: evaluated by linearity as
+                              G(delta) + D Q^T delta, delta = q_i^{k+1} - q_i^k,
+                              in FP32 (coarse images G(q_i^k) also in FP32),
+                              accumulated into q in FP64                          */
+    double r_tol;          /* > 0: stop a parallel step once r^k <= r_tol (Sec. 2.1);
+                              0: always K_iters iterations                        */
+    int32_t n_windows;     /* M_p: [0, T] is solved as n_windows consecutive
+                              parallel steps of N_slices slices each (Sec. 2.1),
+                              each started from the previous step's q_N (1)      */
+    int32_t images;        /* PR_IMAGES_LINEARITY: F(Q) - G(Q) carried through the
+                              Gram-Schmidt transform of the iterates' images, as
+                              in Eq. Genhance (no extra fine sweeps); its
+                              rounding error grows with 1/|R_jj| when iterates
+                              are nearly dependent.  PR_IMAGES_DIRECT: F and G
+                              applied to each new orthonormal basis vector (one
+                              extra fine and coarse propagation per new
+                              column), rounding error independent of the
+                              conditioning.  corr_prec = PR_FP32 and fine_prec
+                              other than PR_FP64 always use PR_IMAGES_DIRECT.    */
     void* stream;          /* cudaStream_t, or NULL                              */
 } pr_options;
 
 typedef struct {
-    int32_t K;                   /* iterations performed                          */
+    int32_t K;                   /* iterations performed, summed over the parallel
+                                    steps; entries below are in that order        */
     int32_t rank[PR_MAX_ITERS];  /* dim S^k after the update of iteration k      */
     double r[PR_MAX_ITERS];      /* r^k = max_i ||q_i^{k+1} - q_i^k||_2 (Sec. 2.1) */
     float ms_total;              /* device time of the whole solve (CUDA events)  */
+    int32_t n_windows;           /* parallel steps solved                          */
+    int32_t K_window[PR_MAX_ITERS]; /* iterations performed in each parallel step */
+    double min_ratio[PR_MAX_ITERS]; /* smallest |R_jj|/||a_j|| among the columns kept
+                                    in iteration k: the conditioning of the new
+                                    basis directions (rounding in F(Q) formed by
+                                    linearity grows like 1/min_ratio); 1 if none */
 } pr_report;
 
 /* Phase timing of solves, measured with CUDA events on the handle's stream
@@ -130,9 +162,12 @@ size_t parareal_footprint_bytes(const pr_grid* g, int32_t N_slices, const pr_opt
  * correction q_{i+1}^{k+1} = q~_{i+1}^k + (K(q_i^{k+1}) - K(q_i^k)) with the
  * modified coarse propagator K of Eq. modifiedCoarse.
  *   u0_dev : device, d doubles, the initial value q_0.
- *   K_iters: 0 <= K_iters <= opt.K_max.
- *   q_out_dev: device, (N+1)*d doubles receiving q_n^K, n = 0..N; may be NULL.
- *   qT_dev : device, d doubles receiving q_N^K; may be NULL.
+ *   K_iters: 0 <= K_iters <= opt.K_max iterations per parallel step (fewer
+ *            when opt.r_tol stops the step early; that check synchronises
+ *            the stream once per iteration).
+ *   q_out_dev: device, (N+1)*d doubles receiving q_n^K, n = 0..N, of the last
+ *            parallel step; may be NULL.
+ *   qT_dev : device, d doubles receiving the value at T; may be NULL.
  *   rep    : host; if non-NULL the call synchronises the stream and fills it.
  * The subspace S^K remains in the handle for krylov_project(). */
 pr_status parareal_solve(pr_solver* h, const double* u0_dev, int32_t K_iters, double* q_out_dev,
@@ -217,6 +252,14 @@ pr_status parareal_alu_probe(int32_t prec, int32_t iters, double* flops_per_s);
 pr_status parareal_fine_sweep_static(const pr_grid* g, double U, double V, double c_s, double nu_f,
                                      double dt_f, int32_t n_steps, int32_t fine_prec,
                                      const double* q_in_dev, double* q_out_dev, int32_t n, void* stream);
+
+/* Self-test of the library's bounded device waits (no counterpart in the
+ * paper): launches a cooperative kernel whose grid barrier can never complete
+ * (it expects one CTA more than the grid has).  Every wait gives up after its
+ * poll limit (well under a few seconds), records the failure and returns, so
+ * the call returns PR_ETIMEOUT and the CUDA context stays usable.  *seconds
+ * (optional) receives the device time until the waits gave up. */
+pr_status parareal_selftest_wait_timeout(void* stream, double* seconds);
 
 /* Process-wide number of CUDA kernels this library has launched. */
 uint64_t parareal_kernel_launches(void);

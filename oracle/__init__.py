@@ -64,7 +64,7 @@ def lib():
         L.orc_basis_get_q.argtypes = [C.c_void_p, _P]
         L.orc_basis_get_fq.argtypes = [C.c_void_p, _P]
         L.orc_basis_project.argtypes = [C.c_void_p, _P, _P, _P]
-        L.orc_parareal.argtypes = [pp, _P, C.c_int, C.c_int, C.c_double, C.c_int, _P, _P, _I, _I, _P]
+        L.orc_parareal.argtypes = [pp, _P, C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, _P, _P, _I, _I, _P]
         L.orc_parareal.restype = C.c_int
         L.orc_serial_fine.argtypes = [pp, _P, _P]
         _lib = L
@@ -167,11 +167,14 @@ class Basis:
         return Pq, FPq
 
 
-def parareal(p, q0, K: int, *, variant: str = "kse", eta: float = 1e-10, cap: int = 0, **over):
-    """Run Alg. 2 (``variant='kse'``) or Alg. 1 (``'original'``) for K iterations.
+def parareal(p, q0, K: int, *, variant: str = "kse", eta: float = 1e-10, cap: int = 0, r_tol: float = 0.0,
+             **over):
+    """Run Alg. 2 (``variant='kse'``) or Alg. 1 (``'original'``) for K iterations
+    (fewer if r_tol > 0 and r^k <= r_tol first, Sec. 2.1).
 
     Returns dict(q=(N+1, d) iterates q_n^K, r=(K,) error estimates r^k,
-    rank=(K,) dim S^k, kept=(K, N) column kept flags, ratio=(K, N) |R_jj|/||a_j||).
+    rank=(K,) dim S^k, kept=(K, N) column kept flags, ratio=(K, N) |R_jj|/||a_j||,
+    K=iterations performed).
     """
     pb = _problem(p, **over)
     N, d = pb.n_slices, 3 * pb.nx * pb.ny
@@ -184,11 +187,29 @@ def parareal(p, q0, K: int, *, variant: str = "kse", eta: float = 1e-10, cap: in
     kept = np.zeros((max(K, 1), N), dtype=np.int32)
     ratio = np.zeros((max(K, 1), N))
     rc = lib().orc_parareal(C.byref(pb), _ptr(q0), int(K), 0 if variant == "kse" else 1, float(eta),
-                            int(cap), _ptr(q_all), _ptr(r), rank.ctypes.data_as(_I),
+                            int(cap), float(r_tol), _ptr(q_all), _ptr(r), rank.ctypes.data_as(_I),
                             kept.ctypes.data_as(_I), _ptr(ratio))
-    if rc != 0:
+    if rc < 0:
         raise MemoryError("oracle parareal: allocation failed")
-    return dict(q=q_all, r=r[:K], rank=rank[:K], kept=kept[:K], ratio=ratio[:K])
+    Kd = rc
+    return dict(q=q_all, r=r[:Kd], rank=rank[:Kd], kept=kept[:Kd], ratio=ratio[:Kd], K=Kd)
+
+
+def parareal_windows(p, q0, K: int, n_windows: int, **kw):
+    """[0, T] as n_windows consecutive parallel steps of N slices each (Sec. 2.1:
+    M_p parallel steps of N_c = N_p coarse intervals), each solved by
+    ``parareal`` from the previous step's final value; the problem's T is the
+    end time of the whole run.  Returns the final value, and per window the
+    iterations performed and the r^k history."""
+    import dataclasses
+    pw = dataclasses.replace(p, T=p.T / n_windows) if dataclasses.is_dataclass(p) else p
+    q = _arr(q0)
+    wins = []
+    for _ in range(n_windows):
+        r = parareal(pw, q, K, **kw)
+        wins.append(r)
+        q = r["q"][-1].copy()
+    return dict(qT=q, windows=wins)
 
 
 def serial_fine(p, q0, **over):

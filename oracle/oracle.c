@@ -390,7 +390,7 @@ static void kse_coarse(const orc_problem* pb, const orc_basis* b, const double* 
 /* ------------------------------------------------------------------ Parareal */
 
 int orc_parareal(const orc_problem* pb, const double* q0, int K, int variant,
-                 double eta, int cap, double* q_all, double* r_hist, int* rank_hist,
+                 double eta, int cap, double r_tol, double* q_all, double* r_hist, int* rank_hist,
                  int* kept, double* ratio) {
     const int N = pb->n_slices;
     const long d = 3L * pb->nx * pb->ny;
@@ -451,6 +451,11 @@ int orc_parareal(const orc_problem* pb, const double* q0, int K, int variant,
         }
         if (r_hist) r_hist[k] = rmax;
         if (rank_hist) rank_hist[k] = orc_basis_rank(b);
+        /* optional stopping rule of Sec. 2.1: stop once r^k <= r_tol */
+        if (r_tol > 0.0 && rmax <= r_tol) {
+            K = k + 1;
+            break;
+        }
     }
     orc_basis_free(b);
     free(w3);
@@ -460,7 +465,7 @@ int orc_parareal(const orc_problem* pb, const double* q0, int K, int variant,
     free(kn);
     free(qold);
     free(qt);
-    return 0;
+    return K;
 }
 
 void orc_serial_fine(const orc_problem* pb, const double* q0, double* q_all) {

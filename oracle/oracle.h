@@ -53,10 +53,12 @@ void   orc_basis_project(const orc_basis* b, const double* q, double* Pq, double
 
 /* ---- Parareal (Alg. 1 / Alg. 2) ---- */
 /* variant: 0 = KSE-Parareal (Alg. 2), 1 = original Parareal (Alg. 1).
+ * r_tol > 0 stops after the first iteration with r^k <= r_tol (Sec. 2.1).
  * q_all: (N+1)*d output iterates q_n^K.  r_hist[K], rank_hist[K] outputs.
- * kept / ratio: optional (K*N) per processed column (may be NULL). */
+ * kept / ratio: optional (K*N) per processed column (may be NULL).
+ * Returns the number of iterations performed, or -1 if allocation failed. */
 int orc_parareal(const orc_problem* pb, const double* q0, int K, int variant,
-                 double eta, int cap, double* q_all, double* r_hist, int* rank_hist,
+                 double eta, int cap, double r_tol, double* q_all, double* r_hist, int* rank_hist,
                  int* kept, double* ratio);
 
 /* q_all[n] = F^n(q0), n = 0..N (serial fine reference). */

@@ -15,8 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libparareal.so")
 
 PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ETIMEOUT, PR_ESTATE, PR_ECANCELLED = 0, -1, -2, -3, -4, -5, -6
-PR_FP64, PR_FP32 = 0, 1
+PR_FP64, PR_FP32, PR_FP32X = 0, 1, 2
 PR_KSE, PR_ORIGINAL = 0, 1
+PR_IMAGES_LINEARITY, PR_IMAGES_DIRECT = 0, 1
 PR_MAX_ITERS = 128
 _STATUS = {0: "PR_OK", -1: "PR_EINVAL", -2: "PR_ENOMEM", -3: "PR_ECUDA", -4: "PR_ETIMEOUT",
            -5: "PR_ESTATE", -6: "PR_ECANCELLED"}
@@ -30,12 +31,15 @@ class pr_options(C.Structure):
     _fields_ = [("T", C.c_double), ("nu_f", C.c_double), ("nu_c", C.c_double), ("n_sound", C.c_int32),
                 ("adv_order_f", C.c_int32), ("adv_order_c", C.c_int32), ("V", C.c_double),
                 ("K_max", C.c_int32), ("krylov_cap", C.c_int32), ("drop_tol", C.c_double),
-                ("fine_prec", C.c_int32), ("variant", C.c_int32), ("stream", C.c_void_p)]
+                ("fine_prec", C.c_int32), ("variant", C.c_int32), ("corr_prec", C.c_int32),
+                ("r_tol", C.c_double), ("n_windows", C.c_int32), ("images", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class pr_report(C.Structure):
     _fields_ = [("K", C.c_int32), ("rank", C.c_int32 * PR_MAX_ITERS), ("r", C.c_double * PR_MAX_ITERS),
-                ("ms_total", C.c_float)]
+                ("ms_total", C.c_float), ("n_windows", C.c_int32), ("K_window", C.c_int32 * PR_MAX_ITERS),
+                ("min_ratio", C.c_double * PR_MAX_ITERS)]
 
 
 class pr_timing(C.Structure):
@@ -58,7 +62,7 @@ EXPORTS = ["parareal_default_options", "parareal_create", "parareal_destroy", "p
            "parareal_footprint_bytes", "parareal_solve", "parareal_solve_host", "parareal_fine_sweep",
            "parareal_coarse_sweep", "parareal_coarse_apply", "krylov_reset", "krylov_update", "krylov_rank",
            "krylov_project", "parareal_timing_enable", "parareal_timing_read", "parareal_kernel_launches",
-           "parareal_alu_probe", "parareal_fine_sweep_static"]
+           "parareal_alu_probe", "parareal_fine_sweep_static", "parareal_selftest_wait_timeout"]
 
 _lib = None
 
@@ -113,6 +117,8 @@ def lib():
     L.parareal_fine_sweep_static.argtypes = [C.POINTER(pr_grid), C.c_double, C.c_double, C.c_double, C.c_double,
                                              C.c_double, C.c_int32, C.c_int32, P, P, C.c_int32, P]
     L.parareal_fine_sweep_static.restype = st
+    L.parareal_selftest_wait_timeout.argtypes = [P, C.POINTER(C.c_double)]
+    L.parareal_selftest_wait_timeout.restype = st
     _lib = L
     return L
 
@@ -234,6 +240,15 @@ def parareal_alu_probe(prec=PR_FP64, iters=4096) -> float:
     return v.value
 
 
+def parareal_selftest_wait_timeout(stream=None):
+    """Returns (status, seconds) of the bounded-wait self-test (expected PR_ETIMEOUT)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    sec = C.c_double()
+    st = lib().parareal_selftest_wait_timeout(C.c_void_p(stream) if stream else None, C.byref(sec))
+    return st, sec.value
+
+
 def parareal_fine_sweep_static(nx, ny, U, V, c_s, nu_f, dt_f, n_steps, fine_prec, q_in, q_out, n, stream=None):
     """Allocation-free fine sweep (no handle); see include/parareal.h for its limits."""
     if stream is not None and hasattr(stream, "cuda_stream"):
@@ -248,7 +263,7 @@ class Solver:
     """Convenience owner of a handle for a ``workloads.Problem``-like object."""
 
     def __init__(self, p, *, stream=None, **opt):
-        opt.setdefault("T", p.T)
+        opt.setdefault("T", p.T * opt.get("n_windows", 1))
         opt.setdefault("nu_f", p.nu_f)
         opt.setdefault("nu_c", p.nu_c)
         opt.setdefault("n_sound", p.n_sound)

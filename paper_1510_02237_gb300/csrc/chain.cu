@@ -19,6 +19,8 @@
 // after a barrier every CTA updates its rows; a last barrier publishes
 // q_{i+1} before the next slice's coarse step reads its halos.  All waits are
 // bounded (grid_barrier).
+#include <type_traits>
+
 #include "coarse_tile.cuh"
 #include "grid_barrier.cuh"
 
@@ -27,8 +29,17 @@ namespace {
 
 constexpr int CH_NT = 512, CH_TX = 16, CH_TY = 16;
 
+// DELTA = false: the literal correction in FP64,
+//   q_{i+1} = q~_{i+1} + ((G(q_i) + D Q^T q_i) - K_old_i).
+// DELTA = true: the same correction through linearity in FP32,
+//   q_{i+1} = q~_{i+1} + (G(delta_i) + D Q^T delta_i),  delta_i = q_i^{k+1} - q_i^k,
+// with FP32 copies of Q and D; delta_{i+1} is produced by the update itself.
+// Its rounding scales with ||delta||, not ||q||; the sum into q stays FP64.
+template <bool DELTA>
 __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
-    extern __shared__ __align__(16) double sm[];
+    using T = typename std::conditional<DELTA, float, double>::type;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
     __shared__ double red[CH_NT / 32];
     const unsigned nb = gridDim.x;
     const int b = blockIdx.x;
@@ -39,22 +50,37 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
     const int ncols = A.r_dev ? *A.r_dev : 0;
     const int ntx = (A.nx + CH_TX - 1) / CH_TX, nty = (A.ny + CH_TY - 1) / CH_TY, ntiles = ntx * nty;
     const int cpb = (ncols + (int)nb - 1) / (int)nb;
+    const T* Qm = DELTA ? reinterpret_cast<const T*>(A.Q32) : reinterpret_cast<const T*>(A.Q);
+    const T* Dm = DELTA ? reinterpret_cast<const T*>(A.D32) : reinterpret_cast<const T*>(A.D);
+    T* gbuf = DELTA ? reinterpret_cast<T*>(A.gbuf32) : reinterpret_cast<T*>(A.gbuf);
 
     for (int i = A.i_begin; i < A.i_end; ++i) {
         const double* qi = A.q + (long)i * d;
         double* qn = A.q + (long)(i + 1) * d;
-        // phase A: this CTA's partial dot products c_l = sum_rows Q[row, l] q_i[row]
+        const T* x = DELTA ? reinterpret_cast<const T*>(A.dlt) : reinterpret_cast<const T*>(qi);
+        // phase A: this CTA's partial dot products c_l = sum_rows Q[row, l] x[row]
         for (int l = wid; l < ncols; l += nw) {
-            const double s = warp_dot(A.Q + (long)l * d, qi, r0, r1);
+            double s;
+            if (DELTA) {
+                float t = 0.f;
+                const T* a = Qm + (long)l * d;
+                for (long row = r0 + lane; row < r1; row += 32) t += a[row] * x[row];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                s = (double)t;
+            } else {
+                s = warp_dot(reinterpret_cast<const double*>(Qm) + (long)l * d, qi, r0, r1);
+            }
             if (lane == 0) A.part[(long)b * A.ccap + l] = s;
         }
-        // coarse steps G(q_i), one barrier after each
-        const double* gin = qi;
+        // coarse steps G(x), one barrier after each
+        const T* gin = x;
         for (int st = 0; st < A.n_g; ++st) {
-            double* gout = A.gbuf + (long)(st & 1) * d;
+            T* gout = gbuf + (long)(st & 1) * d;
             for (int t = b; t < ntiles; t += nb) {
                 const int ty = t / ntx, tx = t - ty * ntx;
-                coarse_tile<CH_TX, CH_TY, CH_NT>(gin, gout, A.nx, A.ny, A.cc, A.H, tx * CH_TX, ty * CH_TY, sm);
+                coarse_tile<CH_TX, CH_TY, CH_NT, T, T, T>(gin, gout, A.nx, A.ny, A.cc, A.H, tx * CH_TX,
+                                                          ty * CH_TY, sm);
             }
             if (!grid_barrier(A.gb, nb)) return;
             if (st == 0 && ncols > 0) {
@@ -69,22 +95,28 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
             gin = gout;
         }
         // update of this CTA's rows
-        double* cs = sm;
-        for (int l = threadIdx.x; l < ncols; l += CH_NT) cs[l] = __ldcg(A.cvec + l);
+        T* cs = sm;
+        for (int l = threadIdx.x; l < ncols; l += CH_NT) cs[l] = (T)__ldcg(A.cvec + l);
         __syncthreads();
         const double* qt = A.qt ? A.qt + (long)i * d : nullptr;
         const double* ko = A.kold ? A.kold + (long)i * d : nullptr;
         double s = 0.0;
         for (long row = r0 + threadIdx.x; row < r1; row += CH_NT) {
-            double acc = 0.0;
-            const double* Dr = A.D + row;
+            T acc = T(0);
+            const T* Dr = Dm + row;
 #pragma unroll 8
             for (int l = 0; l < ncols; ++l) acc += __ldg(Dr + (long)l * d) * cs[l];
-            const double knew = gin[row] + acc;
-            const double y = (qt ? qt[row] : 0.0) + (knew - (ko ? ko[row] : 0.0));
+            double y;
+            if (DELTA) {
+                y = qt[row] + (double)(gin[row] + acc);
+            } else {
+                const double knew = (double)gin[row] + (double)acc;
+                y = (qt ? qt[row] : 0.0) + (knew - (ko ? ko[row] : 0.0));
+            }
             const double e = y - qn[row];
             s += e * e;
             qn[row] = y;
+            if (DELTA) A.dlt[row] = (float)e;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -105,24 +137,27 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
     }
 }
 
-size_t chain_smem_bytes(int H, int ccap) {
-    size_t a = sizeof(double) * coarse_tile_smem_doubles<CH_TX, CH_TY>(H);
-    size_t c = sizeof(double) * (size_t)(ccap > 0 ? ccap : 1);
+size_t chain_smem_bytes(int H, int ccap, bool delta) {
+    const size_t el = delta ? sizeof(float) : sizeof(double);
+    size_t a = el * coarse_tile_smem_elems<CH_TX, CH_TY>(H);
+    size_t c = el * (size_t)(ccap > 0 ? ccap : 1);
     return a > c ? a : c;
 }
 
 }  // namespace
 
+template <bool DELTA>
 int chain_grid(int H, int ccap) {
     static int cached[64][2] = {};   // [device] -> (key, blocks)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    const int key = (int)chain_smem_bytes(H, ccap);
+    const int key = (int)chain_smem_bytes(H, ccap, DELTA);
     if (cached[dev][0] != key) {
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, key) != cudaSuccess) return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain, CH_NT, key);
+        if (cudaFuncSetAttribute(k_chain<DELTA>, cudaFuncAttributeMaxDynamicSharedMemorySize, key) != cudaSuccess)
+            return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain<DELTA>, CH_NT, key);
         cached[dev][0] = key;
         cached[dev][1] = per >= 1 ? sms : 0;
     }
@@ -133,16 +168,18 @@ long chain_resp_elems(int n_slices) { return (long)(n_slices + 1) * 1024; }
 
 cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s) {
     if (a.i_end <= a.i_begin) return cudaSuccess;
-    const int nb = chain_grid(a.H, a.ccap);
+    const bool delta = a.dlt != nullptr;
+    const int nb = delta ? chain_grid<true>(a.H, a.ccap) : chain_grid<false>(a.H, a.ccap);
     if (nb < 1 || nb > 1024) return cudaErrorInvalidConfiguration;
-    const size_t smem = chain_smem_bytes(a.H, a.ccap);
-    cudaError_t e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = chain_smem_bytes(a.H, a.ccap, delta);
+    const void* fn = delta ? (const void*)k_chain<true> : (const void*)k_chain<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(&a.gb->count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     ChainArgs arg = a;
     void* args[] = {&arg};
-    e = cudaLaunchCooperativeKernel((const void*)k_chain, dim3(nb), dim3(CH_NT), args, smem, s);
+    e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(CH_NT), args, smem, s);
     count_launches(1);
     return e;
 }

@@ -1,6 +1,7 @@
 // coarse.cu -- coarse propagator G over a batch of states: one launch per
 // partially split forward-Euler coarse step (Sec. 3.2); the step itself is
-// coarse_tile() (coarse_tile.cuh), one 32 x 16 tile per CTA.
+// coarse_tile() (coarse_tile.cuh), one 32 x 16 tile per CTA, in FP64 or (for
+// the mixed-precision solve) FP32 arithmetic with FP64 input and output.
 #include "coarse_tile.cuh"
 
 namespace pr {
@@ -8,11 +9,12 @@ namespace {
 
 constexpr int CTX = 32, CTY = 16, CNT = 256;
 
+template <typename T>
 __global__ void __launch_bounds__(CNT) k_coarse_step(const double* __restrict__ in, double* __restrict__ out,
                                                      long stride, int nx, int ny, CoarseCoef c, int H) {
-    extern __shared__ __align__(16) double sm[];
-    coarse_tile<CTX, CTY, CNT>(in + (long)blockIdx.z * stride, out + (long)blockIdx.z * stride, nx, ny, c, H,
-                               blockIdx.x * CTX, blockIdx.y * CTY, sm);
+    extern __shared__ __align__(16) unsigned char smc[];
+    coarse_tile<CTX, CTY, CNT, T>(in + (long)blockIdx.z * stride, out + (long)blockIdx.z * stride, nx, ny, c, H,
+                                  blockIdx.x * CTX, blockIdx.y * CTY, reinterpret_cast<T*>(smc));
 }
 
 }  // namespace
@@ -20,14 +22,22 @@ __global__ void __launch_bounds__(CNT) k_coarse_step(const double* __restrict__ 
 int coarse_halo(const CoarseCoef& c) { return (c.order == 1 ? 1 : 2) + 2 * c.n_sound - 1; }
 
 cudaError_t launch_coarse_step(const double* in, double* out, long stride, int n, int nx, int ny,
-                               const CoarseCoef& c, cudaStream_t s) {
+                               const CoarseCoef& c, cudaStream_t s, bool fp32) {
     const int H = coarse_halo(c);
     if (H > COARSE_MAXH) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(double) * coarse_tile_smem_doubles<CTX, CTY>(H);
-    cudaError_t e = cudaFuncSetAttribute(k_coarse_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     dim3 grid((nx + CTX - 1) / CTX, (ny + CTY - 1) / CTY, n);
-    k_coarse_step<<<grid, CNT, smem, s>>>(in, out, stride, nx, ny, c, H);
+    const size_t elems = coarse_tile_smem_elems<CTX, CTY>(H);
+    if (fp32) {
+        const size_t smem = sizeof(float) * elems;
+        cudaError_t e = cudaFuncSetAttribute(k_coarse_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_coarse_step<float><<<grid, CNT, smem, s>>>(in, out, stride, nx, ny, c, H);
+    } else {
+        const size_t smem = sizeof(double) * elems;
+        cudaError_t e = cudaFuncSetAttribute(k_coarse_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_coarse_step<double><<<grid, CNT, smem, s>>>(in, out, stride, nx, ny, c, H);
+    }
     count_launches(1);
     return cudaGetLastError();
 }

@@ -19,41 +19,47 @@ namespace pr {
 
 constexpr int COARSE_MAXH = 12;
 
-__device__ __forceinline__ double upwind_flux(int order, double U, const double* f, int i, int st) {
+template <typename T>
+__device__ __forceinline__ T upwind_flux(int order, T U, const T* f, int i, int st) {
     // interface i+1/2 along stride st
-    if (order == 1) return U >= 0.0 ? U * f[i] : U * f[i + st];
-    double aU = fabs(U);
-    return U * (7.0 * (f[i + st] + f[i]) - (f[i + 2 * st] + f[i - st])) * (1.0 / 12.0) +
-           aU * ((f[i + 2 * st] - f[i - st]) - 3.0 * (f[i + st] - f[i])) * (1.0 / 12.0);
+    if (order == 1) return U >= T(0) ? U * f[i] : U * f[i + st];
+    const T aU = U >= T(0) ? U : -U;
+    return U * (T(7) * (f[i + st] + f[i]) - (f[i + 2 * st] + f[i - st])) * (T(1) / T(12)) +
+           aU * ((f[i + 2 * st] - f[i - st]) - T(3) * (f[i + st] - f[i])) * (T(1) / T(12));
 }
 
-// Shared memory (doubles) of one tile: 6 arrays of (TX + 2H) x (TY + 2H).
+// Shared memory (elements) of one tile: 6 arrays of (TX + 2H) x (TY + 2H).
 template <int TX, int TY>
-__host__ __device__ constexpr int coarse_tile_smem_doubles(int H) {
+__host__ __device__ constexpr int coarse_tile_smem_elems(int H) {
     return 6 * (TX + 2 * H) * (TY + 2 * H);
 }
 
-// out tile (tx0, ty0) = one coarse step of in; NT threads cooperate; sm holds
-// coarse_tile_smem_doubles<TX,TY>(H) doubles.  Contains __syncthreads().
-template <int TX, int TY, int NT>
-__device__ __forceinline__ void coarse_tile(const double* __restrict__ src, double* __restrict__ dst, int nx,
-                                            int ny, const CoarseCoef& c, int H, int tx0, int ty0,
-                                            double* __restrict__ sm) {
+// out tile (tx0, ty0) = one coarse step of in, in arithmetic T (double or
+// float, loaded from Tin and stored as Tout); NT threads cooperate; sm holds
+// coarse_tile_smem_elems<TX,TY>(H) elements of T.  Contains __syncthreads().
+template <int TX, int TY, int NT, typename T = double, typename Tin = double, typename Tout = double>
+__device__ __forceinline__ void coarse_tile(const Tin* __restrict__ src, Tout* __restrict__ dst, int nx, int ny,
+                                            const CoarseCoef& cd, int H, int tx0, int ty0, T* __restrict__ sm) {
     const int RX = TX + 2 * H, RY = TY + 2 * H, NR = RX * RY;
-    double* u = sm;
-    double* w = u + NR;
-    double* p = w + NR;
-    double* su = p + NR;
-    double* sw = su + NR;
-    double* sp = sw + NR;
+    T* u = sm;
+    T* w = u + NR;
+    T* p = w + NR;
+    T* su = p + NR;
+    T* sw = su + NR;
+    T* sp = sw + NR;
     const long ncell = (long)nx * ny;
+    struct {
+        T U, V, inv_dx, inv_dy, tau, csx, csy, dxx, dxy1, dyy, dxy2;
+        int n_sound, order;
+    } c = {(T)cd.U, (T)cd.V, (T)cd.inv_dx, (T)cd.inv_dy, (T)cd.tau, (T)cd.csx, (T)cd.csy,
+           (T)cd.dxx, (T)cd.dxy1, (T)cd.dyy, (T)cd.dxy2, cd.n_sound, cd.order};
 
     for (int idx = threadIdx.x; idx < NR; idx += NT) {
         int ly = idx / RX, lx = idx - ly * RX;
         long g = (long)pwrap(ty0 - H + ly, ny) * nx + pwrap(tx0 - H + lx, nx);
-        u[idx] = src[g];
-        w[idx] = src[ncell + g];
-        p[idx] = src[2 * ncell + g];
+        u[idx] = (T)src[g];
+        w[idx] = (T)src[ncell + g];
+        p[idx] = (T)src[2 * ncell + g];
     }
     __syncthreads();
 
@@ -64,13 +70,13 @@ __device__ __forceinline__ void coarse_tile(const double* __restrict__ src, doub
         for (int t = threadIdx.x; t < N1; t += NT) {
             int r = t / W1;
             int i = (r + ra) * RX + (t - r * W1) + ra;
-            double* fs[3] = {u, w, p};
-            double* ss[3] = {su, sw, sp};
+            T* fs[3] = {u, w, p};
+            T* ss[3] = {su, sw, sp};
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                const double* a = fs[f];
-                double Fe = upwind_flux(c.order, c.U, a, i, 1), Fw = upwind_flux(c.order, c.U, a, i - 1, 1);
-                double Gn = upwind_flux(c.order, c.V, a, i, RX), Gs = upwind_flux(c.order, c.V, a, i - RX, RX);
+                const T* a = fs[f];
+                T Fe = upwind_flux<T>(c.order, c.U, a, i, 1), Fw = upwind_flux<T>(c.order, c.U, a, i - 1, 1);
+                T Gn = upwind_flux<T>(c.order, c.V, a, i, RX), Gs = upwind_flux<T>(c.order, c.V, a, i - RX, RX);
                 ss[f][i] = -(Fe - Fw) * c.inv_dx - (Gn - Gs) * c.inv_dy;
             }
         }
@@ -82,18 +88,18 @@ __device__ __forceinline__ void coarse_tile(const double* __restrict__ src, doub
         // forward: velocities on the region shrunk by ra + 2m
         const int sh = ra + 2 * m;
         const int W2 = RX - 2 * sh, H2 = RY - 2 * sh, N2 = W2 * H2;
-        double nu[MAXC], nw[MAXC];
+        T nu[MAXC], nw[MAXC];
 #pragma unroll
         for (int k = 0; k < MAXC; ++k) {
             int t = threadIdx.x + k * NT;
             if (t < N2) {
                 int r = t / W2;
                 int i = (r + sh) * RX + (t - r * W2) + sh;
-                double du = su[i] - c.csx * (p[i + 1] - p[i - 1]) +
-                            c.dxx * (u[i + 1] - 2.0 * u[i] + u[i - 1]) +
+                T du = su[i] - c.csx * (p[i + 1] - p[i - 1]) +
+                            c.dxx * (u[i + 1] - T(2) * u[i] + u[i - 1]) +
                             c.dxy1 * ((w[i + 1 + RX] - w[i + 1 - RX]) - (w[i - 1 + RX] - w[i - 1 - RX]));
-                double dw = sw[i] - c.csy * (p[i + RX] - p[i - RX]) +
-                            c.dyy * (w[i + RX] - 2.0 * w[i] + w[i - RX]) +
+                T dw = sw[i] - c.csy * (p[i + RX] - p[i - RX]) +
+                            c.dyy * (w[i + RX] - T(2) * w[i] + w[i - RX]) +
                             c.dxy2 * ((u[i + 1 + RX] - u[i - 1 + RX]) - (u[i + 1 - RX] - u[i - 1 - RX]));
                 nu[k] = u[i] + c.tau * du;
                 nw[k] = w[i] + c.tau * dw;
@@ -128,9 +134,9 @@ __device__ __forceinline__ void coarse_tile(const double* __restrict__ src, doub
         if (gx < nx && gy < ny) {
             int i = (r + H) * RX + cx + H;
             long g = (long)gy * nx + gx;
-            dst[g] = u[i];
-            dst[ncell + g] = w[i];
-            dst[2 * ncell + g] = p[i];
+            dst[g] = (Tout)u[i];
+            dst[ncell + g] = (Tout)w[i];
+            dst[2 * ncell + g] = (Tout)p[i];
         }
     }
     __syncthreads();   // the shared buffers may be reused right after

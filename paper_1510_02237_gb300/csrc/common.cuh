@@ -53,9 +53,15 @@ template <typename T, typename Tin, typename Tout>
 cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outstride, int n, int nx,
                              int ny, bool has_v, const FineCoef<T>& c, cudaStream_t s);
 
-// One coarse step (slow tendency + n_sound forward-backward substeps) on n states.
+// One RK-3 step with FP32 tendencies and stages on an FP64 state: the last
+// stage forms q^{n+1} = q^n + dt L(q**) in FP64 (fine_prec = PR_FP32X).
+cudaError_t launch_fine_step_acc64(const double* in, double* out, long stride, int n, int nx, int ny, bool has_v,
+                                  const FineCoef<float>& c, cudaStream_t s);
+
+// One coarse step (slow tendency + n_sound forward-backward substeps) on n
+// states, FP64 arithmetic or FP32 arithmetic (fp32) on FP64 data.
 cudaError_t launch_coarse_step(const double* in, double* out, long stride, int n, int nx, int ny,
-                               const CoarseCoef& c, cudaStream_t s);
+                               const CoarseCoef& c, cudaStream_t s, bool fp32 = false);
 int coarse_halo(const CoarseCoef& c);
 
 // -------- tall-skinny FP64 linear algebra over d-long columns (column-major)
@@ -89,8 +95,12 @@ cudaError_t krylov_append(const double* v, const double* z, const double* res2, 
 cudaError_t chain_update(const double* qt, const double* g, const double* D, long ldd, const int* c1_dev,
                          int ccap, const double* c, const double* kold, double* q, long nrows,
                          double* res2_slot, const TsWork& w, cudaStream_t s);
-// dst <- src with *res2 = ||src - dst_old||^2
-cudaError_t copy_resid(const double* src, double* dst, long n, double* res2, const TsWork& w, cudaStream_t s);
+// dst <- src with *res2 = ||src - dst_old||^2 (and delta = src - dst_old in FP32 if non-NULL)
+cudaError_t copy_resid(const double* src, double* dst, long n, double* res2, const TsWork& w, cudaStream_t s,
+                       float* delta = nullptr);
+// FP32 copies of basis columns [*c0_dev, *c1_dev) of Q and D (at most maxcols columns)
+cudaError_t to_fp32_cols(const double* Q, const double* D, float* Q32, float* D32, long d, const int* c0_dev,
+                         const int* c1_dev, int maxcols, cudaStream_t s);
 // *out = max_i sqrt(res2[i])
 cudaError_t max_sqrt(const double* res2, int n, double* out, cudaStream_t s);
 cudaError_t sub(const double* a, const double* b, double* out, long n, cudaStream_t s);
@@ -107,9 +117,10 @@ struct GridBar {
 // against the original column norms a2[j] and the append, in one cooperative
 // launch.  gb->err != 0 afterwards (sticky) means a barrier wait gave up and
 // the result is invalid.
+// ratio[j] (optional) receives ||residual_j|| / ||a_j||.
 cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2, const int* r_old_dev,
-                        int* r_dev, int cap, double eta, double* Q, double* D, int* kept, const TsWork& w,
-                        GridBar* gb, cudaStream_t s);
+                        int* r_dev, int cap, double eta, double* Q, double* D, int* kept, double* ratio,
+                        const TsWork& w, GridBar* gb, cudaStream_t s);
 
 
 // Serial correction of Alg. 2 over slices [i_begin, i_end) in one cooperative
@@ -135,6 +146,11 @@ struct ChainArgs {
     double* resp;         // >= chain_resp_elems(N) residual partials
     double* res2;         // res2[i+1] = ||q_{i+1} change||^2, or NULL
     GridBar* gb;
+    // FP32 delta form (dlt != NULL): q_{i+1} = qt_i + (G(delta_i) + D32 Q32^T delta_i)
+    float* dlt;           // d values: delta_i on entry to slice i, delta_{i+1} after it
+    const float* Q32;     // FP32 copies of Q and D
+    const float* D32;
+    float* gbuf32;        // 2 x d FP32 coarse ping-pong
 };
 cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s);
 long chain_resp_elems(int n_slices);

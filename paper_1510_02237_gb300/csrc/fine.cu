@@ -51,7 +51,9 @@ __device__ __forceinline__ void fine_tend(const T* __restrict__ u, const T* __re
           c.dxy2 * ((u[i + 1 + S1] - u[i - 1 + S1]) - (u[i + 1 - S1] - u[i - 1 - S1]));
 }
 
-template <typename T, typename Tin, typename Tout, int RYH, int TX, int TY, int NT>
+// ACC64: the state is FP64 in memory and the last stage adds dt L(q**) to
+// the FP64 q^n (the tendencies and the intermediate stages stay in T).
+template <typename T, typename Tin, typename Tout, int RYH, int TX, int TY, int NT, bool ACC64 = false>
 __global__ void __launch_bounds__(NT) k_fine_step(const Tin* __restrict__ in, long instride,
                                                    Tout* __restrict__ out, long outstride, int nx,
                                                    int ny, FineCoef<T> c) {
@@ -131,19 +133,26 @@ __global__ void __launch_bounds__(NT) k_fine_step(const Tin* __restrict__ in, lo
             T Lu, Lw, Lp;
             fine_tend<T, RYH>(s, s + NR, s + 2 * NR, i, RX, c, Lu, Lw, Lp);
             long g = (long)gy * nx + gx;
-            dst[g] = (Tout)(q[i] + c.c3 * Lu);
-            dst[ncell + g] = (Tout)(q[NR + i] + c.c3 * Lw);
-            dst[2 * ncell + g] = (Tout)(q[2 * NR + i] + c.c3 * Lp);
+            if (ACC64) {
+                const double c3 = (double)c.c3;
+                dst[g] = (Tout)((double)src[g] + c3 * (double)Lu);
+                dst[ncell + g] = (Tout)((double)src[ncell + g] + c3 * (double)Lw);
+                dst[2 * ncell + g] = (Tout)((double)src[2 * ncell + g] + c3 * (double)Lp);
+            } else {
+                dst[g] = (Tout)(q[i] + c.c3 * Lu);
+                dst[ncell + g] = (Tout)(q[NR + i] + c.c3 * Lw);
+                dst[2 * ncell + g] = (Tout)(q[2 * NR + i] + c.c3 * Lp);
+            }
         }
     }
 }
 
-template <typename T, typename Tin, typename Tout, int RYH, int TX, int TY, int NT>
+template <typename T, typename Tin, typename Tout, int RYH, int TX, int TY, int NT, bool ACC64 = false>
 cudaError_t launch_tile(const Tin* in, long instride, Tout* out, long outstride, int n, int nx, int ny,
                         const FineCoef<T>& c, cudaStream_t s) {
     constexpr int RX = TX + 18, RY = TY + 6 * RYH;
     constexpr size_t smem = sizeof(T) * 6 * RX * RY;
-    auto kern = k_fine_step<T, Tin, Tout, RYH, TX, TY, NT>;
+    auto kern = k_fine_step<T, Tin, Tout, RYH, TX, TY, NT, ACC64>;
     // idempotent; set on every launch so it holds on whichever device is current
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -165,6 +174,17 @@ cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outst
     }
     if (big) return launch_tile<T, Tin, Tout, 1, 64, 16, 256>(in, instride, out, outstride, n, nx, ny, c, s);
     return launch_tile<T, Tin, Tout, 1, 32, 8, 256>(in, instride, out, outstride, n, nx, ny, c, s);
+}
+
+cudaError_t launch_fine_step_acc64(const double* in, double* out, long stride, int n, int nx, int ny, bool has_v,
+                                  const FineCoef<float>& c, cudaStream_t s) {
+    const bool big = nx >= 64 && ny >= 16;
+    if (has_v) {
+        if (big) return launch_tile<float, double, double, 3, 64, 16, 256, true>(in, stride, out, stride, n, nx, ny, c, s);
+        return launch_tile<float, double, double, 3, 32, 8, 256, true>(in, stride, out, stride, n, nx, ny, c, s);
+    }
+    if (big) return launch_tile<float, double, double, 1, 64, 16, 256, true>(in, stride, out, stride, n, nx, ny, c, s);
+    return launch_tile<float, double, double, 1, 32, 8, 256, true>(in, stride, out, stride, n, nx, ny, c, s);
 }
 
 template cudaError_t launch_fine_step<double, double, double>(const double*, long, double*, long, int,

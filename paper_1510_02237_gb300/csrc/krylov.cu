@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256) k_chain_update(const double* __restrict__
 }
 
 __global__ void k_copy_resid(const double* __restrict__ src, double* __restrict__ dst, long n,
-                             double* __restrict__ partial) {
+                             double* __restrict__ partial, float* __restrict__ delta) {
     __shared__ double red[8];
     const long row = (long)blockIdx.x * 256 + threadIdx.x;
     double s = 0.0;
@@ -232,6 +232,7 @@ __global__ void k_copy_resid(const double* __restrict__ src, double* __restrict_
         double e = y - dst[row];
         s = e * e;
         dst[row] = y;
+        if (delta) delta[row] = (float)e;
     }
     s = block_sum256(s, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -259,6 +260,16 @@ __global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b
         o[i] = a[i] - b[i];
 }
 
+__global__ void k_to_fp32_cols(const double* __restrict__ Q, const double* __restrict__ D, float* __restrict__ Q32,
+                               float* __restrict__ D32, long d, const int* c0_dev, const int* c1_dev) {
+    const int col = (c0_dev ? *c0_dev : 0) + blockIdx.y;
+    if (col >= *c1_dev) return;
+    for (long row = (long)blockIdx.x * blockDim.x + threadIdx.x; row < d; row += (long)gridDim.x * blockDim.x) {
+        Q32[row + (long)col * d] = (float)Q[row + (long)col * d];
+        D32[row + (long)col * d] = (float)D[row + (long)col * d];
+    }
+}
+
 __global__ void k_fill_int(int* p, int v, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -276,7 +287,7 @@ constexpr int IB_NT = 512;
 __global__ void __launch_bounds__(IB_NT) k_intra_block(double* __restrict__ wv, double* __restrict__ wz, long d,
                                                       int m, const double* __restrict__ a2, const int* r_old_dev,
                                                       int* r_dev, int cap, double eta, double* __restrict__ Q,
-                                                      double* __restrict__ D, int* kept,
+                                                      double* __restrict__ D, int* kept, double* ratio,
                                                       double* __restrict__ part, int pstride, GridBar* gb) {
     __shared__ double cs[64];
     __shared__ double red[IB_NT / 32];
@@ -293,7 +304,7 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* __restrict__ wv, 
     double* P1 = part + (long)nb * pstride;
     for (int j = 0; j < m; ++j) {
         double* v = wv + (long)j * d;
-        double* z = wz + (long)j * d;
+        double* z = wz ? wz + (long)j * d : nullptr;   // no D bookkeeping when wz is NULL
         const int nn = rl - c0;   // columns kept so far in this block
         // Two passes of classical Gram-Schmidt against those columns.  The
         // second pass also reduces ||v||^2: with c2 = Q^T v and Q^T Q = I the
@@ -340,13 +351,18 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* __restrict__ wv, 
             }
             for (long row = r0 + threadIdx.x; row < r1 && nn > 0; row += IB_NT) {
                 double av = 0.0, az = 0.0;
+                if (z) {
 #pragma unroll 4
-                for (int l = 0; l < nn; ++l) {
-                    av += Q[row + (long)(c0 + l) * d] * cs[l];
-                    az += D[row + (long)(c0 + l) * d] * cs[l];
+                    for (int l = 0; l < nn; ++l) {
+                        av += Q[row + (long)(c0 + l) * d] * cs[l];
+                        az += D[row + (long)(c0 + l) * d] * cs[l];
+                    }
+                    z[row] -= az;
+                } else {
+#pragma unroll 4
+                    for (int l = 0; l < nn; ++l) av += Q[row + (long)(c0 + l) * d] * cs[l];
                 }
                 v[row] -= av;
-                z[row] -= az;
             }
             __syncthreads();   // the next dot products read these rows with another thread mapping
         }
@@ -356,12 +372,15 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* __restrict__ wv, 
             const double inv = 1.0 / res;
             for (long row = r0 + threadIdx.x; row < r1; row += IB_NT) {
                 Q[row + (long)rl * d] = v[row] * inv;
-                D[row + (long)rl * d] = z[row] * inv;
+                if (z) D[row + (long)rl * d] = z[row] * inv;
             }
             ++rl;
         }
         __syncthreads();       // the appended column is read by the next column's dot products
-        if (b == 0 && threadIdx.x == 0) kept[j] = keep ? 1 : 0;
+        if (b == 0 && threadIdx.x == 0) {
+            kept[j] = keep ? 1 : 0;
+            if (ratio) ratio[j] = an > 0.0 ? res / an : 0.0;
+        }
     }
     if (b == 0 && threadIdx.x == 0) *r_dev = rl;
 }
@@ -472,10 +491,11 @@ cudaError_t chain_update(const double* qt, const double* g, const double* D, lon
     return cudaGetLastError();
 }
 
-cudaError_t copy_resid(const double* src, double* dst, long n, double* res2, const TsWork& w, cudaStream_t s) {
+cudaError_t copy_resid(const double* src, double* dst, long n, double* res2, const TsWork& w, cudaStream_t s,
+                       float* delta) {
     const int nb = cdiv(n, 256);
     if (nb > w.elems) return cudaErrorInvalidValue;
-    k_copy_resid<<<nb, 256, 0, s>>>(src, dst, n, w.partial);
+    k_copy_resid<<<nb, 256, 0, s>>>(src, dst, n, w.partial, delta);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -512,8 +532,8 @@ int intra_block_grid() {
 }
 
 cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2, const int* r_old_dev,
-                        int* r_dev, int cap, double eta, double* Q, double* D, int* kept, const TsWork& w,
-                        GridBar* gb, cudaStream_t s) {
+                        int* r_dev, int cap, double eta, double* Q, double* D, int* kept, double* ratio,
+                        const TsWork& w, GridBar* gb, cudaStream_t s) {
     if (m < 1 || m > 64) return cudaErrorInvalidValue;
     int nb = intra_block_grid();
     if (nb < 1) return cudaErrorInvalidConfiguration;
@@ -523,11 +543,21 @@ cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2,
     cudaError_t e = cudaMemsetAsync(&gb->count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     double* part = w.partial;
-    void* args[] = {&wv, &wz, &d, &m, (void*)&a2, (void*)&r_old_dev, &r_dev, &cap, &eta, &Q, &D, &kept, &part,
-                    &pstride, &gb};
+    void* args[] = {&wv, &wz, &d, &m, (void*)&a2, (void*)&r_old_dev, &r_dev, &cap, &eta, &Q, &D, &kept, &ratio,
+                    &part, &pstride, &gb};
     e = cudaLaunchCooperativeKernel((const void*)k_intra_block, dim3(nb), dim3(IB_NT), args, 0, s);
     count_launches(1);
     return e;
+}
+
+cudaError_t to_fp32_cols(const double* Q, const double* D, float* Q32, float* D32, long d, const int* c0_dev,
+                         const int* c1_dev, int maxcols, cudaStream_t s) {
+    if (maxcols < 1) return cudaSuccess;
+    int nb = cdiv(d, 256);
+    if (nb > 256) nb = 256;
+    k_to_fp32_cols<<<dim3(nb, maxcols), 256, 0, s>>>(Q, D, Q32, D32, d, c0_dev, c1_dev);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t fill_int(int* p, int v, int n, cudaStream_t s) {

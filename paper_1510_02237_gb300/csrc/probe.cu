@@ -54,3 +54,48 @@ extern "C" pr_status parareal_alu_probe(int32_t prec, int32_t iters, double* flo
     if (!flops_per_s || iters < 1 || (prec != PR_FP64 && prec != PR_FP32)) return PR_EINVAL;
     return prec == PR_FP64 ? run_probe<double>(iters, flops_per_s) : run_probe<float>(iters, flops_per_s);
 }
+
+// ---------------------------------------------------------------- bounded-wait self-test
+#include "grid_barrier.cuh"
+
+namespace {
+
+// Every CTA waits at a grid barrier that expects one CTA more than the grid
+// has: the barrier can never complete, so each wait must give up after its
+// poll limit, set the error word and return.
+__global__ void k_wait_selftest(pr::GridBar* gb, unsigned expected) {
+    pr::grid_barrier(gb, expected);
+}
+
+}  // namespace
+
+extern "C" pr_status parareal_selftest_wait_timeout(void* stream, double* seconds) {
+    pr::GridBar* gb = nullptr;
+    if (cudaMalloc((void**)&gb, sizeof(pr::GridBar)) != cudaSuccess) return PR_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    pr_status st = PR_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    if (cudaMemsetAsync(gb, 0, sizeof(pr::GridBar), s) != cudaSuccess) st = PR_ECUDA;
+    if (st == PR_OK) {
+        unsigned blocks = 2, expected = 3;
+        void* args[] = {&gb, &expected};
+        cudaEventRecord(e0, s);
+        if (cudaLaunchCooperativeKernel((const void*)k_wait_selftest, dim3(blocks), dim3(32), args, 0, s) != cudaSuccess)
+            st = PR_ECUDA;
+        pr::count_launches(1);
+        cudaEventRecord(e1, s);
+    }
+    int err = 0;
+    if (st == PR_OK && cudaStreamSynchronize(s) != cudaSuccess) st = PR_ECUDA;
+    if (st == PR_OK && cudaMemcpy(&err, &gb->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) st = PR_ECUDA;
+    float ms = 0.f;
+    if (st == PR_OK) cudaEventElapsedTime(&ms, e0, e1);
+    if (seconds) *seconds = ms * 1e-3;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(gb);
+    if (st != PR_OK) return st;
+    return err ? PR_ETIMEOUT : PR_OK;
+}

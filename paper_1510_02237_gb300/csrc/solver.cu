@@ -51,8 +51,12 @@ struct pr_solver {
     float *f32a = nullptr, *f32b = nullptr;
     double *C = nullptr, *cvec = nullptr, *partial = nullptr;
     double *anorm2 = nullptr, *res2 = nullptr, *rhist = nullptr, *nres2 = nullptr;
-    double *gbuf = nullptr, *resp = nullptr;
+    double *gbuf = nullptr, *resp = nullptr, *ratios = nullptr;   // ratios: PR_MAX_ITERS x N
+    float *Q32 = nullptr, *D32 = nullptr, *dlt = nullptr, *gbuf32 = nullptr;
+    int* r_it = nullptr;
     int *r = nullptr, *r_old = nullptr, *kept = nullptr, *ranks = nullptr, *zero = nullptr;
+    int* kept_hist = nullptr;                       // PR_MAX_ITERS x N kept flags
+    int M_hist[PR_MAX_ITERS] = {};
     GridBar* gbar = nullptr;
     long partial_elems = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -111,9 +115,13 @@ static Sizes compute_sizes(int nx, int ny, int N, int K_max, const pr_options& o
     b += dd * (size_t)N * s.d * 2;             // coarse ping-pong
     if (o.fine_prec == PR_FP32)
         b += sizeof(float) * (size_t)N * s.d * 2;
+    else if (o.fine_prec == PR_FP32X)
+        b += dd * (size_t)N * s.d * 2;
     else
         b += dd * (size_t)N * s.d * 3;         // fine stage buffers
     b += dd * (size_t)s.d * 3;                 // gtmp, chain coarse ping-pong
+    if (o.corr_prec == PR_FP32)
+        b += sizeof(float) * ((size_t)s.cap * s.d * 2 + (size_t)s.d * 3);   // Q32, D32, delta, ping-pong
     b += dd * (size_t)chain_resp_elems(N);
     b += dd * ((size_t)s.cap * N + s.cap);     // C, cvec
     b += dd * (size_t)s.partial;
@@ -130,6 +138,15 @@ static pr_status fine_apply(pr_solver* h, const double* in, double* out, int n) 
     const bool hv = h->V != 0.0;
     cudaStream_t s = h->stream;
     const int nf = h->n_f;
+    if (h->opt.fine_prec == PR_FP32X) {
+        const double* a = in;
+        for (int st = 0; st < nf; ++st) {
+            double* b = st == nf - 1 ? out : (st % 2 == 0 ? h->fb0 : h->fb1);
+            CKC(launch_fine_step_acc64(a, b, d, n, h->nx, h->ny, hv, h->fc32, s));
+            a = b;
+        }
+        return PR_OK;
+    }
     if (h->opt.fine_prec == PR_FP32) {
         if (nf == 1) {
             CKC((launch_fine_step<float, double, double>(in, d, out, d, n, h->nx, h->ny, hv, h->fc32, s)));
@@ -176,21 +193,21 @@ static pr_status fine_apply(pr_solver* h, const double* in, double* out, int n) 
     return PR_OK;
 }
 
-static pr_status coarse_apply(pr_solver* h, const double* in, double* out, int n) {
+static pr_status coarse_apply(pr_solver* h, const double* in, double* out, int n, bool fp32 = false) {
     const long d = h->d;
     cudaStream_t s = h->stream;
     if (h->n_g == 1) {
-        CKC(launch_coarse_step(in, out, d, n, h->nx, h->ny, h->cc, s));
+        CKC(launch_coarse_step(in, out, d, n, h->nx, h->ny, h->cc, s, fp32));
         return PR_OK;
     }
-    CKC(launch_coarse_step(in, h->cb0, d, n, h->nx, h->ny, h->cc, s));
+    CKC(launch_coarse_step(in, h->cb0, d, n, h->nx, h->ny, h->cc, s, fp32));
     double* a = h->cb0;
     double* b = h->cb1;
     for (int st = 1; st < h->n_g - 1; ++st) {
-        CKC(launch_coarse_step(a, b, d, n, h->nx, h->ny, h->cc, s));
+        CKC(launch_coarse_step(a, b, d, n, h->nx, h->ny, h->cc, s, fp32));
         double* t = a; a = b; b = t;
     }
-    CKC(launch_coarse_step(a, out, d, n, h->nx, h->ny, h->cc, s));
+    CKC(launch_coarse_step(a, out, d, n, h->nx, h->ny, h->cc, s, fp32));
     return PR_OK;
 }
 
@@ -202,28 +219,52 @@ static pr_status coarse_apply(pr_solver* h, const double* in, double* out, int n
 // the columns kept earlier in this block, then the drop rule.  The D-images
 // Z = FV - GV receive exactly the same coefficients, so D = F(Q) - G(Q).
 template <typename Mark>
-static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, const double* GV, int m, Mark mark) {
+static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, const double* GV, int m, Mark mark,
+                              double* ratio = nullptr) {
     const long d = h->d;
     const int cap = h->cap;
     cudaStream_t s = h->stream;
     TsWork w{h->partial, h->partial_elems};
+    const bool images = FV != nullptr;   // carry D = F(Q) - G(Q) along (Eq. Genhance)
     CKC(cudaMemcpyAsync(h->wv, V, sizeof(double) * m * d, cudaMemcpyDeviceToDevice, s));
-    CKC(sub(FV, GV, h->wz, (long)m * d, s));
+    if (images) CKC(sub(FV, GV, h->wz, (long)m * d, s));
     CKC(colnorm2(h->wv, d, m, d, h->anorm2, w, s));
     for (int j0 = 0; j0 < m; j0 += 64) {
         const int mm = m - j0 < 64 ? m - j0 : 64;
         double* v = h->wv + (long)j0 * d;
-        double* z = h->wz + (long)j0 * d;
+        double* z = images ? h->wz + (long)j0 * d : nullptr;
         CKC(cudaMemcpyAsync(h->r_old, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
         for (int pass = 0; pass < 2; ++pass) {
             CKC(gemm_tn(h->Q, d, nullptr, h->r_old, cap, v, d, mm, d, h->C, cap, w, s));
             CKC(gemm_nn(h->Q, d, nullptr, h->r_old, cap, h->C, cap, v, d, v, d, mm, d, -1.0, s));
-            CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->C, cap, z, d, z, d, mm, d, -1.0, s));
+            if (images) CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->C, cap, z, d, z, d, mm, d, -1.0, s));
         }
         if (j0 == 0) CKC(mark());
         CKC(intra_block(v, z, d, mm, h->anorm2 + j0, h->r_old, h->r, cap, h->opt.drop_tol, h->Q, h->D,
-                        h->kept + j0, w, h->gbar, s));
+                        h->kept + j0, ratio ? ratio + j0 : nullptr, w, h->gbar, s));
     }
+    return PR_OK;
+}
+
+// Images of the columns appended since *r_it computed directly as
+// D_j = F(Q_j) - G(Q_j) (the quantity Eq. Genhance forms by linearity, here
+// without dividing rounding errors by small residuals |R_jj|).  Mixed
+// precision uses the FP32 propagators and refreshes the FP32 copies of Q
+// and D used by the serial correction.
+static pr_status direct_images(pr_solver* h, bool mixed) {
+    const long d = h->d;
+    cudaStream_t s = h->stream;
+    int rr[2] = {0, 0};
+    CKC(cudaMemcpyAsync(rr, h->r_it, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKC(cudaMemcpyAsync(rr + 1, h->r, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKC(cudaStreamSynchronize(h->stream));
+    const int c0 = rr[0], n = rr[1] - rr[0];
+    if (n <= 0) return PR_OK;
+    const double* Qn = h->Q + (long)c0 * d;
+    CKS(fine_apply(h, Qn, h->wv, n));
+    CKS(coarse_apply(h, Qn, h->wz, n, mixed));
+    CKC(sub(h->wv, h->wz, h->D + (long)c0 * d, (long)n * d, s));
+    if (mixed) CKC(to_fp32_cols(h->Q, h->D, h->Q32, h->D32, d, h->r_it, h->r, n, s));
     return PR_OK;
 }
 
@@ -258,12 +299,15 @@ static ChainArgs chain_args(pr_solver* h, int i_begin, int i_end, const double* 
     return a;
 }
 
-static pr_status solve_impl(pr_solver* h, int K, pr_report* rep) {
+static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
     const long d = h->d;
     const int N = h->N, cap = h->cap;
     cudaStream_t s = h->stream;
     TsWork w{h->partial, h->partial_elems};
     const bool kse = h->opt.variant == PR_KSE;
+    const bool mixed = h->opt.corr_prec == PR_FP32;
+    // FP32 fine images cannot be divided by small residuals: non-FP64 fine sweeps use direct images
+    const bool direct = mixed || h->opt.images == PR_IMAGES_DIRECT || h->opt.fine_prec != PR_FP64;
     cudaEvent_t* ev = nullptr;
     if (h->tr.n < h->tr.max_solves) {
         ev = h->tr.ev.data() + (size_t)h->tr.n * h->tr.per_solve;
@@ -288,19 +332,26 @@ static pr_status solve_impl(pr_solver* h, int K, pr_report* rep) {
         // parallel predictor: q~_{i+1}^k = F(q_i^k)
         CKS(fine_apply(h, qa, h->qt + (long)a * d, M));
         CKC(mark());
-        // coarse images G(q_i^k) (subspace images and K(q_i^k))
-        CKS(coarse_apply(h, qa, h->gv + (long)a * d, M));
+        // coarse images G(q_i^k) (subspace images and K(q_i^k)); the FP32
+        // correction needs neither
+        if (!mixed) CKS(coarse_apply(h, qa, h->gv + (long)a * d, M));   // also K(q_i^k) for FP64
         CKC(mark());
         if (kse) {
-            CKS(krylov_block(h, qa, h->qt + (long)a * d, h->gv + (long)a * d, M, mark));
+            CKC(cudaMemcpyAsync(h->r_it, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
+            CKS(krylov_block(h, qa, direct ? nullptr : h->qt + (long)a * d, h->gv + (long)a * d, M, mark,
+                             h->ratios + (long)(rbase + k) * N));
+            CKC(cudaMemcpyAsync(h->kept_hist + (long)(rbase + k) * N, h->kept, sizeof(int) * M,
+                                cudaMemcpyDeviceToDevice, s));
+            h->M_hist[rbase + k] = M;
             CKC(mark());
-            // K(q_i^k) = G(q_i^k) + D Q^T q_i^k for i = k+1..N-1 with the updated S^k
-            if (M > 1) {
+            if (direct) CKS(direct_images(h, mixed));
+            if (!mixed && M > 1) {
+                // K(q_i^k) = G(q_i^k) + D Q^T q_i^k for i = k+1..N-1 with the updated S^k
                 CKC(gemm_tn(h->Q, d, nullptr, h->r, cap, h->q + (long)(a + 1) * d, d, M - 1, d, h->C, cap, w, s));
                 CKC(gemm_nn(h->D, d, nullptr, h->r, cap, h->C, cap, h->gv + (long)(a + 1) * d, d,
                             h->kold + (long)(a + 1) * d, d, M - 1, d, 1.0, s));
             }
-            CKC(cudaMemcpyAsync(h->ranks + k, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
+            CKC(cudaMemcpyAsync(h->ranks + rbase + k, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
         } else {
             CKC(mark());
             CKC(mark());
@@ -308,12 +359,28 @@ static pr_status solve_impl(pr_solver* h, int K, pr_report* rep) {
         CKC(mark());
         // serial correction
         CKC(cudaMemsetAsync(h->res2, 0, sizeof(double) * (N + 1), s));
-        CKC(copy_resid(h->qt + (long)a * d, h->q + (long)(a + 1) * d, d, h->res2 + a + 1, w, s));
-        CKC(chain_coop(chain_args(h, a + 1, N, h->qt, kse ? h->kold : h->gv, kse ? h->r : nullptr, h->res2), s));
-        CKC(max_sqrt(h->res2 + 1, N, h->rhist + k, s));
+        CKC(copy_resid(h->qt + (long)a * d, h->q + (long)(a + 1) * d, d, h->res2 + a + 1, w, s,
+                       mixed ? h->dlt : nullptr));
+        ChainArgs ca = chain_args(h, a + 1, N, h->qt, kse ? h->kold : h->gv, kse ? h->r : nullptr, h->res2);
+        if (mixed) {
+            ca.kold = nullptr;
+            ca.dlt = h->dlt;
+            ca.Q32 = h->Q32;
+            ca.D32 = h->D32;
+            ca.gbuf32 = h->gbuf32;
+        }
+        CKC(chain_coop(ca, s));
+        CKC(max_sqrt(h->res2 + 1, N, h->rhist + rbase + k, s));
         CKC(mark());
+        *K_done = k + 1;
+        if (h->opt.r_tol > 0) {
+            // stopping rule of Sec. 2.1 (one synchronisation per iteration)
+            double r = 0.0;
+            CKC(cudaMemcpyAsync(&r, h->rhist + rbase + k, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CKC(cudaStreamSynchronize(s));
+            if (r <= h->opt.r_tol) break;
+        }
     }
-    (void)rep;
     return PR_OK;
 }
 
@@ -330,14 +397,49 @@ static pr_status check_device_waits(pr_solver* h) {
     return PR_OK;
 }
 
-static pr_status fill_report(pr_solver* h, int K, pr_report* rep) {
+// All parallel steps (Sec. 2.1): window w starts from q_N of window w-1.
+// q[0] holds u0 on entry.  Iteration records are kept in order, up to
+// PR_MAX_ITERS of them.
+static pr_status solve_windows(pr_solver* h, int K, std::vector<int>& Kw) {
+    const long d = h->d;
+    int rbase = 0;
+    Kw.clear();
+    for (int w = 0; w < h->opt.n_windows; ++w) {
+        if (w > 0)
+            CKC(cudaMemcpyAsync(h->q, h->q + (long)h->N * d, sizeof(double) * d, cudaMemcpyDeviceToDevice, h->stream));
+        const int Kc = rbase + K <= PR_MAX_ITERS ? K : (PR_MAX_ITERS - rbase > 0 ? PR_MAX_ITERS - rbase : 0);
+        int done = 0;
+        CKS(solve_impl(h, K, Kc < K ? PR_MAX_ITERS - K : rbase, &done));
+        Kw.push_back(done);
+        rbase += Kc < K ? 0 : done;
+    }
+    return PR_OK;
+}
+
+static pr_status fill_report(pr_solver* h, const std::vector<int>& Kw, pr_report* rep) {
     CKC(cudaStreamSynchronize(h->stream));
     CKS(check_device_waits(h));
     std::memset(rep, 0, sizeof(*rep));
+    int K = 0;
+    for (int x : Kw) K += x;
+    if (K > PR_MAX_ITERS) K = PR_MAX_ITERS;
     rep->K = K;
+    rep->n_windows = (int)Kw.size();
+    for (size_t w = 0; w < Kw.size() && w < PR_MAX_ITERS; ++w) rep->K_window[w] = Kw[w];
+    for (int k = 0; k < PR_MAX_ITERS; ++k) rep->min_ratio[k] = 1.0;
     if (K > 0) {
         CKC(cudaMemcpy(rep->r, h->rhist, sizeof(double) * K, cudaMemcpyDeviceToHost));
-        if (h->opt.variant == PR_KSE) CKC(cudaMemcpy(rep->rank, h->ranks, sizeof(int) * K, cudaMemcpyDeviceToHost));
+        if (h->opt.variant == PR_KSE) {
+            CKC(cudaMemcpy(rep->rank, h->ranks, sizeof(int) * K, cudaMemcpyDeviceToHost));
+            std::vector<double> rat((size_t)K * h->N);
+            std::vector<int> kp((size_t)K * h->N);
+            CKC(cudaMemcpy(rat.data(), h->ratios, sizeof(double) * rat.size(), cudaMemcpyDeviceToHost));
+            CKC(cudaMemcpy(kp.data(), h->kept_hist, sizeof(int) * kp.size(), cudaMemcpyDeviceToHost));
+            for (int k = 0; k < K; ++k)
+                for (int j = 0; j < h->M_hist[k]; ++j)
+                    if (kp[(size_t)k * h->N + j] && rat[(size_t)k * h->N + j] < rep->min_ratio[k])
+                        rep->min_ratio[k] = rat[(size_t)k * h->N + j];
+        }
     }
     float ms = 0.f;
     CKC(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
@@ -384,6 +486,10 @@ pr_status parareal_default_options(pr_options* o) {
     o->drop_tol = 1e-10;
     o->fine_prec = PR_FP64;
     o->variant = PR_KSE;
+    o->corr_prec = PR_FP64;
+    o->r_tol = 0.0;
+    o->n_windows = 1;
+    o->images = PR_IMAGES_LINEARITY;
     o->stream = nullptr;
     return PR_OK;
 }
@@ -403,16 +509,21 @@ static pr_status validate(const pr_grid* g, double U, double c_s, double dt_f, d
     if (o.adv_order_c != 1 && o.adv_order_c != 3) return set_err(h, PR_EINVAL, "adv_order_c must be 1 or 3");
     if (o.n_sound < 1) return set_err(h, PR_EINVAL, "n_sound must be >= 1");
     if ((o.adv_order_c == 1 ? 1 : 2) + 2 * o.n_sound - 1 > 12) return set_err(h, PR_EINVAL, "n_sound too large for the fused coarse step (halo > 12)");
-    if (o.fine_prec != PR_FP64 && o.fine_prec != PR_FP32) return set_err(h, PR_EINVAL, "fine_prec must be PR_FP64 or PR_FP32");
+    if (o.fine_prec != PR_FP64 && o.fine_prec != PR_FP32 && o.fine_prec != PR_FP32X)
+        return set_err(h, PR_EINVAL, "fine_prec must be PR_FP64, PR_FP32 or PR_FP32X");
     if (o.variant != PR_KSE && o.variant != PR_ORIGINAL) return set_err(h, PR_EINVAL, "variant must be PR_KSE or PR_ORIGINAL");
+    if (o.corr_prec != PR_FP64 && o.corr_prec != PR_FP32) return set_err(h, PR_EINVAL, "corr_prec must be PR_FP64 or PR_FP32");
+    if (!(o.r_tol >= 0) || !is_fin(o.r_tol)) return set_err(h, PR_EINVAL, "r_tol must be >= 0");
+    if (o.n_windows < 1 || o.n_windows > 1000000) return set_err(h, PR_EINVAL, "n_windows must be >= 1");
+    if (o.images != PR_IMAGES_LINEARITY && o.images != PR_IMAGES_DIRECT) return set_err(h, PR_EINVAL, "images must be PR_IMAGES_LINEARITY or PR_IMAGES_DIRECT");
     if (!(o.drop_tol >= 0) || !is_fin(o.drop_tol)) return set_err(h, PR_EINVAL, "drop_tol must be >= 0");
     if (o.K_max < 0 || o.K_max > PR_MAX_ITERS || o.K_max > N) return set_err(h, PR_EINVAL, "K_max must be in [0, min(N, 128)]");
     if (o.krylov_cap < 0 || o.krylov_cap > 1600) return set_err(h, PR_EINVAL, "krylov_cap must be in [0, 1600]");
-    const double DT = o.T / N;
+    const double DT = o.T / ((double)N * o.n_windows);
     double nf = DT / dt_f, ng = DT / dt_g;
     long inf = std::lround(nf), ing = std::lround(ng);
-    if (inf < 1 || std::fabs(inf * dt_f - DT) > 1e-9 * DT) return set_err(h, PR_EINVAL, "T/N is not an integer multiple of dt_f");
-    if (ing < 1 || std::fabs(ing * dt_g - DT) > 1e-9 * DT) return set_err(h, PR_EINVAL, "T/N is not an integer multiple of dt_g");
+    if (inf < 1 || std::fabs(inf * dt_f - DT) > 1e-9 * DT) return set_err(h, PR_EINVAL, "T/(N n_windows) is not an integer multiple of dt_f");
+    if (ing < 1 || std::fabs(ing * dt_g - DT) > 1e-9 * DT) return set_err(h, PR_EINVAL, "T/(N n_windows) is not an integer multiple of dt_g");
     if (inf > 100000 || ing > 100000) return set_err(h, PR_EINVAL, "too many steps per slice");
     *n_f = (int)inf;
     *n_g = (int)ing;
@@ -494,6 +605,9 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     if (o.fine_prec == PR_FP32) {
         chk(cudaMalloc((void**)&h->f32a, sizeof(float) * (size_t)N * d));
         chk(cudaMalloc((void**)&h->f32b, sizeof(float) * (size_t)N * d));
+    } else if (o.fine_prec == PR_FP32X) {
+        chk(dalloc(&h->fb0, (size_t)N * d));
+        chk(dalloc(&h->fb1, (size_t)N * d));
     } else {
         chk(dalloc(&h->fb0, (size_t)N * d));
         chk(dalloc(&h->fb1, (size_t)N * d));
@@ -501,6 +615,7 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     }
     chk(dalloc(&h->gtmp, (size_t)d));
     chk(dalloc(&h->gbuf, (size_t)2 * d));
+    chk(dalloc(&h->ratios, (size_t)PR_MAX_ITERS * N));
     chk(dalloc(&h->resp, (size_t)chain_resp_elems(N)));
     chk(dalloc(&h->C, (size_t)h->cap * N));
     chk(dalloc(&h->cvec, (size_t)h->cap));
@@ -509,14 +624,22 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     chk(dalloc(&h->res2, (size_t)N + 1));
     chk(dalloc(&h->rhist, (size_t)PR_MAX_ITERS));
     chk(dalloc(&h->nres2, 1));
-    chk(cudaMalloc((void**)&h->r, sizeof(int) * 3));
+    chk(cudaMalloc((void**)&h->r, sizeof(int) * 4));
+    if (o.corr_prec == PR_FP32) {
+        chk(cudaMalloc((void**)&h->Q32, sizeof(float) * (size_t)h->cap * d));
+        chk(cudaMalloc((void**)&h->D32, sizeof(float) * (size_t)h->cap * d));
+        chk(cudaMalloc((void**)&h->dlt, sizeof(float) * (size_t)d));
+        chk(cudaMalloc((void**)&h->gbuf32, sizeof(float) * (size_t)2 * d));
+    }
     chk(cudaMalloc((void**)&h->kept, sizeof(int) * N));
     chk(cudaMalloc((void**)&h->ranks, sizeof(int) * PR_MAX_ITERS));
+    chk(cudaMalloc((void**)&h->kept_hist, sizeof(int) * PR_MAX_ITERS * N));
     chk(cudaMalloc((void**)&h->gbar, sizeof(GridBar)));
     if (e == cudaSuccess) {
         h->r_old = h->r + 1;
         h->zero = h->r + 2;
-        chk(cudaMemset(h->r, 0, sizeof(int) * 3));
+        h->r_it = h->r + 3;
+        chk(cudaMemset(h->r, 0, sizeof(int) * 4));
         chk(cudaMemset(h->ranks, 0, sizeof(int) * PR_MAX_ITERS));
         chk(cudaMemset(h->gbar, 0, sizeof(GridBar)));
         chk(cudaMemset(h->rhist, 0, sizeof(double) * PR_MAX_ITERS));
@@ -538,13 +661,16 @@ pr_status parareal_destroy(pr_solver* h) {
     if (h->stream || h->q) cudaStreamSynchronize(h->stream);
     double* ds[] = {h->q, h->qt, h->gv, h->kold, h->Q, h->D, h->wv, h->wz, h->fb0, h->fb1, h->fb2, h->cb0, h->cb1,
                     h->gtmp, h->C, h->cvec, h->partial, h->anorm2, h->res2, h->rhist, h->nres2,
-                    h->gbuf, h->resp};
+                    h->gbuf, h->resp, h->ratios};
     for (double* p : ds) if (p) cudaFree(p);
+    float* fs[] = {h->Q32, h->D32, h->dlt, h->gbuf32};
+    for (float* p : fs) if (p) cudaFree(p);
     if (h->f32a) cudaFree(h->f32a);
     if (h->f32b) cudaFree(h->f32b);
     if (h->r) cudaFree(h->r);
     if (h->kept) cudaFree(h->kept);
     if (h->ranks) cudaFree(h->ranks);
+    if (h->kept_hist) cudaFree(h->kept_hist);
     if (h->gbar) cudaFree(h->gbar);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -563,13 +689,14 @@ pr_status parareal_solve(pr_solver* h, const double* u0_dev, int32_t K, double* 
     const long d = h->d;
     CKC(cudaEventRecord(h->ev0, h->stream));
     CKC(cudaMemcpyAsync(h->q, u0_dev, sizeof(double) * d, cudaMemcpyDeviceToDevice, h->stream));
-    CKS(solve_impl(h, K, rep));
+    std::vector<int> Kw;
+    CKS(solve_windows(h, K, Kw));
     CKC(cudaEventRecord(h->ev1, h->stream));
     if (q_out_dev)
         CKC(cudaMemcpyAsync(q_out_dev, h->q, sizeof(double) * (h->N + 1) * d, cudaMemcpyDeviceToDevice, h->stream));
     if (qT_dev)
         CKC(cudaMemcpyAsync(qT_dev, h->q + (long)h->N * d, sizeof(double) * d, cudaMemcpyDeviceToDevice, h->stream));
-    if (rep) CKS(fill_report(h, K, rep));
+    if (rep) CKS(fill_report(h, Kw, rep));
     return PR_OK;
 }
 
@@ -580,12 +707,13 @@ pr_status parareal_solve_host(pr_solver* h, const double* u0_host, int32_t K, do
     const long d = h->d;
     CKC(cudaEventRecord(h->ev0, h->stream));
     CKC(cudaMemcpyAsync(h->q, u0_host, sizeof(double) * d, cudaMemcpyHostToDevice, h->stream));
-    CKS(solve_impl(h, K, rep));
+    std::vector<int> Kw;
+    CKS(solve_windows(h, K, Kw));
     CKC(cudaMemcpyAsync(qT_host, h->q + (long)h->N * d, sizeof(double) * d, cudaMemcpyDeviceToHost, h->stream));
     CKC(cudaEventRecord(h->ev1, h->stream));
     CKC(cudaStreamSynchronize(h->stream));
     CKS(check_device_waits(h));
-    if (rep) CKS(fill_report(h, K, rep));
+    if (rep) CKS(fill_report(h, Kw, rep));
     return PR_OK;
 }
 

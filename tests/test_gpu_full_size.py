@@ -1,0 +1,107 @@
+"""The benchmark workload (256x128, N = 32, K = 6, cap 192, three seeded ICs)
+against oracle reference values stored by tests/golden/make_oracle_reference.py.
+
+Forming F(Q) by linearity (Eq. Genhance) divides rounding errors by the
+residual ratios |R_jj|/||a_j|| of the new columns, and the errors compound
+from column to column.  Where every kept ratio of the iterations that feed a
+correction is >= 1e-3 (the Gaussian IC) the GPU's FP64 solve must reproduce
+the oracle: r^k to 1e-9 relative, q_N^K samples to 1e-11 of ||q_N||.  The
+filtered-noise IC's last iterations keep ratios down to 3e-4 (r^k to 1e-6).
+The Fourier IC keeps ratios down to 5e-6 from the first iteration on, so two
+correct FP64 evaluations of the method legitimately drift apart; for it the
+results must be finite, of the oracle's size, and the error against the
+serial fine solution within a decade of the oracle's.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_1510_02237_gb300")
+
+pytestmark = pytest.mark.gpu
+
+REF = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_256x128_N32_K6.json")
+
+
+@pytest.fixture(scope="module")
+def ref():
+    import __graft_entry__ as g
+    g.build()
+    torch.cuda.set_device(0)
+    with open(REF) as fh:
+        return json.load(fh)
+
+
+def _solve(p, q0, K, cap, **opt):
+    with P.Solver(p, stream=torch.cuda.current_stream(), K_max=K, krylov_cap=cap, **opt) as s:
+        out = torch.empty(p.d, dtype=torch.float64, device="cuda")
+        rep = P.parareal_solve(s.h, torch.from_numpy(q0).cuda(), K, qT=out)
+        qs = torch.from_numpy(q0).cuda()
+        for _ in range(p.n_slices):
+            nxt = torch.empty_like(qs)
+            P.parareal_fine_sweep(s.h, qs, nxt, 1)
+            qs = nxt
+        torch.cuda.synchronize()
+        return out.cpu().numpy(), qs.cpu().numpy(), rep
+
+
+@pytest.mark.parametrize("ic", [0, 1, 2], ids=["gaussian+noise", "fourier8", "filtered_noise16"])
+def test_fp64_solve_against_oracle_reference(ref, ic):
+    wl = W.workload_medium()
+    p = wl.problem
+    name, f = wl.ics[ic]
+    R = ref["ics"][name]
+    idx = np.array(ref["sample_indices"])
+    got, qs, rep = _solve(p, f().ravel(), wl.K, wl.krylov_cap)
+    r = np.array(rep.r[:wl.K])
+    assert list(rep.rank[:wl.K]) == R["rank"]
+    # the serial fine solution is well conditioned: always within 1e-12
+    assert np.max(np.abs(qs[idx] - np.array(R["qseq_sample"]))) < 1e-12 * R["qseq_norm"]
+    # the first iteration's columns (the coarse chain) are the oracle's: same conditioning
+    assert abs(rep.min_ratio[0] - R["min_kept_ratio"][0]) < 1e-4 * R["min_kept_ratio"][0]
+    worst = min(R["min_kept_ratio"][:wl.K - 1])
+    if worst >= 1e-4:
+        assert np.allclose(np.array(rep.min_ratio[:wl.K]), R["min_kept_ratio"], rtol=1e-3)
+    if worst >= 1e-3:
+        assert np.allclose(r, R["r"], rtol=1e-9, atol=0)
+        assert np.max(np.abs(got[idx] - np.array(R["qN_sample"]))) < 1e-11 * R["qN_norm"]
+    elif worst >= 1e-4:
+        assert np.allclose(r, R["r"], rtol=1e-6, atol=0)
+        assert np.max(np.abs(got[idx] - np.array(R["qN_sample"]))) < 1e-7 * R["qN_norm"]
+    else:
+        assert np.all(np.isfinite(got)) and np.linalg.norm(got) < 10 * R["qN_norm"]
+        eps = np.linalg.norm(got - qs) / np.linalg.norm(qs)
+        assert 0.1 * R["eps"] < eps < 10 * R["eps"]
+
+
+@pytest.mark.parametrize("ic", [0, 1, 2], ids=["gaussian+noise", "fourier8", "filtered_noise16"])
+def test_mixed_and_direct_images_accuracy(ref, ic):
+    """Direct images (FP64) and the mixed-precision solve (FP32 fine sweep and
+    correction, direct FP32 images, FP64 Gram-Schmidt).  For the Gaussian IC
+    the error against the serial fine solution moves by <= 1e-5 (measured
+    4e-8).  The filtered-noise IC excites the band in which the coarse step
+    grows by 1.09 per step (see the oracle pins), so FP32 rounding in the
+    correction is amplified ~1.09^62 along the chain (measured 3.7e-5); the
+    Fourier IC's nearly dependent iterates make the subspace itself
+    sensitive (eps/ratio).  Those two are held to <= 1e-4 and to the size of
+    the oracle's error respectively."""
+    wl = W.workload_medium()
+    p = wl.problem
+    name, f = wl.ics[ic]
+    R = ref["ics"][name]
+    q0 = f().ravel()
+    g64, qs, rep64 = _solve(p, q0, wl.K, wl.krylov_cap, images=P.PR_IMAGES_DIRECT)
+    gmx, _, repmx = _solve(p, q0, wl.K, wl.krylov_cap, fine_prec=P.PR_FP32, corr_prec=P.PR_FP32)
+    assert np.all(np.isfinite(g64)) and np.all(np.isfinite(gmx))
+    e64 = np.linalg.norm(g64 - qs) / np.linalg.norm(qs)
+    emx = np.linalg.norm(gmx - qs) / np.linalg.norm(qs)
+    budget = {0: 1e-5, 1: 10 * R["eps"], 2: 1e-4}[ic]
+    assert abs(e64 - emx) <= budget, (e64, emx)
+    assert list(rep64.rank[:wl.K]) == list(repmx.rank[:wl.K]) == R["rank"]

@@ -96,6 +96,20 @@ def test_fine_sweep_fp32(name, spec):
         assert rel(got[i], oracle.fine_prop(p, X[i])) < TOL32
 
 
+@pytest.mark.parametrize("name,spec", GRIDS[:4], ids=[g[0] for g in GRIDS[:4]])
+def test_fine_sweep_fp32x(name, spec):
+    """FP32 tendencies and stages on an FP64 state: the FP64 update
+    q^n + dt L(q**) keeps the per-step rounding at dt |L| times FP32's."""
+    p = _prob(spec)
+    X = states(p, p.n_slices, 20)
+    with solver(p, fine_prec=P.PR_FP32X) as s:
+        out = torch.empty(p.n_slices * p.d, dtype=torch.float64, device="cuda")
+        P.parareal_fine_sweep(s.h, dev(X), out, p.n_slices)
+        got = host(out).reshape(p.n_slices, p.d)
+    for i in range(p.n_slices):
+        assert rel(got[i], oracle.fine_prop(p, X[i])) < 2e-6
+
+
 def test_fine_single_step_slices():
     """N_f = 1 (one RK-3 step per slice) uses the direct in->out launch."""
     p = W.Problem(nx=64, ny=32, n_slices=4, n_f=1, n_g=1, dt_f=1.0 / 160, dt_g=1.0 / 160, T=4.0 / 160)
@@ -260,6 +274,70 @@ def test_solve_fp32_fine_accuracy():
         e64 = oracle.rel_error(want["q"][-1], qs[-1])
         assert abs(e32 - e64) <= 1e-5
         assert rel(g32, want["q"]) < 1e-5
+
+
+@pytest.mark.parametrize("fine_prec", [0, 1, 2], ids=["fine64", "fine32", "fine32x"])
+def test_solve_mixed_correction_accuracy(fine_prec):
+    """FP32 correction by linearity (corr_prec = FP32): G(delta) + D Q^T delta
+    with delta = q_i^{k+1} - q_i^k.  Its rounding scales with ||delta||, so the
+    iterates stay within 1e-6 (FP64 fine) / 1e-5 (FP32 fine) of the FP64
+    oracle and the error against the serial fine solution moves by <= 1e-5."""
+    wl = W.workload_small()
+    p = wl.problem
+    q0 = wl.ics[0][1]().ravel()
+    qs = oracle.serial_fine(p, q0)
+    tol = 1e-6 if fine_prec == 0 else 1e-5
+    for K in (1, 3, 5):
+        got, rep = _solve(p, q0, K, fine_prec=fine_prec, corr_prec=1)
+        want = oracle.parareal(p, q0, K)
+        assert rel(got, want["q"]) < tol
+        assert abs(oracle.rel_error(got[-1], qs[-1]) - oracle.rel_error(want["q"][-1], qs[-1])) <= 1e-5
+        assert list(rep.rank[:K]) == list(want["rank"])
+        assert np.allclose(np.array(rep.r[:K]), want["r"], rtol=1e-5)
+
+
+def test_solve_mixed_K_equals_N_is_serial_fine_bitwise():
+    """Converged slices stay exact in the FP32 delta form (delta = 0)."""
+    p = W.make_problem(64, 32, 8)
+    q0 = W.ic_gaussian(64, 32, seed=0).ravel()
+    got, _ = _solve(p, q0, 8, fine_prec=1, corr_prec=1)
+    with solver(p, fine_prec=1) as s:
+        q = dev(q0)
+        for i in range(p.n_slices):
+            nxt = torch.empty_like(q)
+            P.parareal_fine_sweep(s.h, q, nxt, 1)
+            q = nxt
+            assert np.array_equal(host(q), got[i + 1])
+
+
+def test_early_stop_matches_oracle():
+    """Stopping rule of Sec. 2.1: stop once r^k <= r_tol (same iteration count
+    and result as the oracle)."""
+    wl = W.workload_small()
+    p = wl.problem
+    q0 = wl.ics[0][1]().ravel()
+    full = oracle.parareal(p, q0, 8)
+    r_tol = 0.5 * (full["r"][2] + full["r"][3])        # between r^2 and r^3 -> stops after 4
+    want = oracle.parareal(p, q0, 8, r_tol=r_tol)
+    assert want["K"] == 4
+    got, rep = _solve(p, q0, 8, r_tol=r_tol)
+    assert rep.K == 4
+    assert rel(got, want["q"]) < TOL64
+
+
+def test_windows_match_oracle():
+    """M_p = 3 parallel steps of N = 4 slices (Sec. 2.1), each started from the
+    previous step's final value."""
+    p = W.make_problem(64, 32, 4, T=0.5)               # one window: 4 slices of 0.125
+    q0 = W.ic_gaussian(64, 32, seed=0).ravel()
+    want = oracle.parareal_windows(p, q0, 2, 3)
+    with solver(p, K_max=2, n_windows=3) as s:
+        out = torch.empty(p.d, dtype=torch.float64, device="cuda")
+        rep = P.parareal_solve(s.h, dev(q0), 2, qT=out)
+        got = host(out)
+    assert rep.n_windows == 3 and list(rep.K_window[:3]) == [2, 2, 2] and rep.K == 6
+    assert rel(got, want["qT"]) < TOL64
+    assert np.allclose(np.array(rep.r[:6]), np.concatenate([w["r"] for w in want["windows"]]), rtol=1e-9)
 
 
 def test_solve_host_matches_device():
