@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-stream sweep")
     ap.add_argument("--case", choices=["fine", "solve"], default=None,
                     help="small isolated case for profiler captures: 'fine' = three fine sweeps over all "
                          "32 slices of the 256x128 workload; 'solve' = two solves of its first IC")
@@ -211,6 +212,84 @@ def rel_l2(a, b):
 
 def torch_norm(x):
     return x.double().norm().item()
+
+
+def batching_workload(P, torch):
+    """64 independent uneven instances (grids 64x32..256x128, N 8..32, K <= N/2,
+    U in [0.05, 0.2]; FP32 fine sweep on an FP64 state, FP64 correction):
+    solved one after another on one stream with every SM available, then all
+    together as one CUDA graph whose branches run on per-instance streams with
+    SM-limited grid-synchronised kernels.  Each is timed with CUDA events after
+    one untimed pass; the results of the two are compared bit for bit."""
+    from paper_1510_02237_gb300.serve import default_sm_limit
+    insts = W.workload_batch(64)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    opt = {"fine_prec": P.PR_FP32X}
+    u0s = [torch.from_numpy(i.initial_value().ravel()).cuda() for i in insts]
+    res = {"instances": len(insts), "solves": len(insts), "fine_prec": "f32 tendencies, f64 state",
+           "corr_prec": "f64", "cells_total": int(sum(i.problem.ncell for i in insts)),
+           "fine_cell_steps_total": float(sum(sum(i.problem.n_slices - k for k in range(i.K)) * i.problem.n_f
+                                              * i.problem.ncell for i in insts))}
+    main = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # sequential, all SMs per solve
+    seq = [P.Solver(i.problem, stream=main, K_max=i.K, **opt) for i in insts]
+    outs_a = [torch.empty_like(u) for u in u0s]
+    for rep in range(2):
+        torch.cuda.synchronize()
+        e0.record(main)
+        for s, i, u, o in zip(seq, insts, u0s, outs_a):
+            P.parareal_solve(s.h, u, i.K, qT=o, report=False)
+        e1.record(main)
+        torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    for s in seq:
+        s.close()
+    # one graph, per-instance streams and SM limits
+    streams = [P.new_stream() for _ in insts]
+    bat = [P.Solver(i.problem, stream=st, K_max=i.K, sm_limit=default_sm_limit(i.problem.d, sms), **opt)
+           for i, st in zip(insts, streams)]
+    outs_b = [torch.empty_like(u) for u in u0s]
+    side = P.new_stream()
+    g = P.parareal_batch_create([s.h for s in bat], u0s, [i.K for i in insts], outs_b, side)
+    for rep in range(2):
+        torch.cuda.synchronize()
+        e0.record(side)
+        P.parareal_batch_launch(g)
+        e1.record(side)
+        torch.cuda.synchronize()
+    ms_bat = e0.elapsed_time(e1)
+    P.parareal_batch_destroy(g)
+    # the same SM limits without concurrency, for the bitwise comparison
+    same = 0
+    for s, i, u, o in zip(bat, insts, u0s, outs_b):
+        ref = torch.empty_like(u)
+        P.parareal_solve(s.h, u, i.K, qT=ref, report=False)
+        torch.cuda.synchronize()
+        same += int(torch.equal(ref, o))
+    for s in bat:
+        s.close()
+    res.update({"ms_sequential": ms_seq, "ms_batched_graph": ms_bat,
+                "solves_per_s_sequential": len(insts) / (ms_seq / 1e3),
+                "solves_per_s_batched": len(insts) / (ms_bat / 1e3), "speedup": ms_seq / ms_bat,
+                "results_bitwise_equal_alone": f"{same}/{len(insts)}"})
+    return res
+
+
+def serving_workload(P, torch, rates=(10, 30, 100, 300, 1000), n_req=120):
+    """Poisson request streams (seed 7) of solves with grids 64x32..512x256,
+    N 8..64, K 1..5, served in mixed precision with continuous batching under a
+    150 GB footprint budget; per rate the p50/p99 latency (arrival to result in
+    host memory) and the completed solves per second."""
+    from paper_1510_02237_gb300 import serve
+    out = {"requests_per_rate": n_req, "budget_bytes": 150e9, "mode": "mixed", "rates": {}}
+    srv = serve.Server(budget_bytes=150e9, max_inflight=16, mode="mixed")
+    srv.run(W.request_stream(1000.0, 8, seed=99))          # create slots untimed
+    for lam in rates:
+        _, st = srv.run(W.request_stream(float(lam), n_req, seed=7))
+        out["rates"][str(lam)] = st.summary()
+    srv.close()
+    return out
 
 
 def precision_workload(P, torch, stream):
@@ -377,6 +456,8 @@ def run_ours(args):
     line = None
     if rank == 0:
         precision = precision_workload(P, torch, stream)
+        batching = batching_workload(P, torch)
+        serving = serving_workload(P, torch) if not args.no_serving else None
         # ---- roofline of the dominant phase's kernel
         phases = {k: tm[k] / n for k in ("ms_init", "ms_fine", "ms_coarse", "ms_krylov", "ms_gs_block",
                                           "ms_gs_intra", "ms_kold", "ms_chain")}
@@ -421,6 +502,8 @@ def run_ours(args):
             "fp64_fma_tflops": peak,
             "mixed": mixed,
             "precision_workload": precision,
+            "batching": batching,
+            "serving": serving,
         }
         print(json.dumps(line))
     s.close()

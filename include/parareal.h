@@ -94,6 +94,9 @@ typedef struct {
                               column), rounding error independent of the
                               conditioning.  corr_prec = PR_FP32 and fine_prec
                               other than PR_FP64 always use PR_IMAGES_DIRECT.    */
+    int32_t sm_limit;      /* > 0: the handle's grid-synchronised kernels use at
+                              most this many SMs, so solves of several handles on
+                              different streams run side by side (0: all SMs)    */
     void* stream;          /* cudaStream_t, or NULL                              */
 } pr_options;
 
@@ -227,6 +230,30 @@ pr_status parareal_timing_read(pr_solver* h, pr_timing* t, int32_t reset);
  * x 32 FMAs per thread), the denominator of the ALU roofline.  Allocates a
  * small device buffer, synchronises the legacy default stream. */
 pr_status parareal_alu_probe(int32_t prec, int32_t iters, double* flops_per_s);
+
+/* ---- batches of independent solves (no counterpart in the paper: the
+ *      instances are independent problems; this only schedules them) ---- */
+
+/* Solve n independent problems side by side: each handle's solve is
+ * enqueued on the handle's own stream (handles must have distinct non-NULL
+ * streams to overlap; use pr_options.sm_limit so their grid-synchronised
+ * kernels fit next to each other), then every stream is synchronised.
+ * u0_dev[i], qT_dev[i]: device, d_i doubles; K[i] iterations. */
+pr_status parareal_solve_batch(pr_solver* const* hs, int32_t n, const double* const* u0_dev, const int32_t* K,
+                               double* const* qT_dev);
+
+typedef struct pr_batch pr_batch;
+/* Capture the n solves of parareal_solve_batch (same arguments, which stay
+ * bound to the batch: refill u0_dev[i] before each launch) into one CUDA
+ * graph that forks from `stream` into the handles' streams and joins back.
+ * Handles must be distinct, with non-NULL streams other than `stream`;
+ * handles sharing a stream run one after the other.  Requires r_tol = 0 on
+ * every handle.  Allocates the graph only. */
+pr_status parareal_batch_create(pr_solver* const* hs, int32_t n, const double* const* u0_dev, const int32_t* K,
+                                double* const* qT_dev, void* stream, pr_batch** out);
+/* Enqueue one replay of the batch graph on its stream (asynchronous). */
+pr_status parareal_batch_launch(pr_batch* b);
+pr_status parareal_batch_destroy(pr_batch* b);
 
 /* Allocation-free fine sweep, for callers that cannot allocate device memory
  * where they need F: code running while a stream is captured into a CUDA

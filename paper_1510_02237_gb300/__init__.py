@@ -33,7 +33,7 @@ class pr_options(C.Structure):
                 ("K_max", C.c_int32), ("krylov_cap", C.c_int32), ("drop_tol", C.c_double),
                 ("fine_prec", C.c_int32), ("variant", C.c_int32), ("corr_prec", C.c_int32),
                 ("r_tol", C.c_double), ("n_windows", C.c_int32), ("images", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("sm_limit", C.c_int32), ("stream", C.c_void_p)]
 
 
 class pr_report(C.Structure):
@@ -62,7 +62,8 @@ EXPORTS = ["parareal_default_options", "parareal_create", "parareal_destroy", "p
            "parareal_footprint_bytes", "parareal_solve", "parareal_solve_host", "parareal_fine_sweep",
            "parareal_coarse_sweep", "parareal_coarse_apply", "krylov_reset", "krylov_update", "krylov_rank",
            "krylov_project", "parareal_timing_enable", "parareal_timing_read", "parareal_kernel_launches",
-           "parareal_alu_probe", "parareal_fine_sweep_static", "parareal_selftest_wait_timeout"]
+           "parareal_alu_probe", "parareal_fine_sweep_static", "parareal_selftest_wait_timeout",
+           "parareal_solve_batch", "parareal_batch_create", "parareal_batch_launch", "parareal_batch_destroy"]
 
 _lib = None
 
@@ -119,6 +120,15 @@ def lib():
     L.parareal_fine_sweep_static.restype = st
     L.parareal_selftest_wait_timeout.argtypes = [P, C.POINTER(C.c_double)]
     L.parareal_selftest_wait_timeout.restype = st
+    PP = C.POINTER(C.c_void_p)
+    L.parareal_solve_batch.argtypes = [PP, C.c_int32, PP, C.POINTER(C.c_int32), PP]
+    L.parareal_solve_batch.restype = st
+    L.parareal_batch_create.argtypes = [PP, C.c_int32, PP, C.POINTER(C.c_int32), PP, P, C.POINTER(P)]
+    L.parareal_batch_create.restype = st
+    L.parareal_batch_launch.argtypes = [P]
+    L.parareal_batch_launch.restype = st
+    L.parareal_batch_destroy.argtypes = [P]
+    L.parareal_batch_destroy.restype = st
     _lib = L
     return L
 
@@ -238,6 +248,55 @@ def parareal_alu_probe(prec=PR_FP64, iters=4096) -> float:
     v = C.c_double()
     _check(None, lib().parareal_alu_probe(int(prec), int(iters), C.byref(v)))
     return v.value
+
+
+def _ptr_array(xs):
+    arr = (C.c_void_p * len(xs))()
+    for i, x in enumerate(xs):
+        arr[i] = x.value if isinstance(x, C.c_void_p) else (x.data_ptr() if hasattr(x, "data_ptr") else int(x))
+    return arr
+
+
+_cudart = None
+
+
+def new_stream():
+    """A dedicated non-blocking CUDA stream (torch.cuda.Stream() recycles a
+    pool of 32), wrapped as a torch.cuda.ExternalStream."""
+    global _cudart
+    import torch
+    if _cudart is None:
+        lib()
+        _cudart = C.CDLL("libcudart.so.13")
+        _cudart.cudaStreamCreateWithFlags.argtypes = [C.POINTER(C.c_void_p), C.c_uint]
+    s = C.c_void_p()
+    if _cudart.cudaStreamCreateWithFlags(C.byref(s), 1) != 0:
+        raise PararealError(PR_ECUDA, "cudaStreamCreateWithFlags failed")
+    return torch.cuda.ExternalStream(s.value)
+
+
+def parareal_solve_batch(hs, u0s, Ks, qTs):
+    n = len(hs)
+    _check(None, lib().parareal_solve_batch(_ptr_array(hs), n, _ptr_array(u0s), (C.c_int32 * n)(*Ks),
+                                            _ptr_array(qTs)))
+
+
+def parareal_batch_create(hs, u0s, Ks, qTs, stream):
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    n = len(hs)
+    b = C.c_void_p()
+    _check(None, lib().parareal_batch_create(_ptr_array(hs), n, _ptr_array(u0s), (C.c_int32 * n)(*Ks),
+                                             _ptr_array(qTs), C.c_void_p(stream), C.byref(b)))
+    return b
+
+
+def parareal_batch_launch(b):
+    _check(None, lib().parareal_batch_launch(b))
+
+
+def parareal_batch_destroy(b):
+    _check(None, lib().parareal_batch_destroy(b))
 
 
 def parareal_selftest_wait_timeout(stream=None):

@@ -169,7 +169,8 @@ long chain_resp_elems(int n_slices) { return (long)(n_slices + 1) * 1024; }
 cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s) {
     if (a.i_end <= a.i_begin) return cudaSuccess;
     const bool delta = a.dlt != nullptr;
-    const int nb = delta ? chain_grid<true>(a.H, a.ccap) : chain_grid<false>(a.H, a.ccap);
+    int nb = delta ? chain_grid<true>(a.H, a.ccap) : chain_grid<false>(a.H, a.ccap);
+    if (a.max_blocks > 0 && nb > a.max_blocks) nb = a.max_blocks;
     if (nb < 1 || nb > 1024) return cudaErrorInvalidConfiguration;
     const size_t smem = chain_smem_bytes(a.H, a.ccap, delta);
     const void* fn = delta ? (const void*)k_chain<true> : (const void*)k_chain<false>;

@@ -11,10 +11,17 @@ constexpr int CTX = 32, CTY = 16, CNT = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(CNT) k_coarse_step(const double* __restrict__ in, double* __restrict__ out,
-                                                     long stride, int nx, int ny, CoarseCoef c, int H) {
+                                                     long stride, int nx, int ny, CoarseCoef c, int H, SliceMap map) {
     extern __shared__ __align__(16) unsigned char smc[];
-    coarse_tile<CTX, CTY, CNT, T>(in + (long)blockIdx.z * stride, out + (long)blockIdx.z * stride, nx, ny, c, H,
-                                  blockIdx.x * CTX, blockIdx.y * CTY, reinterpret_cast<T*>(smc));
+    long zi = blockIdx.z, zo = blockIdx.z;
+    if (map.end) {
+        const int b0 = *map.beg;
+        if ((int)blockIdx.z >= *map.end - b0) return;
+        if (map.in_map) zi += b0;
+        if (map.out_map) zo += b0;
+    }
+    coarse_tile<CTX, CTY, CNT, T>(in + zi * stride, out + zo * stride, nx, ny, c, H, blockIdx.x * CTX,
+                                  blockIdx.y * CTY, reinterpret_cast<T*>(smc));
 }
 
 }  // namespace
@@ -22,7 +29,7 @@ __global__ void __launch_bounds__(CNT) k_coarse_step(const double* __restrict__ 
 int coarse_halo(const CoarseCoef& c) { return (c.order == 1 ? 1 : 2) + 2 * c.n_sound - 1; }
 
 cudaError_t launch_coarse_step(const double* in, double* out, long stride, int n, int nx, int ny,
-                               const CoarseCoef& c, cudaStream_t s, bool fp32) {
+                               const CoarseCoef& c, cudaStream_t s, bool fp32, const SliceMap& map) {
     const int H = coarse_halo(c);
     if (H > COARSE_MAXH) return cudaErrorInvalidValue;
     dim3 grid((nx + CTX - 1) / CTX, (ny + CTY - 1) / CTY, n);
@@ -31,12 +38,12 @@ cudaError_t launch_coarse_step(const double* in, double* out, long stride, int n
         const size_t smem = sizeof(float) * elems;
         cudaError_t e = cudaFuncSetAttribute(k_coarse_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_coarse_step<float><<<grid, CNT, smem, s>>>(in, out, stride, nx, ny, c, H);
+        k_coarse_step<float><<<grid, CNT, smem, s>>>(in, out, stride, nx, ny, c, H, map);
     } else {
         const size_t smem = sizeof(double) * elems;
         cudaError_t e = cudaFuncSetAttribute(k_coarse_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_coarse_step<double><<<grid, CNT, smem, s>>>(in, out, stride, nx, ny, c, H);
+        k_coarse_step<double><<<grid, CNT, smem, s>>>(in, out, stride, nx, ny, c, H, map);
     }
     count_launches(1);
     return cudaGetLastError();

@@ -46,22 +46,34 @@ struct CoarseCoef {
 // ------------------------------------------------------------ launchers
 // Each returns a cudaError_t from the launch.
 
+// Optional device-side slice mapping of a batched launch: slices z >= *end -
+// *beg are skipped; with in_map (out_map) the input (output) slice is
+// *beg + z instead of z.  Lets a launch act on a column range the host does
+// not know (e.g. the columns the last subspace update kept).
+struct SliceMap {
+    const int* beg = nullptr;
+    const int* end = nullptr;
+    bool in_map = false, out_map = false;
+};
+
 // One RK-3 step on n states.  in/out element types select FP64 or FP32
 // arithmetic (T) with conversion at the boundary.  instride/outstride are
 // element strides between consecutive states.
 template <typename T, typename Tin, typename Tout>
 cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outstride, int n, int nx,
-                             int ny, bool has_v, const FineCoef<T>& c, cudaStream_t s);
+                             int ny, bool has_v, const FineCoef<T>& c, cudaStream_t s,
+                             const SliceMap& sm = SliceMap());
 
 // One RK-3 step with FP32 tendencies and stages on an FP64 state: the last
 // stage forms q^{n+1} = q^n + dt L(q**) in FP64 (fine_prec = PR_FP32X).
 cudaError_t launch_fine_step_acc64(const double* in, double* out, long stride, int n, int nx, int ny, bool has_v,
-                                  const FineCoef<float>& c, cudaStream_t s);
+                                  const FineCoef<float>& c, cudaStream_t s, const SliceMap& sm = SliceMap());
 
 // One coarse step (slow tendency + n_sound forward-backward substeps) on n
 // states, FP64 arithmetic or FP32 arithmetic (fp32) on FP64 data.
 cudaError_t launch_coarse_step(const double* in, double* out, long stride, int n, int nx, int ny,
-                               const CoarseCoef& c, cudaStream_t s, bool fp32 = false);
+                               const CoarseCoef& c, cudaStream_t s, bool fp32 = false,
+                               const SliceMap& sm = SliceMap());
 int coarse_halo(const CoarseCoef& c);
 
 // -------- tall-skinny FP64 linear algebra over d-long columns (column-major)
@@ -104,6 +116,9 @@ cudaError_t to_fp32_cols(const double* Q, const double* D, float* Q32, float* D3
 // *out = max_i sqrt(res2[i])
 cudaError_t max_sqrt(const double* res2, int n, double* out, cudaStream_t s);
 cudaError_t sub(const double* a, const double* b, double* out, long n, cudaStream_t s);
+// out[(*beg + j) d + i] = a[j d + i] - b[j d + i] for slices j < *end - *beg (at most maxn)
+cudaError_t sub_mapped(const double* a, const double* b, double* out, long d, int maxn, const int* beg,
+                       const int* end, cudaStream_t s);
 cudaError_t fill_int(int* p, int v, int n, cudaStream_t s);
 
 // Grid-barrier state of a cooperative launch (zeroed before each launch).
@@ -118,9 +133,10 @@ struct GridBar {
 // launch.  gb->err != 0 afterwards (sticky) means a barrier wait gave up and
 // the result is invalid.
 // ratio[j] (optional) receives ||residual_j|| / ||a_j||.
+// max_blocks > 0 caps the cooperative grid (one CTA per SM).
 cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2, const int* r_old_dev,
                         int* r_dev, int cap, double eta, double* Q, double* D, int* kept, double* ratio,
-                        const TsWork& w, GridBar* gb, cudaStream_t s);
+                        const TsWork& w, GridBar* gb, cudaStream_t s, int max_blocks = 0);
 
 
 // Serial correction of Alg. 2 over slices [i_begin, i_end) in one cooperative
@@ -151,6 +167,7 @@ struct ChainArgs {
     const float* Q32;     // FP32 copies of Q and D
     const float* D32;
     float* gbuf32;        // 2 x d FP32 coarse ping-pong
+    int max_blocks;       // > 0: cap on the cooperative grid (one CTA per SM)
 };
 cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s);
 long chain_resp_elems(int n_slices);
@@ -170,6 +187,7 @@ struct FineSweepArgs {
     int n, nx, ny, nsteps;
     FineCoefK c;
     GridBar* gb;
+    int max_sms;           // > 0: cap on the SMs used (CTAs = SMs x CTAs per SM)
 };
 cudaError_t fine_sweep_coop(const FineSweepArgs& a, bool has_v, cudaStream_t s);
 

@@ -56,15 +56,22 @@ __device__ __forceinline__ void fine_tend(const T* __restrict__ u, const T* __re
 template <typename T, typename Tin, typename Tout, int RYH, int TX, int TY, int NT, bool ACC64 = false>
 __global__ void __launch_bounds__(NT) k_fine_step(const Tin* __restrict__ in, long instride,
                                                    Tout* __restrict__ out, long outstride, int nx,
-                                                   int ny, FineCoef<T> c) {
+                                                   int ny, FineCoef<T> c, SliceMap map) {
     constexpr int HX = 9, HY = 3 * RYH;
     constexpr int RX = TX + 2 * HX, RY = TY + 2 * HY, NR = RX * RY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* q = reinterpret_cast<T*>(smem_raw);
     T* s = q + 3 * NR;
     const long ncell = (long)nx * ny;
-    const Tin* src = in + (long)blockIdx.z * instride;
-    Tout* dst = out + (long)blockIdx.z * outstride;
+    long zi = blockIdx.z, zo = blockIdx.z;
+    if (map.end) {
+        const int b0 = *map.beg;
+        if ((int)blockIdx.z >= *map.end - b0) return;
+        if (map.in_map) zi += b0;
+        if (map.out_map) zo += b0;
+    }
+    const Tin* src = in + zi * instride;
+    Tout* dst = out + zo * outstride;
     const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
 
     // load the haloed region (periodic wrap)
@@ -149,7 +156,7 @@ __global__ void __launch_bounds__(NT) k_fine_step(const Tin* __restrict__ in, lo
 
 template <typename T, typename Tin, typename Tout, int RYH, int TX, int TY, int NT, bool ACC64 = false>
 cudaError_t launch_tile(const Tin* in, long instride, Tout* out, long outstride, int n, int nx, int ny,
-                        const FineCoef<T>& c, cudaStream_t s) {
+                        const FineCoef<T>& c, cudaStream_t s, const SliceMap& map) {
     constexpr int RX = TX + 18, RY = TY + 6 * RYH;
     constexpr size_t smem = sizeof(T) * 6 * RX * RY;
     auto kern = k_fine_step<T, Tin, Tout, RYH, TX, TY, NT, ACC64>;
@@ -157,7 +164,7 @@ cudaError_t launch_tile(const Tin* in, long instride, Tout* out, long outstride,
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, n);
-    kern<<<grid, NT, smem, s>>>(in, instride, out, outstride, nx, ny, c);
+    kern<<<grid, NT, smem, s>>>(in, instride, out, outstride, nx, ny, c, map);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -166,41 +173,41 @@ cudaError_t launch_tile(const Tin* in, long instride, Tout* out, long outstride,
 
 template <typename T, typename Tin, typename Tout>
 cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outstride, int n, int nx,
-                             int ny, bool has_v, const FineCoef<T>& c, cudaStream_t s) {
+                             int ny, bool has_v, const FineCoef<T>& c, cudaStream_t s, const SliceMap& map) {
     const bool big = nx >= 64 && ny >= 16;
     if (has_v) {
-        if (big) return launch_tile<T, Tin, Tout, 3, 64, 16, 256>(in, instride, out, outstride, n, nx, ny, c, s);
-        return launch_tile<T, Tin, Tout, 3, 32, 8, 256>(in, instride, out, outstride, n, nx, ny, c, s);
+        if (big) return launch_tile<T, Tin, Tout, 3, 64, 16, 256>(in, instride, out, outstride, n, nx, ny, c, s, map);
+        return launch_tile<T, Tin, Tout, 3, 32, 8, 256>(in, instride, out, outstride, n, nx, ny, c, s, map);
     }
-    if (big) return launch_tile<T, Tin, Tout, 1, 64, 16, 256>(in, instride, out, outstride, n, nx, ny, c, s);
-    return launch_tile<T, Tin, Tout, 1, 32, 8, 256>(in, instride, out, outstride, n, nx, ny, c, s);
+    if (big) return launch_tile<T, Tin, Tout, 1, 64, 16, 256>(in, instride, out, outstride, n, nx, ny, c, s, map);
+    return launch_tile<T, Tin, Tout, 1, 32, 8, 256>(in, instride, out, outstride, n, nx, ny, c, s, map);
 }
 
 cudaError_t launch_fine_step_acc64(const double* in, double* out, long stride, int n, int nx, int ny, bool has_v,
-                                  const FineCoef<float>& c, cudaStream_t s) {
+                                  const FineCoef<float>& c, cudaStream_t s, const SliceMap& map) {
     const bool big = nx >= 64 && ny >= 16;
     if (has_v) {
-        if (big) return launch_tile<float, double, double, 3, 64, 16, 256, true>(in, stride, out, stride, n, nx, ny, c, s);
-        return launch_tile<float, double, double, 3, 32, 8, 256, true>(in, stride, out, stride, n, nx, ny, c, s);
+        if (big) return launch_tile<float, double, double, 3, 64, 16, 256, true>(in, stride, out, stride, n, nx, ny, c, s, map);
+        return launch_tile<float, double, double, 3, 32, 8, 256, true>(in, stride, out, stride, n, nx, ny, c, s, map);
     }
-    if (big) return launch_tile<float, double, double, 1, 64, 16, 256, true>(in, stride, out, stride, n, nx, ny, c, s);
-    return launch_tile<float, double, double, 1, 32, 8, 256, true>(in, stride, out, stride, n, nx, ny, c, s);
+    if (big) return launch_tile<float, double, double, 1, 64, 16, 256, true>(in, stride, out, stride, n, nx, ny, c, s, map);
+    return launch_tile<float, double, double, 1, 32, 8, 256, true>(in, stride, out, stride, n, nx, ny, c, s, map);
 }
 
 template cudaError_t launch_fine_step<double, double, double>(const double*, long, double*, long, int,
                                                               int, int, bool, const FineCoef<double>&,
-                                                              cudaStream_t);
+                                                              cudaStream_t, const SliceMap&);
 template cudaError_t launch_fine_step<float, double, float>(const double*, long, float*, long, int, int,
                                                             int, bool, const FineCoef<float>&,
-                                                            cudaStream_t);
+                                                            cudaStream_t, const SliceMap&);
 template cudaError_t launch_fine_step<float, float, float>(const float*, long, float*, long, int, int,
                                                            int, bool, const FineCoef<float>&,
-                                                           cudaStream_t);
+                                                           cudaStream_t, const SliceMap&);
 template cudaError_t launch_fine_step<float, float, double>(const float*, long, double*, long, int, int,
                                                             int, bool, const FineCoef<float>&,
-                                                            cudaStream_t);
+                                                            cudaStream_t, const SliceMap&);
 template cudaError_t launch_fine_step<float, double, double>(const double*, long, double*, long, int,
                                                              int, int, bool, const FineCoef<float>&,
-                                                             cudaStream_t);
+                                                             cudaStream_t, const SliceMap&);
 
 }  // namespace pr

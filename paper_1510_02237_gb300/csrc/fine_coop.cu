@@ -113,17 +113,20 @@ __global__ void __launch_bounds__(FC_NT) k_fine_coop(FineSweepArgs a) {
 }
 
 template <bool HV>
-int coop_blocks() {
-    static int cached[64] = {};
+int coop_blocks(int max_sms) {
+    static int cached[64][2] = {};   // [device] -> (SMs, CTAs per SM)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    if (!cached[dev]) {
+    if (!cached[dev][0]) {
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fine_coop<HV>, FC_NT, 0);
-        cached[dev] = per >= 1 ? sms * per : -1;
+        cached[dev][0] = sms;
+        cached[dev][1] = per;
     }
-    return cached[dev];
+    if (cached[dev][1] < 1) return -1;
+    const int sms = max_sms > 0 && max_sms < cached[dev][0] ? max_sms : cached[dev][0];
+    return sms * cached[dev][1];
 }
 
 }  // namespace
@@ -146,7 +149,7 @@ FineCoefK make_fine_coef_k(double U, double V, double cs, double dx, double dy, 
 }
 
 cudaError_t fine_sweep_coop(const FineSweepArgs& a, bool has_v, cudaStream_t s) {
-    const int nb = has_v ? coop_blocks<true>() : coop_blocks<false>();
+    const int nb = has_v ? coop_blocks<true>(a.max_sms) : coop_blocks<false>(a.max_sms);
     if (nb < 1) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaMemsetAsync(&a.gb->count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;

@@ -270,6 +270,18 @@ __global__ void k_to_fp32_cols(const double* __restrict__ Q, const double* __res
     }
 }
 
+__global__ void k_sub_mapped(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out,
+                             long d, const int* beg, const int* end) {
+    const int j = blockIdx.y;
+    const int b0 = *beg;
+    if (j >= *end - b0) return;
+    double* o = out + (long)(b0 + j) * d;
+    const double* x = a + (long)j * d;
+    const double* y = b + (long)j * d;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < d; i += (long)gridDim.x * blockDim.x)
+        o[i] = x[i] - y[i];
+}
+
 __global__ void k_fill_int(int* p, int v, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -533,9 +545,10 @@ int intra_block_grid() {
 
 cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2, const int* r_old_dev,
                         int* r_dev, int cap, double eta, double* Q, double* D, int* kept, double* ratio,
-                        const TsWork& w, GridBar* gb, cudaStream_t s) {
+                        const TsWork& w, GridBar* gb, cudaStream_t s, int max_blocks) {
     if (m < 1 || m > 64) return cudaErrorInvalidValue;
     int nb = intra_block_grid();
+    if (max_blocks > 0 && nb > max_blocks) nb = max_blocks;
     if (nb < 1) return cudaErrorInvalidConfiguration;
     int pstride = 64;
     if ((long)2 * nb * pstride > w.elems) return cudaErrorInvalidValue;
@@ -556,6 +569,16 @@ cudaError_t to_fp32_cols(const double* Q, const double* D, float* Q32, float* D3
     int nb = cdiv(d, 256);
     if (nb > 256) nb = 256;
     k_to_fp32_cols<<<dim3(nb, maxcols), 256, 0, s>>>(Q, D, Q32, D32, d, c0_dev, c1_dev);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t sub_mapped(const double* a, const double* b, double* out, long d, int maxn, const int* beg,
+                       const int* end, cudaStream_t s) {
+    if (maxn < 1) return cudaSuccess;
+    int nb = cdiv(d, 256);
+    if (nb > 256) nb = 256;
+    k_sub_mapped<<<dim3(nb, maxn), 256, 0, s>>>(a, b, out, d, beg, end);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -133,36 +133,40 @@ static Sizes compute_sizes(int nx, int ny, int N, int K_max, const pr_options& o
 
 // ------------------------------------------------------------------ propagators
 
-static pr_status fine_apply(pr_solver* h, const double* in, double* out, int n) {
+// F on n states.  With a slice map (first: the first step, rest: later steps)
+// only the slices the map admits are propagated (see SliceMap).
+static pr_status fine_apply(pr_solver* h, const double* in, double* out, int n, const SliceMap* first = nullptr,
+                            const SliceMap* rest = nullptr) {
     const long d = h->d;
     const bool hv = h->V != 0.0;
     cudaStream_t s = h->stream;
     const int nf = h->n_f;
+    const SliceMap m0 = first ? *first : SliceMap(), m1 = rest ? *rest : SliceMap();
     if (h->opt.fine_prec == PR_FP32X) {
         const double* a = in;
         for (int st = 0; st < nf; ++st) {
             double* b = st == nf - 1 ? out : (st % 2 == 0 ? h->fb0 : h->fb1);
-            CKC(launch_fine_step_acc64(a, b, d, n, h->nx, h->ny, hv, h->fc32, s));
+            CKC(launch_fine_step_acc64(a, b, d, n, h->nx, h->ny, hv, h->fc32, s, st == 0 ? m0 : m1));
             a = b;
         }
         return PR_OK;
     }
     if (h->opt.fine_prec == PR_FP32) {
         if (nf == 1) {
-            CKC((launch_fine_step<float, double, double>(in, d, out, d, n, h->nx, h->ny, hv, h->fc32, s)));
+            CKC((launch_fine_step<float, double, double>(in, d, out, d, n, h->nx, h->ny, hv, h->fc32, s, m0)));
             return PR_OK;
         }
-        CKC((launch_fine_step<float, double, float>(in, d, h->f32a, d, n, h->nx, h->ny, hv, h->fc32, s)));
+        CKC((launch_fine_step<float, double, float>(in, d, h->f32a, d, n, h->nx, h->ny, hv, h->fc32, s, m0)));
         float* a = h->f32a;
         float* b = h->f32b;
         for (int st = 1; st < nf - 1; ++st) {
-            CKC((launch_fine_step<float, float, float>(a, d, b, d, n, h->nx, h->ny, hv, h->fc32, s)));
+            CKC((launch_fine_step<float, float, float>(a, d, b, d, n, h->nx, h->ny, hv, h->fc32, s, m1)));
             float* t = a; a = b; b = t;
         }
-        CKC((launch_fine_step<float, float, double>(a, d, out, d, n, h->nx, h->ny, hv, h->fc32, s)));
+        CKC((launch_fine_step<float, float, double>(a, d, out, d, n, h->nx, h->ny, hv, h->fc32, s, m1)));
         return PR_OK;
     }
-    if (h->fb2) {
+    if (h->fb2 && !first) {
         FineSweepArgs a{};
         a.in = in;
         a.out = out;
@@ -175,39 +179,42 @@ static pr_status fine_apply(pr_solver* h, const double* in, double* out, int n) 
         a.nsteps = nf;
         a.c = h->fck;
         a.gb = h->gbar;
+        a.max_sms = h->opt.sm_limit;
         CKC(fine_sweep_coop(a, hv, s));
         return PR_OK;
     }
     if (nf == 1) {
-        CKC((launch_fine_step<double, double, double>(in, d, out, d, n, h->nx, h->ny, hv, h->fc64, s)));
+        CKC((launch_fine_step<double, double, double>(in, d, out, d, n, h->nx, h->ny, hv, h->fc64, s, m0)));
         return PR_OK;
     }
-    CKC((launch_fine_step<double, double, double>(in, d, h->fb0, d, n, h->nx, h->ny, hv, h->fc64, s)));
+    CKC((launch_fine_step<double, double, double>(in, d, h->fb0, d, n, h->nx, h->ny, hv, h->fc64, s, m0)));
     double* a = h->fb0;
     double* b = h->fb1;
     for (int st = 1; st < nf - 1; ++st) {
-        CKC((launch_fine_step<double, double, double>(a, d, b, d, n, h->nx, h->ny, hv, h->fc64, s)));
+        CKC((launch_fine_step<double, double, double>(a, d, b, d, n, h->nx, h->ny, hv, h->fc64, s, m1)));
         double* t = a; a = b; b = t;
     }
-    CKC((launch_fine_step<double, double, double>(a, d, out, d, n, h->nx, h->ny, hv, h->fc64, s)));
+    CKC((launch_fine_step<double, double, double>(a, d, out, d, n, h->nx, h->ny, hv, h->fc64, s, m1)));
     return PR_OK;
 }
 
-static pr_status coarse_apply(pr_solver* h, const double* in, double* out, int n, bool fp32 = false) {
+static pr_status coarse_apply(pr_solver* h, const double* in, double* out, int n, bool fp32 = false,
+                              const SliceMap* first = nullptr, const SliceMap* rest = nullptr) {
     const long d = h->d;
     cudaStream_t s = h->stream;
+    const SliceMap m0 = first ? *first : SliceMap(), m1 = rest ? *rest : SliceMap();
     if (h->n_g == 1) {
-        CKC(launch_coarse_step(in, out, d, n, h->nx, h->ny, h->cc, s, fp32));
+        CKC(launch_coarse_step(in, out, d, n, h->nx, h->ny, h->cc, s, fp32, m0));
         return PR_OK;
     }
-    CKC(launch_coarse_step(in, h->cb0, d, n, h->nx, h->ny, h->cc, s, fp32));
+    CKC(launch_coarse_step(in, h->cb0, d, n, h->nx, h->ny, h->cc, s, fp32, m0));
     double* a = h->cb0;
     double* b = h->cb1;
     for (int st = 1; st < h->n_g - 1; ++st) {
-        CKC(launch_coarse_step(a, b, d, n, h->nx, h->ny, h->cc, s, fp32));
+        CKC(launch_coarse_step(a, b, d, n, h->nx, h->ny, h->cc, s, fp32, m1));
         double* t = a; a = b; b = t;
     }
-    CKC(launch_coarse_step(a, out, d, n, h->nx, h->ny, h->cc, s, fp32));
+    CKC(launch_coarse_step(a, out, d, n, h->nx, h->ny, h->cc, s, fp32, m1));
     return PR_OK;
 }
 
@@ -241,7 +248,7 @@ static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, c
         }
         if (j0 == 0) CKC(mark());
         CKC(intra_block(v, z, d, mm, h->anorm2 + j0, h->r_old, h->r, cap, h->opt.drop_tol, h->Q, h->D,
-                        h->kept + j0, ratio ? ratio + j0 : nullptr, w, h->gbar, s));
+                        h->kept + j0, ratio ? ratio + j0 : nullptr, w, h->gbar, s, h->opt.sm_limit));
     }
     return PR_OK;
 }
@@ -251,20 +258,18 @@ static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, c
 // without dividing rounding errors by small residuals |R_jj|).  Mixed
 // precision uses the FP32 propagators and refreshes the FP32 copies of Q
 // and D used by the serial correction.
-static pr_status direct_images(pr_solver* h, bool mixed) {
+static pr_status direct_images(pr_solver* h, bool mixed, int maxn) {
     const long d = h->d;
     cudaStream_t s = h->stream;
-    int rr[2] = {0, 0};
-    CKC(cudaMemcpyAsync(rr, h->r_it, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CKC(cudaMemcpyAsync(rr + 1, h->r, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CKC(cudaStreamSynchronize(h->stream));
-    const int c0 = rr[0], n = rr[1] - rr[0];
-    if (n <= 0) return PR_OK;
-    const double* Qn = h->Q + (long)c0 * d;
-    CKS(fine_apply(h, Qn, h->wv, n));
-    CKS(coarse_apply(h, Qn, h->wz, n, mixed));
-    CKC(sub(h->wv, h->wz, h->D + (long)c0 * d, (long)n * d, s));
-    if (mixed) CKC(to_fp32_cols(h->Q, h->D, h->Q32, h->D32, d, h->r_it, h->r, n, s));
+    // columns [*r_it, *r) of Q: at most maxn, the exact count known only on the device
+    SliceMap first, rest;
+    first.beg = rest.beg = h->r_it;
+    first.end = rest.end = h->r;
+    first.in_map = true;
+    CKS(fine_apply(h, h->Q, h->wv, maxn, &first, &rest));
+    CKS(coarse_apply(h, h->Q, h->wz, maxn, mixed, &first, &rest));
+    CKC(sub_mapped(h->wv, h->wz, h->D, d, maxn, h->r_it, h->r, s));
+    if (mixed) CKC(to_fp32_cols(h->Q, h->D, h->Q32, h->D32, d, h->r_it, h->r, maxn, s));
     return PR_OK;
 }
 
@@ -296,6 +301,7 @@ static ChainArgs chain_args(pr_solver* h, int i_begin, int i_end, const double* 
     a.resp = h->resp;
     a.res2 = res2;
     a.gb = h->gbar;
+    a.max_blocks = h->opt.sm_limit;
     return a;
 }
 
@@ -344,7 +350,7 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
                                 cudaMemcpyDeviceToDevice, s));
             h->M_hist[rbase + k] = M;
             CKC(mark());
-            if (direct) CKS(direct_images(h, mixed));
+            if (direct) CKS(direct_images(h, mixed, M));
             if (!mixed && M > 1) {
                 // K(q_i^k) = G(q_i^k) + D Q^T q_i^k for i = k+1..N-1 with the updated S^k
                 CKC(gemm_tn(h->Q, d, nullptr, h->r, cap, h->q + (long)(a + 1) * d, d, M - 1, d, h->C, cap, w, s));
@@ -490,6 +496,7 @@ pr_status parareal_default_options(pr_options* o) {
     o->r_tol = 0.0;
     o->n_windows = 1;
     o->images = PR_IMAGES_LINEARITY;
+    o->sm_limit = 0;
     o->stream = nullptr;
     return PR_OK;
 }
@@ -516,6 +523,7 @@ static pr_status validate(const pr_grid* g, double U, double c_s, double dt_f, d
     if (!(o.r_tol >= 0) || !is_fin(o.r_tol)) return set_err(h, PR_EINVAL, "r_tol must be >= 0");
     if (o.n_windows < 1 || o.n_windows > 1000000) return set_err(h, PR_EINVAL, "n_windows must be >= 1");
     if (o.images != PR_IMAGES_LINEARITY && o.images != PR_IMAGES_DIRECT) return set_err(h, PR_EINVAL, "images must be PR_IMAGES_LINEARITY or PR_IMAGES_DIRECT");
+    if (o.sm_limit < 0) return set_err(h, PR_EINVAL, "sm_limit must be >= 0");
     if (!(o.drop_tol >= 0) || !is_fin(o.drop_tol)) return set_err(h, PR_EINVAL, "drop_tol must be >= 0");
     if (o.K_max < 0 || o.K_max > PR_MAX_ITERS || o.K_max > N) return set_err(h, PR_EINVAL, "K_max must be in [0, min(N, 128)]");
     if (o.krylov_cap < 0 || o.krylov_cap > 1600) return set_err(h, PR_EINVAL, "krylov_cap must be in [0, 1600]");
@@ -835,5 +843,115 @@ pr_status parareal_timing_read(pr_solver* h, pr_timing* t, int32_t reset) {
 }
 
 uint64_t parareal_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------ batches
+
+pr_status parareal_solve_batch(pr_solver* const* hs, int32_t n, const double* const* u0_dev, const int32_t* K,
+                               double* const* qT_dev) {
+    if (!hs || !u0_dev || !K || !qT_dev || n < 1) return PR_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!hs[i] || !u0_dev[i] || !qT_dev[i] || K[i] < 0 || K[i] > hs[i]->K_max) return PR_EINVAL;
+    for (int i = 0; i < n; ++i) CKS(parareal_solve(hs[i], u0_dev[i], K[i], nullptr, qT_dev[i], nullptr));
+    for (int i = 0; i < n; ++i) {
+        pr_solver* h = hs[i];
+        CKC(cudaStreamSynchronize(h->stream));
+        CKS(check_device_waits(h));
+    }
+    return PR_OK;
+}
+
+}  // extern "C"
+
+struct pr_batch {
+    std::vector<pr_solver*> hs;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> ev;   // fork + one join per handle
+};
+
+static void batch_free(pr_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
+    delete b;
+}
+
+extern "C" {
+
+pr_status parareal_batch_create(pr_solver* const* hs, int32_t n, const double* const* u0_dev, const int32_t* K,
+                                double* const* qT_dev, void* stream, pr_batch** out) {
+    pr_solver* h = nullptr;
+    if (!out) return set_err(h, PR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!hs || !u0_dev || !K || !qT_dev || n < 1) return set_err(h, PR_EINVAL, "NULL or empty batch");
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i] || !u0_dev[i] || !qT_dev[i] || K[i] < 0 || K[i] > hs[i]->K_max)
+            return set_err(h, PR_EINVAL, "invalid batch entry");
+        if (hs[i]->opt.r_tol > 0) return set_err(h, PR_EINVAL, "batch graphs need r_tol = 0");
+        if (!hs[i]->stream || hs[i]->stream == (cudaStream_t)stream)
+            return set_err(h, PR_EINVAL, "every handle needs a non-NULL stream other than the batch stream");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return set_err(h, PR_EINVAL, "handles must be distinct");
+    }
+    pr_batch* b = new (std::nothrow) pr_batch();
+    if (!b) return set_err(h, PR_ENOMEM, "host allocation failed");
+    b->hs.assign(hs, hs + n);
+    b->stream = (cudaStream_t)stream;
+    b->ev.assign((size_t)n + 1, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto& x : b->ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return set_err(h, PR_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    }
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev[0], b->stream);
+    pr_status st = PR_OK;
+    for (int i = 0; i < n && e == cudaSuccess && st == PR_OK; ++i) {
+        e = cudaStreamWaitEvent(hs[i]->stream, b->ev[0], 0);
+        if (e != cudaSuccess) break;
+        st = parareal_solve(hs[i], u0_dev[i], K[i], nullptr, qT_dev[i], nullptr);
+        if (st != PR_OK) break;
+        e = cudaEventRecord(b->ev[i + 1], hs[i]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev[i + 1], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    b->graph = g;
+    if (st != PR_OK || e != cudaSuccess) {
+        std::string msg = st != PR_OK ? std::string("capture of a solve failed: ") + parareal_last_error(hs[0])
+                                      : std::string("stream capture: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        batch_free(b);
+        return set_err(h, st != PR_OK ? st : PR_ECUDA, msg);
+    }
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return set_err(h, PR_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return PR_OK;
+}
+
+pr_status parareal_batch_launch(pr_batch* b) {
+    pr_solver* h = nullptr;
+    if (!b) return PR_EINVAL;
+    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) return set_err(h, PR_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+    return PR_OK;
+}
+
+pr_status parareal_batch_destroy(pr_batch* b) {
+    if (!b) return PR_EINVAL;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    return PR_OK;
+}
 
 }  // extern "C"

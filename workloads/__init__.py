@@ -209,3 +209,57 @@ def workload_large() -> Workload:
 def krylov_bound(n_slices: int, K: int) -> int:
     """Natural bound on dim S^k after K iterations: sum_{k<K} (N - k) new columns."""
     return sum(n_slices - k for k in range(K))
+
+
+# ---------------------------------------------------------------- batches and request streams
+
+@dataclass
+class Instance:
+    """One independent solve of a batch or a request stream."""
+    problem: Problem
+    K: int
+    ic: str              # "gaussian" or "fourier"
+    seed: int
+
+    def initial_value(self) -> np.ndarray:
+        nx, ny = self.problem.nx, self.problem.ny
+        if self.ic == "gaussian":
+            return ic_gaussian(nx, ny, seed=self.seed)
+        return ic_fourier(nx, ny, seed=self.seed, n_modes=8, kmax=8.0)
+
+
+def workload_batch(n: int = 64, seed: int = 1000):
+    """n independent instances: grid uniform in {64x32, 128x64, 256x128},
+    N uniform in {8, 16, 32}, K uniform in 1..N/2, U uniform in [0.05, 0.2],
+    c_s = 1; instance i uses seed 1000+i, Gaussian IC for even i, Fourier
+    modes for odd i."""
+    rng = np.random.default_rng(seed)
+    grids = [(64, 32), (128, 64), (256, 128)]
+    out = []
+    for i in range(n):
+        nx, ny = grids[rng.integers(0, 3)]
+        N = int(rng.choice([8, 16, 32]))
+        K = int(rng.integers(1, N // 2 + 1))
+        U = float(rng.uniform(0.05, 0.2))
+        p = make_problem(nx, ny, N, U=U)
+        out.append(Instance(p, K, "gaussian" if i % 2 == 0 else "fourier", seed + i))
+    return out
+
+
+def request_stream(rate: float, n: int, seed: int = 7):
+    """Poisson request stream: exponential inter-arrival times of mean 1/rate
+    seconds; each request draws a grid uniform in {64x32, 128x64, 256x128,
+    512x256}, N uniform in {8, 16, 32, 64}, K uniform in 1..5 (K <= N), U = 0.1,
+    c_s = 1, and a seeded Gaussian or Fourier IC.  Returns (arrival_s, Instance)."""
+    rng = np.random.default_rng(seed)
+    grids = [(64, 32), (128, 64), (256, 128), (512, 256)]
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        nx, ny = grids[rng.integers(0, 4)]
+        N = int(rng.choice([8, 16, 32, 64]))
+        K = int(min(N, rng.integers(1, 6)))
+        p = make_problem(nx, ny, N)
+        out.append((t, Instance(p, K, "gaussian" if rng.integers(0, 2) == 0 else "fourier", seed * 100000 + i)))
+    return out
