@@ -53,10 +53,10 @@ def _sha(path):
         return hashlib.sha256(f.read()).hexdigest()[:12]
 
 
-# DRAM traffic of one fine RK-3 step launch from an ncu capture of the same
-# kernel source (profiles/fine_step_fp64_256x128_N32.md: 25.2 MB read + 0.04 MB
-# written for 32 x 32768 cells); reported as null once fine.cu changes.
-FINE_TRAFFIC = {"source_sha": "ba315e77be3c", "bytes_per_cell_step": 24.0}
+# DRAM traffic of one FP64 fine-sweep launch from an ncu capture of the same
+# kernel source (profiles/fine_coop_fp64_256x128.md: 26.9 MB read + 652.3 MB
+# written for 31 slices x 32768 cells x 20 steps); null once fine_coop.cu changes.
+FINE_TRAFFIC = {"source_sha": "01539c4e1650", "bytes_per_cell_step": 33.4}
 
 
 def parse():
@@ -465,12 +465,13 @@ def run_ours(args):
         fine_flops = tm["fine_cell_steps"] * FINE_FLOPS_PER_CELL_STEP
         achieved = fine_flops / (tm["ms_fine"] / 1e3) / 1e12
         peak = fp64_peak / 1e12
-        src = os.path.join(ROOT, "paper_1510_02237_gb300", "csrc", "fine.cu")
+        src = os.path.join(ROOT, "paper_1510_02237_gb300", "csrc", "fine_coop.cu")
         traffic = None
         if FINE_TRAFFIC["source_sha"] == _sha(src) and FINE_TRAFFIC["bytes_per_cell_step"]:
             cells_per_launch = tm["fine_cell_steps"] / tm["fine_launches"]
             traffic = FINE_TRAFFIC["bytes_per_cell_step"] * cells_per_launch
-        roof = {"kernel": "k_fine_step<double> (one RK-3 step, stages fused)", "bound": "alu",
+        roof = {"kernel": "k_fine_coop<false> (FP64 fine sweep: all RK-3 stages of all steps, one cooperative launch)",
+                "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": "measured FP64 FMA probe (parareal_alu_probe), same run",
                 "algorithmic_flops_per_cell_step": FINE_FLOPS_PER_CELL_STEP,

@@ -24,6 +24,7 @@
 using namespace pr;
 
 static std::atomic<uint64_t> g_launches{0};
+extern "C" uint64_t parareal_kernel_launches(void);
 void pr::count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 // Ring of CUDA events recording the phase boundaries of up to max_solves solves:
@@ -32,6 +33,7 @@ struct TimingRing {
     int max_solves = 0, per_solve = 0, n = 0;
     std::vector<cudaEvent_t> ev;
     std::vector<int> K;
+    std::vector<long> fine_launches;
 };
 
 struct pr_solver {
@@ -61,6 +63,7 @@ struct pr_solver {
     long partial_elems = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     TimingRing tr;
+    long fine_launch_acc = 0;   // fine-predictor kernel launches of the current solve
     std::string err;
 };
 
@@ -318,6 +321,7 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
     if (h->tr.n < h->tr.max_solves) {
         ev = h->tr.ev.data() + (size_t)h->tr.n * h->tr.per_solve;
         h->tr.K[h->tr.n] = K;
+        h->tr.fine_launches[h->tr.n] = 0;
         h->tr.n += 1;
     }
     int evi = 0;
@@ -336,7 +340,9 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
         const int a = k, M = N - k;
         double* qa = h->q + (long)a * d;
         // parallel predictor: q~_{i+1}^k = F(q_i^k)
+        const uint64_t l0 = parareal_kernel_launches();
         CKS(fine_apply(h, qa, h->qt + (long)a * d, M));
+        if (ev) h->tr.fine_launches[h->tr.n - 1] += (long)(parareal_kernel_launches() - l0);
         CKC(mark());
         // coarse images G(q_i^k) (subspace images and K(q_i^k)); the FP32
         // correction needs neither
@@ -802,6 +808,7 @@ pr_status parareal_timing_enable(pr_solver* h, int32_t max_solves) {
     h->tr.per_solve = 2 + 6 * h->K_max;
     h->tr.ev.assign((size_t)max_solves * h->tr.per_solve, nullptr);
     h->tr.K.assign((size_t)max_solves, 0);
+    h->tr.fine_launches.assign((size_t)max_solves, 0);
     for (auto& e : h->tr.ev) {
         cudaError_t x = cudaEventCreate(&e);
         if (x != cudaSuccess) {
@@ -834,8 +841,8 @@ pr_status parareal_timing_read(pr_solver* h, pr_timing* t, int32_t reset) {
                 t->ms_total += ms;
             }
             t->fine_cell_steps += (double)(h->N - k) * h->n_f * ncell;
-            t->fine_launches += h->n_f;
         }
+        t->fine_launches += h->tr.fine_launches[sidx];
         t->n_solves += 1;
     }
     if (reset) h->tr.n = 0;
