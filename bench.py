@@ -295,8 +295,9 @@ def serving_workload(P, torch, rates=(10, 30, 100, 300, 1000), n_req=120):
 def precision_workload(P, torch, stream):
     """512x256, N = 64, K = 5, power-law Fourier IC: one solve each in plain FP64
     (images by linearity, as in the paper), FP64 with direct images, and mixed
-    precision (FP32 tendencies on an FP64 state, FP32 correction, FP64
-    Gram-Schmidt), each timed with CUDA events after one untimed solve, with
+    precision (FP32 tendencies on an FP64 state, FP32 correction, FP64-accurate
+    Gram-Schmidt with its projections on FP64 units or, the served form, on the
+    tensor cores), each timed with CUDA events after one untimed solve, with
     the error of each against the serial FP64 fine solution."""
     wl = W.workload_large()
     p, K = wl.problem, wl.K
@@ -304,7 +305,9 @@ def precision_workload(P, torch, stream):
     res = {"workload": wl.name, "grid": f"{p.nx}x{p.ny}", "N_slices": p.n_slices, "K": K}
     qs = None
     for tag, opt in (("fp64", {}), ("fp64_direct", {"images": P.PR_IMAGES_DIRECT}),
-                     ("mixed", {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32})):
+                     ("mixed_proj_fp64", {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32}),
+                     ("mixed", {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32,
+                                "proj_prec": P.PR_PROJ_SPLIT_BF16})):
         s = P.Solver(p, stream=stream, K_max=K, **opt)
         out = torch.empty(p.d, dtype=torch.float64, device="cuda")
         P.parareal_solve(s.h, u0, K, qT=out, report=False)
@@ -409,49 +412,73 @@ def run_ours(args):
     e2e = {"value": solves / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": nsol * p.d * 8,
            "d2h_bytes_per_step": nsol * p.d * 8}
 
-    # ---- mixed precision on the same workload: FP32 fine sweep, FP32 correction
-    #      by linearity, FP64 Gram-Schmidt and accumulation
-    sm = P.Solver(p, stream=stream, K_max=K, krylov_cap=wl.krylov_cap, fine_prec=P.PR_FP32X, corr_prec=P.PR_FP32)
-    outs_m = [torch.empty(p.d, dtype=torch.float64, device="cuda") for _ in ics]
+    # ---- other arithmetic on the same workload, timed the same way:
+    #      mixed precision (the served form: FP32X fine sweep, FP32 correction by
+    #      linearity, direct images, Gram-Schmidt FP64-accurate with its
+    #      projections on the tensor cores), and the FP64 solve with the
+    #      tensor-core projections
+    def variant(opt):
+        sv = P.Solver(p, stream=stream, K_max=K, krylov_cap=wl.krylov_cap, **opt)
+        outs_v = [torch.empty(p.d, dtype=torch.float64, device="cuda") for _ in ics]
 
-    def step_m():
-        for u0, out in zip(u0s, outs_m):
-            P.parareal_solve(sm.h, u0, K, qT=out, report=False)
+        def step_v():
+            for u0, out in zip(u0s, outs_v):
+                P.parareal_solve(sv.h, u0, K, qT=out, report=False)
 
-    for _ in range(max(3, args.warmup)):
-        step_m()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        step_m()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_m = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_m], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_m = float(t.item())
-    mixed = {"value": solves / (ms_m / 1e3), "unit": "solves/s",
-             "fine_prec": "f32 tendencies and stages, f64 state", "corr_prec": "f32 (delta form)",
-             "images": "direct F(Q) - G(Q) in f32", "gram_schmidt": "f64",
-             "speedup_vs_fp64": (solves / (ms_m / 1e3)) / value}
-    if rank == 0:
+        for _ in range(max(3, args.warmup)):
+            step_v()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        P.parareal_timing_enable(sv.h, args.steps * nsol)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_v()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_v = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms_v], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_v = float(t.item())
+        tv = P.parareal_timing_read(sv.h)
+        ph = {k: tv[k] / tv["n_solves"] for k in ("ms_init", "ms_fine", "ms_coarse", "ms_krylov", "ms_gs_block",
+                                                   "ms_gs_intra", "ms_kold", "ms_chain")}
+        return sv, outs_v, solves / (ms_v / 1e3), ph
+
+    def per_ic_errors(outs_v):
         per_ic = {}
         for j in range(nsol):
             qs = serial_fine_gpu(P, s, u0s[j], p.n_slices)
             rep = P.parareal_solve(s.h, u0s[j], K, qT=outs[j], report=True)
-            a, b_ = rel_l2(outs[j], qs), rel_l2(outs_m[j], qs)
-            per_ic[wl.ics[j][0]] = {"eps_fp64": a, "eps_mixed": b_, "abs_diff": abs(a - b_),
+            a, b_ = rel_l2(outs[j], qs), rel_l2(outs_v[j], qs)
+            per_ic[wl.ics[j][0]] = {"eps_fp64": a, "eps": b_, "abs_diff": abs(a - b_),
                                     "min_kept_ratio": min(rep.min_ratio[:K])}
-        mixed.update({"per_ic": per_ic,
+        return per_ic
+
+    sm, outs_m, v_m, ph_m = variant({"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32,
+                                     "proj_prec": P.PR_PROJ_SPLIT_BF16})
+    mixed = {"value": v_m, "unit": "solves/s",
+             "fine_prec": "f32 tendencies and stages, f64 state", "corr_prec": "f32 (delta form)",
+             "images": "direct F(Q) - G(Q) in f32",
+             "gram_schmidt": "f64-accurate: Q^T V and V - Q C on the BF16 tensor cores (8 exact digit slices, "
+                             "f64 combination); norms, drop rule, in-block passes in f64",
+             "speedup_vs_fp64": v_m / value, "phases_ms_per_solve": ph_m}
+    if rank == 0:
+        mixed.update({"per_ic": per_ic_errors(outs_m),
                       "eps_def": "||q_N^K - q_seq(T)|| / ||q_seq(T)|| against N serial FP64 fine sweeps",
-                      "note": "|eps_mixed - eps_fp64| <= 1e-5 holds for the well-conditioned IC; the "
+                      "note": "|eps - eps_fp64| <= 1e-5 holds for the well-conditioned IC; the "
                               "filtered-noise IC excites the coarse step's growing band (FP32 rounding "
                               "amplified along the chain), the Fourier IC has nearly dependent iterates "
                               "(min kept ratio ~1e-5)"})
     sm.close()
+    st_, outs_t, v_t, ph_t = variant({"proj_prec": P.PR_PROJ_SPLIT_BF16})
+    fp64_tc = {"value": v_t, "unit": "solves/s", "speedup_vs_fp64": v_t / value,
+               "what": "the FP64 solve with Q^T V, V - Q C and Q^T q on the tensor cores (FP64-accurate split "
+                       "digits)", "phases_ms_per_solve": ph_t}
+    if rank == 0:
+        fp64_tc["per_ic"] = per_ic_errors(outs_t)
+    st_.close()
 
     line = None
     if rank == 0:
@@ -502,6 +529,7 @@ def run_ours(args):
             "clocks": clk,
             "fp64_fma_tflops": peak,
             "mixed": mixed,
+            "fp64_tensor_core_projection": fp64_tc,
             "precision_workload": precision,
             "batching": batching,
             "serving": serving,

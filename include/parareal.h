@@ -53,6 +53,13 @@ enum { PR_FP64 = 0, PR_FP32 = 1, PR_FP32X = 2 };   /* arithmetic of the fine swe
                                                       dt L(q**) formed in FP64)      */
 enum { PR_KSE = 0, PR_ORIGINAL = 1 };              /* Alg. 2 / Alg. 1                */
 enum { PR_IMAGES_LINEARITY = 0, PR_IMAGES_DIRECT = 1 };  /* how F(Q) is formed          */
+enum { PR_PROJ_FP64 = 0, PR_PROJ_SPLIT_BF16 = 1 };  /* arithmetic of the projections
+                                                      Q^T V and V - Q C of the
+                                                      subspace update: FP64 units,
+                                                      or FP64-accurate products on
+                                                      the BF16 tensor cores (each
+                                                      FP64 column split into 8
+                                                      exact 7-bit digit slices)     */
 #define PR_MAX_ITERS 128
 
 typedef struct {
@@ -98,6 +105,17 @@ typedef struct {
                               most this many SMs, so solves of several handles on
                               different streams run side by side (0: all SMs)    */
     void* stream;          /* cudaStream_t, or NULL                              */
+    int32_t proj_prec;     /* PR_PROJ_FP64 or PR_PROJ_SPLIT_BF16: how the
+                              subspace update (Eq. subspaceUpdate) forms Q^T V
+                              and V - Q C, and how K(q_i^k) forms Q^T q
+                              (Eq. modifiedCoarse).  PR_PROJ_SPLIT_BF16
+                              orthogonalises the new columns in blocks of 16
+                              with these products on the tensor cores, to FP64
+                              accuracy (norms, the drop rule, the in-block
+                              Gram-Schmidt and products with D stay FP64); it
+                              needs 3*nx*ny to be a multiple of 8 and adds about
+                              32*cap*3*nx*ny bytes of digit slices to the
+                              footprint (default PR_PROJ_FP64)                  */
 } pr_options;
 
 typedef struct {
@@ -279,6 +297,28 @@ pr_status parareal_batch_destroy(pr_batch* b);
 pr_status parareal_fine_sweep_static(const pr_grid* g, double U, double V, double c_s, double nu_f,
                                      double dt_f, int32_t n_steps, int32_t fine_prec,
                                      const double* q_in_dev, double* q_out_dev, int32_t n, void* stream);
+
+/* FP64-accurate tall-skinny products on the BF16 tensor cores, the same
+ * kernels the subspace update uses with PR_PROJ_SPLIT_BF16 (Eq.
+ * subspaceUpdate, Eq. modifiedCoarse: the projection coefficients Q^T q and
+ * the update q - Q c), exposed for direct use and testing.  All matrices are
+ * column-major FP64 device buffers.  Each column of both operands is written
+ * as 2^E times 8 digits of 7 bits, the 43 leading digit products are summed
+ * exactly in FP32 over chunks of 256 contraction elements and the chunks are
+ * combined in FP64: per term the error is at most 2^-55 (max|a| |b_k| +
+ * |a_k| max|b|) + 2^-58 max|a| max|b| (a, b the two columns), plus the FP64
+ * rounding of the combination.
+ *   tn:  C (m x n, ld ldc) = A^T B,  A: k x m (ld lda), B: k x n (ld ldb).
+ *   nn:  Y (k x n, ld ldy) <- Y - A B,  A: k x m (ld lda), B: m x n (ld ldb).
+ * k must be a multiple of 8 (>= 8), 1 <= m <= 16384, n >= 1.  Not the solve's
+ * allocation-free path: each call allocates its digit buffers, enqueues on
+ * `stream` (cudaStream_t or NULL), synchronises it and frees them.  Returns
+ * PR_EINVAL for bad sizes or NULL pointers, PR_ENOMEM, PR_ECUDA, or
+ * PR_ETIMEOUT if a pipeline wait of the kernel gave up. */
+pr_status parareal_split_gemm_tn(const double* A, int64_t lda, int32_t m, const double* B, int64_t ldb,
+                                 int32_t n, int64_t k, double* C, int64_t ldc, void* stream);
+pr_status parareal_split_gemm_nn(const double* A, int64_t lda, int32_t m, const double* B, int64_t ldb,
+                                 int32_t n, int64_t k, double* Y, int64_t ldy, void* stream);
 
 /* Self-test of the library's bounded device waits (no counterpart in the
  * paper): launches a cooperative kernel whose grid barrier can never complete

@@ -18,6 +18,7 @@ PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ETIMEOUT, PR_ESTATE, PR_ECANCELLED = 0
 PR_FP64, PR_FP32, PR_FP32X = 0, 1, 2
 PR_KSE, PR_ORIGINAL = 0, 1
 PR_IMAGES_LINEARITY, PR_IMAGES_DIRECT = 0, 1
+PR_PROJ_FP64, PR_PROJ_SPLIT_BF16 = 0, 1
 PR_MAX_ITERS = 128
 _STATUS = {0: "PR_OK", -1: "PR_EINVAL", -2: "PR_ENOMEM", -3: "PR_ECUDA", -4: "PR_ETIMEOUT",
            -5: "PR_ESTATE", -6: "PR_ECANCELLED"}
@@ -33,7 +34,7 @@ class pr_options(C.Structure):
                 ("K_max", C.c_int32), ("krylov_cap", C.c_int32), ("drop_tol", C.c_double),
                 ("fine_prec", C.c_int32), ("variant", C.c_int32), ("corr_prec", C.c_int32),
                 ("r_tol", C.c_double), ("n_windows", C.c_int32), ("images", C.c_int32),
-                ("sm_limit", C.c_int32), ("stream", C.c_void_p)]
+                ("sm_limit", C.c_int32), ("stream", C.c_void_p), ("proj_prec", C.c_int32)]
 
 
 class pr_report(C.Structure):
@@ -63,7 +64,8 @@ EXPORTS = ["parareal_default_options", "parareal_create", "parareal_destroy", "p
            "parareal_coarse_sweep", "parareal_coarse_apply", "krylov_reset", "krylov_update", "krylov_rank",
            "krylov_project", "parareal_timing_enable", "parareal_timing_read", "parareal_kernel_launches",
            "parareal_alu_probe", "parareal_fine_sweep_static", "parareal_selftest_wait_timeout",
-           "parareal_solve_batch", "parareal_batch_create", "parareal_batch_launch", "parareal_batch_destroy"]
+           "parareal_solve_batch", "parareal_batch_create", "parareal_batch_launch", "parareal_batch_destroy",
+           "parareal_split_gemm_tn", "parareal_split_gemm_nn"]
 
 _lib = None
 
@@ -129,6 +131,11 @@ def lib():
     L.parareal_batch_launch.restype = st
     L.parareal_batch_destroy.argtypes = [P]
     L.parareal_batch_destroy.restype = st
+    i64, i32 = C.c_int64, C.c_int32
+    for name in ("parareal_split_gemm_tn", "parareal_split_gemm_nn"):
+        f = getattr(L, name)
+        f.argtypes = [P, i64, i32, P, i64, i32, i64, P, i64, P]
+        f.restype = st
     _lib = L
     return L
 
@@ -316,6 +323,39 @@ def parareal_fine_sweep_static(nx, ny, U, V, c_s, nu_f, dt_f, n_steps, fine_prec
                                                   float(c_s), float(nu_f), float(dt_f), int(n_steps),
                                                   int(fine_prec), _ptr(q_in), _ptr(q_out), int(n),
                                                   C.c_void_p(stream) if stream else None))
+
+
+def _ld(t):
+    """Leading dimension of a (columns, rows) tensor holding a column-major
+    matrix (the stride of a size-1 dimension carries no information)."""
+    if t.stride(-1) != 1:
+        raise ValueError("columns must be contiguous")
+    return t.stride(0) if t.shape[0] > 1 else t.shape[1]
+
+
+def _split_gemm(name, A, B, out, m, n, k, lda, ldb, ldo, stream):
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(None, getattr(lib(), name)(_ptr(A), int(lda), int(m), _ptr(B), int(ldb), int(n), int(k), _ptr(out),
+                                      int(ldo), C.c_void_p(stream) if stream else None))
+
+
+def parareal_split_gemm_tn(A, B, C_out, stream=None):
+    """C_out (m x n) = A^T B on the tensor cores, FP64-accurate.  A: k x m and
+    B: k x n column-major FP64 device tensors, i.e. torch tensors of shape
+    (m, k) and (n, k); C_out of shape (n, m)."""
+    m, k = A.shape
+    n = B.shape[0]
+    _split_gemm("parareal_split_gemm_tn", A, B, C_out, m, n, k, _ld(A), _ld(B), _ld(C_out), stream)
+
+
+def parareal_split_gemm_nn(A, B, Y, stream=None):
+    """Y (k x n) <- Y - A B on the tensor cores, FP64-accurate.  A: k x m,
+    B: m x n, Y: k x n column-major FP64 device tensors, i.e. torch tensors of
+    shape (m, k), (n, m) and (n, k)."""
+    m, k = A.shape
+    n = B.shape[0]
+    _split_gemm("parareal_split_gemm_nn", A, B, Y, m, n, k, _ld(A), _ld(B), _ld(Y), stream)
 
 
 class Solver:

@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "parareal.h"
+#include "split_gemm.h"
 
 using namespace pr;
 
@@ -29,11 +30,17 @@ void pr::count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_o
 
 // Ring of CUDA events recording the phase boundaries of up to max_solves solves:
 // [start, init end, then per iteration: fine end, coarse end, krylov end, chain end].
+// With the tensor-core projection the in-block Gram-Schmidt of every 16-column
+// sub-block is bracketed by a pair of events (sub, per solve and iteration
+// up to sub_per_iter pairs) so that it can be told apart from the projections.
 struct TimingRing {
     int max_solves = 0, per_solve = 0, n = 0;
     std::vector<cudaEvent_t> ev;
     std::vector<int> K;
     std::vector<long> fine_launches;
+    int sub_per_iter = 0;
+    std::vector<cudaEvent_t> sub;
+    std::vector<int> nsub;   // pairs recorded, per solve and iteration
 };
 
 struct pr_solver {
@@ -60,6 +67,8 @@ struct pr_solver {
     int* kept_hist = nullptr;                       // PR_MAX_ITERS x N kept flags
     int M_hist[PR_MAX_ITERS] = {};
     GridBar* gbar = nullptr;
+    SplitGemm sg;                 // tensor-core projection state (proj_prec = PR_PROJ_SPLIT_BF16)
+    bool use_sg = false;
     long partial_elems = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     TimingRing tr;
@@ -130,6 +139,7 @@ static Sizes compute_sizes(int nx, int ny, int N, int K_max, const pr_options& o
     b += dd * (size_t)s.partial;
     b += dd * (size_t)(N + (N + 1) + PR_MAX_ITERS + 1);
     b += sizeof(int) * (size_t)(3 + N + PR_MAX_ITERS);
+    if (o.proj_prec == PR_PROJ_SPLIT_BF16) b += sg_bytes(s.d, s.cap);
     s.bytes = b;
     return s;
 }
@@ -228,9 +238,9 @@ static pr_status coarse_apply(pr_solver* h, const double* in, double* out, int n
 // Gram-Schmidt against the basis present at entry, then two passes against
 // the columns kept earlier in this block, then the drop rule.  The D-images
 // Z = FV - GV receive exactly the same coefficients, so D = F(Q) - G(Q).
-template <typename Mark>
+template <typename Mark, typename SubMark>
 static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, const double* GV, int m, Mark mark,
-                              double* ratio = nullptr) {
+                              SubMark sub_mark, double* ratio = nullptr) {
     const long d = h->d;
     const int cap = h->cap;
     cudaStream_t s = h->stream;
@@ -239,6 +249,31 @@ static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, c
     CKC(cudaMemcpyAsync(h->wv, V, sizeof(double) * m * d, cudaMemcpyDeviceToDevice, s));
     if (images) CKC(sub(FV, GV, h->wz, (long)m * d, s));
     CKC(colnorm2(h->wv, d, m, d, h->anorm2, w, s));
+    if (h->use_sg) {
+        // Sub-blocks of SG_N columns: two passes of block classical
+        // Gram-Schmidt against every column kept so far, with C = Q^T v and
+        // v - Q C on the tensor cores (FP64-accurate, split digits), then the
+        // in-block passes, drop rule and append in FP64, and the digits of
+        // the appended columns for the next products.
+        for (int j0 = 0; j0 < m; j0 += SG_N) {
+            const int mm = m - j0 < SG_N ? m - j0 : SG_N;
+            double* v = h->wv + (long)j0 * d;
+            double* z = images ? h->wz + (long)j0 * d : nullptr;
+            CKC(cudaMemcpyAsync(h->r_old, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
+            for (int pass = 0; pass < 2; ++pass) {
+                CKC(sg_cgs_pass(&h->sg, v, d, mm, h->r_old, s));
+                if (images)
+                    CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->sg.C, h->sg.cap_pad, z, d, z, d, mm, d, -1.0, s));
+            }
+            CKC(sub_mark(0));
+            CKC(intra_block(v, z, d, mm, h->anorm2 + j0, h->r_old, h->r, cap, h->opt.drop_tol, h->Q, h->D,
+                            h->kept + j0, ratio ? ratio + j0 : nullptr, w, h->gbar, s, h->opt.sm_limit));
+            CKC(sg_append(&h->sg, h->Q, d, h->r_old, h->r, 0, mm, s));
+            CKC(sub_mark(1));
+        }
+        CKC(mark());
+        return PR_OK;
+    }
     for (int j0 = 0; j0 < m; j0 += 64) {
         const int mm = m - j0 < 64 ? m - j0 : 64;
         double* v = h->wv + (long)j0 * d;
@@ -277,6 +312,7 @@ static pr_status direct_images(pr_solver* h, bool mixed, int maxn) {
 }
 
 static cudaError_t no_mark() { return cudaSuccess; }
+static cudaError_t no_sub_mark(int) { return cudaSuccess; }
 
 // ------------------------------------------------------------------ the solve
 
@@ -326,6 +362,14 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
     }
     int evi = 0;
     auto mark = [&]() -> cudaError_t { return ev ? cudaEventRecord(ev[evi++], s) : cudaSuccess; };
+    int iter = 0;
+    auto sub_mark = [&](int) -> cudaError_t {
+        if (!ev) return cudaSuccess;
+        const size_t base = ((size_t)(h->tr.n - 1) * h->K_max + iter) * (size_t)h->tr.sub_per_iter;
+        int& ns = h->tr.nsub[(size_t)(h->tr.n - 1) * h->K_max + iter];
+        if (ns >= 2 * h->tr.sub_per_iter) return cudaSuccess;
+        return cudaEventRecord(h->tr.sub[2 * base + ns++], s);
+    };
     CKC(mark());
 
     // initialisation: q_{i+1}^0 = G(q_i^0), serially (q[0] already holds u0)
@@ -333,7 +377,10 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
     CKC(fill_int(h->r, 0, 1, s));
     CKC(mark());
 
+    if (ev)
+        for (int k = 0; k < h->K_max; ++k) h->tr.nsub[(size_t)(h->tr.n - 1) * h->K_max + k] = 0;
     for (int k = 0; k < K; ++k) {
+        iter = k;
         // Slices i < k satisfy q_i^{k} = q_i^{k-1} bit for bit (the correction
         // of a converged slice is K(q) - K(q) = 0), so their fine images, their
         // columns (already in S) and their corrections are skipped.
@@ -350,7 +397,7 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
         CKC(mark());
         if (kse) {
             CKC(cudaMemcpyAsync(h->r_it, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
-            CKS(krylov_block(h, qa, direct ? nullptr : h->qt + (long)a * d, h->gv + (long)a * d, M, mark,
+            CKS(krylov_block(h, qa, direct ? nullptr : h->qt + (long)a * d, h->gv + (long)a * d, M, mark, sub_mark,
                              h->ratios + (long)(rbase + k) * N));
             CKC(cudaMemcpyAsync(h->kept_hist + (long)(rbase + k) * N, h->kept, sizeof(int) * M,
                                 cudaMemcpyDeviceToDevice, s));
@@ -359,9 +406,20 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
             if (direct) CKS(direct_images(h, mixed, M));
             if (!mixed && M > 1) {
                 // K(q_i^k) = G(q_i^k) + D Q^T q_i^k for i = k+1..N-1 with the updated S^k
-                CKC(gemm_tn(h->Q, d, nullptr, h->r, cap, h->q + (long)(a + 1) * d, d, M - 1, d, h->C, cap, w, s));
-                CKC(gemm_nn(h->D, d, nullptr, h->r, cap, h->C, cap, h->gv + (long)(a + 1) * d, d,
-                            h->kold + (long)(a + 1) * d, d, M - 1, d, 1.0, s));
+                if (h->use_sg) {
+                    // projection coefficients Q^T q on the tensor cores, 16 slices at a time
+                    for (int j0 = 0; j0 < M - 1; j0 += SG_N) {
+                        const int mm = M - 1 - j0 < SG_N ? M - 1 - j0 : SG_N;
+                        const long off = (long)(a + 1 + j0) * d;
+                        CKC(sg_project(&h->sg, h->q + off, d, mm, h->r, s));
+                        CKC(gemm_nn(h->D, d, nullptr, h->r, cap, h->sg.C, h->sg.cap_pad, h->gv + off, d,
+                                    h->kold + off, d, mm, d, 1.0, s));
+                    }
+                } else {
+                    CKC(gemm_tn(h->Q, d, nullptr, h->r, cap, h->q + (long)(a + 1) * d, d, M - 1, d, h->C, cap, w, s));
+                    CKC(gemm_nn(h->D, d, nullptr, h->r, cap, h->C, cap, h->gv + (long)(a + 1) * d, d,
+                                h->kold + (long)(a + 1) * d, d, M - 1, d, 1.0, s));
+                }
             }
             CKC(cudaMemcpyAsync(h->ranks + rbase + k, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
         } else {
@@ -398,6 +456,7 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
 
 static void timing_free(pr_solver* h) {
     for (cudaEvent_t e : h->tr.ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->tr.sub) cudaEventDestroy(e);
     h->tr = TimingRing();
 }
 
@@ -406,6 +465,10 @@ static pr_status check_device_waits(pr_solver* h) {
     int err = 0;
     CKC(cudaMemcpy(&err, &h->gbar->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) return set_err(h, PR_ETIMEOUT, "a grid barrier wait gave up; results of this handle are invalid");
+    if (h->use_sg) {
+        CKC(cudaMemcpy(&err, h->sg.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) return set_err(h, PR_ETIMEOUT, "a tensor-core pipeline wait gave up; results of this handle are invalid");
+    }
     return PR_OK;
 }
 
@@ -530,6 +593,10 @@ static pr_status validate(const pr_grid* g, double U, double c_s, double dt_f, d
     if (o.n_windows < 1 || o.n_windows > 1000000) return set_err(h, PR_EINVAL, "n_windows must be >= 1");
     if (o.images != PR_IMAGES_LINEARITY && o.images != PR_IMAGES_DIRECT) return set_err(h, PR_EINVAL, "images must be PR_IMAGES_LINEARITY or PR_IMAGES_DIRECT");
     if (o.sm_limit < 0) return set_err(h, PR_EINVAL, "sm_limit must be >= 0");
+    if (o.proj_prec != PR_PROJ_FP64 && o.proj_prec != PR_PROJ_SPLIT_BF16)
+        return set_err(h, PR_EINVAL, "proj_prec must be PR_PROJ_FP64 or PR_PROJ_SPLIT_BF16");
+    if (o.proj_prec == PR_PROJ_SPLIT_BF16 && (3L * g->nx * g->ny) % 8 != 0)
+        return set_err(h, PR_EINVAL, "PR_PROJ_SPLIT_BF16 needs 3*nx*ny to be a multiple of 8");
     if (!(o.drop_tol >= 0) || !is_fin(o.drop_tol)) return set_err(h, PR_EINVAL, "drop_tol must be >= 0");
     if (o.K_max < 0 || o.K_max > PR_MAX_ITERS || o.K_max > N) return set_err(h, PR_EINVAL, "K_max must be in [0, min(N, 128)]");
     if (o.krylov_cap < 0 || o.krylov_cap > 1600) return set_err(h, PR_EINVAL, "krylov_cap must be in [0, 1600]");
@@ -660,6 +727,10 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
         chk(cudaEventCreate(&h->ev0));
         chk(cudaEventCreate(&h->ev1));
     }
+    if (e == cudaSuccess && o.proj_prec == PR_PROJ_SPLIT_BF16) {
+        chk(sg_init(&h->sg, d, h->cap));
+        h->use_sg = e == cudaSuccess;
+    }
     if (e != cudaSuccess) {
         std::string msg = std::string("device allocation failed: ") + cudaGetErrorString(e);
         cudaGetLastError();
@@ -686,6 +757,7 @@ pr_status parareal_destroy(pr_solver* h) {
     if (h->ranks) cudaFree(h->ranks);
     if (h->kept_hist) cudaFree(h->kept_hist);
     if (h->gbar) cudaFree(h->gbar);
+    if (h->use_sg) sg_free(&h->sg);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     timing_free(h);
@@ -766,7 +838,7 @@ pr_status krylov_update(pr_solver* h, const double* V_dev, const double* FV_dev,
     if (!V_dev || !FV_dev) return set_err(h, PR_EINVAL, "NULL buffer");
     if (m < 1 || m > h->N) return set_err(h, PR_EINVAL, "m must be in [1, N_slices]");
     CKS(coarse_apply(h, V_dev, h->gv, m));
-    CKS(krylov_block(h, V_dev, FV_dev, h->gv, m, no_mark));
+    CKS(krylov_block(h, V_dev, FV_dev, h->gv, m, no_mark, no_sub_mark));
     if (kept_host) {
         CKC(cudaMemcpyAsync(kept_host, h->kept, sizeof(int) * m, cudaMemcpyDeviceToHost, h->stream));
         CKC(cudaStreamSynchronize(h->stream));
@@ -809,6 +881,16 @@ pr_status parareal_timing_enable(pr_solver* h, int32_t max_solves) {
     h->tr.ev.assign((size_t)max_solves * h->tr.per_solve, nullptr);
     h->tr.K.assign((size_t)max_solves, 0);
     h->tr.fine_launches.assign((size_t)max_solves, 0);
+    h->tr.sub_per_iter = h->use_sg ? (h->N + SG_N - 1) / SG_N : 0;
+    h->tr.sub.assign((size_t)max_solves * h->K_max * 2 * h->tr.sub_per_iter, nullptr);
+    h->tr.nsub.assign((size_t)max_solves * h->K_max, 0);
+    for (auto& e : h->tr.sub) {
+        cudaError_t x = cudaEventCreate(&e);
+        if (x != cudaSuccess) {
+            timing_free(h);
+            return set_err(h, PR_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(x));
+        }
+    }
     for (auto& e : h->tr.ev) {
         cudaError_t x = cudaEventCreate(&e);
         if (x != cudaSuccess) {
@@ -839,6 +921,17 @@ pr_status parareal_timing_read(pr_solver* h, pr_timing* t, int32_t reset) {
                 *acc[ph] += ms;
                 if (ph >= 2 && ph <= 4) t->ms_krylov += ms;
                 t->ms_total += ms;
+            }
+            if (h->tr.sub_per_iter > 0) {
+                // in-block Gram-Schmidt segments inside the projection phase
+                const size_t it = (size_t)sidx * h->K_max + k;
+                const int ns = h->tr.nsub[it];
+                cudaEvent_t* se = h->tr.sub.data() + 2 * it * h->tr.sub_per_iter;
+                for (int p = 0; p + 1 < ns; p += 2) {
+                    CKC(cudaEventElapsedTime(&ms, se[p], se[p + 1]));
+                    t->ms_gs_block -= ms;
+                    t->ms_gs_intra += ms;
+                }
             }
             t->fine_cell_steps += (double)(h->N - k) * h->n_f * ncell;
         }

@@ -21,7 +21,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (PR_FP32, PR_FP32X, PR_FP64, Solver, new_stream, parareal_footprint_bytes, parareal_solve)
+from . import (PR_FP32, PR_FP32X, PR_FP64, PR_PROJ_SPLIT_BF16, Solver, new_stream, parareal_footprint_bytes,
+               parareal_solve)
 
 
 @dataclass
@@ -95,6 +96,8 @@ class Server:
         opt = {"K_max": K_max}
         if self.mode == "mixed":
             opt.update(fine_prec=PR_FP32X, corr_prec=PR_FP32)
+            if (3 * p.nx * p.ny) % 8 == 0:
+                opt.update(proj_prec=PR_PROJ_SPLIT_BF16)
         if self.sm_limit:
             opt["sm_limit"] = self.sm_limit(p.d, self.sms)
         return opt

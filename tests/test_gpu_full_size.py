@@ -52,14 +52,17 @@ def _solve(p, q0, K, cap, **opt):
         return out.cpu().numpy(), qs.cpu().numpy(), rep
 
 
+@pytest.mark.parametrize("proj", [0, 1], ids=["proj_fp64", "proj_split_bf16"])
 @pytest.mark.parametrize("ic", [0, 1, 2], ids=["gaussian+noise", "fourier8", "filtered_noise16"])
-def test_fp64_solve_against_oracle_reference(ref, ic):
+def test_fp64_solve_against_oracle_reference(ref, ic, proj):
+    """Both projection arithmetics (FP64 units, FP64-accurate split digits on
+    the tensor cores) are held to the same bounds."""
     wl = W.workload_medium()
     p = wl.problem
     name, f = wl.ics[ic]
     R = ref["ics"][name]
     idx = np.array(ref["sample_indices"])
-    got, qs, rep = _solve(p, f().ravel(), wl.K, wl.krylov_cap)
+    got, qs, rep = _solve(p, f().ravel(), wl.K, wl.krylov_cap, proj_prec=proj)
     r = np.array(rep.r[:wl.K])
     assert list(rep.rank[:wl.K]) == R["rank"]
     # the serial fine solution is well conditioned: always within 1e-12
