@@ -67,9 +67,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream sweep")
-    ap.add_argument("--case", choices=["fine", "solve"], default=None,
+    ap.add_argument("--case", choices=["fine", "solve", "solve_mixed"], default=None,
                     help="small isolated case for profiler captures: 'fine' = three fine sweeps over all "
-                         "32 slices of the 256x128 workload; 'solve' = two solves of its first IC")
+                         "32 slices of the 256x128 workload; 'solve' = two solves of its first IC; "
+                         "'solve_mixed' = the same in mixed precision with the tensor-core projections")
     return ap.parse_args()
 
 
@@ -550,7 +551,10 @@ def run_case(args):
     torch.cuda.set_device(0)
     wl = W.workload_medium()
     p = wl.problem
-    s = P.Solver(p, stream=torch.cuda.current_stream(), K_max=wl.K, krylov_cap=wl.krylov_cap)
+    opt = {}
+    if args.case == "solve_mixed":
+        opt = {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32, "proj_prec": P.PR_PROJ_SPLIT_BF16}
+    s = P.Solver(p, stream=torch.cuda.current_stream(), K_max=wl.K, krylov_cap=wl.krylov_cap, **opt)
     q0 = torch.from_numpy(wl.ics[0][1]().ravel()).cuda()
     if args.case == "fine":
         X = q0.repeat(p.n_slices)

@@ -29,6 +29,41 @@ namespace {
 
 constexpr int CH_NT = 512, CH_TX = 16, CH_TY = 16;
 
+// FP32 dot product of a and x over rows [r0, r1) by one warp, accumulated in
+// FP32 in a fixed order (deterministic).  With vec (both columns 16-byte
+// aligned at r0, r0 a multiple of 4) four float4 loads per operand are in
+// flight per lane.
+__device__ __forceinline__ float warp_dot_f32(const float* __restrict__ a, const float* __restrict__ x, long r0,
+                                              long r1, bool vec) {
+    const int lane = threadIdx.x & 31;
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+    long tail = r0;
+    if (vec) {
+        const float4* a4 = reinterpret_cast<const float4*>(a + r0);
+        const float4* x4 = reinterpret_cast<const float4*>(x + r0);
+        const long n4 = (r1 - r0) >> 2;
+        long i = lane;
+        for (; i + 96 < n4; i += 128) {
+            const float4 p0 = __ldg(a4 + i), p1 = __ldg(a4 + i + 32), p2 = __ldg(a4 + i + 64), p3 = __ldg(a4 + i + 96);
+            const float4 y0 = x4[i], y1 = x4[i + 32], y2 = x4[i + 64], y3 = x4[i + 96];
+            t0 += p0.x * y0.x + p0.y * y0.y + p0.z * y0.z + p0.w * y0.w;
+            t1 += p1.x * y1.x + p1.y * y1.y + p1.z * y1.z + p1.w * y1.w;
+            t2 += p2.x * y2.x + p2.y * y2.y + p2.z * y2.z + p2.w * y2.w;
+            t3 += p3.x * y3.x + p3.y * y3.y + p3.z * y3.z + p3.w * y3.w;
+        }
+        for (; i < n4; i += 32) {
+            const float4 p0 = __ldg(a4 + i), y0 = x4[i];
+            t0 += p0.x * y0.x + p0.y * y0.y + p0.z * y0.z + p0.w * y0.w;
+        }
+        tail = r0 + 4 * n4;
+    }
+    for (long row = tail + lane; row < r1; row += 32) t0 += a[row] * x[row];
+    float t = (t0 + t1) + (t2 + t3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+}
+
 // DELTA = false: the literal correction in FP64,
 //   q_{i+1} = q~_{i+1} + ((G(q_i) + D Q^T q_i) - K_old_i).
 // DELTA = true: the same correction through linearity in FP32,
@@ -44,7 +79,7 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
     const unsigned nb = gridDim.x;
     const int b = blockIdx.x;
     const long d = A.d;
-    const long rpb = (d + nb - 1) / nb;
+    const long rpb = ((d + nb - 1) / nb + 31) / 32 * 32;   // rows per CTA, a multiple of 32
     const long r0 = min(d, (long)b * rpb), r1 = min(d, r0 + rpb);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = CH_NT / 32;
     const int ncols = A.r_dev ? *A.r_dev : 0;
@@ -62,12 +97,8 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
         for (int l = wid; l < ncols; l += nw) {
             double s;
             if (DELTA) {
-                float t = 0.f;
-                const T* a = Qm + (long)l * d;
-                for (long row = r0 + lane; row < r1; row += 32) t += a[row] * x[row];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                s = (double)t;
+                s = (double)warp_dot_f32(reinterpret_cast<const float*>(Qm) + (long)l * d,
+                                         reinterpret_cast<const float*>(x), r0, r1, (d & 3) == 0);
             } else {
                 s = warp_dot(reinterpret_cast<const double*>(Qm) + (long)l * d, qi, r0, r1);
             }
@@ -101,6 +132,35 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
         const double* qt = A.qt ? A.qt + (long)i * d : nullptr;
         const double* ko = A.kold ? A.kold + (long)i * d : nullptr;
         double s = 0.0;
+        if (DELTA && (d & 3) == 0) {
+            // four consecutive rows per thread: 16-byte loads of D32, eight
+            // basis columns in flight
+            const float* gq = reinterpret_cast<const float*>(gin);
+            for (long row = r0 + 4 * threadIdx.x; row < r1; row += 4 * CH_NT) {
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4* Dr = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Dm) + row);
+                const long st = d >> 2;
+#pragma unroll 8
+                for (int l = 0; l < ncols; ++l) {
+                    const float4 dv = __ldg(Dr + (long)l * st);
+                    const float cl = (float)cs[l];
+                    acc.x += dv.x * cl;
+                    acc.y += dv.y * cl;
+                    acc.z += dv.z * cl;
+                    acc.w += dv.w * cl;
+                }
+                const float av[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const long rw = row + u;
+                    const double y = qt[rw] + (double)(gq[rw] + av[u]);
+                    const double e = y - qn[rw];
+                    s += e * e;
+                    qn[rw] = y;
+                    A.dlt[rw] = (float)e;
+                }
+            }
+        } else
         for (long row = r0 + threadIdx.x; row < r1; row += CH_NT) {
             T acc = T(0);
             const T* Dr = Dm + row;

@@ -134,9 +134,17 @@ struct GridBar {
 // the result is invalid.
 // ratio[j] (optional) receives ||residual_j|| / ||a_j||.
 // max_blocks > 0 caps the cooperative grid (one CTA per SM).
+// compact: the kept columns (normalised) are written in order to the first
+// slots of wv (and wz) instead of Q[:, *r_dev] (and D); *r_dev still counts them.
 cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2, const int* r_old_dev,
                         int* r_dev, int cap, double eta, double* Q, double* D, int* kept, double* ratio,
-                        const TsWork& w, GridBar* gb, cudaStream_t s, int max_blocks = 0);
+                        const TsWork& w, GridBar* gb, cudaStream_t s, int max_blocks = 0, bool compact = false);
+// Re-orthonormalisation of n = *nk_dev <= m <= 64 nearly orthonormal columns W
+// (ld d) by Cholesky QR: G = W^T W = R^T R (G, Rinv: 64 x 64 scratch), the
+// result W R^-1 written to Q[:, *off_dev + j] (and Z R^-1 to D when Z != NULL).
+cudaError_t cholqr_block(double* W, double* Z, long d, int m, const int* nk_dev, double* G, double* Rinv,
+                         double* Q, double* D, const int* off_dev, const TsWork& w, cudaStream_t s);
+cudaError_t sub_int(const int* a, const int* b, int* out, cudaStream_t s);
 
 
 // Serial correction of Alg. 2 over slices [i_begin, i_end) in one cooperative

@@ -296,13 +296,13 @@ __global__ void k_fill_int(int* p, int v, int n) {
 // coefficients and take identical decisions.  Partial buffers alternate
 // between two halves, so one barrier per reduction suffices.
 constexpr int IB_NT = 512;
-__global__ void __launch_bounds__(IB_NT) k_intra_block(double* __restrict__ wv, double* __restrict__ wz, long d,
-                                                      int m, const double* __restrict__ a2, const int* r_old_dev,
-                                                      int* r_dev, int cap, double eta, double* __restrict__ Q,
-                                                      double* __restrict__ D, int* kept, double* ratio,
-                                                      double* __restrict__ part, int pstride, GridBar* gb) {
+__global__ void __launch_bounds__(IB_NT) k_intra_block(double* wv, double* wz, long d, int m,
+                                                      const double* __restrict__ a2, const int* r_old_dev,
+                                                      int* r_dev, int cap, double eta, double* Qb, double* Db,
+                                                      int* kept, double* ratio, double* __restrict__ part,
+                                                      int pstride, GridBar* gb, bool compact) {
     __shared__ double cs[64];
-    __shared__ double red[IB_NT / 32];
+    __shared__ double sred[IB_NT / 32][17];
     __shared__ double s_res2;   // pstride >= 64: slot 63 carries ||v||^2 partials (nn <= 63)
     const unsigned nb = gridDim.x;
     const int b = blockIdx.x;
@@ -311,6 +311,11 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* __restrict__ wv, 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = IB_NT / 32;
     const int c0 = *r_old_dev;
     int rl = *r_dev;
+    // Kept columns go to Q[:, rl] (and D) or, compacted, to slot rl - c0 of
+    // the work block itself (Qb = wv, Db = wz): in both cases column c of the
+    // block's kept set is at Q[(c0 + c) d] below.
+    double* Q = compact ? Qb - (long)c0 * d : Qb;
+    double* D = (compact && Db) ? Db - (long)c0 * d : Db;
     int buf = 0;
     double* P0 = part;
     double* P1 = part + (long)nb * pstride;
@@ -328,22 +333,71 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* __restrict__ wv, 
         for (int pass = 0; pass < npass; ++pass) {
             double* P = buf ? P1 : P0;
             const bool last = pass == npass - 1;
-            for (int l = wid; l < nn; l += nw) {
-                const double s = warp_dot(Q + (long)(c0 + l) * d, v, r0, r1);
-                if (lane == 0) P[(long)b * pstride + l] = s;
-            }
-            if (last) {
-                double s = 0.0;
-                for (long row = r0 + threadIdx.x; row < r1; row += IB_NT) s += v[row] * v[row];
+            // This CTA's partial dot products with the nn kept columns (and
+            // ||v||^2 in the last pass).  Up to 16 columns: every thread walks
+            // its rows once, reading v once and the columns together (many
+            // loads in flight), then the CTA sums the thread values in a
+            // fixed order.  More columns: one warp per column.
+            if (nn > 16) {
+                for (int l = wid; l < nn; l += nw) {
+                    const double s = warp_dot(Q + (long)(c0 + l) * d, v, r0, r1);
+                    if (lane == 0) P[(long)b * pstride + l] = s;
+                }
+                if (last) {
+                    double s = 0.0;
+                    for (long row = r0 + threadIdx.x; row < r1; row += IB_NT) s += v[row] * v[row];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) red[wid] = s;
+                    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    if (lane == 0) sred[wid][16] = s;
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        double t = 0.0;
+                        for (int q = 0; q < nw; ++q) t += sred[q][16];
+                        P[(long)b * pstride + 63] = t;
+                    }
+                }
+            } else
+            for (int l0 = 0; l0 < nn || (last && l0 == 0); l0 += 16) {
+                const int lc = min(16, nn - l0);
+                const bool norm = last && l0 == 0;
+                double acc[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+                double nv = 0.0;
+                for (long row = r0 + threadIdx.x; row < r1; row += IB_NT) {
+                    const double x = v[row];
+                    nv += x * x;
+                    const double* q = Q + (long)(c0 + l0) * d + row;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        if (k < lc) acc[k] += q[(long)k * d] * x;
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    if (k < lc) {
+                        double t = acc[k];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                        if (lane == 0) sred[wid][k] = t;
+                    }
+                }
+                if (norm) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+                    if (lane == 0) sred[wid][16] = nv;
+                }
                 __syncthreads();
-                if (threadIdx.x == 0) {
+                if ((int)threadIdx.x < lc) {
                     double t = 0.0;
-                    for (int q = 0; q < nw; ++q) t += red[q];
+                    for (int w = 0; w < nw; ++w) t += sred[w][threadIdx.x];
+                    P[(long)b * pstride + l0 + threadIdx.x] = t;
+                }
+                if (norm && threadIdx.x == 32) {
+                    double t = 0.0;
+                    for (int w = 0; w < nw; ++w) t += sred[w][16];
                     P[(long)b * pstride + 63] = t;
                 }
+                __syncthreads();
             }
             if (!grid_barrier(gb, nb)) return;
             for (int l = wid; l < nn; l += nw) {
@@ -398,6 +452,75 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* __restrict__ wv, 
 }
 
 }  // namespace
+
+// *out = *a - *b
+__global__ void k_sub_int(const int* a, const int* b, int* out) { *out = *a - *b; }
+
+// Cholesky factor of the Gram matrix G = W^T W of n = *n_dev <= 64 nearly
+// orthonormal columns, G = R^T R with R upper triangular, and R^{-1}
+// (upper, ld 64, zero below the diagonal, columns >= n zero), in one CTA.  A non-positive pivot
+// (impossible for nearly orthonormal W) yields NaN, so that it cannot pass
+// silently.
+__global__ void k_cholqr(const double* __restrict__ G, int ldg, const int* n_dev, double* __restrict__ Rinv) {
+    __shared__ double R[64][65];
+    const int n = min(*n_dev, 64);
+    for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
+        const int i = idx % 64, j = idx / 64;
+        R[i][j] = (i <= j && j < n) ? G[i + (long)j * ldg] : 0.0;
+        Rinv[i + 64L * j] = 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            double t = R[k][k];
+            for (int p = 0; p < k; ++p) t -= R[p][k] * R[p][k];
+            R[k][k] = t > 0.0 ? sqrt(t) : __longlong_as_double(0x7FF8000000000000ll);
+        }
+        __syncthreads();
+        for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+            double t = R[k][j];
+            for (int p = 0; p < k; ++p) t -= R[p][k] * R[p][j];
+            R[k][j] = t / R[k][k];
+        }
+        __syncthreads();
+    }
+    // R X = I by back substitution, one column of X = R^-1 per thread
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double* x = Rinv + 64L * j;
+        for (int i = j; i >= 0; --i) {
+            double t = i == j ? 1.0 : 0.0;
+            for (int p = i + 1; p <= j; ++p) t -= R[i][p] * x[p];
+            x[i] = t / R[i][i];
+        }
+    }
+}
+
+// out[:, *off_dev + j] = sum_{i <= j} W[:, i] Rinv[i, j] for j < *n_dev
+// (Rinv upper, ld 64): one row per thread, 16 output columns at a time.
+__global__ void k_apply_upper(const double* __restrict__ W, long d, const double* __restrict__ Rinv,
+                              const int* n_dev, double* out, const int* off_dev) {
+    __shared__ double Rs[64 * 64];
+    const int n = min(*n_dev, 64);
+    for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) Rs[idx] = Rinv[idx];
+    __syncthreads();
+    double* o = out + (long)(*off_dev) * d;
+    for (long row = (long)blockIdx.x * blockDim.x + threadIdx.x; row < d; row += (long)gridDim.x * blockDim.x) {
+        for (int j0 = 0; j0 < n; j0 += 16) {
+            double acc[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+            const int iend = min(n, j0 + 16);
+            for (int i = 0; i < iend; ++i) {
+                const double w = W[row + (long)i * d];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) acc[k] += w * Rs[i + 64 * (j0 + k)];
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (j0 + k < n) o[row + (long)(j0 + k) * d] = acc[k];
+        }
+    }
+}
 
 constexpr int TN_RPC = 512;   // rows per chunk, gemm_tn
 constexpr int GV_RPC = 1024;  // rows per chunk, gemv_tn
@@ -545,7 +668,11 @@ int intra_block_grid() {
 
 cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2, const int* r_old_dev,
                         int* r_dev, int cap, double eta, double* Q, double* D, int* kept, double* ratio,
-                        const TsWork& w, GridBar* gb, cudaStream_t s, int max_blocks) {
+                        const TsWork& w, GridBar* gb, cudaStream_t s, int max_blocks, bool compact) {
+    if (compact) {
+        Q = wv;
+        D = wz;
+    }
     if (m < 1 || m > 64) return cudaErrorInvalidValue;
     int nb = intra_block_grid();
     if (max_blocks > 0 && nb > max_blocks) nb = max_blocks;
@@ -557,7 +684,7 @@ cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2,
     if (e != cudaSuccess) return e;
     double* part = w.partial;
     void* args[] = {&wv, &wz, &d, &m, (void*)&a2, (void*)&r_old_dev, &r_dev, &cap, &eta, &Q, &D, &kept, &ratio,
-                    &part, &pstride, &gb};
+                    &part, &pstride, &gb, &compact};
     e = cudaLaunchCooperativeKernel((const void*)k_intra_block, dim3(nb), dim3(IB_NT), args, 0, s);
     count_launches(1);
     return e;
@@ -579,6 +706,31 @@ cudaError_t sub_mapped(const double* a, const double* b, double* out, long d, in
     int nb = cdiv(d, 256);
     if (nb > 256) nb = 256;
     k_sub_mapped<<<dim3(nb, maxn), 256, 0, s>>>(a, b, out, d, beg, end);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t cholqr_block(double* W, double* Z, long d, int m, const int* nk_dev, double* G, double* Rinv,
+                         double* Q, double* D, const int* off_dev, const TsWork& w, cudaStream_t s) {
+    if (m < 1 || m > 64) return cudaErrorInvalidValue;
+    // G = W^T W over the kept columns, R^-1 of its Cholesky factor, then
+    // Q[:, off + j] = (W R^-1)_j and D likewise
+    cudaError_t e = gemm_tn(W, d, nullptr, nk_dev, m, W, d, m, d, G, 64, w, s);
+    if (e != cudaSuccess) return e;
+    k_cholqr<<<1, 64, 0, s>>>(G, 64, nk_dev, Rinv);
+    int nb = cdiv(d, 256);
+    if (nb > 4 * 152) nb = 4 * 152;
+    k_apply_upper<<<nb, 256, 0, s>>>(W, d, Rinv, nk_dev, Q, off_dev);
+    count_launches(2);
+    if (Z) {
+        k_apply_upper<<<nb, 256, 0, s>>>(Z, d, Rinv, nk_dev, D, off_dev);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t sub_int(const int* a, const int* b, int* out, cudaStream_t s) {
+    k_sub_int<<<1, 1, 0, s>>>(a, b, out);
     count_launches(1);
     return cudaGetLastError();
 }

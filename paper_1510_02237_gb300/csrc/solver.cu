@@ -63,7 +63,8 @@ struct pr_solver {
     double *gbuf = nullptr, *resp = nullptr, *ratios = nullptr;   // ratios: PR_MAX_ITERS x N
     float *Q32 = nullptr, *D32 = nullptr, *dlt = nullptr, *gbuf32 = nullptr;
     int* r_it = nullptr;
-    int *r = nullptr, *r_old = nullptr, *kept = nullptr, *ranks = nullptr, *zero = nullptr;
+    int *r = nullptr, *r_old = nullptr, *kept = nullptr, *ranks = nullptr, *zero = nullptr, *nk = nullptr;
+    double *G = nullptr, *Rinv = nullptr;   // 64 x 64 Gram matrix and R^-1 of the block Cholesky QR
     int* kept_hist = nullptr;                       // PR_MAX_ITERS x N kept flags
     int M_hist[PR_MAX_ITERS] = {};
     GridBar* gbar = nullptr;
@@ -118,6 +119,8 @@ static Sizes compute_sizes(int nx, int ny, int N, int K_max, const pr_options& o
     if (cap > s.d) cap = (int)s.d;
     s.cap = cap < 1 ? 1 : cap;
     s.partial = tswork_elems(s.d, s.cap, N);
+    const long pg = tswork_elems(s.d, 64, 64);   // Gram matrices of the block Cholesky QR
+    if (pg > s.partial) s.partial = pg;
     size_t dd = sizeof(double);
     size_t b = 0;
     b += dd * (size_t)(N + 1) * s.d;           // q
@@ -136,6 +139,7 @@ static Sizes compute_sizes(int nx, int ny, int N, int K_max, const pr_options& o
         b += sizeof(float) * ((size_t)s.cap * s.d * 2 + (size_t)s.d * 3);   // Q32, D32, delta, ping-pong
     b += dd * (size_t)chain_resp_elems(N);
     b += dd * ((size_t)s.cap * N + s.cap);     // C, cvec
+    b += dd * 2 * 64 * 64;                     // G, Rinv
     b += dd * (size_t)s.partial;
     b += dd * (size_t)(N + (N + 1) + PR_MAX_ITERS + 1);
     b += sizeof(int) * (size_t)(3 + N + PR_MAX_ITERS);
@@ -233,11 +237,43 @@ static pr_status coarse_apply(pr_solver* h, const double* in, double* out, int n
 
 // ------------------------------------------------------------------ subspace update
 
+// One classical Gram-Schmidt pass of the mm columns v (and their D-images z)
+// against the basis columns [0, *r_old): C = Q^T v, v <- v - Q C, z <- z - D C,
+// on the FP64 units or with the tensor-core projections.
+static pr_status block_pass(pr_solver* h, double* v, double* z, int mm) {
+    const long d = h->d;
+    const int cap = h->cap;
+    cudaStream_t s = h->stream;
+    TsWork w{h->partial, h->partial_elems};
+    if (h->use_sg) {
+        CKC(sg_cgs_pass(&h->sg, v, d, mm, h->r_old, s));
+        if (z) CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->sg.C, h->sg.cap_pad, z, d, z, d, mm, d, -1.0, s));
+    } else {
+        CKC(gemm_tn(h->Q, d, nullptr, h->r_old, cap, v, d, mm, d, h->C, cap, w, s));
+        CKC(gemm_nn(h->Q, d, nullptr, h->r_old, cap, h->C, cap, v, d, v, d, mm, d, -1.0, s));
+        if (z) CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->C, cap, z, d, z, d, mm, d, -1.0, s));
+    }
+    return PR_OK;
+}
+
 // Append the m columns V (with fine images FV and coarse images GV) to the
-// subspace, in order (Eq. subspaceUpdate): two passes of block classical
-// Gram-Schmidt against the basis present at entry, then two passes against
-// the columns kept earlier in this block, then the drop rule.  The D-images
-// Z = FV - GV receive exactly the same coefficients, so D = F(Q) - G(Q).
+// subspace, in order (Eq. subspaceUpdate), by block Gram-Schmidt with
+// reorthogonalisation of the orthonormalised block (the BCGS2 of Barlow and
+// Smoktunowicz), in blocks of B columns (16 with the tensor-core
+// projections, 64 otherwise):
+//   1. one projection pass of the block against the basis present at entry;
+//   2. classical Gram-Schmidt twice within the block, column by column, with
+//      the drop rule on the residual ratio; the kept columns, normalised,
+//      are compacted in place;
+//   3. a second projection pass of that orthonormal block against the basis;
+//   4. Cholesky QR of the block (its Gram matrix is I up to rounding) and
+//      the append.
+// Step 3 restores orthogonality to the basis that step 2 loses when the
+// block's own columns are nearly dependent (in-block ratios of 1e-6 leave
+// components of size eps / 1e-6 along the old basis, and they compound from
+// block to block); the drop decisions and ratios come from step 2.  The
+// D-images Z = FV - GV receive exactly the same transformations, so
+// D = F(Q) - G(Q).
 template <typename Mark, typename SubMark>
 static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, const double* GV, int m, Mark mark,
                               SubMark sub_mark, double* ratio = nullptr) {
@@ -249,45 +285,23 @@ static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, c
     CKC(cudaMemcpyAsync(h->wv, V, sizeof(double) * m * d, cudaMemcpyDeviceToDevice, s));
     if (images) CKC(sub(FV, GV, h->wz, (long)m * d, s));
     CKC(colnorm2(h->wv, d, m, d, h->anorm2, w, s));
-    if (h->use_sg) {
-        // Sub-blocks of SG_N columns: two passes of block classical
-        // Gram-Schmidt against every column kept so far, with C = Q^T v and
-        // v - Q C on the tensor cores (FP64-accurate, split digits), then the
-        // in-block passes, drop rule and append in FP64, and the digits of
-        // the appended columns for the next products.
-        for (int j0 = 0; j0 < m; j0 += SG_N) {
-            const int mm = m - j0 < SG_N ? m - j0 : SG_N;
-            double* v = h->wv + (long)j0 * d;
-            double* z = images ? h->wz + (long)j0 * d : nullptr;
-            CKC(cudaMemcpyAsync(h->r_old, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
-            for (int pass = 0; pass < 2; ++pass) {
-                CKC(sg_cgs_pass(&h->sg, v, d, mm, h->r_old, s));
-                if (images)
-                    CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->sg.C, h->sg.cap_pad, z, d, z, d, mm, d, -1.0, s));
-            }
-            CKC(sub_mark(0));
-            CKC(intra_block(v, z, d, mm, h->anorm2 + j0, h->r_old, h->r, cap, h->opt.drop_tol, h->Q, h->D,
-                            h->kept + j0, ratio ? ratio + j0 : nullptr, w, h->gbar, s, h->opt.sm_limit));
-            CKC(sg_append(&h->sg, h->Q, d, h->r_old, h->r, 0, mm, s));
-            CKC(sub_mark(1));
-        }
-        CKC(mark());
-        return PR_OK;
-    }
-    for (int j0 = 0; j0 < m; j0 += 64) {
-        const int mm = m - j0 < 64 ? m - j0 : 64;
+    const int B = h->use_sg ? SG_N : 64;
+    for (int j0 = 0; j0 < m; j0 += B) {
+        const int mm = m - j0 < B ? m - j0 : B;
         double* v = h->wv + (long)j0 * d;
         double* z = images ? h->wz + (long)j0 * d : nullptr;
         CKC(cudaMemcpyAsync(h->r_old, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
-        for (int pass = 0; pass < 2; ++pass) {
-            CKC(gemm_tn(h->Q, d, nullptr, h->r_old, cap, v, d, mm, d, h->C, cap, w, s));
-            CKC(gemm_nn(h->Q, d, nullptr, h->r_old, cap, h->C, cap, v, d, v, d, mm, d, -1.0, s));
-            if (images) CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->C, cap, z, d, z, d, mm, d, -1.0, s));
-        }
-        if (j0 == 0) CKC(mark());
+        CKS(block_pass(h, v, z, mm));
+        CKC(sub_mark(0));
         CKC(intra_block(v, z, d, mm, h->anorm2 + j0, h->r_old, h->r, cap, h->opt.drop_tol, h->Q, h->D,
-                        h->kept + j0, ratio ? ratio + j0 : nullptr, w, h->gbar, s, h->opt.sm_limit));
+                        h->kept + j0, ratio ? ratio + j0 : nullptr, w, h->gbar, s, h->opt.sm_limit, true));
+        CKC(sub_mark(1));
+        CKC(sub_int(h->r, h->r_old, h->nk, s));
+        CKS(block_pass(h, v, z, mm));
+        CKC(cholqr_block(v, z, d, mm, h->nk, h->G, h->Rinv, h->Q, h->D, h->r_old, w, s));
+        if (h->use_sg) CKC(sg_append(&h->sg, h->Q, d, h->r_old, h->r, 0, mm, s));
     }
+    CKC(mark());
     return PR_OK;
 }
 
@@ -705,7 +719,9 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     chk(dalloc(&h->res2, (size_t)N + 1));
     chk(dalloc(&h->rhist, (size_t)PR_MAX_ITERS));
     chk(dalloc(&h->nres2, 1));
-    chk(cudaMalloc((void**)&h->r, sizeof(int) * 4));
+    chk(cudaMalloc((void**)&h->r, sizeof(int) * 8));
+    chk(dalloc(&h->G, 64 * 64));
+    chk(dalloc(&h->Rinv, 64 * 64));
     if (o.corr_prec == PR_FP32) {
         chk(cudaMalloc((void**)&h->Q32, sizeof(float) * (size_t)h->cap * d));
         chk(cudaMalloc((void**)&h->D32, sizeof(float) * (size_t)h->cap * d));
@@ -720,7 +736,8 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
         h->r_old = h->r + 1;
         h->zero = h->r + 2;
         h->r_it = h->r + 3;
-        chk(cudaMemset(h->r, 0, sizeof(int) * 4));
+        h->nk = h->r + 4;
+        chk(cudaMemset(h->r, 0, sizeof(int) * 8));
         chk(cudaMemset(h->ranks, 0, sizeof(int) * PR_MAX_ITERS));
         chk(cudaMemset(h->gbar, 0, sizeof(GridBar)));
         chk(cudaMemset(h->rhist, 0, sizeof(double) * PR_MAX_ITERS));
@@ -746,7 +763,7 @@ pr_status parareal_destroy(pr_solver* h) {
     if (h->stream || h->q) cudaStreamSynchronize(h->stream);
     double* ds[] = {h->q, h->qt, h->gv, h->kold, h->Q, h->D, h->wv, h->wz, h->fb0, h->fb1, h->fb2, h->cb0, h->cb1,
                     h->gtmp, h->C, h->cvec, h->partial, h->anorm2, h->res2, h->rhist, h->nres2,
-                    h->gbuf, h->resp, h->ratios};
+                    h->gbuf, h->resp, h->ratios, h->G, h->Rinv};
     for (double* p : ds) if (p) cudaFree(p);
     float* fs[] = {h->Q32, h->D32, h->dlt, h->gbuf32};
     for (float* p : fs) if (p) cudaFree(p);
@@ -881,7 +898,7 @@ pr_status parareal_timing_enable(pr_solver* h, int32_t max_solves) {
     h->tr.ev.assign((size_t)max_solves * h->tr.per_solve, nullptr);
     h->tr.K.assign((size_t)max_solves, 0);
     h->tr.fine_launches.assign((size_t)max_solves, 0);
-    h->tr.sub_per_iter = h->use_sg ? (h->N + SG_N - 1) / SG_N : 0;
+    h->tr.sub_per_iter = (h->N + (h->use_sg ? SG_N : 64) - 1) / (h->use_sg ? SG_N : 64);
     h->tr.sub.assign((size_t)max_solves * h->K_max * 2 * h->tr.sub_per_iter, nullptr);
     h->tr.nsub.assign((size_t)max_solves * h->K_max, 0);
     for (auto& e : h->tr.sub) {

@@ -395,52 +395,87 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long m
     return red[32];
 }
 
-// exps[c] for columns c = c0 + blockIdx.x (c < *c1_dev when given).
-__global__ void k_col_exp(const double* __restrict__ X, long ldx, long nrows, const int* c0_dev, const int* c1_dev,
-                          int c0_host, int* exps) {
+// keys[c] = max over a share of the rows of the |x| key of column
+// c = c0 + blockIdx.y (c < *c1_dev when given); keys zeroed beforehand.
+// Many CTAs per column, so the column maxima stream at full bandwidth.
+__global__ void k_col_max(const double* __restrict__ X, long ldx, long nrows, const int* c0_dev, const int* c1_dev,
+                          int c0_host, unsigned long long* keys) {
     __shared__ unsigned long long red[33];
-    const int c = (c0_dev ? *c0_dev : c0_host) + (int)blockIdx.x;
+    const int c = (c0_dev ? *c0_dev : c0_host) + (int)blockIdx.y;
     if (c1_dev && c >= *c1_dev) return;
     const double* x = X + (long)c * ldx;
     unsigned long long m = 0;
-    for (long row = threadIdx.x; row < nrows; row += blockDim.x) {
+    for (long row = (long)blockIdx.x * blockDim.x + threadIdx.x; row < nrows; row += (long)gridDim.x * blockDim.x) {
         const unsigned long long b = abs_bits(x[row]);
         m = b > m ? b : m;
     }
     m = block_max_u64(m, red);
-    if (threadIdx.x == 0) exps[c] = exponent_of_max(m);
+    if (threadIdx.x == 0 && m > 0) atomicMax(keys + c, m);
 }
 
-// Digits of basis columns [c0, c1) of Q in the column layout Xc[s][c][row]
-// (rows = contraction of Q^T V) and the row layout Xr[s][row][c]
-// (columns = contraction of Q C).
-__global__ void k_digits_basis(const double* __restrict__ Q, long ldq, long d, const int* c0_dev, const int* c1_dev,
-                               int c0_host, int maxcols, const int* __restrict__ exps, __nv_bfloat16* Xc,
-                               __nv_bfloat16* Xr, int cap_pad) {
+// Digits of basis columns [c0, c1) (at most SG_N) of Q in the column layout
+// Xc[s][c][row] (rows = contraction of Q^T V) and the row layout
+// Xr[s][row][c] (columns = contraction of Q C); exps[c] from the column
+// maxima keys.  A CTA takes 128 rows: digits are formed one row per thread
+// (column-layout stores coalesced along rows), staged in shared memory, and
+// the row-layout stores are issued with consecutive threads on consecutive
+// columns of a row.
+constexpr int DB_ROWS = 128;
+__global__ void __launch_bounds__(DB_ROWS) k_digits_basis(const double* __restrict__ Q, long ldq, long d,
+                                                          const int* c0_dev, const int* c1_dev, int c0_host,
+                                                          int maxcols, const unsigned long long* __restrict__ keys,
+                                                          int* exps, __nv_bfloat16* Xc, __nv_bfloat16* Xr,
+                                                          int cap_pad) {
+    __shared__ __nv_bfloat16 tile[SG_S][DB_ROWS][SG_N];
+    __shared__ int se[SG_N];
     const int c0 = c0_dev ? *c0_dev : c0_host;
     const int c1 = c1_dev ? min(*c1_dev, c0 + maxcols) : c0 + maxcols;
-    for (long row = (long)blockIdx.x * blockDim.x + threadIdx.x; row < d; row += (long)gridDim.x * blockDim.x) {
-        for (int c = c0; c < c1; ++c) {
-            __nv_bfloat16 dg[SG_S];
-            digits8(Q[row + (long)c * ldq], exps[c], dg);
+    const int nc = min(c1 - c0, SG_N);
+    if (nc <= 0) return;
+    if (threadIdx.x < nc) {
+        se[threadIdx.x] = exponent_of_max(keys[c0 + threadIdx.x]);
+        if (blockIdx.x == 0) exps[c0 + threadIdx.x] = se[threadIdx.x];
+    }
+    __syncthreads();
+    for (long r0 = (long)blockIdx.x * DB_ROWS; r0 < d; r0 += (long)gridDim.x * DB_ROWS) {
+        const long row = r0 + threadIdx.x;
+        if (row < d) {
+            for (int j = 0; j < nc; ++j) {
+                __nv_bfloat16 dg[SG_S];
+                digits8(Q[row + (long)(c0 + j) * ldq], se[j], dg);
 #pragma unroll
-            for (int s = 0; s < SG_S; ++s) {
-                Xc[((long)s * cap_pad + c) * d + row] = dg[s];
-                Xr[((long)s * d + row) * cap_pad + c] = dg[s];
+                for (int s = 0; s < SG_S; ++s) {
+                    Xc[((long)s * cap_pad + c0 + j) * d + row] = dg[s];
+                    tile[s][threadIdx.x][j] = dg[s];
+                }
             }
         }
+        __syncthreads();
+        for (int s = 0; s < SG_S; ++s) {
+            for (int idx = threadIdx.x; idx < DB_ROWS * SG_N; idx += DB_ROWS) {
+                const int rl = idx / SG_N, j = idx % SG_N;
+                if (j < nc && r0 + rl < d) Xr[((long)s * d + r0 + rl) * cap_pad + c0 + j] = tile[s][rl][j];
+            }
+        }
+        __syncthreads();
     }
 }
 
 // Digits of the block V (m columns, ld ldv) into Vs[s][j][row]; columns
 // j in [m, SG_N) are zero.
-__global__ void k_digits_block(const double* __restrict__ V, long ldv, long d, int m, const int* __restrict__ exps,
-                               __nv_bfloat16* Vs) {
+__global__ void k_digits_block(const double* __restrict__ V, long ldv, long d, int m,
+                               const unsigned long long* __restrict__ keys, int* exps, __nv_bfloat16* Vs) {
+    __shared__ int se[SG_N];
+    if (threadIdx.x < SG_N) {
+        se[threadIdx.x] = threadIdx.x < m ? exponent_of_max(keys[threadIdx.x]) : 0;
+        if (blockIdx.x == 0) exps[threadIdx.x] = se[threadIdx.x];
+    }
+    __syncthreads();
     for (long row = (long)blockIdx.x * blockDim.x + threadIdx.x; row < d; row += (long)gridDim.x * blockDim.x) {
         for (int j = 0; j < SG_N; ++j) {
             __nv_bfloat16 dg[SG_S];
             if (j < m) {
-                digits8(V[row + (long)j * ldv], exps[j], dg);
+                digits8(V[row + (long)j * ldv], se[j], dg);
             } else {
 #pragma unroll
                 for (int s = 0; s < SG_S; ++s) dg[s] = __float2bfloat16_rn(0.f);
@@ -456,43 +491,53 @@ __global__ void k_digits_block(const double* __restrict__ V, long ldv, long d, i
 // launched on tn_grid CTAs, summed in a fixed order), or C given (Cin).  Then
 // the folded column C'[l] = 2^{E_l} C[l, j] (l < r; zero up to kpad), its
 // exponent G_j and its digits Cs[s][j][l].  Columns j >= m are zero.
-__global__ void k_finish(const double* __restrict__ ws, int rows_pad, int tn_grid, long d, const int* r_dev,
-                         const int* __restrict__ Eq, const int* __restrict__ Fv, int m, double* C, int ldc,
-                         const double* __restrict__ Cin, int ldcin, __nv_bfloat16* Cs, int kpad, int* Gc) {
+constexpr int FIN_T = 1024;   // threads of k_finish: 4 groups of 256 rows
+__global__ void __launch_bounds__(FIN_T) k_finish(const double* __restrict__ ws, int rows_pad, int tn_grid, long d,
+                                                  const int* r_dev, const int* __restrict__ Eq,
+                                                  const int* __restrict__ Fv, int m, double* C, int ldc,
+                                                  const double* __restrict__ Cin, int ldcin, __nv_bfloat16* Cs,
+                                                  int kpad, int* Gc) {
     extern __shared__ double cp[];   // kpad values
+    __shared__ double part[4][256];
     __shared__ unsigned long long red[33];
     const int j = blockIdx.x;
     const int r = min(*r_dev, kpad);
     int tiles = 1, nsplit = 1;
     long kps = 0;
     if (ws && r > 0) tn_layout(r, d, tn_grid, &tiles, &nsplit, &kps);
+    const int grp = threadIdx.x >> 8, li = threadIdx.x & 255;
     unsigned long long mb = 0;
-    for (int l = threadIdx.x; l < kpad; l += blockDim.x) {
-        double v = 0.0;
-        if (j < m && l < r) {
-            double c;
-            if (ws) {
+    for (int l0 = 0; l0 < kpad; l0 += 256) {
+        const int l = l0 + li;
+        const bool live = j < m && l < r;
+        if (ws) {
+            // group grp sums the splits k = grp, grp + 4, ... in order
+            double s = 0.0;
+            if (live) {
                 const double* p = ws + (long)j * rows_pad + l;
                 const long st = (long)SG_N * rows_pad;
-                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                int k = 0;
-                for (; k + 3 < nsplit; k += 4) {
-                    s0 += p[k * st];
-                    s1 += p[(k + 1) * st];
-                    s2 += p[(k + 2) * st];
-                    s3 += p[(k + 3) * st];
-                }
-                for (; k < nsplit; ++k) s0 += p[k * st];
-                c = ldexp((s0 + s1) + (s2 + s3), Eq[l] + Fv[j] - 14);
-                C[l + (long)j * ldc] = c;
-            } else {
-                c = Cin[l + (long)j * ldcin];
+                for (int k = grp; k < nsplit; k += 4) s += p[k * st];
             }
-            v = ldexp(c, Eq[l]);
+            part[grp][li] = s;
         }
-        cp[l] = v;
-        const unsigned long long b = abs_bits(v);
-        mb = b > mb ? b : mb;
+        __syncthreads();
+        if (grp == 0 && l < kpad) {
+            double v = 0.0;
+            if (live) {
+                double cc;
+                if (ws) {
+                    cc = ldexp((part[0][li] + part[1][li]) + (part[2][li] + part[3][li]), Eq[l] + Fv[j] - 14);
+                    C[l + (long)j * ldc] = cc;
+                } else {
+                    cc = Cin[l + (long)j * ldcin];
+                }
+                v = ldexp(cc, Eq[l]);
+            }
+            cp[l] = v;
+            const unsigned long long b = abs_bits(v);
+            mb = b > mb ? b : mb;
+        }
+        __syncthreads();
     }
     mb = block_max_u64(mb, red);
     const int G = exponent_of_max(mb);
@@ -565,7 +610,7 @@ size_t sg_bytes(long d, int cap) {
     b += 2 * (size_t)SG_S * cap_pad * d * 2;         // Xc, Xr
     b += (size_t)SG_S * SG_N * d * 2;                // Vs
     b += (size_t)SG_S * SG_N * cap_pad * 2;          // Cs
-    b += sizeof(int) * ((size_t)cap_pad + 2 * SG_N + 1);
+    b += sizeof(int) * ((size_t)cap_pad + 2 * SG_N + 1) + sizeof(unsigned long long) * ((size_t)cap_pad + SG_N);
     b += sizeof(double) * ((size_t)grid * cap_pad * SG_N + (size_t)SG_N * cap_pad);
     return b;
 }
@@ -594,6 +639,8 @@ cudaError_t sg_init(SplitGemm* g, long d, int cap) {
     SG_ALLOC(g->Vs, (size_t)SG_S * SG_N * d * 2);
     SG_ALLOC(g->Cs, (size_t)SG_S * SG_N * cp * 2);
     SG_ALLOC(g->Eq, sizeof(int) * cp);
+    SG_ALLOC(g->Kq, sizeof(unsigned long long) * cp);
+    SG_ALLOC(g->Kv, sizeof(unsigned long long) * SG_N);
     SG_ALLOC(g->Fv, sizeof(int) * SG_N);
     SG_ALLOC(g->Gc, sizeof(int) * SG_N);
     SG_ALLOC(g->err, sizeof(int));
@@ -626,6 +673,8 @@ void sg_free(SplitGemm* g) {
     cudaFree(g->Vs);
     cudaFree(g->Cs);
     cudaFree(g->Eq);
+    cudaFree(g->Kq);
+    cudaFree(g->Kv);
     cudaFree(g->Fv);
     cudaFree(g->Gc);
     cudaFree(g->err);
@@ -634,26 +683,46 @@ void sg_free(SplitGemm* g) {
     *g = SplitGemm();
 }
 
+static int colmax_blocks(long d) {
+    long nb = (d + 256 * 16 - 1) / (256 * 16);
+    return (int)(nb < 1 ? 1 : nb > 128 ? 128 : nb);
+}
+
 cudaError_t sg_append(SplitGemm* g, const double* Q, long ldq, const int* c0_dev, const int* c1_dev, int c0_host,
                       int maxcols, cudaStream_t s) {
-    if (maxcols < 1) return cudaSuccess;
-    k_col_exp<<<maxcols, 512, 0, s>>>(Q, ldq, g->d, c0_dev, c1_dev, c0_host, g->Eq);
-    long nb = cdivl(g->d, 256);
-    if (nb > 4 * 152) nb = 4 * 152;
-    k_digits_basis<<<(int)nb, 256, 0, s>>>(Q, ldq, g->d, c0_dev, c1_dev, c0_host, maxcols, g->Eq, g->Xc, g->Xr,
-                                            g->cap_pad);
-    count_launches(2);
-    return cudaGetLastError();
+    for (int j0 = 0; j0 < maxcols; j0 += SG_N) {
+        // columns [c0 + j0, c0 + j0 + SG_N) of the (device-side) range
+        const int nc = maxcols - j0 < SG_N ? maxcols - j0 : SG_N;
+        cudaError_t e = cudaMemsetAsync(g->Kq, 0, sizeof(unsigned long long) * g->cap_pad, s);
+        if (e != cudaSuccess) return e;
+        if (c0_dev) {
+            if (j0 > 0) return cudaErrorInvalidValue;   // device ranges: at most SG_N columns per call
+            k_col_max<<<dim3(colmax_blocks(g->d), nc), 256, 0, s>>>(Q, ldq, g->d, c0_dev, c1_dev, 0, g->Kq);
+        } else {
+            k_col_max<<<dim3(colmax_blocks(g->d), nc), 256, 0, s>>>(Q, ldq, g->d, nullptr, nullptr, c0_host + j0,
+                                                                   g->Kq);
+        }
+        long nb = cdivl(g->d, DB_ROWS);
+        if (nb > 8 * 152) nb = 8 * 152;
+        k_digits_basis<<<(int)nb, DB_ROWS, 0, s>>>(Q, ldq, g->d, c0_dev, c1_dev, c0_host + j0, nc, g->Kq, g->Eq,
+                                                   g->Xc, g->Xr, g->cap_pad);
+        count_launches(2);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t sg_project(SplitGemm* g, const double* v, long ldv, int m, const int* r_dev, cudaStream_t s) {
     if (m < 1 || m > SG_N) return cudaErrorInvalidValue;
-    k_col_exp<<<m, 512, 0, s>>>(v, ldv, g->d, nullptr, nullptr, 0, g->Fv);
+    cudaError_t e = cudaMemsetAsync(g->Kv, 0, sizeof(unsigned long long) * SG_N, s);
+    if (e != cudaSuccess) return e;
+    k_col_max<<<dim3(colmax_blocks(g->d), m), 256, 0, s>>>(v, ldv, g->d, nullptr, nullptr, 0, g->Kv);
     long nb = cdivl(g->d, 256);
     if (nb > 4 * 152) nb = 4 * 152;
-    k_digits_block<<<(int)nb, 256, 0, s>>>(v, ldv, g->d, m, g->Fv, g->Vs);
+    k_digits_block<<<(int)nb, 256, 0, s>>>(v, ldv, g->d, m, g->Kv, g->Fv, g->Vs);
     count_launches(2);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     SgArgs a{};
     a.mode = 0;
@@ -667,7 +736,7 @@ cudaError_t sg_project(SplitGemm* g, const double* v, long ldv, int m, const int
     a.err = g->err;
     e = launch_mma(g->mapXc, g->mapVs, a, dim3((unsigned)g->grid), s);
     if (e != cudaSuccess) return e;
-    k_finish<<<SG_N, 256, sizeof(double) * g->cap_pad, s>>>(g->ws, g->cap_pad, g->grid, g->d, r_dev, g->Eq, g->Fv, m,
+    k_finish<<<SG_N, FIN_T, sizeof(double) * g->cap_pad, s>>>(g->ws, g->cap_pad, g->grid, g->d, r_dev, g->Eq, g->Fv, m,
                                                             g->C, g->cap_pad, nullptr, 0, g->Cs, g->cap_pad, g->Gc);
     count_launches(1);
     return cudaGetLastError();
@@ -699,7 +768,7 @@ cudaError_t sg_cgs_pass(SplitGemm* g, double* v, long ldv, int m, const int* r_d
 cudaError_t sg_update(SplitGemm* g, double* v, long ldv, int m, const double* C, int ldc, const int* r_dev,
                       cudaStream_t s) {
     if (m < 1 || m > SG_N) return cudaErrorInvalidValue;
-    k_finish<<<SG_N, 256, sizeof(double) * g->cap_pad, s>>>(nullptr, 0, 0, g->d, r_dev, g->Eq, nullptr, m, nullptr, 0,
+    k_finish<<<SG_N, FIN_T, sizeof(double) * g->cap_pad, s>>>(nullptr, 0, 0, g->d, r_dev, g->Eq, nullptr, m, nullptr, 0,
                                                             C, ldc, g->Cs, g->cap_pad, g->Gc);
     count_launches(1);
     cudaError_t e = cudaGetLastError();

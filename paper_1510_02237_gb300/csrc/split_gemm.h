@@ -40,6 +40,8 @@ struct SplitGemm {
     int* Eq = nullptr;             // [cap] column exponents of Q
     int* Fv = nullptr;             // [SG_N] column exponents of V
     int* Gc = nullptr;             // [SG_N] column exponents of 2^{E_l} C
+    unsigned long long* Kq = nullptr;   // [cap_pad] column maxima keys (|x| bit patterns) of Q
+    unsigned long long* Kv = nullptr;   // [SG_N] the same for V
     double* ws = nullptr;          // [grid][SG_N][cap_pad] partial sums of Q^T V
     double* C = nullptr;           // [SG_N][cap_pad] coefficients Q^T V (column-major, ld cap_pad)
     int* err = nullptr;            // sticky: a pipeline wait gave up
@@ -51,7 +53,9 @@ size_t sg_bytes(long d, int cap);
 // Allocate and set up (tensor maps included); d must be a multiple of 8.
 cudaError_t sg_init(SplitGemm* g, long d, int cap);
 void sg_free(SplitGemm* g);
-// Digits of columns [c0, c1) of Q (device range, at most maxcols) in both layouts.
+// Digits of columns [c0, c1) of Q in both layouts: a device range (c0_dev,
+// c1_dev; at most maxcols <= SG_N columns) or host columns [c0_host,
+// c0_host + maxcols).
 cudaError_t sg_append(SplitGemm* g, const double* Q, long ldq, const int* c0_dev, const int* c1_dev, int c0_host,
                       int maxcols, cudaStream_t s);
 // One classical Gram-Schmidt pass of the m <= SG_N columns v (ld ldv) against

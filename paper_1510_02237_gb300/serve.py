@@ -92,8 +92,10 @@ class Server:
         self.bytes = 0
 
     # ---------------------------------------------------------------- slots
-    def _options(self, p, K_max):
-        opt = {"K_max": K_max}
+    def solver_options(self, p) -> dict:
+        """Options of the handles this server creates for problem p (also what
+        reproduces a served result with a handle of one's own)."""
+        opt = {}
         if self.mode == "mixed":
             opt.update(fine_prec=PR_FP32X, corr_prec=PR_FP32)
             if (3 * p.nx * p.ny) % 8 == 0:
@@ -101,6 +103,9 @@ class Server:
         if self.sm_limit:
             opt["sm_limit"] = self.sm_limit(p.d, self.sms)
         return opt
+
+    def _options(self, p, K_max):
+        return dict(self.solver_options(p), K_max=K_max)
 
     def _key(self, inst):
         p = inst.problem

@@ -86,12 +86,12 @@ def test_server_results_equal_alone_and_budget_holds():
     budget = 3.0e9
     srv = serve.Server(budget_bytes=budget, max_inflight=5, mode="mixed")
     results, stats = srv.run(reqs)
-    sms = srv.sms
+    opts = [srv.solver_options(inst.problem) for _, inst in reqs]
     srv.close()
     assert stats.completed == len(reqs) and stats.peak_bytes <= budget
     assert 2 <= stats.peak_inflight <= 5     # requests overlapped on the device, within the limit
-    for (t, inst), r in zip(reqs, results):
-        want = _alone(inst, fine_prec=P.PR_FP32X, corr_prec=P.PR_FP32,
-                      sm_limit=serve.default_sm_limit(inst.problem.d, sms))
+    for (t, inst), r, opt in zip(reqs, results, opts):
+        assert opt["proj_prec"] == P.PR_PROJ_SPLIT_BF16 and opt["corr_prec"] == P.PR_FP32
+        want = _alone(inst, **opt)
         assert np.array_equal(r.qT, want)
         assert r.latency > 0
