@@ -295,18 +295,24 @@ def serving_workload(P, torch, rates=(10, 30, 100, 300, 1000), n_req=120):
 
 def precision_workload(P, torch, stream):
     """512x256, N = 64, K = 5, power-law Fourier IC: one solve each in plain FP64
-    (images by linearity, as in the paper), FP64 with direct images, and mixed
-    precision (FP32 tendencies on an FP64 state, FP32 correction, FP64-accurate
-    Gram-Schmidt with its projections on FP64 units or, the served form, on the
-    tensor cores), each timed with CUDA events after one untimed solve, with
-    the error of each against the serial FP64 fine solution."""
+    (images by linearity, as in the paper), FP64 with direct images, FP64 with
+    direct images and the tensor-core projections, and the served mixed-precision
+    form (FP32 tendencies on an FP64 state, FP32 correction, FP64-accurate
+    Gram-Schmidt with the tensor-core projections), each timed with CUDA events
+    after one untimed solve, with the error of each against the serial FP64
+    fine solution.  Mixed and FP64 are compared at equal algorithm (same
+    Gram-Schmidt blocking): at this workload the iterate matrix is so nearly
+    dependent (condition ~1e15 after column scaling) that the subspace's last
+    directions, and with them eps, depend on the order of rounding in any
+    FP64 Gram-Schmidt."""
     wl = W.workload_large()
     p, K = wl.problem, wl.K
     u0 = torch.from_numpy(wl.ics[0][1]().ravel()).cuda()
     res = {"workload": wl.name, "grid": f"{p.nx}x{p.ny}", "N_slices": p.n_slices, "K": K}
     qs = None
     for tag, opt in (("fp64", {}), ("fp64_direct", {"images": P.PR_IMAGES_DIRECT}),
-                     ("mixed_proj_fp64", {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32}),
+                     ("fp64_direct_tc_projection", {"images": P.PR_IMAGES_DIRECT,
+                                                    "proj_prec": P.PR_PROJ_SPLIT_BF16}),
                      ("mixed", {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32,
                                 "proj_prec": P.PR_PROJ_SPLIT_BF16})):
         s = P.Solver(p, stream=stream, K_max=K, **opt)
@@ -319,10 +325,14 @@ def precision_workload(P, torch, stream):
                     "min_kept_ratio": [float(x) for x in rep.min_ratio[:K]]}
         s.close()
     res["speedup_mixed_vs_fp64"] = res["fp64"]["ms_per_solve"] / res["mixed"]["ms_per_solve"]
-    res["abs_eps_diff_mixed_vs_fp64_direct"] = abs(res["fp64_direct"]["eps"] - res["mixed"]["eps"])
-    res["note"] = ("the first iteration's columns are nearly dependent (min kept ratio ~1e-6): F(Q) formed "
-                   "by linearity (fp64) carries amplified rounding; fp64_direct is the well-conditioned FP64 "
-                   "evaluation the mixed solve is compared with")
+    res["abs_eps_diff_mixed_vs_fp64_same_algorithm"] = abs(res["fp64_direct_tc_projection"]["eps"]
+                                                           - res["mixed"]["eps"])
+    res["abs_eps_diff_between_fp64_gram_schmidt_blockings"] = abs(res["fp64_direct"]["eps"]
+                                                                 - res["fp64_direct_tc_projection"]["eps"])
+    res["note"] = ("eps of the FP64 solves depends on the Gram-Schmidt's rounding: the 64 first-iteration "
+                   "iterates have condition 4.6e15 after column scaling, and a 1e-16 relative perturbation "
+                   "moves the projector onto their span by 13-19 %; images by linearity (fp64) add the "
+                   "1/min-ratio amplification of Eq. Genhance")
     return res
 
 

@@ -39,8 +39,9 @@ constexpr int SG_THREADS = 256;
 
 struct SgArgs {
     int mode;               // 0: partial sums of Q^T V;  1: V <- V - Q C
-    int a_rows_per_slice;   // outer-coordinate offset between digit slices, long operand
-    int b_rows_per_slice;   // same, narrow operand
+    long a_slice_units;     // long operand: units between digit slices
+    long a_kb_units;        //   units between contraction blocks (= its row groups)
+    long b_slice_units;     // narrow operand: units between digit slices (2 per block)
     const int* rows_dev;    // mode 0: valid rows (basis columns r)
     int rows_host;          // bound on the rows of the long operand (mode 0: cap, mode 1: d)
     const int* k_dev;       // mode 1: contraction length (basis columns); NULL: k_host
@@ -80,12 +81,13 @@ __device__ __forceinline__ void sg_fail(int* err, volatile int* abort_flag) {
 // pipeline counters run on across items, so loads of the next item overlap
 // the epilogue of the current one.
 __global__ void __launch_bounds__(SG_THREADS, 1)
-    k_split_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const SgArgs a) {
+    k_split_mma(const __grid_constant__ CUtensorMap mapA16, const __grid_constant__ CUtensorMap mapA2,
+                const __grid_constant__ CUtensorMap mapB2, const SgArgs a) {
     extern __shared__ unsigned char sg_raw[];
     __shared__ __align__(8) uint64_t bars[2 * SG_NST + 5];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort;
-    __shared__ int s_exp[SG_N];
+    __shared__ double s_scale[SG_N];   // mode 1: 2^{G_n - 14}
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int n_items, tiles = 1, nsplit = 1, rows;
@@ -139,14 +141,16 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
         tc::fence_barrier_init();
         s_abort = 0;
     }
-    if (threadIdx.x < SG_N) s_exp[threadIdx.x] = (a.mode == 1 && a.vexp) ? a.vexp[threadIdx.x] : 0;
+    if (threadIdx.x < SG_N)
+        s_scale[threadIdx.x] = (a.mode == 1 && a.vexp) ? ldexp(1.0, a.vexp[threadIdx.x] - 14) : 0.0;
     if (warp == 2) {
         tc::tmem_alloc(tc::smem_u32(&tmem_slot), SG_TMEM_COLS);
         tc::tmem_relinquish();
     }
     if (warp == 0 && lane == 0) {
-        tc::tma_prefetch_map(&mapA);
-        tc::tma_prefetch_map(&mapB);
+        tc::tma_prefetch_map(&mapA16);
+        tc::tma_prefetch_map(&mapA2);
+        tc::tma_prefetch_map(&mapB2);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -165,6 +169,9 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
                 long kb, ke;
                 item(i, row0, kb, ke, split);
                 const int ns = (int)((ke - kb + SG_KC - 1) / SG_KC);
+                // row groups of 8 to load: the tile's valid rows, rounded up to 16
+                const int ng = ((min(SG_BM, rows - row0) + 15) / 16) * 2;
+                const uint32_t bytes = (uint32_t)SG_S * (uint32_t)(ng * 512 + SG_B_TILE);
                 for (int j = 0; j < ns; ++j, ++it) {
                     const int st = it % SG_NST;
                     const uint32_t ph = (uint32_t)(it / SG_NST) & 1u;
@@ -173,14 +180,21 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
                         ok = false;
                         break;
                     }
-                    tc::mbar_expect_tx(full(st), SG_STAGE);
-                    const int k = (int)(kb + (long)j * SG_KC);
+                    tc::mbar_expect_tx(full(st), bytes);
+                    const long kblk = kb / SG_KC + j;
                     const uint32_t sa = sbase + st * SG_STAGE;
                     const uint32_t sb = sa + SG_S * SG_A_TILE;
 #pragma unroll 1
                     for (int s = 0; s < SG_S; ++s) {
-                        tc::tma_load_2d(sa + s * SG_A_TILE, &mapA, k, s * a.a_rows_per_slice + row0, full(st));
-                        tc::tma_load_2d(sb + s * SG_B_TILE, &mapB, k, s * a.b_rows_per_slice, full(st));
+                        const int ua = (int)(s * a.a_slice_units + kblk * a.a_kb_units + row0 / 8);
+                        if (ng == 16) {
+                            tc::tma_load_2d(sa + s * SG_A_TILE, &mapA16, 0, ua, full(st));
+                        } else {
+                            for (int u = 0; u < ng; u += 2)
+                                tc::tma_load_2d(sa + s * SG_A_TILE + u * 512, &mapA2, 0, ua + u, full(st));
+                        }
+                        tc::tma_load_2d(sb + s * SG_B_TILE, &mapB2, 0, (int)(s * a.b_slice_units + kblk * 2),
+                                        full(st));
                     }
                     issued[st] += 1;
                 }
@@ -296,13 +310,16 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
                 tc::mbar_arrive(tempty(buf));
             }
             if (!ok) break;
+            // (double)hi is exact (|hi| < 2^50 for up to 64 chunks); lo may
+            // round, below 2^-53 of its own size; the power-of-two scalings
+            // are exact, and the combination rounds once.
             const int row = row0 + q * 32 + lane;
             if (a.mode == 0) {
                 if (row < rows) {
 #pragma unroll
                     for (int n = 0; n < SG_N; ++n) {
                         const double t = (nanmask >> n) & 1u ? __longlong_as_double(0x7FF8000000000000ll)
-                                                               : ldexp((double)hi[n], -21) + ldexp((double)lo[n], -56);
+                                                               : fma((double)hi[n], 0x1p-21, (double)lo[n] * 0x1p-56);
                         a.ws[((long)split * SG_N + n) * a.rows_pad + row] = t;
                     }
                 }
@@ -311,8 +328,9 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
                 for (int n = 0; n < SG_N; ++n) {
                     if (n < a.ncols) {
                         const double t = (nanmask >> n) & 1u ? __longlong_as_double(0x7FF8000000000000ll)
-                                                               : ldexp((double)hi[n], -21) + ldexp((double)lo[n], -56);
-                        a.v[row + (long)n * a.ldv] -= ldexp(t, s_exp[n] - 14);
+                                                               : fma((double)hi[n], 0x1p-21, (double)lo[n] * 0x1p-56);
+                        double* o = a.v + row + (long)n * a.ldv;
+                        *o = fma(-t, s_scale[n], *o);
                     }
                 }
             }
@@ -377,6 +395,13 @@ __device__ __forceinline__ void digits8(double x, int E, __nv_bfloat16 (&dg)[SG_
     dg[0] = __float2bfloat16_rn((float)T);
 }
 
+// Element offset of (row r8 in [0, 8), contraction index k in [0, 32)) inside
+// a 512-byte operand unit: 64-byte rows, 16-byte chunks XOR-swizzled with
+// bits 1-2 of the row (the 64-byte swizzle the tensor cores' descriptors name).
+__device__ __forceinline__ int unit_elem(int r8, int k) {
+    return r8 * 32 + ((((k >> 3) ^ (r8 >> 1)) & 3) << 3) + (k & 7);
+}
+
 __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long m, unsigned long long* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -413,20 +438,15 @@ __global__ void k_col_max(const double* __restrict__ X, long ldx, long nrows, co
     if (threadIdx.x == 0 && m > 0) atomicMax(keys + c, m);
 }
 
-// Digits of basis columns [c0, c1) (at most SG_N) of Q in the column layout
-// Xc[s][c][row] (rows = contraction of Q^T V) and the row layout
-// Xr[s][row][c] (columns = contraction of Q C); exps[c] from the column
-// maxima keys.  A CTA takes 128 rows: digits are formed one row per thread
-// (column-layout stores coalesced along rows), staged in shared memory, and
-// the row-layout stores are issued with consecutive threads on consecutive
-// columns of a row.
-constexpr int DB_ROWS = 128;
-__global__ void __launch_bounds__(DB_ROWS) k_digits_basis(const double* __restrict__ Q, long ldq, long d,
-                                                          const int* c0_dev, const int* c1_dev, int c0_host,
-                                                          int maxcols, const unsigned long long* __restrict__ keys,
-                                                          int* exps, __nv_bfloat16* Xc, __nv_bfloat16* Xr,
-                                                          int cap_pad) {
-    __shared__ __nv_bfloat16 tile[SG_S][DB_ROWS][SG_N];
+// Digits of basis columns [c0, c1) (at most SG_N) of Q into both operand
+// layouts: Xc (rows = basis columns, contraction = state rows) and Xr (rows =
+// state rows, contraction = basis columns); exps[c] from the column maxima
+// keys.  One state row per thread; for a given column, consecutive threads
+// fill consecutive elements of a 64-byte Xc row, and each thread fills its
+// own Xr row.
+__global__ void k_digits_basis(const double* __restrict__ Q, long ldq, long d, const int* c0_dev, const int* c1_dev,
+                               int c0_host, int maxcols, const unsigned long long* __restrict__ keys, int* exps,
+                               __nv_bfloat16* Xc, __nv_bfloat16* Xr, long nkb, int ngl, int nlb, long ngd) {
     __shared__ int se[SG_N];
     const int c0 = c0_dev ? *c0_dev : c0_host;
     const int c1 = c1_dev ? min(*c1_dev, c0 + maxcols) : c0 + maxcols;
@@ -437,34 +457,31 @@ __global__ void __launch_bounds__(DB_ROWS) k_digits_basis(const double* __restri
         if (blockIdx.x == 0) exps[c0 + threadIdx.x] = se[threadIdx.x];
     }
     __syncthreads();
-    for (long r0 = (long)blockIdx.x * DB_ROWS; r0 < d; r0 += (long)gridDim.x * DB_ROWS) {
-        const long row = r0 + threadIdx.x;
-        if (row < d) {
-            for (int j = 0; j < nc; ++j) {
-                __nv_bfloat16 dg[SG_S];
-                digits8(Q[row + (long)(c0 + j) * ldq], se[j], dg);
+    for (long row = (long)blockIdx.x * blockDim.x + threadIdx.x; row < d; row += (long)gridDim.x * blockDim.x) {
+        const long kb = row >> 5;
+        const int k = (int)(row & 31);
+        for (int j = 0; j < nc; ++j) {
+            const int c = c0 + j;
+            __nv_bfloat16 dg[SG_S];
+            digits8(Q[row + (long)c * ldq], se[j], dg);
+            const long uc = kb * ngl + (c >> 3);
+            const long ur = (long)(c >> 5) * ngd + (row >> 3);
+            const int ec = unit_elem(c & 7, k), er = unit_elem((int)(row & 7), c & 31);
 #pragma unroll
-                for (int s = 0; s < SG_S; ++s) {
-                    Xc[((long)s * cap_pad + c0 + j) * d + row] = dg[s];
-                    tile[s][threadIdx.x][j] = dg[s];
-                }
+            for (int s = 0; s < SG_S; ++s) {
+                Xc[((long)s * nkb * ngl + uc) * 256 + ec] = dg[s];
+                Xr[((long)s * nlb * ngd + ur) * 256 + er] = dg[s];
             }
         }
-        __syncthreads();
-        for (int s = 0; s < SG_S; ++s) {
-            for (int idx = threadIdx.x; idx < DB_ROWS * SG_N; idx += DB_ROWS) {
-                const int rl = idx / SG_N, j = idx % SG_N;
-                if (j < nc && r0 + rl < d) Xr[((long)s * d + r0 + rl) * cap_pad + c0 + j] = tile[s][rl][j];
-            }
-        }
-        __syncthreads();
     }
 }
 
-// Digits of the block V (m columns, ld ldv) into Vs[s][j][row]; columns
-// j in [m, SG_N) are zero.
+// Digits of the block V (m columns, ld ldv) into the Vs operand layout
+// (SG_N rows = the columns, contraction = state rows); columns j in
+// [m, SG_N) are zero.
 __global__ void k_digits_block(const double* __restrict__ V, long ldv, long d, int m,
-                               const unsigned long long* __restrict__ keys, int* exps, __nv_bfloat16* Vs) {
+                               const unsigned long long* __restrict__ keys, int* exps, __nv_bfloat16* Vs,
+                               long nkb) {
     __shared__ int se[SG_N];
     if (threadIdx.x < SG_N) {
         se[threadIdx.x] = threadIdx.x < m ? exponent_of_max(keys[threadIdx.x]) : 0;
@@ -480,8 +497,10 @@ __global__ void k_digits_block(const double* __restrict__ V, long ldv, long d, i
 #pragma unroll
                 for (int s = 0; s < SG_S; ++s) dg[s] = __float2bfloat16_rn(0.f);
             }
+            const long u = (row >> 5) * 2 + (j >> 3);
+            const int e = unit_elem(j & 7, (int)(row & 31));
 #pragma unroll
-            for (int s = 0; s < SG_S; ++s) Vs[((long)s * SG_N + j) * d + row] = dg[s];
+            for (int s = 0; s < SG_S; ++s) Vs[((long)s * nkb * 2 + u) * 256 + e] = dg[s];
         }
     }
 }
@@ -490,7 +509,8 @@ __global__ void k_digits_block(const double* __restrict__ V, long ldv, long d, i
 // 2^{E_l + F_j - 14} sum_splits ws (stored to C; the splits of the product
 // launched on tn_grid CTAs, summed in a fixed order), or C given (Cin).  Then
 // the folded column C'[l] = 2^{E_l} C[l, j] (l < r; zero up to kpad), its
-// exponent G_j and its digits Cs[s][j][l].  Columns j >= m are zero.
+// exponent G_j and its digits in the Cs operand layout (SG_N rows, contraction
+// = basis columns; kpad a multiple of 32).  Columns j >= m are zero.
 constexpr int FIN_T = 1024;   // threads of k_finish: 4 groups of 256 rows
 __global__ void __launch_bounds__(FIN_T) k_finish(const double* __restrict__ ws, int rows_pad, int tn_grid, long d,
                                                   const int* r_dev, const int* __restrict__ Eq,
@@ -544,8 +564,10 @@ __global__ void __launch_bounds__(FIN_T) k_finish(const double* __restrict__ ws,
     for (int l = threadIdx.x; l < kpad; l += blockDim.x) {
         __nv_bfloat16 dg[SG_S];
         digits8(cp[l], G, dg);
+        const long u = (long)(l >> 5) * 2 + (j >> 3);
+        const int e = unit_elem(j & 7, l & 31);
 #pragma unroll
-        for (int s = 0; s < SG_S; ++s) Cs[((long)s * SG_N + j) * kpad + l] = dg[s];
+        for (int s = 0; s < SG_S; ++s) Cs[((long)s * (kpad >> 5) * 2 + u) * 256 + e] = dg[s];
     }
     if (threadIdx.x == 0) Gc[j] = G;
 }
@@ -566,17 +588,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// BF16 2-D map: inner (contiguous) extent `inner`, `outer` rows, box
-// SG_KC x box_rows, 64-byte swizzle, zero fill outside.
-bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_rows) {
+// BF16 2-D map over `units` operand units of 512 bytes (256 elements each,
+// stored already in the tensor cores' swizzled layout, so no TMA swizzle), box
+// of `box_units` consecutive units, zero fill beyond the end.
+bool make_map(CUtensorMap* m, const void* base, uint64_t units, uint32_t box_units) {
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[2] = {inner, outer};
-    cuuint64_t strides[1] = {inner * 2};
-    cuuint32_t box[2] = {(cuuint32_t)SG_KC, box_rows};
+    cuuint64_t dims[2] = {256, units};
+    cuuint64_t strides[1] = {512};
+    cuuint32_t box[2] = {256, box_units};
     cuuint32_t es[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -587,14 +610,15 @@ int sm_count() {
     return n > 0 ? n : 1;
 }
 
-cudaError_t launch_mma(const CUtensorMap& A, const CUtensorMap& B, const SgArgs& a, dim3 grid, cudaStream_t s) {
+cudaError_t launch_mma(const CUtensorMap& A16, const CUtensorMap& A2, const CUtensorMap& B2, const SgArgs& a,
+                       dim3 grid, cudaStream_t s) {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
         attr = cudaFuncSetAttribute(k_split_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, SG_DSMEM);
     });
     if (attr != cudaSuccess) return attr;
-    k_split_mma<<<grid, SG_THREADS, SG_DSMEM, s>>>(A, B, a);
+    k_split_mma<<<grid, SG_THREADS, SG_DSMEM, s>>>(A16, A2, B2, a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -607,8 +631,9 @@ size_t sg_bytes(long d, int cap) {
     const long cap_pad = cdivl(cap, SG_KC) * SG_KC;
     const long grid = 1024;   // bound on the SM count
     size_t b = 0;
-    b += 2 * (size_t)SG_S * cap_pad * d * 2;         // Xc, Xr
-    b += (size_t)SG_S * SG_N * d * 2;                // Vs
+    const long dp = cdivl(d, SG_KC) * SG_KC;
+    b += 2 * (size_t)SG_S * cap_pad * dp * 2;        // Xc, Xr
+    b += (size_t)SG_S * SG_N * dp * 2;               // Vs
     b += (size_t)SG_S * SG_N * cap_pad * 2;          // Cs
     b += sizeof(int) * ((size_t)cap_pad + 2 * SG_N + 1) + sizeof(unsigned long long) * ((size_t)cap_pad + SG_N);
     b += sizeof(double) * ((size_t)grid * cap_pad * SG_N + (size_t)SG_N * cap_pad);
@@ -624,6 +649,12 @@ cudaError_t sg_init(SplitGemm* g, long d, int cap) {
     g->grid = sm_count();
     if (g->grid > 1024) g->grid = 1024;
     const long cp = g->cap_pad;
+    g->nkb = cdivl(d, SG_KC);
+    g->nlb = (int)(cp / SG_KC);
+    g->ngl = (int)(cp / 8);
+    g->ngd = d / 8;
+    const size_t uXc = (size_t)SG_S * g->nkb * g->ngl, uXr = (size_t)SG_S * g->nlb * g->ngd;
+    const size_t uVs = (size_t)SG_S * g->nkb * 2, uCs = (size_t)SG_S * g->nlb * 2;
     cudaError_t e;
 #define SG_ALLOC(ptr, bytes)                                        \
     if ((e = cudaMalloc((void**)&(ptr), (bytes))) != cudaSuccess) { \
@@ -634,10 +665,10 @@ cudaError_t sg_init(SplitGemm* g, long d, int cap) {
         sg_free(g);                                                 \
         return e;                                                   \
     }
-    SG_ALLOC(g->Xc, (size_t)SG_S * cp * d * 2);
-    SG_ALLOC(g->Xr, (size_t)SG_S * cp * d * 2);
-    SG_ALLOC(g->Vs, (size_t)SG_S * SG_N * d * 2);
-    SG_ALLOC(g->Cs, (size_t)SG_S * SG_N * cp * 2);
+    SG_ALLOC(g->Xc, uXc * 512);
+    SG_ALLOC(g->Xr, uXr * 512);
+    SG_ALLOC(g->Vs, uVs * 512);
+    SG_ALLOC(g->Cs, uCs * 512);
     SG_ALLOC(g->Eq, sizeof(int) * cp);
     SG_ALLOC(g->Kq, sizeof(unsigned long long) * cp);
     SG_ALLOC(g->Kv, sizeof(unsigned long long) * SG_N);
@@ -656,10 +687,9 @@ cudaError_t sg_init(SplitGemm* g, long d, int cap) {
         sg_free(g);
         return attr;
     }
-    const bool ok = make_map(&g->mapXc, g->Xc, (uint64_t)d, (uint64_t)SG_S * cp, SG_BM) &&
-                    make_map(&g->mapXr, g->Xr, (uint64_t)cp, (uint64_t)SG_S * d, SG_BM) &&
-                    make_map(&g->mapVs, g->Vs, (uint64_t)d, (uint64_t)SG_S * SG_N, SG_N) &&
-                    make_map(&g->mapCs, g->Cs, (uint64_t)cp, (uint64_t)SG_S * SG_N, SG_N);
+    const bool ok = make_map(&g->mapXc16, g->Xc, uXc, 16) && make_map(&g->mapXc2, g->Xc, uXc, 2) &&
+                    make_map(&g->mapXr16, g->Xr, uXr, 16) && make_map(&g->mapXr2, g->Xr, uXr, 2) &&
+                    make_map(&g->mapVs2, g->Vs, uVs, 2) && make_map(&g->mapCs2, g->Cs, uCs, 2);
     if (!ok) {
         sg_free(g);
         return cudaErrorNotSupported;
@@ -702,10 +732,10 @@ cudaError_t sg_append(SplitGemm* g, const double* Q, long ldq, const int* c0_dev
             k_col_max<<<dim3(colmax_blocks(g->d), nc), 256, 0, s>>>(Q, ldq, g->d, nullptr, nullptr, c0_host + j0,
                                                                    g->Kq);
         }
-        long nb = cdivl(g->d, DB_ROWS);
+        long nb = cdivl(g->d, 256);
         if (nb > 8 * 152) nb = 8 * 152;
-        k_digits_basis<<<(int)nb, DB_ROWS, 0, s>>>(Q, ldq, g->d, c0_dev, c1_dev, c0_host + j0, nc, g->Kq, g->Eq,
-                                                   g->Xc, g->Xr, g->cap_pad);
+        k_digits_basis<<<(int)nb, 256, 0, s>>>(Q, ldq, g->d, c0_dev, c1_dev, c0_host + j0, nc, g->Kq, g->Eq, g->Xc,
+                                               g->Xr, g->nkb, g->ngl, g->nlb, g->ngd);
         count_launches(2);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -720,21 +750,22 @@ cudaError_t sg_project(SplitGemm* g, const double* v, long ldv, int m, const int
     k_col_max<<<dim3(colmax_blocks(g->d), m), 256, 0, s>>>(v, ldv, g->d, nullptr, nullptr, 0, g->Kv);
     long nb = cdivl(g->d, 256);
     if (nb > 4 * 152) nb = 4 * 152;
-    k_digits_block<<<(int)nb, 256, 0, s>>>(v, ldv, g->d, m, g->Kv, g->Fv, g->Vs);
+    k_digits_block<<<(int)nb, 256, 0, s>>>(v, ldv, g->d, m, g->Kv, g->Fv, g->Vs, g->nkb);
     count_launches(2);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     SgArgs a{};
     a.mode = 0;
-    a.a_rows_per_slice = g->cap_pad;
-    a.b_rows_per_slice = SG_N;
+    a.a_slice_units = g->nkb * g->ngl;
+    a.a_kb_units = g->ngl;
+    a.b_slice_units = g->nkb * 2;
     a.rows_dev = r_dev;
     a.rows_host = g->cap;
     a.k_host = g->d;
     a.ws = g->ws;
     a.rows_pad = g->cap_pad;
     a.err = g->err;
-    e = launch_mma(g->mapXc, g->mapVs, a, dim3((unsigned)g->grid), s);
+    e = launch_mma(g->mapXc16, g->mapXc2, g->mapVs2, a, dim3((unsigned)g->grid), s);
     if (e != cudaSuccess) return e;
     k_finish<<<SG_N, FIN_T, sizeof(double) * g->cap_pad, s>>>(g->ws, g->cap_pad, g->grid, g->d, r_dev, g->Eq, g->Fv, m,
                                                             g->C, g->cap_pad, nullptr, 0, g->Cs, g->cap_pad, g->Gc);
@@ -745,8 +776,9 @@ cudaError_t sg_project(SplitGemm* g, const double* v, long ldv, int m, const int
 static cudaError_t sg_apply_update(SplitGemm* g, double* v, long ldv, int m, const int* r_dev, cudaStream_t s) {
     SgArgs a{};
     a.mode = 1;
-    a.a_rows_per_slice = (int)g->d;
-    a.b_rows_per_slice = SG_N;
+    a.a_slice_units = (long)g->nlb * g->ngd;
+    a.a_kb_units = g->ngd;
+    a.b_slice_units = (long)g->nlb * 2;
     a.rows_host = (int)g->d;
     a.k_dev = r_dev;
     a.k_host = g->cap;
@@ -756,7 +788,7 @@ static cudaError_t sg_apply_update(SplitGemm* g, double* v, long ldv, int m, con
     a.ncols = m;
     a.err = g->err;
     long tiles = cdivl(g->d, SG_BM);
-    return launch_mma(g->mapXr, g->mapCs, a, dim3((unsigned)(tiles < g->grid ? tiles : g->grid)), s);
+    return launch_mma(g->mapXr16, g->mapXr2, g->mapCs2, a, dim3((unsigned)(tiles < g->grid ? tiles : g->grid)), s);
 }
 
 cudaError_t sg_cgs_pass(SplitGemm* g, double* v, long ldv, int m, const int* r_dev, cudaStream_t s) {

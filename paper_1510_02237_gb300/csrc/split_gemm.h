@@ -33,10 +33,18 @@ struct SplitGemm {
     long d = 0;                  // rows of Q (contraction length of Q^T V)
     int cap = 0, cap_pad = 0;    // basis capacity, padded to SG_KC
     int grid = 0;                // CTAs of the persistent product kernel (one per SM)
-    __nv_bfloat16* Xc = nullptr;   // [S][cap_pad][d]  digits of Q, column layout (K = rows)
-    __nv_bfloat16* Xr = nullptr;   // [S][d][cap_pad]  digits of Q, row layout (K = columns)
-    __nv_bfloat16* Vs = nullptr;   // [S][SG_N][d]     digits of the block V
-    __nv_bfloat16* Cs = nullptr;   // [S][SG_N][cap_pad] digits of 2^{E_l} C
+    // Digit slices in the tensor cores' operand layout: units of 8 rows x 32
+    // contraction elements (512 bytes, 64-byte swizzle applied), ordered
+    // [slice][contraction block][row group], so a 128-row operand tile of
+    // one contraction block is 8 KB of consecutive memory.
+    long nkb = 0;                  // contraction blocks of 32 over d
+    int nlb = 0;                   // contraction blocks of 32 over cap_pad
+    int ngl = 0;                   // row groups of 8 over cap_pad (basis columns)
+    long ngd = 0;                  // row groups of 8 over d (state rows)
+    __nv_bfloat16* Xc = nullptr;   // Q for Q^T V: rows = basis columns, contraction = state rows
+    __nv_bfloat16* Xr = nullptr;   // Q for Q C: rows = state rows, contraction = basis columns
+    __nv_bfloat16* Vs = nullptr;   // V (SG_N rows = its columns), contraction = state rows
+    __nv_bfloat16* Cs = nullptr;   // 2^{E_l} C (SG_N rows), contraction = basis columns
     int* Eq = nullptr;             // [cap] column exponents of Q
     int* Fv = nullptr;             // [SG_N] column exponents of V
     int* Gc = nullptr;             // [SG_N] column exponents of 2^{E_l} C
@@ -45,7 +53,7 @@ struct SplitGemm {
     double* ws = nullptr;          // [grid][SG_N][cap_pad] partial sums of Q^T V
     double* C = nullptr;           // [SG_N][cap_pad] coefficients Q^T V (column-major, ld cap_pad)
     int* err = nullptr;            // sticky: a pipeline wait gave up
-    CUtensorMap mapXc, mapXr, mapVs, mapCs;
+    CUtensorMap mapXc16, mapXc2, mapXr16, mapXr2, mapVs2, mapCs2;   // boxes of 16 / 2 units
 };
 
 // Bytes of device memory sg_init allocates for (d, cap).
