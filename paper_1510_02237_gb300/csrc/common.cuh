@@ -139,11 +139,14 @@ struct GridBar {
 cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2, const int* r_old_dev,
                         int* r_dev, int cap, double eta, double* Q, double* D, int* kept, double* ratio,
                         const TsWork& w, GridBar* gb, cudaStream_t s, int max_blocks = 0, bool compact = false);
-// Re-orthonormalisation of n = *nk_dev <= m <= 64 nearly orthonormal columns W
-// (ld d) by Cholesky QR: G = W^T W = R^T R (G, Rinv: 64 x 64 scratch), the
-// result W R^-1 written to Q[:, *off_dev + j] (and Z R^-1 to D when Z != NULL).
-cudaError_t cholqr_block(double* W, double* Z, long d, int m, const int* nk_dev, double* G, double* Rinv,
-                         double* Q, double* D, const int* off_dev, const TsWork& w, cudaStream_t s);
+// Re-orthonormalisation of n = *nk_dev <= m <= 64 nearly orthonormal columns
+// W = Q1 - Q C2 (ld d; Q1 orthonormal, C2 = Q^T Q1 with *r2_dev rows, ld ldc2)
+// by Cholesky QR: G = W^T W = I - C2^T C2 = R^T R (G, Rinv: 64 x 64 scratch),
+// the result W R^-1 written to Q[:, *off_dev + j] (and Z R^-1 to D when
+// Z != NULL).
+cudaError_t cholqr_block(double* W, double* Z, long d, int m, const int* nk_dev, const double* C2, int ldc2,
+                         const int* r2_dev, double* G, double* Rinv, double* Q, double* D, const int* off_dev,
+                         cudaStream_t s);
 cudaError_t sub_int(const int* a, const int* b, int* out, cudaStream_t s);
 
 

@@ -372,14 +372,25 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* wv, double* wz, l
                     for (int k = 0; k < 16; ++k)
                         if (k < lc) acc[k] += q[(long)k * d] * x;
                 }
+                // warp sums of the 16 accumulators by recursive halving: at
+                // each step a lane keeps half of its values and adds its
+                // partner's copy of them (16 shuffles instead of 80); lane L
+                // ends with the sum for column kof(L), in a fixed order
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    if (k < lc) {
-                        double t = acc[k];
+                for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+                    const bool up = (lane & o) != 0;
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                        if (lane == 0) sred[wid][k] = t;
+                    for (int i = 0; i < h; ++i) {
+                        const double send = up ? acc[i] : acc[i + h];
+                        const double keep = up ? acc[i + h] : acc[i];
+                        acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
                     }
+                }
+                acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+                {
+                    const int kof = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                                    ((lane >> 1) & 1);
+                    if ((lane & 1) == 0 && kof < lc) sred[wid][kof] = acc[0];
                 }
                 if (norm) {
 #pragma unroll
@@ -493,6 +504,25 @@ __global__ void k_cholqr(const double* __restrict__ G, int ldg, const int* n_dev
             x[i] = t / R[i][i];
         }
     }
+}
+
+// Gram matrix of the reprojected block W = Q1 - Q C (Q1: in-block
+// orthonormal columns, Q: the orthonormal basis, C = Q^T Q1 with *r_dev rows):
+// W^T W = Q1^T Q1 - C^T C = I - C^T C up to rounding, because Q1^T Q1 = I and
+// Q^T Q = I to working accuracy.  G[i + 64 j] for i, j < *n_dev, one CTA per
+// column j, entries summed over the rows of C in a fixed order.
+__global__ void k_gram_c(const double* __restrict__ C, int ldc, const int* r_dev, const int* n_dev, double* G) {
+    __shared__ double part[4][64];
+    const int j = blockIdx.x;
+    const int n = min(*n_dev, 64), r = *r_dev;
+    const int i = threadIdx.x & 63, grp = threadIdx.x >> 6;   // 4 groups of 64 threads
+    double s = 0.0;
+    if (j < n && i < n)
+        for (int l = grp; l < r; l += 4) s += C[l + (long)i * ldc] * C[l + (long)j * ldc];
+    part[grp][i] = s;
+    __syncthreads();
+    if (grp == 0 && j < n && i < n)
+        G[i + 64L * j] = (i == j ? 1.0 : 0.0) - ((part[0][i] + part[1][i]) + (part[2][i] + part[3][i]));
 }
 
 // out[:, *off_dev + j] = sum_{i <= j} W[:, i] Rinv[i, j] for j < *n_dev
@@ -710,14 +740,15 @@ cudaError_t sub_mapped(const double* a, const double* b, double* out, long d, in
     return cudaGetLastError();
 }
 
-cudaError_t cholqr_block(double* W, double* Z, long d, int m, const int* nk_dev, double* G, double* Rinv,
-                         double* Q, double* D, const int* off_dev, const TsWork& w, cudaStream_t s) {
+cudaError_t cholqr_block(double* W, double* Z, long d, int m, const int* nk_dev, const double* C2, int ldc2,
+                         const int* r2_dev, double* G, double* Rinv, double* Q, double* D, const int* off_dev,
+                         cudaStream_t s) {
     if (m < 1 || m > 64) return cudaErrorInvalidValue;
-    // G = W^T W over the kept columns, R^-1 of its Cholesky factor, then
-    // Q[:, off + j] = (W R^-1)_j and D likewise
-    cudaError_t e = gemm_tn(W, d, nullptr, nk_dev, m, W, d, m, d, G, 64, w, s);
-    if (e != cudaSuccess) return e;
+    // G = W^T W = I - C2^T C2 over the kept columns, R^-1 of its Cholesky
+    // factor, then Q[:, off + j] = (W R^-1)_j and D likewise
+    k_gram_c<<<m, 256, 0, s>>>(C2, ldc2, r2_dev, nk_dev, G);
     k_cholqr<<<1, 64, 0, s>>>(G, 64, nk_dev, Rinv);
+    count_launches(1);
     int nb = cdiv(d, 256);
     if (nb > 4 * 152) nb = 4 * 152;
     k_apply_upper<<<nb, 256, 0, s>>>(W, d, Rinv, nk_dev, Q, off_dev);

@@ -298,7 +298,8 @@ static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, c
         CKC(sub_mark(1));
         CKC(sub_int(h->r, h->r_old, h->nk, s));
         CKS(block_pass(h, v, z, mm));
-        CKC(cholqr_block(v, z, d, mm, h->nk, h->G, h->Rinv, h->Q, h->D, h->r_old, w, s));
+        CKC(cholqr_block(v, z, d, mm, h->nk, h->use_sg ? h->sg.C : h->C, h->use_sg ? h->sg.cap_pad : cap, h->r_old,
+                         h->G, h->Rinv, h->Q, h->D, h->r_old, s));
         if (h->use_sg) CKC(sg_append(&h->sg, h->Q, d, h->r_old, h->r, 0, mm, s));
     }
     CKC(mark());

@@ -8,9 +8,10 @@
 // rows of the long operand (basis columns for Q^T V, state rows for V - Q C)
 // against all SG_N = 16 columns of the narrow operand, over a range of the
 // contraction.  Warp 0 streams the 8 digit slices of both operands through a
-// 3-stage TMA pipeline (64-byte rows, 64-byte swizzle), warp 1 issues the 43
-// digit-product MMAs per 16 contraction elements into 9 FP32 accumulators
-// (double-buffered across 256-element chunks), and warps
+// 3-stage TMA pipeline (operand tiles stored pre-swizzled), warp 1 issues 8
+// MMAs per 16 contraction elements -- one per digit slice of the long operand
+// against the stacked slices of the narrow one, 43 digit products in all --
+// into 9 FP32 accumulators (double-buffered across 256-element chunks), and warps
 // 4-7 drain each chunk from TMEM and combine it in FP64.  Every wait is
 // bounded; on expiry the sticky error word is set and the CTA winds down.
 #include <cstdio>
@@ -30,11 +31,21 @@ constexpr int SG_NST = 3;                          // pipeline stages
 constexpr int SG_NG = SG_S + 1;                    // accumulator groups: s + t = 2 .. S + 2
 constexpr int SG_A_TILE = SG_BM * SG_KC * 2;       // bytes per slice tile of the long operand
 constexpr int SG_B_TILE = SG_N * SG_KC * 2;        // bytes per slice tile of the narrow operand
-constexpr int SG_STAGE = SG_S * (SG_A_TILE + SG_B_TILE);
+// a stage: S tiles of the long operand, S tiles of the narrow operand and one
+// tile of zeros after them (written once), so that the narrow operand's
+// slices t = 0..S read as one operand of (S + 1) * SG_N rows
+constexpr int SG_STAGE = SG_S * SG_A_TILE + (SG_S + 1) * SG_B_TILE;
 constexpr int SG_SPC = SG_L / SG_KC;               // stages per exact chunk
 constexpr int SG_TMEM_COLS = 512;                  // two accumulator sets (2 x 9 x 16 columns)
 constexpr int SG_DSMEM = SG_NST * SG_STAGE + 1024; // + alignment slack for the 64-byte swizzle
-constexpr uint32_t SG_IDESC = tc::idesc_bf16_f32(SG_BM, SG_N);
+// MMA s (the long operand's digit slice s) multiplies the narrow operand's
+// slices t = 0 .. S - s stacked along N, so its output columns are the
+// accumulator groups g = s + t = s .. S: one MMA per slice instead of one per
+// digit pair.  Slice 0 also takes the zero tile (t = S) so that its first MMA
+// of a chunk initialises all S + 1 groups.
+__host__ __device__ constexpr uint32_t sg_idesc(int s) {
+    return tc::idesc_bf16_f32(SG_BM, (s == 0 ? SG_S + 1 : SG_S + 1 - s) * SG_N);
+}
 constexpr int SG_THREADS = 256;
 
 struct SgArgs {
@@ -81,7 +92,8 @@ __device__ __forceinline__ void sg_fail(int* err, volatile int* abort_flag) {
 // pipeline counters run on across items, so loads of the next item overlap
 // the epilogue of the current one.
 __global__ void __launch_bounds__(SG_THREADS, 1)
-    k_split_mma(const __grid_constant__ CUtensorMap mapA16, const __grid_constant__ CUtensorMap mapA2,
+    k_split_mma(const __grid_constant__ CUtensorMap mapA16, const __grid_constant__ CUtensorMap mapA8,
+                const __grid_constant__ CUtensorMap mapA4, const __grid_constant__ CUtensorMap mapA2,
                 const __grid_constant__ CUtensorMap mapB2, const SgArgs a) {
     extern __shared__ unsigned char sg_raw[];
     __shared__ __align__(8) uint64_t bars[2 * SG_NST + 5];
@@ -141,6 +153,12 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
         tc::fence_barrier_init();
         s_abort = 0;
     }
+    // the zero tile of every stage (never overwritten by the loads)
+    for (int st = 0; st < SG_NST; ++st) {
+        uint4* z = reinterpret_cast<uint4*>(base + st * SG_STAGE + SG_S * SG_A_TILE + SG_S * SG_B_TILE);
+        for (int i = threadIdx.x; i < SG_B_TILE / 16; i += SG_THREADS) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor cores
     if (threadIdx.x < SG_N)
         s_scale[threadIdx.x] = (a.mode == 1 && a.vexp) ? ldexp(1.0, a.vexp[threadIdx.x] - 14) : 0.0;
     if (warp == 2) {
@@ -149,6 +167,8 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
     }
     if (warp == 0 && lane == 0) {
         tc::tma_prefetch_map(&mapA16);
+        tc::tma_prefetch_map(&mapA8);
+        tc::tma_prefetch_map(&mapA4);
         tc::tma_prefetch_map(&mapA2);
         tc::tma_prefetch_map(&mapB2);
     }
@@ -187,11 +207,20 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
 #pragma unroll 1
                     for (int s = 0; s < SG_S; ++s) {
                         const int ua = (int)(s * a.a_slice_units + kblk * a.a_kb_units + row0 / 8);
+                        // the ng row groups as boxes of 16, 8, 4 and 2 units (at most 3 loads)
                         if (ng == 16) {
                             tc::tma_load_2d(sa + s * SG_A_TILE, &mapA16, 0, ua, full(st));
                         } else {
-                            for (int u = 0; u < ng; u += 2)
-                                tc::tma_load_2d(sa + s * SG_A_TILE + u * 512, &mapA2, 0, ua + u, full(st));
+                            int u = 0;
+                            if (ng & 8) {
+                                tc::tma_load_2d(sa + s * SG_A_TILE, &mapA8, 0, ua, full(st));
+                                u += 8;
+                            }
+                            if (ng & 4) {
+                                tc::tma_load_2d(sa + s * SG_A_TILE + u * 512, &mapA4, 0, ua + u, full(st));
+                                u += 4;
+                            }
+                            if (ng & 2) tc::tma_load_2d(sa + s * SG_A_TILE + u * 512, &mapA2, 0, ua + u, full(st));
                         }
                         tc::tma_load_2d(sb + s * SG_B_TILE, &mapB2, 0, (int)(s * a.b_slice_units + kblk * 2),
                                         full(st));
@@ -238,17 +267,15 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
                         const uint32_t sb = sa + SG_S * SG_A_TILE;
 #pragma unroll
                         for (int kk = 0; kk < SG_KC / 16; ++kk) {
+                            const uint64_t bd = tc::desc_kmajor_sw64(sb + kk * 32);
 #pragma unroll
                             for (int s = 0; s < SG_S; ++s) {
                                 const uint64_t ad = tc::desc_kmajor_sw64(sa + s * SG_A_TILE + kk * 32);
-#pragma unroll
-                                for (int t = 0; s + t <= SG_S && t < SG_S; ++t) {
-                                    const int g = s + t;
-                                    const uint64_t bd = tc::desc_kmajor_sw64(sb + t * SG_B_TILE + kk * 32);
-                                    tc::mma_bf16(dbase + (uint32_t)(g * SG_N), ad, bd, SG_IDESC, (init >> g) & 1u);
-                                    init |= 1u << g;
-                                }
+                                // slice 0 (groups 0..S) overwrites at the chunk's first step; the
+                                // others then accumulate into groups s..S
+                                tc::mma_bf16(dbase + (uint32_t)(s * SG_N), ad, bd, sg_idesc(s), init | (s > 0));
                             }
+                            init = 1u;
                         }
                         tc::mma_commit(empty(st));
                     }
@@ -441,12 +468,17 @@ __global__ void k_col_max(const double* __restrict__ X, long ldx, long nrows, co
 // Digits of basis columns [c0, c1) (at most SG_N) of Q into both operand
 // layouts: Xc (rows = basis columns, contraction = state rows) and Xr (rows =
 // state rows, contraction = basis columns); exps[c] from the column maxima
-// keys.  One state row per thread; for a given column, consecutive threads
-// fill consecutive elements of a 64-byte Xc row, and each thread fills its
-// own Xr row.
-__global__ void k_digits_basis(const double* __restrict__ Q, long ldq, long d, const int* c0_dev, const int* c1_dev,
-                               int c0_host, int maxcols, const unsigned long long* __restrict__ keys, int* exps,
-                               __nv_bfloat16* Xc, __nv_bfloat16* Xr, long nkb, int ngl, int nlb, long ngd) {
+// keys.  A CTA takes 128 state rows: one row per thread forms the digits and
+// stores Xc (consecutive threads on consecutive elements of a 64-byte row);
+// the digits are staged in shared memory and the Xr stores are issued with
+// consecutive threads on consecutive basis columns of a state row.
+constexpr int DB_ROWS = 128;
+__global__ void __launch_bounds__(DB_ROWS) k_digits_basis(const double* __restrict__ Q, long ldq, long d,
+                                                          const int* c0_dev, const int* c1_dev, int c0_host,
+                                                          int maxcols, const unsigned long long* __restrict__ keys,
+                                                          int* exps, __nv_bfloat16* Xc, __nv_bfloat16* Xr, long nkb,
+                                                          int ngl, int nlb, long ngd) {
+    __shared__ __nv_bfloat16 tile[SG_S][DB_ROWS][SG_N];
     __shared__ int se[SG_N];
     const int c0 = c0_dev ? *c0_dev : c0_host;
     const int c1 = c1_dev ? min(*c1_dev, c0 + maxcols) : c0 + maxcols;
@@ -457,22 +489,37 @@ __global__ void k_digits_basis(const double* __restrict__ Q, long ldq, long d, c
         if (blockIdx.x == 0) exps[c0 + threadIdx.x] = se[threadIdx.x];
     }
     __syncthreads();
-    for (long row = (long)blockIdx.x * blockDim.x + threadIdx.x; row < d; row += (long)gridDim.x * blockDim.x) {
-        const long kb = row >> 5;
-        const int k = (int)(row & 31);
-        for (int j = 0; j < nc; ++j) {
-            const int c = c0 + j;
-            __nv_bfloat16 dg[SG_S];
-            digits8(Q[row + (long)c * ldq], se[j], dg);
-            const long uc = kb * ngl + (c >> 3);
-            const long ur = (long)(c >> 5) * ngd + (row >> 3);
-            const int ec = unit_elem(c & 7, k), er = unit_elem((int)(row & 7), c & 31);
+    for (long r0 = (long)blockIdx.x * DB_ROWS; r0 < d; r0 += (long)gridDim.x * DB_ROWS) {
+        const long row = r0 + threadIdx.x;
+        if (row < d) {
+            const long kb = row >> 5;
+            const int k = (int)(row & 31);
+            for (int j = 0; j < nc; ++j) {
+                const int cc = c0 + j;
+                __nv_bfloat16 dg[SG_S];
+                digits8(Q[row + (long)cc * ldq], se[j], dg);
+                const long uc = kb * ngl + (cc >> 3);
+                const int ec = unit_elem(cc & 7, k);
 #pragma unroll
-            for (int s = 0; s < SG_S; ++s) {
-                Xc[((long)s * nkb * ngl + uc) * 256 + ec] = dg[s];
-                Xr[((long)s * nlb * ngd + ur) * 256 + er] = dg[s];
+                for (int s = 0; s < SG_S; ++s) {
+                    Xc[((long)s * nkb * ngl + uc) * 256 + ec] = dg[s];
+                    tile[s][threadIdx.x][j] = dg[s];
+                }
             }
         }
+        __syncthreads();
+        for (int s = 0; s < SG_S; ++s) {
+            for (int idx = threadIdx.x; idx < DB_ROWS * SG_N; idx += DB_ROWS) {
+                const int rl = idx / SG_N, j = idx % SG_N;
+                const long rw = r0 + rl;
+                if (j < nc && rw < d) {
+                    const int cc = c0 + j;
+                    const long ur = (long)(cc >> 5) * ngd + (rw >> 3);
+                    Xr[((long)s * nlb * ngd + ur) * 256 + unit_elem((int)(rw & 7), cc & 31)] = tile[s][rl][j];
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -610,15 +657,14 @@ int sm_count() {
     return n > 0 ? n : 1;
 }
 
-cudaError_t launch_mma(const CUtensorMap& A16, const CUtensorMap& A2, const CUtensorMap& B2, const SgArgs& a,
-                       dim3 grid, cudaStream_t s) {
+cudaError_t launch_mma(const CUtensorMap* A, const CUtensorMap& B2, const SgArgs& a, dim3 grid, cudaStream_t s) {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
         attr = cudaFuncSetAttribute(k_split_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, SG_DSMEM);
     });
     if (attr != cudaSuccess) return attr;
-    k_split_mma<<<grid, SG_THREADS, SG_DSMEM, s>>>(A16, A2, B2, a);
+    k_split_mma<<<grid, SG_THREADS, SG_DSMEM, s>>>(A[0], A[1], A[2], A[3], B2, a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -687,9 +733,11 @@ cudaError_t sg_init(SplitGemm* g, long d, int cap) {
         sg_free(g);
         return attr;
     }
-    const bool ok = make_map(&g->mapXc16, g->Xc, uXc, 16) && make_map(&g->mapXc2, g->Xc, uXc, 2) &&
-                    make_map(&g->mapXr16, g->Xr, uXr, 16) && make_map(&g->mapXr2, g->Xr, uXr, 2) &&
-                    make_map(&g->mapVs2, g->Vs, uVs, 2) && make_map(&g->mapCs2, g->Cs, uCs, 2);
+    bool ok = make_map(&g->mapVs2, g->Vs, uVs, 2) && make_map(&g->mapCs2, g->Cs, uCs, 2);
+    for (int i = 0; i < 4; ++i) {
+        ok = ok && make_map(&g->mapXc[i], g->Xc, uXc, 16u >> i);
+        ok = ok && make_map(&g->mapXr[i], g->Xr, uXr, 16u >> i);
+    }
     if (!ok) {
         sg_free(g);
         return cudaErrorNotSupported;
@@ -732,9 +780,9 @@ cudaError_t sg_append(SplitGemm* g, const double* Q, long ldq, const int* c0_dev
             k_col_max<<<dim3(colmax_blocks(g->d), nc), 256, 0, s>>>(Q, ldq, g->d, nullptr, nullptr, c0_host + j0,
                                                                    g->Kq);
         }
-        long nb = cdivl(g->d, 256);
+        long nb = cdivl(g->d, DB_ROWS);
         if (nb > 8 * 152) nb = 8 * 152;
-        k_digits_basis<<<(int)nb, 256, 0, s>>>(Q, ldq, g->d, c0_dev, c1_dev, c0_host + j0, nc, g->Kq, g->Eq, g->Xc,
+        k_digits_basis<<<(int)nb, DB_ROWS, 0, s>>>(Q, ldq, g->d, c0_dev, c1_dev, c0_host + j0, nc, g->Kq, g->Eq, g->Xc,
                                                g->Xr, g->nkb, g->ngl, g->nlb, g->ngd);
         count_launches(2);
         e = cudaGetLastError();
@@ -765,7 +813,7 @@ cudaError_t sg_project(SplitGemm* g, const double* v, long ldv, int m, const int
     a.ws = g->ws;
     a.rows_pad = g->cap_pad;
     a.err = g->err;
-    e = launch_mma(g->mapXc16, g->mapXc2, g->mapVs2, a, dim3((unsigned)g->grid), s);
+    e = launch_mma(g->mapXc, g->mapVs2, a, dim3((unsigned)g->grid), s);
     if (e != cudaSuccess) return e;
     k_finish<<<SG_N, FIN_T, sizeof(double) * g->cap_pad, s>>>(g->ws, g->cap_pad, g->grid, g->d, r_dev, g->Eq, g->Fv, m,
                                                             g->C, g->cap_pad, nullptr, 0, g->Cs, g->cap_pad, g->Gc);
@@ -788,7 +836,7 @@ static cudaError_t sg_apply_update(SplitGemm* g, double* v, long ldv, int m, con
     a.ncols = m;
     a.err = g->err;
     long tiles = cdivl(g->d, SG_BM);
-    return launch_mma(g->mapXr16, g->mapXr2, g->mapCs2, a, dim3((unsigned)(tiles < g->grid ? tiles : g->grid)), s);
+    return launch_mma(g->mapXr, g->mapCs2, a, dim3((unsigned)(tiles < g->grid ? tiles : g->grid)), s);
 }
 
 cudaError_t sg_cgs_pass(SplitGemm* g, double* v, long ldv, int m, const int* r_dev, cudaStream_t s) {

@@ -53,7 +53,8 @@ struct SplitGemm {
     double* ws = nullptr;          // [grid][SG_N][cap_pad] partial sums of Q^T V
     double* C = nullptr;           // [SG_N][cap_pad] coefficients Q^T V (column-major, ld cap_pad)
     int* err = nullptr;            // sticky: a pipeline wait gave up
-    CUtensorMap mapXc16, mapXc2, mapXr16, mapXr2, mapVs2, mapCs2;   // boxes of 16 / 2 units
+    CUtensorMap mapXc[4], mapXr[4];   // boxes of 16, 8, 4 and 2 units
+    CUtensorMap mapVs2, mapCs2;       // boxes of 2 units
 };
 
 // Bytes of device memory sg_init allocates for (d, cap).
