@@ -67,10 +67,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream sweep")
-    ap.add_argument("--case", choices=["fine", "solve", "solve_mixed"], default=None,
+    ap.add_argument("--case", choices=["fine", "fine32", "solve", "solve_mixed"], default=None,
                     help="small isolated case for profiler captures: 'fine' = three fine sweeps over all "
-                         "32 slices of the 256x128 workload; 'solve' = two solves of its first IC; "
-                         "'solve_mixed' = the same in mixed precision with the tensor-core projections")
+                         "32 slices of the 256x128 workload; 'fine32' = three FP32 fine sweeps over the 64 "
+                         "slices of the 512x256 workload; 'solve' = two solves of the 256x128 workload's "
+                         "first IC; 'solve_mixed' = the same in mixed precision with the tensor-core projections")
     return ap.parse_args()
 
 
@@ -336,6 +337,57 @@ def precision_workload(P, torch, stream):
     return res
 
 
+def hbm_peak():
+    """Measured HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the
+    earlier GB300 measurement used as fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def fine_sweep_fp32(P, torch, stream):
+    """The batched FP32 fine sweep on the 512x256 workload: F applied to all
+    64 slices at once (the predictor of its first iteration), 20 RK-3 steps:
+    step 1 converts the FP64 states (shared-memory tile kernel), steps 2-20
+    run the row-streamed kernel k_fine_rows (TMA row ring, registers,
+    shuffles), the last writing FP64.  Algorithmic bytes per cell: 36 (first
+    step: FP64 read, FP32 write) + 18 x 24 (FP32 read + write) + 36 (last
+    step: FP32 read, FP64 write) = 504 B; inputs and outputs (201 MB of FP32
+    ping-pong plus 403 MB FP64) exceed the L2."""
+    wl = W.workload_large()
+    p = wl.problem
+    s = P.Solver(p, stream=stream, K_max=1, fine_prec=P.PR_FP32)
+    X = torch.from_numpy(wl.ics[0][1]().ravel()).cuda().repeat(p.n_slices)
+    Y = torch.empty_like(X)
+    for _ in range(3):
+        P.parareal_fine_sweep(s.h, X, Y, p.n_slices)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    n0 = P.parareal_kernel_launches()
+    e0.record(stream)
+    for _ in range(reps):
+        P.parareal_fine_sweep(s.h, X, Y, p.n_slices)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = (P.parareal_kernel_launches() - n0) // reps
+    ms = e0.elapsed_time(e1) / reps
+    s.close()
+    cells = p.n_slices * p.ncell
+    bytes_ = cells * (36 + 36 + (p.n_f - 2) * 24)
+    peak, src = hbm_peak()
+    achieved = bytes_ / (ms / 1e3) / 1e9
+    return {"workload": f"{wl.name} predictor: {p.n_slices} slices x {p.nx}x{p.ny}, {p.n_f} RK-3 steps, FP32",
+            "kernels": "k_fine_rows (19 of 20 launches), k_fine_step<float,double,float> (first step)",
+            "ms_per_sweep": ms, "launches_per_sweep": launches,
+            "cell_steps_per_s": cells * p.n_f / (ms / 1e3),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": src,
+                         "algorithmic_bytes_per_cell_sweep": 504, "bytes_per_sweep": bytes_}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -493,6 +545,7 @@ def run_ours(args):
 
     line = None
     if rank == 0:
+        fine32 = fine_sweep_fp32(P, torch, stream)
         precision = precision_workload(P, torch, stream)
         batching = batching_workload(P, torch)
         serving = serving_workload(P, torch) if not args.no_serving else None
@@ -539,6 +592,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clk,
             "fp64_fma_tflops": peak,
+            "fine_sweep_fp32": fine32,
             "mixed": mixed,
             "fp64_tensor_core_projection": fp64_tc,
             "precision_workload": precision,
@@ -559,14 +613,16 @@ def run_case(args):
 
     import paper_1510_02237_gb300 as P
     torch.cuda.set_device(0)
-    wl = W.workload_medium()
+    wl = W.workload_large() if args.case == "fine32" else W.workload_medium()
     p = wl.problem
     opt = {}
+    if args.case == "fine32":
+        opt = {"fine_prec": P.PR_FP32}
     if args.case == "solve_mixed":
         opt = {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32, "proj_prec": P.PR_PROJ_SPLIT_BF16}
     s = P.Solver(p, stream=torch.cuda.current_stream(), K_max=wl.K, krylov_cap=wl.krylov_cap, **opt)
     q0 = torch.from_numpy(wl.ics[0][1]().ravel()).cuda()
-    if args.case == "fine":
+    if args.case in ("fine", "fine32"):
         X = q0.repeat(p.n_slices)
         Y = torch.empty_like(X)
         for _ in range(3):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libparareal.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["fine.cu", "coarse.cu", "krylov.cu", "solver.cu", "probe.cu", "static_scratch.cu", "chain.cu", "fine_coop.cu",
+SOURCES = ["fine.cu", "fine_rows.cu", "coarse.cu", "krylov.cu", "solver.cu", "probe.cu", "static_scratch.cu", "chain.cu", "fine_coop.cu",
            "split_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

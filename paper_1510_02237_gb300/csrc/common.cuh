@@ -64,6 +64,19 @@ cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outst
                              int ny, bool has_v, const FineCoef<T>& c, cudaStream_t s,
                              const SliceMap& sm = SliceMap());
 
+// One RK-3 step in FP32 arithmetic streamed row by row (fine_rows.cu), for
+// FP32 input, V = 0 and nx a multiple of 128 up to 1024 with 16-byte aligned
+// states.  Returns false (nothing launched) outside that case; otherwise
+// *err holds the launch status.
+template <typename Tin, typename Tout>
+bool launch_fine_rows(const Tin* in, long instride, Tout* out, long outstride, int n, int nx, int ny, bool has_v,
+                      const FineCoef<float>& c, cudaStream_t s, const SliceMap& map, cudaError_t* err);
+
+// Process-wide flag of the row-streamed kernel (synchronising read): 1 once a
+// wait for one of its TMA row loads gave up (results since then invalid),
+// -1 if it could not be read; reset clears it.
+int fine_rows_wait_error(bool reset);
+
 // One RK-3 step with FP32 tendencies and stages on an FP64 state: the last
 // stage forms q^{n+1} = q^n + dt L(q**) in FP64 (fine_prec = PR_FP32X).
 cudaError_t launch_fine_step_acc64(const double* in, double* out, long stride, int n, int nx, int ny, bool has_v,

@@ -17,6 +17,8 @@
 // V = 0, else 3).  Stage 1 is computed on the tile shrunk by one stage
 // radius, stage 2 by two, stage 3 on the tile itself, so each step reads the
 // state from memory once and writes it once.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace pr {
@@ -174,6 +176,11 @@ cudaError_t launch_tile(const Tin* in, long instride, Tout* out, long outstride,
 template <typename T, typename Tin, typename Tout>
 cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outstride, int n, int nx,
                              int ny, bool has_v, const FineCoef<T>& c, cudaStream_t s, const SliceMap& map) {
+    if constexpr (std::is_same<T, float>::value) {
+        cudaError_t e = cudaSuccess;
+        if (launch_fine_rows<Tin, Tout>(in, instride, out, outstride, n, nx, ny, has_v, c, s, map, &e))
+            return e;
+    }
     const bool big = nx >= 64 && ny >= 16;
     if (has_v) {
         if (big) return launch_tile<T, Tin, Tout, 3, 64, 16, 256>(in, instride, out, outstride, n, nx, ny, c, s, map);

@@ -110,6 +110,48 @@ def test_fine_sweep_fp32x(name, spec):
         assert rel(got[i], oracle.fine_prop(p, X[i])) < 2e-6
 
 
+# Grids whose rows are a multiple of 128 cells (V = 0) take the row-streamed
+# FP32 kernel: one warp per 128 cells of a row, 1 to 8 warps per row; row
+# ranges of the persistent grid cross slice boundaries and, with few rows,
+# wrap around the periodic y-direction.
+ROW_GRIDS = [
+    ("128x64", dict(nx=128, ny=64, N=4)),
+    ("256x24", dict(nx=256, ny=24, N=5)),
+    ("512x16_negU", dict(nx=512, ny=16, N=3, U=-0.12)),
+    ("1024x8", dict(nx=1024, ny=8, N=2)),
+    ("128x4", dict(nx=128, ny=4, N=3)),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32x"])
+@pytest.mark.parametrize("name,spec", ROW_GRIDS, ids=[g[0] for g in ROW_GRIDS])
+def test_fine_sweep_rows(name, spec, prec):
+    p = _prob(spec)
+    X = states(p, p.n_slices, 40)
+    fp, tol = (P.PR_FP32, TOL32) if prec == "fp32" else (P.PR_FP32X, 2e-6)
+    with solver(p, fine_prec=fp) as s:
+        out = torch.empty(p.n_slices * p.d, dtype=torch.float64, device="cuda")
+        P.parareal_fine_sweep(s.h, dev(X), out, p.n_slices)
+        got = host(out).reshape(p.n_slices, p.d)
+    for i in range(p.n_slices):
+        assert rel(got[i], oracle.fine_prop(p, X[i])) < tol
+
+
+def test_fine_sweep_rows_subset():
+    """A sweep over fewer states than the handle's slices (n < N) and a
+    single RK-3 step per slice through the row-streamed kernel."""
+    p = W.Problem(nx=256, ny=12, n_slices=6, n_f=1, n_g=1, dt_f=1.0 / 600, dt_g=1.0 / 600, T=6.0 / 600)
+    X = states(p, 4, 50)
+    for prec, tol in [(P.PR_FP32, TOL32), (P.PR_FP32X, 2e-6)]:
+        with solver(p, fine_prec=prec) as s:
+            out = torch.zeros(6 * p.d, dtype=torch.float64, device="cuda")
+            P.parareal_fine_sweep(s.h, dev(X), out, 4)
+            got = host(out).reshape(6, p.d)
+        for i in range(4):
+            assert rel(got[i], oracle.fine_prop(p, X[i])) < tol
+        assert not got[4:].any()
+
+
 def test_fine_single_step_slices():
     """N_f = 1 (one RK-3 step per slice) uses the direct in->out launch."""
     p = W.Problem(nx=64, ny=32, n_slices=4, n_f=1, n_g=1, dt_f=1.0 / 160, dt_g=1.0 / 160, T=4.0 / 160)
