@@ -9,7 +9,7 @@
 //   the compact grad-div damping (Sec. 3.2, Eq. dampingCoeff).
 // c_k is folded into every coefficient, so each term costs one FMA.
 // Work items are 32-cell segments of grid rows, one per warp (lanes along x,
-// coalesced), spread over all warps of the grid.
+// coalesced); each CTA owns a contiguous range of them.
 #include "grid_barrier.cuh"
 
 namespace pr {
@@ -21,7 +21,10 @@ __device__ __forceinline__ int wrapp(int i, int n) { return i >= n ? i - n : i; 
 __device__ __forceinline__ int wrapm(int i, int n) { return i < 0 ? i + n : i; }
 
 template <bool HV>
-__device__ __forceinline__ void stage_seg(const double* __restrict__ in, const double* __restrict__ qn,
+// in and qn are written by other CTAs earlier in the same launch (ordered by
+// the grid barriers), so they are read through the coherent path, not the
+// read-only one: no __restrict__ on them.
+__device__ __forceinline__ void stage_seg(const double* in, const double* qn,
                                           double* __restrict__ out, long base, int y, int xs, int nx, int ny,
                                           long ncell, const FineCoefK& c, int k) {
     const int lane = threadIdx.x & 31;
@@ -90,8 +93,12 @@ __global__ void __launch_bounds__(FC_NT) k_fine_coop(FineSweepArgs a) {
     const long d = 3 * ncell;
     const int nseg = (a.nx + 31) >> 5;                 // 32-cell segments per grid row
     const int nitems = a.n * a.ny * nseg;
-    const int gw = (blockIdx.x * FC_NT + threadIdx.x) >> 5;
-    const int nwarps = (nb * FC_NT) >> 5;
+    // each CTA takes a contiguous range of work items (consecutive segments
+    // and rows of a slice), so the y-neighbour rows a warp reads were mostly
+    // brought into L1 by the CTA's other warps; its warps share the range
+    // round-robin
+    const int it0 = (int)((long)nitems * blockIdx.x / nb), it1 = (int)((long)nitems * (blockIdx.x + 1) / nb);
+    const int wq = threadIdx.x >> 5, nwq = FC_NT >> 5;
     const double* cur = a.in;
     for (int t = 0; t < a.nsteps; ++t) {
         double* s1 = (cur == a.w1) ? a.w2 : a.w1;
@@ -100,7 +107,7 @@ __global__ void __launch_bounds__(FC_NT) k_fine_coop(FineSweepArgs a) {
         const double* srcs[3] = {cur, s1, s2};
         double* dsts[3] = {s1, s2, dst};
         for (int k = 0; k < 3; ++k) {
-            for (int it = gw; it < nitems; it += nwarps) {
+            for (int it = it0 + wq; it < it1; it += nwq) {
                 const int rr = it / nseg, sg = it - rr * nseg;
                 const int sl = rr / a.ny, y = rr - sl * a.ny;
                 stage_seg<HV>(srcs[k], cur, dsts[k], (long)sl * d, y, sg * 32, a.nx, a.ny, ncell, a.c, k);
