@@ -155,48 +155,96 @@ __device__ __forceinline__ void window1(float (&c)[6], const Src& s, int f, int 
     }
 }
 
+// Packed FP32 pair arithmetic (sm_100 family `.f32x2`): two lanes of work per
+// instruction.  Pairs of consecutive cells whose values sit in one aligned
+// register pair (the own cells 0-1 and 2-3, two shuffled neighbours) cost
+// nothing to form; the others are formed by scalar operations.
+__device__ __forceinline__ unsigned long long pk(float2 v) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {   // a * b + c
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 sp(float a) { return make_float2(a, a); }
+
 // qn + c_k L(X) at the 4 own cells of the centre row, from the rows S (y-1),
-// C (y), N (y+1) of the stage input X.  The terms are accumulated field by
-// field so that only one window is live at a time.
+// C (y), N (y+1) of the stage input X, as two pairs of cells (0,1), (2,3).
+// The terms are accumulated field by field so that only one window is live
+// at a time.  Centre windows c[i+3] = cell x0+i (i = -3..6); neighbour-row
+// windows a[i+1], b[i+1] = cell x0+i (i = -1..4).
 template <int NW, typename SS, typename SC, typename SN>
 __device__ __forceinline__ Row stage_row(const SS& S, const SC& C, const SN& N, const Row& qn, const RowCoef& k,
                                          int kk, int lane) {
-    const float A = k.A[kk], Bx = k.Bx[kk], By = k.By[kk], Cx = k.Cx[kk], Ex = k.Ex[kk], Cy = k.Cy[kk],
-                Ey = k.Ey[kk];
-    float ru[4] = {qn.u.x, qn.u.y, qn.u.z, qn.u.w};
-    float rw[4] = {qn.w.x, qn.w.y, qn.w.z, qn.w.w};
-    float rp[4] = {qn.p.x, qn.p.y, qn.p.z, qn.p.w};
+    const float2 A = sp(k.A[kk]), Bx = sp(k.Bx[kk]), By = sp(k.By[kk]), Cx = sp(k.Cx[kk]), Ex = sp(k.Ex[kk]),
+                 Cy = sp(k.Cy[kk]), Ey = sp(k.Ey[kk]), M9 = sp(-9.f), P45 = sp(45.f), M2 = sp(-2.f),
+                 M2Cy = sp(-2.f * k.Cy[kk]);
+    float2 ru[2] = {f2(qn.u.x, qn.u.y), f2(qn.u.z, qn.u.w)};
+    float2 rw[2] = {f2(qn.w.x, qn.w.y), f2(qn.w.z, qn.w.w)};
+    float2 rp[2] = {f2(qn.p.x, qn.p.y), f2(qn.p.z, qn.p.w)};
+    // 6th-order advective difference of cells (2h, 2h+1) and their centred
+    // difference d1 = c[i+1] - c[i-1]
+    auto adv = [&](const float (&c)[10], int h, float2& d1) {
+        const int m = 2 * h + 3;
+        d1 = f2(c[m + 1] - c[m - 1], c[m + 2] - c[m]);
+        const float2 d3 = f2(c[m + 3] - c[m - 3], c[m + 4] - c[m - 2]);
+        const float2 d2 = sub2(f2(c[m + 2], c[m + 3]), f2(c[m - 2], c[m - 1]));
+        return fma2(P45, d1, fma2(M9, d2, d3));
+    };
     {   // p on the centre row: advection of p, x-acoustics of u
         float c[10];
         window3<NW>(c, C, 2, lane);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int m = i + 3;
-            const float d1 = c[m + 1] - c[m - 1];
-            rp[i] += A * ((c[m + 3] - c[m - 3]) - 9.f * (c[m + 2] - c[m - 2]) + 45.f * d1);
-            ru[i] += Bx * d1;
+        for (int h = 0; h < 2; ++h) {
+            float2 d1;
+            const float2 a6 = adv(c, h, d1);
+            rp[h] = fma2(A, a6, rp[h]);
+            ru[h] = fma2(Bx, d1, ru[h]);
         }
     }
     {   // u on the centre row: advection, x-damping of u, x-acoustics of p
         float c[10];
         window3<NW>(c, C, 0, lane);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int m = i + 3;
-            const float d1 = c[m + 1] - c[m - 1];
-            ru[i] += A * ((c[m + 3] - c[m - 3]) - 9.f * (c[m + 2] - c[m - 2]) + 45.f * d1);
-            ru[i] += Cx * ((c[m + 1] + c[m - 1]) - 2.f * c[m]);
-            rp[i] += Bx * d1;
+        for (int h = 0; h < 2; ++h) {
+            const int m = 2 * h + 3;
+            float2 d1;
+            const float2 a6 = adv(c, h, d1);
+            ru[h] = fma2(A, a6, ru[h]);
+            const float2 lap = fma2(M2, f2(c[m], c[m + 1]), f2(c[m + 1] + c[m - 1], c[m + 2] + c[m]));
+            ru[h] = fma2(Cx, lap, ru[h]);
+            rp[h] = fma2(Bx, d1, rp[h]);
         }
     }
     {   // w on the centre row: advection, centre of the y-damping of w
         float c[10];
         window3<NW>(c, C, 1, lane);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int m = i + 3;
-            rw[i] += A * ((c[m + 3] - c[m - 3]) - 9.f * (c[m + 2] - c[m - 2]) + 45.f * (c[m + 1] - c[m - 1]));
-            rw[i] -= 2.f * Cy * c[m];
+        for (int h = 0; h < 2; ++h) {
+            const int m = 2 * h + 3;
+            float2 d1;
+            const float2 a6 = adv(c, h, d1);
+            rw[h] = fma2(A, a6, rw[h]);
+            rw[h] = fma2(M2Cy, f2(c[m], c[m + 1]), rw[h]);
         }
     }
     {   // w on the neighbouring rows: cross damping of u, y-damping of w, y-acoustics of p
@@ -204,10 +252,14 @@ __device__ __forceinline__ Row stage_row(const SS& S, const SC& C, const SN& N, 
         window1<NW>(a, S, 1, lane);
         window1<NW>(b, N, 1, lane);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            ru[i] += Ex * ((b[i + 2] - a[i + 2]) - (b[i] - a[i]));
-            rw[i] += Cy * (b[i + 1] + a[i + 1]);
-            rp[i] += By * (b[i + 1] - a[i + 1]);
+        for (int h = 0; h < 2; ++h) {
+            const int m = 2 * h + 1;   // index of cell 2h
+            const float2 hb = f2(b[m + 1] - b[m - 1], b[m + 2] - b[m]);
+            const float2 ha = f2(a[m + 1] - a[m - 1], a[m + 2] - a[m]);
+            ru[h] = fma2(Ex, sub2(hb, ha), ru[h]);
+            const float2 bc = f2(b[m], b[m + 1]), ac = f2(a[m], a[m + 1]);
+            rw[h] = fma2(Cy, add2(bc, ac), rw[h]);
+            rp[h] = fma2(By, sub2(bc, ac), rp[h]);
         }
     }
     {   // u on the neighbouring rows: cross damping of w
@@ -215,16 +267,20 @@ __device__ __forceinline__ Row stage_row(const SS& S, const SC& C, const SN& N, 
         window1<NW>(a, S, 0, lane);
         window1<NW>(b, N, 0, lane);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) rw[i] += Ey * ((b[i + 2] - b[i]) - (a[i + 2] - a[i]));
+        for (int h = 0; h < 2; ++h) {
+            const int m = 2 * h + 1;
+            const float2 hb = f2(b[m + 1] - b[m - 1], b[m + 2] - b[m]);
+            const float2 ha = f2(a[m + 1] - a[m - 1], a[m + 2] - a[m]);
+            rw[h] = fma2(Ey, sub2(hb, ha), rw[h]);
+        }
     }
     {   // p on the neighbouring rows: y-acoustics of w
         const float4 sa = S.own(2), sb = N.own(2);
-        const float a[4] = {sa.x, sa.y, sa.z, sa.w}, b[4] = {sb.x, sb.y, sb.z, sb.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) rw[i] += By * (b[i] - a[i]);
+        rw[0] = fma2(By, sub2(f2(sb.x, sb.y), f2(sa.x, sa.y)), rw[0]);
+        rw[1] = fma2(By, sub2(f2(sb.z, sb.w), f2(sa.z, sa.w)), rw[1]);
     }
-    return Row{make_float4(ru[0], ru[1], ru[2], ru[3]), make_float4(rw[0], rw[1], rw[2], rw[3]),
-               make_float4(rp[0], rp[1], rp[2], rp[3])};
+    return Row{make_float4(ru[0].x, ru[0].y, ru[1].x, ru[1].y), make_float4(rw[0].x, rw[0].y, rw[1].x, rw[1].y),
+               make_float4(rp[0].x, rp[0].y, rp[1].x, rp[1].y)};
 }
 
 template <int NW>
