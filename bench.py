@@ -234,8 +234,14 @@ def batching_workload(P, torch):
                                               * i.problem.ncell for i in insts))}
     main = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # sequential, all SMs per solve
+    # sequential, all SMs per solve; fine-step launch shapes autotuned per
+    # problem shape (cached, untimed)
     seq = [P.Solver(i.problem, stream=main, K_max=i.K, **opt) for i in insts]
+    tuned = {}
+    for s, i in zip(seq, insts):
+        t = P.parareal_autotune(s.h)
+        if not t["cached"]:
+            tuned[f"{i.problem.nx}x{i.problem.ny}_N{i.problem.n_slices}"] = t
     outs_a = [torch.empty_like(u) for u in u0s]
     for rep in range(2):
         torch.cuda.synchronize()
@@ -251,6 +257,8 @@ def batching_workload(P, torch):
     streams = [P.new_stream() for _ in insts]
     bat = [P.Solver(i.problem, stream=st, K_max=i.K, sm_limit=default_sm_limit(i.problem.d, sms), **opt)
            for i, st in zip(insts, streams)]
+    for s in bat:
+        P.parareal_autotune(s.h)
     outs_b = [torch.empty_like(u) for u in u0s]
     side = P.new_stream()
     g = P.parareal_batch_create([s.h for s in bat], u0s, [i.K for i in insts], outs_b, side)
@@ -274,7 +282,10 @@ def batching_workload(P, torch):
     res.update({"ms_sequential": ms_seq, "ms_batched_graph": ms_bat,
                 "solves_per_s_sequential": len(insts) / (ms_seq / 1e3),
                 "solves_per_s_batched": len(insts) / (ms_bat / 1e3), "speedup": ms_seq / ms_bat,
-                "results_bitwise_equal_alone": f"{same}/{len(insts)}"})
+                "results_bitwise_equal_alone": f"{same}/{len(insts)}",
+                "autotune": {"what": "FP32X fine step: tile shape of the shared-memory kernel (TX x TY: "
+                                     "0 = 32x8, 1 = 64x8, 2 = 64x16, 3 = 128x8), timed per problem shape",
+                             "per_shape": tuned}})
     return res
 
 

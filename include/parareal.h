@@ -249,6 +249,35 @@ pr_status parareal_timing_read(pr_solver* h, pr_timing* t, int32_t reset);
  * small device buffer, synchronises the legacy default stream. */
 pr_status parareal_alu_probe(int32_t prec, int32_t iters, double* flops_per_s);
 
+/* ---- autotuning of the fine-step launch shape (no counterpart in the
+ *      paper: it only chooses how the same arithmetic is laid out on the GPU) */
+
+typedef struct {
+    int32_t kernel;           /* 0: nothing to tune (FP64 fine sweep, or V != 0);
+                                 1: shared-memory tile kernel (FP32X, or FP32 with
+                                    nx not a multiple of 128);
+                                 2: row-streamed kernel (FP32, V = 0, nx a
+                                    multiple of 128)                              */
+    int32_t choice;           /* kernel 1: tile index (TX x TY cells per CTA:
+                                 0 = 32x8, 1 = 64x8, 2 = 64x16, 3 = 128x8);
+                                 kernel 2: smallest row range per CTA;  -1: none  */
+    int32_t cached;           /* 1: taken from the process-wide cache, not timed  */
+    int32_t n_candidates;     /* candidates timed (0 when cached)                 */
+    int32_t candidates[8];    /* tile indices or rows per CTA, in timing order    */
+    float us_per_step[8];     /* device time of one RK-3 step over all N slices   */
+} pr_tuning;
+
+/* Time the candidate launch shapes of the handle's FP32 fine step on its own
+ * fine-stage buffers (their contents are overwritten; nothing is allocated
+ * on the device), keep the fastest for the handle's later sweeps and record
+ * it in a process-wide cache keyed by (device, nx, ny, N_slices, fine_prec,
+ * V != 0), so handles of the same shape take it without timing.  Every
+ * candidate computes the same values cell by cell: results do not depend on
+ * the choice, bit for bit.  Synchronises the handle's stream; not for use
+ * while the stream is being captured.  out (host, optional) receives the
+ * choice and the timings.  PR_ECUDA if a launch failed. */
+pr_status parareal_autotune(pr_solver* h, pr_tuning* out);
+
 /* ---- batches of independent solves (no counterpart in the paper: the
  *      instances are independent problems; this only schedules them) ---- */
 

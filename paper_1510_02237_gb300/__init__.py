@@ -53,6 +53,16 @@ class pr_timing(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pr_tuning(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("choice", C.c_int32), ("cached", C.c_int32), ("n_candidates", C.c_int32),
+                ("candidates", C.c_int32 * 8), ("us_per_step", C.c_float * 8)]
+
+    def as_dict(self):
+        n = self.n_candidates
+        return {"kernel": ["none", "tile", "rows"][self.kernel], "choice": self.choice, "cached": bool(self.cached),
+                "candidates": list(self.candidates[:n]), "us_per_step": [float(x) for x in self.us_per_step[:n]]}
+
+
 class PararealError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -65,7 +75,7 @@ EXPORTS = ["parareal_default_options", "parareal_create", "parareal_destroy", "p
            "krylov_project", "parareal_timing_enable", "parareal_timing_read", "parareal_kernel_launches",
            "parareal_alu_probe", "parareal_fine_sweep_static", "parareal_selftest_wait_timeout",
            "parareal_solve_batch", "parareal_batch_create", "parareal_batch_launch", "parareal_batch_destroy",
-           "parareal_split_gemm_tn", "parareal_split_gemm_nn"]
+           "parareal_split_gemm_tn", "parareal_split_gemm_nn", "parareal_autotune"]
 
 _lib = None
 
@@ -113,6 +123,8 @@ def lib():
     L.parareal_timing_enable.restype = st
     L.parareal_timing_read.argtypes = [P, C.POINTER(pr_timing), C.c_int32]
     L.parareal_timing_read.restype = st
+    L.parareal_autotune.argtypes = [P, C.POINTER(pr_tuning)]
+    L.parareal_autotune.restype = st
     L.parareal_kernel_launches.argtypes = []
     L.parareal_kernel_launches.restype = C.c_uint64
     L.parareal_alu_probe.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_double)]
@@ -244,6 +256,14 @@ def parareal_timing_enable(h, max_solves):
 def parareal_timing_read(h, reset=True) -> dict:
     t = pr_timing()
     _check(h, lib().parareal_timing_read(h, C.byref(t), 1 if reset else 0))
+    return t.as_dict()
+
+
+def parareal_autotune(h) -> dict:
+    """Time the fine step's candidate launch shapes on the handle's buffers and
+    keep the fastest (cached per shape for the process); returns the choice."""
+    t = pr_tuning()
+    _check(h, lib().parareal_autotune(h, C.byref(t)))
     return t.as_dict()
 
 

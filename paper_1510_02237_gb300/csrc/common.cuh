@@ -56,13 +56,26 @@ struct SliceMap {
     bool in_map = false, out_map = false;
 };
 
+// Launch shape of the FP32 fine step, chosen by the autotuner
+// (parareal_autotune) or left at the built-in heuristic.
+//   tile:     shared-memory tile kernel (V = 0): -1 heuristic, else an index
+//             into fine_tile_shapes (TX x TY cells per CTA);
+//   min_rows: row-streamed kernel: smallest row range per CTA (the grid is
+//             min(resident CTAs, n*ny / min_rows)).
+struct FineLaunch {
+    int tile = -1;
+    int min_rows = 16;
+};
+constexpr int kFineTiles = 4;
+extern const int fine_tile_shapes[kFineTiles][2];
+
 // One RK-3 step on n states.  in/out element types select FP64 or FP32
 // arithmetic (T) with conversion at the boundary.  instride/outstride are
 // element strides between consecutive states.
 template <typename T, typename Tin, typename Tout>
 cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outstride, int n, int nx,
                              int ny, bool has_v, const FineCoef<T>& c, cudaStream_t s,
-                             const SliceMap& sm = SliceMap());
+                             const SliceMap& sm = SliceMap(), const FineLaunch& fl = FineLaunch());
 
 // One RK-3 step in FP32 arithmetic streamed row by row (fine_rows.cu), for
 // FP32 input, V = 0 and nx a multiple of 128 up to 1024 with 16-byte aligned
@@ -70,7 +83,8 @@ cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outst
 // *err holds the launch status.
 template <typename Tin, typename Tout>
 bool launch_fine_rows(const Tin* in, long instride, Tout* out, long outstride, int n, int nx, int ny, bool has_v,
-                      const FineCoef<float>& c, cudaStream_t s, const SliceMap& map, cudaError_t* err);
+                      const FineCoef<float>& c, cudaStream_t s, const SliceMap& map, cudaError_t* err,
+                      int min_rows = 16);
 
 // Process-wide flag of the row-streamed kernel (synchronising read): 1 once a
 // wait for one of its TMA row loads gave up (results since then invalid),
@@ -80,7 +94,10 @@ int fine_rows_wait_error(bool reset);
 // One RK-3 step with FP32 tendencies and stages on an FP64 state: the last
 // stage forms q^{n+1} = q^n + dt L(q**) in FP64 (fine_prec = PR_FP32X).
 cudaError_t launch_fine_step_acc64(const double* in, double* out, long stride, int n, int nx, int ny, bool has_v,
-                                  const FineCoef<float>& c, cudaStream_t s, const SliceMap& sm = SliceMap());
+                                  const FineCoef<float>& c, cudaStream_t s, const SliceMap& sm = SliceMap(),
+                                  const FineLaunch& fl = FineLaunch());
+// true when an FP32-input step of this shape runs on the row-streamed kernel
+bool fine_rows_eligible(int nx, bool has_v);
 
 // One coarse step (slow tendency + n_sound forward-backward substeps) on n
 // states, FP64 arithmetic or FP32 arithmetic (fp32) on FP64 data.

@@ -171,50 +171,67 @@ cudaError_t launch_tile(const Tin* in, long instride, Tout* out, long outstride,
     return cudaGetLastError();
 }
 
+template <typename T, typename Tin, typename Tout, bool ACC64>
+cudaError_t launch_tiles(const Tin* in, long instride, Tout* out, long outstride, int n, int nx, int ny, bool has_v,
+                         const FineCoef<T>& c, cudaStream_t s, const SliceMap& map, const FineLaunch& fl) {
+    const bool big = nx >= 64 && ny >= 16;
+    if (has_v) {
+        if (big)
+            return launch_tile<T, Tin, Tout, 3, 64, 16, 256, ACC64>(in, instride, out, outstride, n, nx, ny, c, s, map);
+        return launch_tile<T, Tin, Tout, 3, 32, 8, 256, ACC64>(in, instride, out, outstride, n, nx, ny, c, s, map);
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        const int t = (fl.tile < 0 || fl.tile >= kFineTiles) ? (big ? 2 : 0) : fl.tile;
+        switch (t) {
+            case 0: return launch_tile<T, Tin, Tout, 1, 32, 8, 256, ACC64>(in, instride, out, outstride, n, nx, ny, c, s, map);
+            case 1: return launch_tile<T, Tin, Tout, 1, 64, 8, 256, ACC64>(in, instride, out, outstride, n, nx, ny, c, s, map);
+            case 3: return launch_tile<T, Tin, Tout, 1, 128, 8, 256, ACC64>(in, instride, out, outstride, n, nx, ny, c, s, map);
+            default: return launch_tile<T, Tin, Tout, 1, 64, 16, 256, ACC64>(in, instride, out, outstride, n, nx, ny, c, s, map);
+        }
+    } else {   // FP64 tile steps (slice-mapped sweeps) keep the fixed shapes
+        if (big) return launch_tile<T, Tin, Tout, 1, 64, 16, 256, ACC64>(in, instride, out, outstride, n, nx, ny, c, s, map);
+        return launch_tile<T, Tin, Tout, 1, 32, 8, 256, ACC64>(in, instride, out, outstride, n, nx, ny, c, s, map);
+    }
+}
+
 }  // namespace
+
+// Candidate tile shapes of the autotuner (V = 0): TX x TY output cells per
+// CTA of 256 threads.
+const int fine_tile_shapes[kFineTiles][2] = {{32, 8}, {64, 8}, {64, 16}, {128, 8}};
 
 template <typename T, typename Tin, typename Tout>
 cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outstride, int n, int nx,
-                             int ny, bool has_v, const FineCoef<T>& c, cudaStream_t s, const SliceMap& map) {
+                             int ny, bool has_v, const FineCoef<T>& c, cudaStream_t s, const SliceMap& map,
+                             const FineLaunch& fl) {
     if constexpr (std::is_same<T, float>::value) {
         cudaError_t e = cudaSuccess;
-        if (launch_fine_rows<Tin, Tout>(in, instride, out, outstride, n, nx, ny, has_v, c, s, map, &e))
+        if (launch_fine_rows<Tin, Tout>(in, instride, out, outstride, n, nx, ny, has_v, c, s, map, &e, fl.min_rows))
             return e;
     }
-    const bool big = nx >= 64 && ny >= 16;
-    if (has_v) {
-        if (big) return launch_tile<T, Tin, Tout, 3, 64, 16, 256>(in, instride, out, outstride, n, nx, ny, c, s, map);
-        return launch_tile<T, Tin, Tout, 3, 32, 8, 256>(in, instride, out, outstride, n, nx, ny, c, s, map);
-    }
-    if (big) return launch_tile<T, Tin, Tout, 1, 64, 16, 256>(in, instride, out, outstride, n, nx, ny, c, s, map);
-    return launch_tile<T, Tin, Tout, 1, 32, 8, 256>(in, instride, out, outstride, n, nx, ny, c, s, map);
+    return launch_tiles<T, Tin, Tout, false>(in, instride, out, outstride, n, nx, ny, has_v, c, s, map, fl);
 }
 
 cudaError_t launch_fine_step_acc64(const double* in, double* out, long stride, int n, int nx, int ny, bool has_v,
-                                  const FineCoef<float>& c, cudaStream_t s, const SliceMap& map) {
-    const bool big = nx >= 64 && ny >= 16;
-    if (has_v) {
-        if (big) return launch_tile<float, double, double, 3, 64, 16, 256, true>(in, stride, out, stride, n, nx, ny, c, s, map);
-        return launch_tile<float, double, double, 3, 32, 8, 256, true>(in, stride, out, stride, n, nx, ny, c, s, map);
-    }
-    if (big) return launch_tile<float, double, double, 1, 64, 16, 256, true>(in, stride, out, stride, n, nx, ny, c, s, map);
-    return launch_tile<float, double, double, 1, 32, 8, 256, true>(in, stride, out, stride, n, nx, ny, c, s, map);
+                                  const FineCoef<float>& c, cudaStream_t s, const SliceMap& map,
+                                  const FineLaunch& fl) {
+    return launch_tiles<float, double, double, true>(in, stride, out, stride, n, nx, ny, has_v, c, s, map, fl);
 }
 
 template cudaError_t launch_fine_step<double, double, double>(const double*, long, double*, long, int,
                                                               int, int, bool, const FineCoef<double>&,
-                                                              cudaStream_t, const SliceMap&);
+                                                              cudaStream_t, const SliceMap&, const FineLaunch&);
 template cudaError_t launch_fine_step<float, double, float>(const double*, long, float*, long, int, int,
                                                             int, bool, const FineCoef<float>&,
-                                                            cudaStream_t, const SliceMap&);
+                                                            cudaStream_t, const SliceMap&, const FineLaunch&);
 template cudaError_t launch_fine_step<float, float, float>(const float*, long, float*, long, int, int,
                                                            int, bool, const FineCoef<float>&,
-                                                           cudaStream_t, const SliceMap&);
+                                                           cudaStream_t, const SliceMap&, const FineLaunch&);
 template cudaError_t launch_fine_step<float, float, double>(const float*, long, double*, long, int, int,
                                                             int, bool, const FineCoef<float>&,
-                                                            cudaStream_t, const SliceMap&);
+                                                            cudaStream_t, const SliceMap&, const FineLaunch&);
 template cudaError_t launch_fine_step<float, double, double>(const double*, long, double*, long, int,
                                                              int, int, bool, const FineCoef<float>&,
-                                                             cudaStream_t, const SliceMap&);
+                                                             cudaStream_t, const SliceMap&, const FineLaunch&);
 
 }  // namespace pr

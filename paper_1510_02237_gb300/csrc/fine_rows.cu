@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(32 * NW, (NW >= 8 ? 1 : 12 / NW))
 
 template <int NW, typename Tin, typename Tout>
 cudaError_t launch_nw(const Tin* in, long instride, Tout* out, long outstride, int n, int nx, int ny,
-                      const RowCoef& k, cudaStream_t s, const SliceMap& map) {
+                      const RowCoef& k, cudaStream_t s, const SliceMap& map, int min_rows) {
     static int cached[64][2] = {};   // [device] -> (SMs, CTAs per SM)
     constexpr int R = ring_rows<Tin>();
     const size_t smem = (size_t)R * 3 * nx * sizeof(Tin) + 8 * R;
@@ -476,9 +476,10 @@ cudaError_t launch_nw(const Tin* in, long instride, Tout* out, long outstride, i
         }
     }
     if (per < 1) return cudaErrorInvalidConfiguration;
-    // at least ~16 rows per CTA keep the 6 halo rows of a range cheap
+    // at least min_rows rows per CTA (default 16) keep the 6 halo rows of a range cheap
+    if (min_rows < 1) min_rows = 1;
     const long rows = (long)n * ny;
-    long G = (rows + 15) / 16;
+    long G = (rows + min_rows - 1) / min_rows;
     if (G > (long)sms * per) G = (long)sms * per;
     if (G < 1) G = 1;
     kern<<<(unsigned)G, 32 * NW, smem, s>>>(in, instride, out, outstride, n, nx, ny, k, map);
@@ -498,16 +499,22 @@ int fine_rows_wait_error(bool reset) {
     return v;
 }
 
+bool fine_rows_eligible(int nx, bool has_v) {
+    const int nw = nx / 128;
+    return !has_v && nx % 128 == 0 && (nw == 1 || nw == 2 || nw == 4 || nw == 8);
+}
+
 template <typename Tin, typename Tout>
 bool launch_fine_rows(const Tin* in, long instride, Tout* out, long outstride, int n, int nx, int ny, bool has_v,
-                      const FineCoef<float>& c, cudaStream_t s, const SliceMap& map, cudaError_t* err) {
+                      const FineCoef<float>& c, cudaStream_t s, const SliceMap& map, cudaError_t* err,
+                      int min_rows) {
     if constexpr (sizeof(Tin) != sizeof(float)) {
         // FP64 input: the per-read conversions to FP32 would run at the FP64
         // rate, so the shared-memory tile kernel (one conversion per cell) serves it
         return false;
     } else {
     const int nw = nx / 128;
-    if (has_v || nx % 128 != 0 || (nw != 1 && nw != 2 && nw != 4 && nw != 8) || ny < 1 || n < 1) return false;
+    if (!fine_rows_eligible(nx, has_v) || ny < 1 || n < 1) return false;
     if (((uintptr_t)in | (uintptr_t)out) % 16 != 0 || instride % 4 != 0 || outstride % 4 != 0) return false;
     RowCoef k;
     const double ck[3] = {(double)c.c1, (double)c.c2, (double)c.c3};
@@ -521,22 +528,22 @@ bool launch_fine_rows(const Tin* in, long instride, Tout* out, long outstride, i
         k.Ey[i] = (float)(ck[i] * (double)c.dxy2);
     }
     switch (nw) {
-        case 1: *err = launch_nw<1, Tin, Tout>(in, instride, out, outstride, n, nx, ny, k, s, map); break;
-        case 2: *err = launch_nw<2, Tin, Tout>(in, instride, out, outstride, n, nx, ny, k, s, map); break;
-        case 4: *err = launch_nw<4, Tin, Tout>(in, instride, out, outstride, n, nx, ny, k, s, map); break;
-        default: *err = launch_nw<8, Tin, Tout>(in, instride, out, outstride, n, nx, ny, k, s, map); break;
+        case 1: *err = launch_nw<1, Tin, Tout>(in, instride, out, outstride, n, nx, ny, k, s, map, min_rows); break;
+        case 2: *err = launch_nw<2, Tin, Tout>(in, instride, out, outstride, n, nx, ny, k, s, map, min_rows); break;
+        case 4: *err = launch_nw<4, Tin, Tout>(in, instride, out, outstride, n, nx, ny, k, s, map, min_rows); break;
+        default: *err = launch_nw<8, Tin, Tout>(in, instride, out, outstride, n, nx, ny, k, s, map, min_rows); break;
     }
     return true;
     }
 }
 
 template bool launch_fine_rows<double, double>(const double*, long, double*, long, int, int, int, bool, const FineCoef<float>&,
-                                        cudaStream_t, const SliceMap&, cudaError_t*);
+                                        cudaStream_t, const SliceMap&, cudaError_t*, int);
 template bool launch_fine_rows<double, float>(const double*, long, float*, long, int, int, int, bool, const FineCoef<float>&,
-                                        cudaStream_t, const SliceMap&, cudaError_t*);
+                                        cudaStream_t, const SliceMap&, cudaError_t*, int);
 template bool launch_fine_rows<float, float>(const float*, long, float*, long, int, int, int, bool, const FineCoef<float>&,
-                                        cudaStream_t, const SliceMap&, cudaError_t*);
+                                        cudaStream_t, const SliceMap&, cudaError_t*, int);
 template bool launch_fine_rows<float, double>(const float*, long, double*, long, int, int, int, bool, const FineCoef<float>&,
-                                        cudaStream_t, const SliceMap&, cudaError_t*);
+                                        cudaStream_t, const SliceMap&, cudaError_t*, int);
 
 }  // namespace pr

@@ -14,6 +14,9 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -74,6 +77,7 @@ struct pr_solver {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     TimingRing tr;
     long fine_launch_acc = 0;   // fine-predictor kernel launches of the current solve
+    FineLaunch fl;              // launch shape of the FP32 fine steps (parareal_autotune)
     std::string err;
 };
 
@@ -163,24 +167,24 @@ static pr_status fine_apply(pr_solver* h, const double* in, double* out, int n, 
         const double* a = in;
         for (int st = 0; st < nf; ++st) {
             double* b = st == nf - 1 ? out : (st % 2 == 0 ? h->fb0 : h->fb1);
-            CKC(launch_fine_step_acc64(a, b, d, n, h->nx, h->ny, hv, h->fc32, s, st == 0 ? m0 : m1));
+            CKC(launch_fine_step_acc64(a, b, d, n, h->nx, h->ny, hv, h->fc32, s, st == 0 ? m0 : m1, h->fl));
             a = b;
         }
         return PR_OK;
     }
     if (h->opt.fine_prec == PR_FP32) {
         if (nf == 1) {
-            CKC((launch_fine_step<float, double, double>(in, d, out, d, n, h->nx, h->ny, hv, h->fc32, s, m0)));
+            CKC((launch_fine_step<float, double, double>(in, d, out, d, n, h->nx, h->ny, hv, h->fc32, s, m0, h->fl)));
             return PR_OK;
         }
-        CKC((launch_fine_step<float, double, float>(in, d, h->f32a, d, n, h->nx, h->ny, hv, h->fc32, s, m0)));
+        CKC((launch_fine_step<float, double, float>(in, d, h->f32a, d, n, h->nx, h->ny, hv, h->fc32, s, m0, h->fl)));
         float* a = h->f32a;
         float* b = h->f32b;
         for (int st = 1; st < nf - 1; ++st) {
-            CKC((launch_fine_step<float, float, float>(a, d, b, d, n, h->nx, h->ny, hv, h->fc32, s, m1)));
+            CKC((launch_fine_step<float, float, float>(a, d, b, d, n, h->nx, h->ny, hv, h->fc32, s, m1, h->fl)));
             float* t = a; a = b; b = t;
         }
-        CKC((launch_fine_step<float, float, double>(a, d, out, d, n, h->nx, h->ny, hv, h->fc32, s, m1)));
+        CKC((launch_fine_step<float, float, double>(a, d, out, d, n, h->nx, h->ny, hv, h->fc32, s, m1, h->fl)));
         return PR_OK;
     }
     if (h->fb2 && !first) {
@@ -963,6 +967,107 @@ pr_status parareal_timing_read(pr_solver* h, pr_timing* t, int32_t reset) {
 }
 
 uint64_t parareal_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------ autotuning
+
+}  // extern "C"
+
+namespace {
+// Process-wide cache of tuned launch shapes: (device, nx, ny, N, fine_prec,
+// V != 0) -> (kernel kind, choice).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> g_tune;
+}  // namespace
+
+extern "C" {
+
+pr_status parareal_autotune(pr_solver* h, pr_tuning* out) {
+    if (!h) return PR_EINVAL;
+    pr_tuning t;
+    std::memset(&t, 0, sizeof(t));
+    t.choice = -1;
+    const bool hv = h->V != 0.0;
+    const int prec = h->opt.fine_prec;
+    int kind = 0;
+    if (prec == PR_FP32X)
+        kind = hv ? 0 : 1;
+    else if (prec == PR_FP32)
+        kind = fine_rows_eligible(h->nx, hv) ? 2 : (hv ? 0 : 1);
+    t.kernel = kind;
+    if (kind == 0) {
+        if (out) *out = t;
+        return PR_OK;
+    }
+    int dev = 0;
+    CKC(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, h->nx, h->ny, h->N, prec, (int)hv);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end() && it->second.first == kind) {
+            if (kind == 1) h->fl.tile = it->second.second; else h->fl.min_rows = it->second.second;
+            t.choice = it->second.second;
+            t.cached = 1;
+            if (out) *out = t;
+            return PR_OK;
+        }
+    }
+    const int nc = kind == 1 ? kFineTiles : 4;
+    const int rows_cand[4] = {8, 16, 32, 64};
+    const long d = h->d;
+    const size_t elems = (size_t)h->N * d;
+    cudaStream_t s = h->stream;
+    if (prec == PR_FP32X)
+        CKC(cudaMemsetAsync(h->fb0, 0, sizeof(double) * elems, s));
+    else
+        CKC(cudaMemsetAsync(h->f32a, 0, sizeof(float) * elems, s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CKC(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return set_err(h, PR_ECUDA, "cudaEventCreate failed");
+    }
+    const int reps = 20;
+    float best = 0.f;
+    int bi = 0;
+    cudaError_t err = cudaSuccess;
+    for (int c = 0; c < nc && err == cudaSuccess; ++c) {
+        FineLaunch fl = h->fl;
+        if (kind == 1) fl.tile = c; else fl.min_rows = rows_cand[c];
+        t.candidates[c] = kind == 1 ? c : rows_cand[c];
+        for (int r = 0; r <= reps && err == cudaSuccess; ++r) {
+            if (r == 1) err = cudaEventRecord(e0, s);
+            if (err != cudaSuccess) break;
+            if (prec == PR_FP32X)
+                err = launch_fine_step_acc64(h->fb0, h->fb1, d, h->N, h->nx, h->ny, hv, h->fc32, s, SliceMap(), fl);
+            else
+                err = launch_fine_step<float, float, float>(h->f32a, d, h->f32b, d, h->N, h->nx, h->ny, hv, h->fc32,
+                                                            s, SliceMap(), fl);
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        t.us_per_step[c] = 1e3f * ms / reps;
+        if (c == 0 || t.us_per_step[c] < best) {
+            best = t.us_per_step[c];
+            bi = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return set_err(h, PR_ECUDA, std::string("autotune: ") + cudaGetErrorString(err));
+    CKS(check_device_waits(h));
+    t.n_candidates = nc;
+    t.choice = t.candidates[bi];
+    if (kind == 1) h->fl.tile = t.choice; else h->fl.min_rows = t.choice;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = std::make_pair(kind, t.choice);
+    }
+    if (out) *out = t;
+    return PR_OK;
+}
 
 // ------------------------------------------------------------------ batches
 

@@ -21,8 +21,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (PR_FP32, PR_FP32X, PR_FP64, PR_PROJ_SPLIT_BF16, Solver, new_stream, parareal_footprint_bytes,
-               parareal_solve)
+from . import (PR_FP32, PR_FP32X, PR_FP64, PR_PROJ_SPLIT_BF16, Solver, new_stream, parareal_autotune,
+               parareal_footprint_bytes, parareal_solve)
 
 
 @dataclass
@@ -80,13 +80,14 @@ class Server:
     """Admit, run and complete requests; see the module docstring."""
 
     def __init__(self, budget_bytes: float = 150e9, max_inflight: int = 16, mode: str = "mixed",
-                 sm_limit=default_sm_limit):
+                 sm_limit=default_sm_limit, autotune: bool = True):
         import torch
         self.torch = torch
         self.budget = float(budget_bytes)
         self.max_inflight = int(max_inflight)
         self.mode = mode
         self.sm_limit = sm_limit
+        self.autotune = autotune
         self.sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         self.slots = collections.defaultdict(list)
         self.bytes = 0
@@ -129,6 +130,8 @@ class Server:
         torch = self.torch
         stream = new_stream()
         solver = Solver(p, stream=stream, **opt)
+        if self.autotune:   # fine-step launch shape, timed once per problem shape (cached)
+            parareal_autotune(solver.h)
         slot = _Slot(key, solver, stream, torch.empty(p.d, dtype=torch.float64, device="cuda"),
                      torch.empty(p.d, dtype=torch.float64, device="cuda"),
                      torch.empty(p.d, dtype=torch.float64).pin_memory(),
