@@ -60,6 +60,12 @@ enum { PR_PROJ_FP64 = 0, PR_PROJ_SPLIT_BF16 = 1 };  /* arithmetic of the project
                                                       the BF16 tensor cores (each
                                                       FP64 column split into 8
                                                       exact 7-bit digit slices)     */
+enum { PR_COARSE_SPLIT_FE = 0, PR_COARSE_RK3 = 1 };  /* coarse propagator G: partially
+                                                      split forward Euler with
+                                                      forward-backward acoustic
+                                                      substeps (Sec. 3.2), or
+                                                      non-split RK-3 of the same
+                                                      operators (Sec. 3.1 demos)  */
 #define PR_MAX_ITERS 128
 
 typedef struct {
@@ -116,6 +122,16 @@ typedef struct {
                               needs 3*nx*ny to be a multiple of 8 and adds about
                               32*cap*3*nx*ny bytes of digit slices to the
                               footprint (default PR_PROJ_FP64)                  */
+    int32_t coarse_scheme; /* PR_COARSE_SPLIT_FE (default): one coarse step is a
+                              partially split forward-Euler step with n_sound
+                              forward-backward acoustic substeps and damping
+                              alpha = nu_c dx^2 / (Delta t / n_sound);
+                              PR_COARSE_RK3: one coarse step is a non-split RK-3
+                              step of length Delta t of the upwind advection
+                              (adv_order_c), centred acoustics and damping with
+                              alpha = nu_c dx^2 / Delta t (n_sound unused) -- the
+                              coarse propagator of the paper's instability
+                              demonstrations (Sec. 3.1, first-order upwind)      */
 } pr_options;
 
 typedef struct {

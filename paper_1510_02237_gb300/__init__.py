@@ -19,6 +19,7 @@ PR_FP64, PR_FP32, PR_FP32X = 0, 1, 2
 PR_KSE, PR_ORIGINAL = 0, 1
 PR_IMAGES_LINEARITY, PR_IMAGES_DIRECT = 0, 1
 PR_PROJ_FP64, PR_PROJ_SPLIT_BF16 = 0, 1
+PR_COARSE_SPLIT_FE, PR_COARSE_RK3 = 0, 1
 PR_MAX_ITERS = 128
 _STATUS = {0: "PR_OK", -1: "PR_EINVAL", -2: "PR_ENOMEM", -3: "PR_ECUDA", -4: "PR_ETIMEOUT",
            -5: "PR_ESTATE", -6: "PR_ECANCELLED"}
@@ -34,7 +35,8 @@ class pr_options(C.Structure):
                 ("K_max", C.c_int32), ("krylov_cap", C.c_int32), ("drop_tol", C.c_double),
                 ("fine_prec", C.c_int32), ("variant", C.c_int32), ("corr_prec", C.c_int32),
                 ("r_tol", C.c_double), ("n_windows", C.c_int32), ("images", C.c_int32),
-                ("sm_limit", C.c_int32), ("stream", C.c_void_p), ("proj_prec", C.c_int32)]
+                ("sm_limit", C.c_int32), ("stream", C.c_void_p), ("proj_prec", C.c_int32),
+                ("coarse_scheme", C.c_int32)]
 
 
 class pr_report(C.Structure):
@@ -388,6 +390,7 @@ class Solver:
         opt.setdefault("n_sound", p.n_sound)
         opt.setdefault("adv_order_f", p.adv_order_f)
         opt.setdefault("adv_order_c", p.adv_order_c)
+        opt.setdefault("coarse_scheme", getattr(p, "coarse_scheme", 0))
         opt.setdefault("V", p.V)
         self.p = p
         self.h = parareal_create(p.nx, p.ny, p.U, p.c_s, p.dt_f, p.dt_g, p.n_slices, stream=stream, **opt)

@@ -26,7 +26,10 @@ __global__ void __launch_bounds__(CNT) k_coarse_step(const double* __restrict__ 
 
 }  // namespace
 
-int coarse_halo(const CoarseCoef& c) { return (c.order == 1 ? 1 : 2) + 2 * c.n_sound - 1; }
+int coarse_halo(const CoarseCoef& c) {
+    const int r = c.order == 1 ? 1 : 2;
+    return c.scheme == 1 ? 3 * r : r + 2 * c.n_sound - 1;
+}
 
 cudaError_t launch_coarse_step(const double* in, double* out, long stride, int n, int nx, int ny,
                                const CoarseCoef& c, cudaStream_t s, bool fp32, const SliceMap& map) {

@@ -11,6 +11,12 @@
 // 1 for the pressure) and the slow tendency by the flux radius r, so the
 // tile loads a halo H = r + 2 n_sound - 1 and shrinks the valid region as
 // the substeps proceed; nothing is written to memory between substeps.
+//
+// scheme = 1 replaces the split step by one non-split RK-3 step of length
+// Delta t of the same operators (upwind advection of order 1 or 3, centred
+// acoustics, damping with alpha = nu_c dx^2 / Delta t): the coarse
+// propagator of the paper's instability demonstrations (Sec. 3.1).  Each
+// stage widens the cone by the flux radius r, so the halo is H = 3 r.
 #pragma once
 
 #include "common.cuh"
@@ -64,6 +70,88 @@ __device__ __forceinline__ void coarse_tile(const Tin* __restrict__ src, Tout* _
     __syncthreads();
 
     const int ra = c.order == 1 ? 1 : 2;
+    constexpr int MAXC = ((TX + 2 * COARSE_MAXH) * (TY + 2 * COARSE_MAXH) + NT - 1) / NT;
+    if (cd.scheme == 1) {
+        // L(a) at index i: upwind advection, centred acoustics, grad-div damping
+        auto tend = [&](const T* au, const T* aw, const T* ap, int i, T& Lu, T& Lw, T& Lp) {
+            const T* fs[3] = {au, aw, ap};
+            T t[3];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const T* a = fs[f];
+                const T Fe = upwind_flux<T>(c.order, c.U, a, i, 1), Fw = upwind_flux<T>(c.order, c.U, a, i - 1, 1);
+                const T Gn = upwind_flux<T>(c.order, c.V, a, i, RX), Gs = upwind_flux<T>(c.order, c.V, a, i - RX, RX);
+                t[f] = -(Fe - Fw) * c.inv_dx - (Gn - Gs) * c.inv_dy;
+            }
+            Lu = t[0] - c.csx * (ap[i + 1] - ap[i - 1]) + c.dxx * (au[i + 1] - T(2) * au[i] + au[i - 1]) +
+                 c.dxy1 * ((aw[i + 1 + RX] - aw[i + 1 - RX]) - (aw[i - 1 + RX] - aw[i - 1 - RX]));
+            Lw = t[1] - c.csy * (ap[i + RX] - ap[i - RX]) + c.dyy * (aw[i + RX] - T(2) * aw[i] + aw[i - RX]) +
+                 c.dxy2 * ((au[i + 1 + RX] - au[i - 1 + RX]) - (au[i + 1 - RX] - au[i - 1 - RX]));
+            Lp = t[2] - (c.csx * (au[i + 1] - au[i - 1]) + c.csy * (aw[i + RX] - aw[i - RX]));
+        };
+        const T c1 = c.tau / T(3), c2 = c.tau / T(2), c3 = c.tau;
+        {   // stage 1: s = q + tau/3 L(q) on the region shrunk by ra
+            const int W1 = RX - 2 * ra, H1 = RY - 2 * ra, N1 = W1 * H1;
+            for (int t = threadIdx.x; t < N1; t += NT) {
+                const int r = t / W1;
+                const int i = (r + ra) * RX + (t - r * W1) + ra;
+                T Lu, Lw, Lp;
+                tend(u, w, p, i, Lu, Lw, Lp);
+                su[i] = u[i] + c1 * Lu;
+                sw[i] = w[i] + c1 * Lw;
+                sp[i] = p[i] + c1 * Lp;
+            }
+        }
+        __syncthreads();
+        {   // stage 2: s <- q + tau/2 L(s) on the region shrunk by 2 ra (the tile
+            // plus ra <= 2 cells around it), staged in registers
+            constexpr int MAXR = ((TX + 4) * (TY + 4) + NT - 1) / NT;
+            const int sh = 2 * ra, W2 = RX - 2 * sh, H2 = RY - 2 * sh, N2 = W2 * H2;
+            T ru[MAXR], rw[MAXR], rp[MAXR];
+#pragma unroll
+            for (int k = 0; k < MAXR; ++k) {
+                const int t = threadIdx.x + k * NT;
+                if (t < N2) {
+                    const int r = t / W2;
+                    const int i = (r + sh) * RX + (t - r * W2) + sh;
+                    T Lu, Lw, Lp;
+                    tend(su, sw, sp, i, Lu, Lw, Lp);
+                    ru[k] = u[i] + c2 * Lu;
+                    rw[k] = w[i] + c2 * Lw;
+                    rp[k] = p[i] + c2 * Lp;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < MAXR; ++k) {
+                const int t = threadIdx.x + k * NT;
+                if (t < N2) {
+                    const int r = t / W2;
+                    const int i = (r + sh) * RX + (t - r * W2) + sh;
+                    su[i] = ru[k];
+                    sw[i] = rw[k];
+                    sp[i] = rp[k];
+                }
+            }
+        }
+        __syncthreads();
+        // stage 3: q' = q + tau L(s) on the tile, written to memory
+        for (int t = threadIdx.x; t < TX * TY; t += NT) {
+            const int r = t / TX, cx = t - r * TX;
+            const int gx = tx0 + cx, gy = ty0 + r;
+            if (gx < nx && gy < ny) {
+                const int i = (r + H) * RX + cx + H;
+                T Lu, Lw, Lp;
+                tend(su, sw, sp, i, Lu, Lw, Lp);
+                const long g = (long)gy * nx + gx;
+                dst[g] = (Tout)(u[i] + c3 * Lu);
+                dst[ncell + g] = (Tout)(w[i] + c3 * Lw);
+                dst[2 * ncell + g] = (Tout)(p[i] + c3 * Lp);
+            }
+        }
+        __syncthreads();   // the shared buffers may be reused right after
+        return;
+    }
     // slow (advective) tendency on the region shrunk by ra
     {
         const int W1 = RX - 2 * ra, H1 = RY - 2 * ra, N1 = W1 * H1;
@@ -83,7 +171,6 @@ __device__ __forceinline__ void coarse_tile(const Tin* __restrict__ src, Tout* _
     }
     __syncthreads();
 
-    constexpr int MAXC = ((TX + 2 * COARSE_MAXH) * (TY + 2 * COARSE_MAXH) + NT - 1) / NT;
     for (int m = 0; m < c.n_sound; ++m) {
         // forward: velocities on the region shrunk by ra + 2m
         const int sh = ra + 2 * m;

@@ -41,6 +41,8 @@ struct CoarseCoef {
     double dyy, dxy2;   // alpha2 / dy^2, alpha2 / (4 dx dy)
     int n_sound;
     int order;          // 1 or 3 (upwind-biased advective flux)
+    int scheme = 0;     // 0: partially split forward Euler; 1: non-split RK-3 with
+                        //    tau = Delta t and alpha = nu_c dx^2 / Delta t
 };
 
 // ------------------------------------------------------------ launchers

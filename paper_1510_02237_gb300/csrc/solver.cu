@@ -588,6 +588,7 @@ pr_status parareal_default_options(pr_options* o) {
     o->images = PR_IMAGES_LINEARITY;
     o->sm_limit = 0;
     o->stream = nullptr;
+    o->coarse_scheme = PR_COARSE_SPLIT_FE;
     return PR_OK;
 }
 
@@ -605,7 +606,10 @@ static pr_status validate(const pr_grid* g, double U, double c_s, double dt_f, d
     if (o.adv_order_f != 6) return set_err(h, PR_EINVAL, "adv_order_f must be 6");
     if (o.adv_order_c != 1 && o.adv_order_c != 3) return set_err(h, PR_EINVAL, "adv_order_c must be 1 or 3");
     if (o.n_sound < 1) return set_err(h, PR_EINVAL, "n_sound must be >= 1");
-    if ((o.adv_order_c == 1 ? 1 : 2) + 2 * o.n_sound - 1 > 12) return set_err(h, PR_EINVAL, "n_sound too large for the fused coarse step (halo > 12)");
+    if (o.coarse_scheme != PR_COARSE_SPLIT_FE && o.coarse_scheme != PR_COARSE_RK3)
+        return set_err(h, PR_EINVAL, "coarse_scheme must be PR_COARSE_SPLIT_FE or PR_COARSE_RK3");
+    if (o.coarse_scheme == PR_COARSE_SPLIT_FE && (o.adv_order_c == 1 ? 1 : 2) + 2 * o.n_sound - 1 > 12)
+        return set_err(h, PR_EINVAL, "n_sound too large for the fused coarse step (halo > 12)");
     if (o.fine_prec != PR_FP64 && o.fine_prec != PR_FP32 && o.fine_prec != PR_FP32X)
         return set_err(h, PR_EINVAL, "fine_prec must be PR_FP64, PR_FP32 or PR_FP32X");
     if (o.variant != PR_KSE && o.variant != PR_ORIGINAL) return set_err(h, PR_EINVAL, "variant must be PR_KSE or PR_ORIGINAL");
@@ -673,7 +677,7 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     h->fc64 = make_fine_coef<double>(U, o.V, c_s, dx, dy, o.nu_f, dt_f);
     h->fc32 = make_fine_coef<float>(U, o.V, c_s, dx, dy, o.nu_f, dt_f);
     h->fck = make_fine_coef_k(U, o.V, c_s, dx, dy, o.nu_f, dt_f);
-    const double tau = dt_g / o.n_sound;
+    const double tau = o.coarse_scheme == PR_COARSE_RK3 ? dt_g : dt_g / o.n_sound;
     const double a1 = o.nu_c * dx * dx / tau, a2 = o.nu_c * dy * dy / tau;
     h->cc.U = U;
     h->cc.V = o.V;
@@ -688,6 +692,7 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     h->cc.dxy2 = a2 / (4.0 * dx * dy);
     h->cc.n_sound = o.n_sound;
     h->cc.order = o.adv_order_c;
+    h->cc.scheme = o.coarse_scheme == PR_COARSE_RK3 ? 1 : 0;
 
     const long d = h->d;
     const int N = h->N;

@@ -102,6 +102,20 @@ def coarse_amplification(p, kx, ky, nsteps):
     return np.linalg.matrix_power(step, nsteps)
 
 
+def coarse_rk3_amplification(p, kx, ky, nsteps):
+    """Non-split RK-3 coarse step of length dt_g: the truncated exponential of
+    dt_g times (upwind advection of order adv_order_c + acoustics + damping
+    with alpha = nu_c dx^2 / dt_g)."""
+    nx, ny = p.nx, p.ny
+    dx, dy = p.lx / nx, p.ly / ny
+    tx, ty = 2 * np.pi * kx / nx, 2 * np.pi * ky / ny
+    a1 = p.nu_c * dx * dx / p.dt_g
+    a2 = p.nu_c * dy * dy / p.dt_g
+    A = fast_symbol(p.c_s, a1, a2, tx, ty, dx, dy)
+    A += adv_symbol(p.adv_order_c, p.U, p.V, tx, ty, dx, dy) * np.eye(3)
+    return np.linalg.matrix_power(rk3_matrix(A, p.dt_g), nsteps)
+
+
 def plane_wave(nx, ny, kx, ky, qhat):
     """Real field Re(qhat_f exp(i(tx*i + ty*j))) on cell indices, shape (3, ny, nx)."""
     i = np.arange(nx)

@@ -178,6 +178,25 @@ def test_coarse_apply(name, spec, order):
         assert rel(got[i], oracle.coarse_prop(p, X[i])) < TOL64
 
 
+def _rk3_coarse(p, order=1):
+    """The RK-3 coarse propagator with a coarse step of two fine steps."""
+    return dataclasses.replace(p, adv_order_c=order, coarse_scheme=1, dt_g=2 * p.dt_f, n_g=p.n_f // 2)
+
+
+@pytest.mark.parametrize("order", [1, 3])
+@pytest.mark.parametrize("name,spec", GRIDS, ids=[g[0] for g in GRIDS])
+def test_coarse_apply_rk3(name, spec, order):
+    """Non-split RK-3 coarse propagator (the instability demonstrations, Sec. 3.1)."""
+    p = _rk3_coarse(_prob(spec), order)
+    X = states(p, p.n_slices, 31)
+    with solver(p) as s:
+        out = torch.empty(p.n_slices * p.d, dtype=torch.float64, device="cuda")
+        P.parareal_coarse_apply(s.h, dev(X), out, p.n_slices)
+        got = host(out).reshape(p.n_slices, p.d)
+    for i in range(p.n_slices):
+        assert rel(got[i], oracle.coarse_prop(p, X[i])) < TOL64
+
+
 def test_coarse_sweep_is_serial_chain():
     p = W.make_problem(64, 32, 8)
     q0 = W.ic_gaussian(64, 32, seed=0).ravel()
@@ -259,6 +278,45 @@ def test_solve_original_parareal_matches_oracle():
     want = oracle.parareal(p, q0, 3, variant="original")
     assert rel(got, want["q"]) < TOL64
     assert np.allclose(np.array(rep.r[:3]), want["r"], rtol=1e-9)
+
+
+@pytest.mark.parametrize("variant", ["kse", "original"])
+def test_solve_rk3_coarse_matches_oracle(variant):
+    """Alg. 2 and Alg. 1 with the RK-3 coarse propagator (serial chain and
+    coarse images through the same coarse tile)."""
+    p = _rk3_coarse(W.make_problem(64, 32, 8))
+    q0 = W.ic_gaussian(64, 32, seed=0).ravel()
+    got, rep = _solve(p, q0, 3, variant=P.PR_KSE if variant == "kse" else P.PR_ORIGINAL)
+    want = oracle.parareal(p, q0, 3, variant=variant)
+    assert rel(got, want["q"]) < TOL64
+    assert np.allclose(np.array(rep.r[:3]), want["r"], rtol=1e-9)
+
+
+def test_instability_demo_matches_oracle():
+    """Sec. 3.1, Fig. 2 (acoustic-advection, c_s = 1): four parallel steps of 6
+    slices, 5 iterations each, RK-3 coarse propagator.  The original Parareal
+    grows by orders of magnitude, KSE-Parareal stays with the sequential fine
+    solution; the GPU reproduces the oracle in both (the original's growth
+    amplifies the rounding-order differences, hence its looser tolerance)."""
+    p = W.demo_instability(40, 1.0)
+    q0 = W.demo_initial_value(40).ravel()
+    M = 4
+    fine = q0
+    for _ in range(M * p.n_slices):
+        fine = oracle.fine_prop(p, fine)
+    pt = dataclasses.replace(p, T=M * p.T)
+    out = {}
+    for variant, tol in (("original", 1e-6), ("kse", 1e-10)):
+        want = oracle.parareal_windows(pt, q0, 5, M, variant=variant)["qT"]
+        with solver(p, K_max=5, n_windows=M, variant=P.PR_KSE if variant == "kse" else P.PR_ORIGINAL) as s:
+            qT = torch.empty(p.d, dtype=torch.float64, device="cuda")
+            P.parareal_solve(s.h, dev(q0), 5, qT=qT)
+            got = host(qT)
+        assert rel(got, want) < tol, variant
+        out[variant] = got
+    assert np.abs(out["original"]).max() > 10 * np.abs(fine).max()
+    assert np.abs(out["kse"]).max() < 1.1 * np.abs(fine).max()
+    assert rel(out["kse"], fine) < 0.1
 
 
 @pytest.mark.parametrize("name,spec", GRIDS[1:], ids=[g[0] for g in GRIDS[1:]])

@@ -131,6 +131,43 @@ def test_coarse_plane_wave_matches_closed_form(order):
         assert _rel(got, want) < 1e-13, (kx, ky, _rel(got, want))
 
 
+@pytest.mark.parametrize("order", [1, 3])
+def test_coarse_rk3_plane_wave_matches_closed_form(order):
+    """The RK-3 coarse propagator of the instability demonstrations (Sec. 3.1)
+    equals R(dt_g A_c)^n on plane waves, A_c the symbol of upwind advection,
+    centred acoustics and damping with alpha = nu_c dx^2 / dt_g."""
+    p = _prob(16, 8, U=0.2, V=-0.1)
+    # a coarse step of 3 fine steps (inside the RK-3 stability region, so the
+    # closed form is not dominated by amplified rounding)
+    p = dataclasses.replace(p, adv_order_c=order, coarse_scheme=1, dt_g=3 * p.dt_f)
+    rng = np.random.default_rng(11)
+    for kx, ky in [(1, 0), (0, 1), (3, 2), (-5, 3), (8, 4)]:
+        qhat = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+        q0 = S.plane_wave(p.nx, p.ny, kx, ky, qhat)
+        got = oracle.coarse_steps(p, q0.ravel(), 2).reshape(3, p.ny, p.nx)
+        want = S.plane_wave(p.nx, p.ny, kx, ky, S.coarse_rk3_amplification(p, kx, ky, 2) @ qhat)
+        assert _rel(got, want) < 1e-13, (kx, ky, _rel(got, want))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("cs", [0.0, 1.0])
+def test_original_parareal_unstable_kse_stable(cs):
+    """Sec. 3.1: with the RK-3 coarse propagator the original Parareal (N_it = 5
+    iterations per parallel step of 6 slices) blows up within a few parallel
+    steps, KSE-Parareal stays with the sequential fine solution."""
+    p = W.demo_instability(40, cs)
+    q0 = W.demo_initial_value(40).ravel()
+    fine, orig, kse = q0.copy(), q0.copy(), q0.copy()
+    for w in range(4):
+        for _ in range(p.n_slices):
+            fine = oracle.fine_prop(p, fine)
+        orig = oracle.parareal(p, orig, 5, variant="original")["q"][-1].copy()
+        kse = oracle.parareal(p, kse, 5, variant="kse")["q"][-1].copy()
+        assert np.abs(kse).max() < 1.1 * np.abs(fine).max()
+    assert np.abs(orig).max() > 10 * np.abs(fine).max()
+    assert _rel(kse, fine) < 0.1
+
+
 def test_coarse_reduces_to_upwind_forward_euler():
     """c_s = 0, nu_c = 0: n_sound substeps with a frozen slow tendency are one
     forward-Euler upwind step of length Delta t (textbook FTBS)."""

@@ -43,6 +43,7 @@ class Problem:
     n_sound: int = 4         # acoustic substeps per coarse step
     adv_order_f: int = 6     # 6th-order centred advective flux in F
     adv_order_c: int = 1     # 1st-order upwind advective flux in G
+    coarse_scheme: int = 0   # G: 0 split forward Euler / forward-backward, 1 RK-3
     lx: float = 1.0
     ly: float = 1.0
 
@@ -204,6 +205,25 @@ def workload_large() -> Workload:
     p = make_problem(512, 256, 64)
     return Workload("mixed_512x256_N64_K5", p, K=5, fine_prec="f32",
                     ics=[("powerlaw16", lambda: ic_power_law(512, 256, seed=0))])
+
+
+def demo_instability(nx: int = 40, c_s: float = 1.0, n_slices: int = 6) -> Problem:
+    """The instability demonstration of Sec. 3.1 (Figs. 1, 2): nx x nx cells on
+    the unit square, U = (1, 1), RK-3 coarse propagator with first-order upwind
+    fluxes and C_c = U dt_g / dx = 0.6, RK-3 fine propagator with sixth-order
+    fluxes and C_f = 0.1 (six fine steps per coarse step), one coarse step per
+    time slice, N_p = 6 slices per parallel step, no divergence damping;
+    c_s = 0 is the pure-advection case.  T is the length of one parallel step."""
+    dt_g = 0.6 / nx
+    return Problem(nx=nx, ny=nx, U=1.0, V=1.0, c_s=c_s, T=n_slices * dt_g, n_slices=n_slices, n_f=6, n_g=1,
+                   dt_f=dt_g / 6, dt_g=dt_g, nu_f=0.0, nu_c=0.0, adv_order_c=1, coarse_scheme=1)
+
+
+def demo_initial_value(nx: int = 40) -> np.ndarray:
+    """Cosine bell in u centred at (0.5, 0.5) (Sec. 3.1); w = p = 0."""
+    q0 = np.zeros((3, nx, nx))
+    q0[0] = ic_cosine_bell(nx, nx)[0]
+    return q0
 
 
 def krylov_bound(n_slices: int, K: int) -> int:
