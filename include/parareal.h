@@ -132,6 +132,14 @@ typedef struct {
                               alpha = nu_c dx^2 / Delta t (n_sound unused) -- the
                               coarse propagator of the paper's instability
                               demonstrations (Sec. 3.1, first-order upwind)      */
+    double omega;          /* solid-body rotation rate (Eq. adVel, gamma): the
+                              advection velocity is (U + omega (y - ly/2),
+                              V - omega (x - lx/2)); in flux form every
+                              x-interface of a row moves with the row's
+                              x-velocity and every y-interface of a column with
+                              the column's y-velocity.  0 (default): constant
+                              (U, V).  The paper's workload: U = V = 0,
+                              omega = pi, c_s = 30                              */
 } pr_options;
 
 typedef struct {

@@ -35,7 +35,7 @@ class _Problem(C.Structure):
                 ("nu_f", C.c_double), ("nu_c", C.c_double), ("n_sound", C.c_int),
                 ("dt_f", C.c_double), ("dt_g", C.c_double), ("n_f", C.c_int), ("n_g", C.c_int),
                 ("n_slices", C.c_int), ("adv_order_f", C.c_int), ("adv_order_c", C.c_int),
-                ("coarse_scheme", C.c_int)]
+                ("coarse_scheme", C.c_int), ("omega", C.c_double)]
 
 
 _P = C.POINTER(C.c_double)
@@ -79,7 +79,7 @@ def _problem(p, **over) -> _Problem:
                     float(g("nu_f")), float(g("nu_c")), int(g("n_sound")),
                     float(g("dt_f")), float(g("dt_g")), int(g("n_f")), int(g("n_g")),
                     int(g("n_slices")), int(g("adv_order_f", 6)), int(g("adv_order_c", 1)),
-                    int(g("coarse_scheme", 0)))
+                    int(g("coarse_scheme", 0)), float(g("omega", 0.0)))
 
 
 def _arr(x, d=None):

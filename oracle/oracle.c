@@ -64,11 +64,25 @@ static double adv_flux(int order, double U, double qm2, double qm1, double q0,
     }
 }
 
+/* Advection velocity (Sec. 3.2, Eq. adVel): the constant (U, V) plus the
+ * solid-body rotation omega (y - ly/2, -(x - lx/2)).  Its x-component depends
+ * on y only and its y-component on x only, so the velocity at every
+ * x-interface of row j is the value at the row's cell centres, and at every
+ * y-interface of column i the value at the column's cell centres. */
+static double u_row(const orc_problem* pb, int j) {
+    const double dy = pb->ly / pb->ny;
+    return pb->U + pb->omega * ((j + 0.5) * dy - 0.5 * pb->ly);
+}
+static double v_col(const orc_problem* pb, int i) {
+    const double dx = pb->lx / pb->nx;
+    return pb->V - pb->omega * ((i + 0.5) * dx - 0.5 * pb->lx);
+}
+
 /* x-interface advective flux of field f at (i+1/2, j) */
 static double fx_adv(const orc_problem* pb, const double* q, int order, int f, int j, int i) {
     const int nx = pb->nx, ny = pb->ny;
     const long ncell = (long)nx * ny;
-    return adv_flux(order, pb->U, AT(q, f, j, i - 2), AT(q, f, j, i - 1), AT(q, f, j, i),
+    return adv_flux(order, u_row(pb, j), AT(q, f, j, i - 2), AT(q, f, j, i - 1), AT(q, f, j, i),
                     AT(q, f, j, i + 1), AT(q, f, j, i + 2), AT(q, f, j, i + 3));
 }
 
@@ -76,7 +90,7 @@ static double fx_adv(const orc_problem* pb, const double* q, int order, int f, i
 static double fy_adv(const orc_problem* pb, const double* q, int order, int f, int j, int i) {
     const int nx = pb->nx, ny = pb->ny;
     const long ncell = (long)nx * ny;
-    return adv_flux(order, pb->V, AT(q, f, j - 2, i), AT(q, f, j - 1, i), AT(q, f, j, i),
+    return adv_flux(order, v_col(pb, i), AT(q, f, j - 2, i), AT(q, f, j - 1, i), AT(q, f, j, i),
                     AT(q, f, j + 1, i), AT(q, f, j + 2, i), AT(q, f, j + 3, i));
 }
 

@@ -29,6 +29,9 @@ typedef struct {
     int adv_order_f;     /* advective flux order of F (1..6)                  */
     int adv_order_c;     /* advective flux order of G (1..6)                  */
     int coarse_scheme;   /* 0: split forward Euler / forward-backward; 1: RK-3 */
+    double omega;        /* solid-body rotation rate: the advection velocity is
+                            (U + omega (y - ly/2), V - omega (x - lx/2)),
+                            Eq. adVel with gamma = omega (0: constant U, V)   */
 } orc_problem;
 
 /* ---- spatial operator and propagators ---- */

@@ -36,7 +36,7 @@ class pr_options(C.Structure):
                 ("fine_prec", C.c_int32), ("variant", C.c_int32), ("corr_prec", C.c_int32),
                 ("r_tol", C.c_double), ("n_windows", C.c_int32), ("images", C.c_int32),
                 ("sm_limit", C.c_int32), ("stream", C.c_void_p), ("proj_prec", C.c_int32),
-                ("coarse_scheme", C.c_int32)]
+                ("coarse_scheme", C.c_int32), ("omega", C.c_double)]
 
 
 class pr_report(C.Structure):
@@ -391,6 +391,7 @@ class Solver:
         opt.setdefault("adv_order_f", p.adv_order_f)
         opt.setdefault("adv_order_c", p.adv_order_c)
         opt.setdefault("coarse_scheme", getattr(p, "coarse_scheme", 0))
+        opt.setdefault("omega", getattr(p, "omega", 0.0))
         opt.setdefault("V", p.V)
         self.p = p
         self.h = parareal_create(p.nx, p.ny, p.U, p.c_s, p.dt_f, p.dt_g, p.n_slices, stream=stream, **opt)

@@ -59,6 +59,18 @@ __device__ __forceinline__ void coarse_tile(const Tin* __restrict__ src, Tout* _
         int n_sound, order;
     } c = {(T)cd.U, (T)cd.V, (T)cd.inv_dx, (T)cd.inv_dy, (T)cd.tau, (T)cd.csx, (T)cd.csy,
            (T)cd.dxx, (T)cd.dxy1, (T)cd.dyy, (T)cd.dxy2, cd.n_sound, cd.order};
+    // advection velocity of the cell at local (lr, lc): constant, or with the
+    // solid-body rotation (Eq. adVel) at the cell's periodic position -- the
+    // x-velocity is that of the row, the y-velocity that of the column
+    auto vel = [&](int lr, int lc, T& Ur, T& Vc) {
+        Ur = c.U;
+        Vc = c.V;
+        if (cd.omega != 0.0) {
+            const int gy = pwrap(ty0 - H + lr, ny), gx = pwrap(tx0 - H + lc, nx);
+            Ur += (T)(cd.omega * ((gy + 0.5) * cd.dy - cd.hly));
+            Vc -= (T)(cd.omega * ((gx + 0.5) * cd.dx - cd.hlx));
+        }
+    };
 
     for (int idx = threadIdx.x; idx < NR; idx += NT) {
         int ly = idx / RX, lx = idx - ly * RX;
@@ -73,14 +85,16 @@ __device__ __forceinline__ void coarse_tile(const Tin* __restrict__ src, Tout* _
     constexpr int MAXC = ((TX + 2 * COARSE_MAXH) * (TY + 2 * COARSE_MAXH) + NT - 1) / NT;
     if (cd.scheme == 1) {
         // L(a) at index i: upwind advection, centred acoustics, grad-div damping
-        auto tend = [&](const T* au, const T* aw, const T* ap, int i, T& Lu, T& Lw, T& Lp) {
+        auto tend = [&](const T* au, const T* aw, const T* ap, int lr, int lc, T& Lu, T& Lw, T& Lp) {
+            const int i = lr * RX + lc;
             const T* fs[3] = {au, aw, ap};
-            T t[3];
+            T t[3], Ur, Vc;
+            vel(lr, lc, Ur, Vc);
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
                 const T* a = fs[f];
-                const T Fe = upwind_flux<T>(c.order, c.U, a, i, 1), Fw = upwind_flux<T>(c.order, c.U, a, i - 1, 1);
-                const T Gn = upwind_flux<T>(c.order, c.V, a, i, RX), Gs = upwind_flux<T>(c.order, c.V, a, i - RX, RX);
+                const T Fe = upwind_flux<T>(c.order, Ur, a, i, 1), Fw = upwind_flux<T>(c.order, Ur, a, i - 1, 1);
+                const T Gn = upwind_flux<T>(c.order, Vc, a, i, RX), Gs = upwind_flux<T>(c.order, Vc, a, i - RX, RX);
                 t[f] = -(Fe - Fw) * c.inv_dx - (Gn - Gs) * c.inv_dy;
             }
             Lu = t[0] - c.csx * (ap[i + 1] - ap[i - 1]) + c.dxx * (au[i + 1] - T(2) * au[i] + au[i - 1]) +
@@ -96,7 +110,7 @@ __device__ __forceinline__ void coarse_tile(const Tin* __restrict__ src, Tout* _
                 const int r = t / W1;
                 const int i = (r + ra) * RX + (t - r * W1) + ra;
                 T Lu, Lw, Lp;
-                tend(u, w, p, i, Lu, Lw, Lp);
+                tend(u, w, p, r + ra, t - r * W1 + ra, Lu, Lw, Lp);
                 su[i] = u[i] + c1 * Lu;
                 sw[i] = w[i] + c1 * Lw;
                 sp[i] = p[i] + c1 * Lp;
@@ -115,7 +129,7 @@ __device__ __forceinline__ void coarse_tile(const Tin* __restrict__ src, Tout* _
                     const int r = t / W2;
                     const int i = (r + sh) * RX + (t - r * W2) + sh;
                     T Lu, Lw, Lp;
-                    tend(su, sw, sp, i, Lu, Lw, Lp);
+                    tend(su, sw, sp, r + sh, t - r * W2 + sh, Lu, Lw, Lp);
                     ru[k] = u[i] + c2 * Lu;
                     rw[k] = w[i] + c2 * Lw;
                     rp[k] = p[i] + c2 * Lp;
@@ -142,7 +156,7 @@ __device__ __forceinline__ void coarse_tile(const Tin* __restrict__ src, Tout* _
             if (gx < nx && gy < ny) {
                 const int i = (r + H) * RX + cx + H;
                 T Lu, Lw, Lp;
-                tend(su, sw, sp, i, Lu, Lw, Lp);
+                tend(su, sw, sp, r + H, cx + H, Lu, Lw, Lp);
                 const long g = (long)gy * nx + gx;
                 dst[g] = (Tout)(u[i] + c3 * Lu);
                 dst[ncell + g] = (Tout)(w[i] + c3 * Lw);
@@ -160,11 +174,13 @@ __device__ __forceinline__ void coarse_tile(const Tin* __restrict__ src, Tout* _
             int i = (r + ra) * RX + (t - r * W1) + ra;
             T* fs[3] = {u, w, p};
             T* ss[3] = {su, sw, sp};
+            T Ur, Vc;
+            vel(r + ra, t - r * W1 + ra, Ur, Vc);
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
                 const T* a = fs[f];
-                T Fe = upwind_flux<T>(c.order, c.U, a, i, 1), Fw = upwind_flux<T>(c.order, c.U, a, i - 1, 1);
-                T Gn = upwind_flux<T>(c.order, c.V, a, i, RX), Gs = upwind_flux<T>(c.order, c.V, a, i - RX, RX);
+                T Fe = upwind_flux<T>(c.order, Ur, a, i, 1), Fw = upwind_flux<T>(c.order, Ur, a, i - 1, 1);
+                T Gn = upwind_flux<T>(c.order, Vc, a, i, RX), Gs = upwind_flux<T>(c.order, Vc, a, i - RX, RX);
                 ss[f][i] = -(Fe - Fw) * c.inv_dx - (Gn - Gs) * c.inv_dy;
             }
         }

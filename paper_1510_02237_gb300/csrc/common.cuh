@@ -29,7 +29,18 @@ struct FineCoef {
     T dyy;    // alpha2 / dy^2
     T dxy2;   // alpha2 / (4 dx dy)
     T c1, c2, c3;   // RK-3 stage lengths dt/3, dt/2, dt
+    // Solid-body rotation (Eq. adVel): the velocity is (U + omega (y - ly/2),
+    // V - omega (x - lx/2)), so row j advects with ax6 + omx yc(j) and column
+    // i with ay6 - omy xc(i), yc(j) = (j + 1/2) dy - ly/2, xc(i) likewise.
+    T omx = T(0);   // omega / (60 dx)
+    T omy = T(0);   // omega / (60 dy)
+    T dx = T(0), dy = T(0), hlx = T(0), hly = T(0);   // cell sizes, lx/2, ly/2
 };
+// Cell-centre coordinates relative to the domain centre (periodic index).
+template <typename T>
+__host__ __device__ __forceinline__ T xcen(const FineCoef<T>& c, int i) { return (T(i) + T(0.5)) * c.dx - c.hlx; }
+template <typename T>
+__host__ __device__ __forceinline__ T ycen(const FineCoef<T>& c, int j) { return (T(j) + T(0.5)) * c.dy - c.hly; }
 
 // Coefficients of one partially split coarse step (Sec. 3.2).
 struct CoarseCoef {
@@ -41,6 +52,8 @@ struct CoarseCoef {
     double dyy, dxy2;   // alpha2 / dy^2, alpha2 / (4 dx dy)
     int n_sound;
     int order;          // 1 or 3 (upwind-biased advective flux)
+    double omega = 0.0;                 // rotation: U + omega yc(j), V - omega xc(i)
+    double dx = 0, dy = 0, hlx = 0, hly = 0;   // cell sizes, lx/2, ly/2
     int scheme = 0;     // 0: partially split forward Euler; 1: non-split RK-3 with
                         //    tau = Delta t and alpha = nu_c dx^2 / Delta t
 };
@@ -221,8 +234,13 @@ long chain_resp_elems(int n_slices);
 // and signed as they enter q^n + c_k L.
 struct FineCoefK {
     double adx[3], ady[3], csx[3], csy[3], dxx[3], dxy1[3], dyy[3], dxy2[3];
+    // rotation (Eq. adVel): row j advects with adx + aomx yc(j), column i with
+    // ady + aomy xc(i); yc, xc cell-centre coordinates about the domain centre
+    double aomx[3], aomy[3];
+    double dx, dy, hlx, hly;
 };
-FineCoefK make_fine_coef_k(double U, double V, double cs, double dx, double dy, double nu, double dt);
+FineCoefK make_fine_coef_k(double U, double V, double cs, double dx, double dy, double nu, double dt,
+                           double omega = 0.0, double lx = 1.0, double ly = 1.0);
 struct FineSweepArgs {
     const double* in;    // n x d, not modified
     double* out;         // n x d

@@ -24,25 +24,39 @@
 namespace pr {
 namespace {
 
+// Advective coefficients (U / 60 dx, V / 60 dy) of the cell at local row lr,
+// column lc of a tile whose local origin is global (gy0, gx0): constant, or
+// varying with the solid-body rotation at the cell's periodic position.
+template <typename T>
+__device__ __forceinline__ void adv_coef(const FineCoef<T>& c, int gy0, int gx0, int lr, int lc, int nx, int ny,
+                                         T& ax, T& ay) {
+    ax = c.ax6;
+    ay = c.ay6;
+    if (c.omx != T(0)) {
+        ax += c.omx * ycen(c, pwrap(gy0 + lr, ny));
+        ay -= c.omy * xcen(c, pwrap(gx0 + lc, nx));
+    }
+}
+
 template <typename T, int RYH>
 __device__ __forceinline__ void fine_tend(const T* __restrict__ u, const T* __restrict__ w,
                                           const T* __restrict__ p, int i, int RX,
-                                          const FineCoef<T>& c, T& Lu, T& Lw, T& Lp) {
+                                          const FineCoef<T>& c, T ax, T ay, T& Lu, T& Lw, T& Lp) {
     const int S1 = RX;
     T du = (u[i + 3] - u[i - 3]) - T(9) * (u[i + 2] - u[i - 2]) + T(45) * (u[i + 1] - u[i - 1]);
     T dw = (w[i + 3] - w[i - 3]) - T(9) * (w[i + 2] - w[i - 2]) + T(45) * (w[i + 1] - w[i - 1]);
     T dp = (p[i + 3] - p[i - 3]) - T(9) * (p[i + 2] - p[i - 2]) + T(45) * (p[i + 1] - p[i - 1]);
-    Lu = -c.ax6 * du;
-    Lw = -c.ax6 * dw;
-    Lp = -c.ax6 * dp;
+    Lu = -ax * du;
+    Lw = -ax * dw;
+    Lp = -ax * dp;
     if (RYH == 3) {
         const int S2 = 2 * RX, S3 = 3 * RX;
         T eu = (u[i + S3] - u[i - S3]) - T(9) * (u[i + S2] - u[i - S2]) + T(45) * (u[i + S1] - u[i - S1]);
         T ew = (w[i + S3] - w[i - S3]) - T(9) * (w[i + S2] - w[i - S2]) + T(45) * (w[i + S1] - w[i - S1]);
         T ep = (p[i + S3] - p[i - S3]) - T(9) * (p[i + S2] - p[i - S2]) + T(45) * (p[i + S1] - p[i - S1]);
-        Lu -= c.ay6 * eu;
-        Lw -= c.ay6 * ew;
-        Lp -= c.ay6 * ep;
+        Lu -= ay * eu;
+        Lw -= ay * ew;
+        Lp -= ay * ep;
     }
     Lu -= c.csx * (p[i + 1] - p[i - 1]);
     Lw -= c.csy * (p[i + S1] - p[i - S1]);
@@ -92,8 +106,9 @@ __global__ void __launch_bounds__(NT) k_fine_step(const Tin* __restrict__ in, lo
         for (int t = threadIdx.x; t < N1; t += NT) {
             int r = t / W1;
             int i = (r + RYH) * RX + (t - r * W1) + 3;
-            T Lu, Lw, Lp;
-            fine_tend<T, RYH>(q, q + NR, q + 2 * NR, i, RX, c, Lu, Lw, Lp);
+            T Lu, Lw, Lp, ax, ay;
+            adv_coef(c, ty0 - HY, tx0 - HX, r + RYH, t - r * W1 + 3, nx, ny, ax, ay);
+            fine_tend<T, RYH>(q, q + NR, q + 2 * NR, i, RX, c, ax, ay, Lu, Lw, Lp);
             s[i] = q[i] + c.c1 * Lu;
             s[NR + i] = q[NR + i] + c.c1 * Lw;
             s[2 * NR + i] = q[2 * NR + i] + c.c1 * Lp;
@@ -111,8 +126,9 @@ __global__ void __launch_bounds__(NT) k_fine_step(const Tin* __restrict__ in, lo
             if (t < N2) {
                 int r = t / W2;
                 int i = (r + 2 * RYH) * RX + (t - r * W2) + 6;
-                T Lu, Lw, Lp;
-                fine_tend<T, RYH>(s, s + NR, s + 2 * NR, i, RX, c, Lu, Lw, Lp);
+                T Lu, Lw, Lp, ax, ay;
+                adv_coef(c, ty0 - HY, tx0 - HX, r + 2 * RYH, t - r * W2 + 6, nx, ny, ax, ay);
+                fine_tend<T, RYH>(s, s + NR, s + 2 * NR, i, RX, c, ax, ay, Lu, Lw, Lp);
                 ru[k] = q[i] + c.c2 * Lu;
                 rw[k] = q[NR + i] + c.c2 * Lw;
                 rp[k] = q[2 * NR + i] + c.c2 * Lp;
@@ -139,8 +155,9 @@ __global__ void __launch_bounds__(NT) k_fine_step(const Tin* __restrict__ in, lo
         int gx = tx0 + cx, gy = ty0 + r;
         if (gx < nx && gy < ny) {
             int i = (r + HY) * RX + cx + HX;
-            T Lu, Lw, Lp;
-            fine_tend<T, RYH>(s, s + NR, s + 2 * NR, i, RX, c, Lu, Lw, Lp);
+            T Lu, Lw, Lp, ax, ay;
+            adv_coef(c, ty0 - HY, tx0 - HX, r + HY, cx + HX, nx, ny, ax, ay);
+            fine_tend<T, RYH>(s, s + NR, s + 2 * NR, i, RX, c, ax, ay, Lu, Lw, Lp);
             long g = (long)gy * nx + gx;
             if (ACC64) {
                 const double c3 = (double)c.c3;

@@ -39,7 +39,10 @@ __device__ __forceinline__ void stage_seg(const double* in, const double* qn,
         Rp2 = (long)wrapp(y + 2, ny) * nx;
         Rp3 = (long)wrapp(y + 3, ny) * nx;
     }
-    const double A = c.adx[k], Ay = c.ady[k], Bx = c.csx[k], By = c.csy[k];
+    // advection coefficients of this row (x) and, below, of each column (y):
+    // constant, or varying with the solid-body rotation (Eq. adVel)
+    const double A = c.adx[k] + c.aomx[k] * ((y + 0.5) * c.dy - c.hly);
+    const double Bx = c.csx[k], By = c.csy[k];
     const double Cx = c.dxx[k], Ex = c.dxy1[k], Cy = c.dyy[k], Ey = c.dxy2[k];
     const double* qu = qn + base;
     const double* qw = qu + ncell;
@@ -50,6 +53,7 @@ __device__ __forceinline__ void stage_seg(const double* in, const double* qn,
     {
         const int x = xs + lane;
         if (x >= nx) return;
+        const double Ay = HV ? c.ady[k] + c.aomy[k] * ((x + 0.5) * c.dx - c.hlx) : 0.0;
         const int xm1 = wrapm(x - 1, nx), xm2 = wrapm(x - 2, nx), xm3 = wrapm(x - 3, nx);
         const int xp1 = wrapp(x + 1, nx), xp2 = wrapp(x + 2, nx), xp3 = wrapp(x + 3, nx);
         // x-advection differences (6th-order centred flux difference)
@@ -138,13 +142,20 @@ int coop_blocks(int max_sms) {
 
 }  // namespace
 
-FineCoefK make_fine_coef_k(double U, double V, double cs, double dx, double dy, double nu, double dt) {
+FineCoefK make_fine_coef_k(double U, double V, double cs, double dx, double dy, double nu, double dt, double omega,
+                           double lx, double ly) {
     const double a1 = nu * dx * dx / dt, a2 = nu * dy * dy / dt;
     const double ck[3] = {dt / 3.0, dt / 2.0, dt};
     FineCoefK c;
+    c.dx = dx;
+    c.dy = dy;
+    c.hlx = 0.5 * lx;
+    c.hly = 0.5 * ly;
     for (int k = 0; k < 3; ++k) {
         c.adx[k] = -ck[k] * (U / (60.0 * dx));
         c.ady[k] = -ck[k] * (V / (60.0 * dy));
+        c.aomx[k] = -ck[k] * (omega / (60.0 * dx));
+        c.aomy[k] = ck[k] * (omega / (60.0 * dy));
         c.csx[k] = -ck[k] * (cs / (2.0 * dx));
         c.csy[k] = -ck[k] * (cs / (2.0 * dy));
         c.dxx[k] = ck[k] * (a1 / (dx * dx));

@@ -159,7 +159,7 @@ static Sizes compute_sizes(int nx, int ny, int N, int K_max, const pr_options& o
 static pr_status fine_apply(pr_solver* h, const double* in, double* out, int n, const SliceMap* first = nullptr,
                             const SliceMap* rest = nullptr) {
     const long d = h->d;
-    const bool hv = h->V != 0.0;
+    const bool hv = h->V != 0.0 || h->opt.omega != 0.0;
     cudaStream_t s = h->stream;
     const int nf = h->n_f;
     const SliceMap m0 = first ? *first : SliceMap(), m1 = rest ? *rest : SliceMap();
@@ -548,9 +548,16 @@ static pr_status fill_report(pr_solver* h, const std::vector<int>& Kw, pr_report
 static bool is_fin(double x) { return std::isfinite(x); }
 
 template <typename T>
-static FineCoef<T> make_fine_coef(double U, double V, double cs, double dx, double dy, double nu, double dt) {
+static FineCoef<T> make_fine_coef(double U, double V, double cs, double dx, double dy, double nu, double dt,
+                                  double omega, double lx, double ly) {
     const double a1 = nu * dx * dx / dt, a2 = nu * dy * dy / dt;
     FineCoef<T> c;
+    c.omx = (T)(omega / (60.0 * dx));
+    c.omy = (T)(omega / (60.0 * dy));
+    c.dx = (T)dx;
+    c.dy = (T)dy;
+    c.hlx = (T)(0.5 * lx);
+    c.hly = (T)(0.5 * ly);
     c.ax6 = (T)(U / (60.0 * dx));
     c.ay6 = (T)(V / (60.0 * dy));
     c.csx = (T)(cs / (2.0 * dx));
@@ -606,6 +613,7 @@ static pr_status validate(const pr_grid* g, double U, double c_s, double dt_f, d
     if (o.adv_order_f != 6) return set_err(h, PR_EINVAL, "adv_order_f must be 6");
     if (o.adv_order_c != 1 && o.adv_order_c != 3) return set_err(h, PR_EINVAL, "adv_order_c must be 1 or 3");
     if (o.n_sound < 1) return set_err(h, PR_EINVAL, "n_sound must be >= 1");
+    if (!is_fin(o.omega)) return set_err(h, PR_EINVAL, "omega must be finite");
     if (o.coarse_scheme != PR_COARSE_SPLIT_FE && o.coarse_scheme != PR_COARSE_RK3)
         return set_err(h, PR_EINVAL, "coarse_scheme must be PR_COARSE_SPLIT_FE or PR_COARSE_RK3");
     if (o.coarse_scheme == PR_COARSE_SPLIT_FE && (o.adv_order_c == 1 ? 1 : 2) + 2 * o.n_sound - 1 > 12)
@@ -674,9 +682,9 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     h->cap = sz.cap;
     h->partial_elems = sz.partial;
     const double dx = h->lx / h->nx, dy = h->ly / h->ny;
-    h->fc64 = make_fine_coef<double>(U, o.V, c_s, dx, dy, o.nu_f, dt_f);
-    h->fc32 = make_fine_coef<float>(U, o.V, c_s, dx, dy, o.nu_f, dt_f);
-    h->fck = make_fine_coef_k(U, o.V, c_s, dx, dy, o.nu_f, dt_f);
+    h->fc64 = make_fine_coef<double>(U, o.V, c_s, dx, dy, o.nu_f, dt_f, o.omega, h->lx, h->ly);
+    h->fc32 = make_fine_coef<float>(U, o.V, c_s, dx, dy, o.nu_f, dt_f, o.omega, h->lx, h->ly);
+    h->fck = make_fine_coef_k(U, o.V, c_s, dx, dy, o.nu_f, dt_f, o.omega, h->lx, h->ly);
     const double tau = o.coarse_scheme == PR_COARSE_RK3 ? dt_g : dt_g / o.n_sound;
     const double a1 = o.nu_c * dx * dx / tau, a2 = o.nu_c * dy * dy / tau;
     h->cc.U = U;
@@ -693,6 +701,11 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     h->cc.n_sound = o.n_sound;
     h->cc.order = o.adv_order_c;
     h->cc.scheme = o.coarse_scheme == PR_COARSE_RK3 ? 1 : 0;
+    h->cc.omega = o.omega;
+    h->cc.dx = dx;
+    h->cc.dy = dy;
+    h->cc.hlx = 0.5 * h->lx;
+    h->cc.hly = 0.5 * h->ly;
 
     const long d = h->d;
     const int N = h->N;
@@ -991,7 +1004,7 @@ pr_status parareal_autotune(pr_solver* h, pr_tuning* out) {
     pr_tuning t;
     std::memset(&t, 0, sizeof(t));
     t.choice = -1;
-    const bool hv = h->V != 0.0;
+    const bool hv = h->V != 0.0 || h->opt.omega != 0.0;
     const int prec = h->opt.fine_prec;
     int kind = 0;
     if (prec == PR_FP32X)

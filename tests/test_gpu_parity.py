@@ -319,6 +319,63 @@ def test_instability_demo_matches_oracle():
     assert rel(out["kse"], fine) < 0.1
 
 
+# ------------------------------------------------------------------ solid-body rotation
+
+ROT_GRIDS = [("64x32", dict(nx=64, ny=32, N=4)), ("40x40", dict(nx=40, ny=40, N=3)),
+             ("96x20", dict(nx=96, ny=20, N=3)), ("128x64", dict(nx=128, ny=64, N=2))]
+
+
+def _rot(spec):
+    """Rotation U = (pi/4) (y - 1/2, -(x - 1/2)) on top of a small constant U."""
+    return dataclasses.replace(_prob(spec), U=0.05, omega=0.25 * np.pi)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32x"])
+@pytest.mark.parametrize("name,spec", ROT_GRIDS, ids=[g[0] for g in ROT_GRIDS])
+def test_fine_sweep_rotation(name, spec, prec):
+    """Variable advection velocity (Eq. adVel): the x-velocity of each row and
+    the y-velocity of each column, at the cell's periodic position."""
+    p = _rot(spec)
+    X = states(p, p.n_slices, 70)
+    fp, tol = {"fp64": (P.PR_FP64, TOL64), "fp32": (P.PR_FP32, TOL32), "fp32x": (P.PR_FP32X, 2e-6)}[prec]
+    with solver(p, fine_prec=fp) as s:
+        out = torch.empty(p.n_slices * p.d, dtype=torch.float64, device="cuda")
+        P.parareal_fine_sweep(s.h, dev(X), out, p.n_slices)
+        got = host(out).reshape(p.n_slices, p.d)
+    for i in range(p.n_slices):
+        assert rel(got[i], oracle.fine_prop(p, X[i])) < tol
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("name,spec", ROT_GRIDS, ids=[g[0] for g in ROT_GRIDS])
+def test_coarse_apply_rotation(name, spec, scheme):
+    p = _rot(spec)
+    if scheme == 1:
+        p = _rk3_coarse(p)
+    X = states(p, p.n_slices, 71)
+    with solver(p) as s:
+        out = torch.empty(p.n_slices * p.d, dtype=torch.float64, device="cuda")
+        P.parareal_coarse_apply(s.h, dev(X), out, p.n_slices)
+        got = host(out).reshape(p.n_slices, p.d)
+    for i in range(p.n_slices):
+        assert rel(got[i], oracle.coarse_prop(p, X[i])) < TOL64
+
+
+def test_paper_rotation_workload_matches_oracle():
+    """The paper's own workload (solid-body rotation, c_s = 30, Sec. 3.2) for
+    three parallel steps of N_p = 6 slices at C_c = 4 with 2 iterations each."""
+    p = W.paper_rotation(40, 4.0, 6)
+    q0 = W.paper_rotation_initial_value(40).ravel()
+    M, K = 3, 2
+    want = oracle.parareal_windows(dataclasses.replace(p, T=M * p.T), q0, K, M)
+    with solver(p, K_max=K, n_windows=M) as s:
+        qT = torch.empty(p.d, dtype=torch.float64, device="cuda")
+        rep = P.parareal_solve(s.h, dev(q0), K, qT=qT)
+        got = host(qT)
+    assert rel(got, want["qT"]) < 1e-10
+    assert list(rep.rank[:M * K]) == [int(x) for w in want["windows"] for x in w["rank"]]
+
+
 @pytest.mark.parametrize("name,spec", GRIDS[1:], ids=[g[0] for g in GRIDS[1:]])
 def test_solve_edge_grids(name, spec):
     p = _prob(spec)

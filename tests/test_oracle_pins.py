@@ -168,6 +168,50 @@ def test_original_parareal_unstable_kse_stable(cs):
     assert _rel(kse, fine) < 0.1
 
 
+@pytest.mark.parametrize("which", ["fine", "coarse_split", "coarse_rk3"])
+def test_rotation_conserves_field_sums(which):
+    """With the solid-body rotation (Eq. adVel) the flux form still conserves
+    the sum of every field exactly (periodic domain)."""
+    p = dataclasses.replace(_prob(24, 16, U=0.0), omega=math.pi, coarse_scheme=1 if which == "coarse_rk3" else 0)
+    q0 = W.ic_random(24, 16, seed=3).ravel()
+    f = oracle.fine_prop if which == "fine" else oracle.coarse_prop
+    q1 = f(p, q0).reshape(3, -1)
+    # exact up to rounding: relative to the sum of magnitudes (the coarse RK-3
+    # step at this Delta t amplifies the grid-scale modes)
+    np.testing.assert_array_less(np.abs(q1.sum(axis=1) - q0.reshape(3, -1).sum(axis=1)),
+                                 1e-14 * np.abs(q1).sum(axis=1) + 1e-300)
+
+
+def test_rotation_advects_a_bump_around_the_centre():
+    """Pure advection (c_s = 0, no damping) by the solid-body rotation
+    U = omega (y - 1/2, -(x - 1/2)): every field is carried rigidly around the
+    centre, q(x, t) = q0(R(-omega t)(x - c) + c).  The sixth-order fluxes with
+    RK-3 at fixed CFL converge to it at third order in the step (the time
+    discretisation dominates)."""
+    def bump(nx, ang):
+        x = (np.arange(nx) + 0.5) / nx
+        X, Y = np.meshgrid(x, x)
+        ca, sa = math.cos(ang), math.sin(ang)
+        xr = ca * (X - 0.5) - sa * (Y - 0.5) + 0.5      # pre-image under a rotation by -ang
+        yr = sa * (X - 0.5) + ca * (Y - 0.5) + 0.5
+        return np.exp(-((xr - 0.5) ** 2 + (yr - 0.65) ** 2) / (2 * 0.05 ** 2))
+
+    errs = []
+    T = 0.25
+    for nx in (48, 96):
+        n = int(round(T / (0.4 / nx / 1.0)))
+        dt = T / n
+        p = W.Problem(nx=nx, ny=nx, U=0.0, V=0.0, c_s=0.0, T=T, n_slices=1, n_f=n, n_g=1, dt_f=dt, dt_g=T,
+                      nu_f=0.0, nu_c=0.0, omega=math.pi)
+        q0 = np.stack([bump(nx, 0.0)] * 3).ravel()
+        got = oracle.fine_prop(p, q0).reshape(3, nx, nx)
+        # the rotation (y - 1/2, -(x - 1/2)) turns clockwise: q(x, T) is q0 at
+        # the point turned back counter-clockwise by omega T
+        want = bump(nx, math.pi * T)
+        errs.append(max(_rel(got[f], want) for f in range(3)))
+    assert errs[0] < 2e-2 and errs[1] < errs[0] / 6.0, errs
+
+
 def test_coarse_reduces_to_upwind_forward_euler():
     """c_s = 0, nu_c = 0: n_sound substeps with a frozen slow tendency are one
     forward-Euler upwind step of length Delta t (textbook FTBS)."""

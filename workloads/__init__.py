@@ -44,6 +44,8 @@ class Problem:
     adv_order_f: int = 6     # 6th-order centred advective flux in F
     adv_order_c: int = 1     # 1st-order upwind advective flux in G
     coarse_scheme: int = 0   # G: 0 split forward Euler / forward-backward, 1 RK-3
+    omega: float = 0.0       # solid-body rotation rate (Eq. adVel): velocity
+                             # (U + omega (y - ly/2), V - omega (x - lx/2))
     lx: float = 1.0
     ly: float = 1.0
 
@@ -223,6 +225,30 @@ def demo_initial_value(nx: int = 40) -> np.ndarray:
     """Cosine bell in u centred at (0.5, 0.5) (Sec. 3.1); w = p = 0."""
     q0 = np.zeros((3, nx, nx))
     q0[0] = ic_cosine_bell(nx, nx)[0]
+    return q0
+
+
+def paper_rotation(nx: int = 40, C_c: float = 2.0, N_p: int = 6, C_f: float = 0.2) -> Problem:
+    """The paper's acoustic-advection workload (Sec. 3.2, Eq. adVel; Tables
+    1-2, Figs. 3-10): solid-body rotation U = pi (y - 1/2, -(x - 1/2)) on the
+    unit square with nx x nx cells, c_s = 30, fine RK-3 with sixth-order
+    advective fluxes at C_f = c_s dt / dx = 0.2 (Eq. cflNumbers) and
+    nu_f = 0.005, coarse partially split forward Euler with first-order upwind
+    fluxes at C_c = c_s Delta t / dx, N_sound = 4 and nu_c = 0.1.  A time slice
+    is one coarse step ("coarse interval") and a parallel step has N_p of them;
+    T is the length of one parallel step, so [0, 2] takes 2 / T of them."""
+    dx = 1.0 / nx
+    dt_g = C_c * dx / 30.0
+    n_f = int(round(C_c / C_f))
+    return Problem(nx=nx, ny=nx, U=0.0, V=0.0, c_s=30.0, T=N_p * dt_g, n_slices=N_p, n_f=n_f, n_g=1,
+                   dt_f=dt_g / n_f, dt_g=dt_g, nu_f=0.005, nu_c=0.1, n_sound=4, adv_order_f=6, adv_order_c=1,
+                   omega=math.pi)
+
+
+def paper_rotation_initial_value(nx: int = 40) -> np.ndarray:
+    """Cosine bell in u centred at (0.5, 0.65) (Sec. 3.2); w = p = 0."""
+    q0 = np.zeros((3, nx, nx))
+    q0[0] = ic_cosine_bell(nx, nx, 0.5, 0.65)[0]
     return q0
 
 
