@@ -399,6 +399,60 @@ def fine_sweep_fp32(P, torch, stream):
                          "algorithmic_bytes_per_cell_sweep": 504, "bytes_per_sweep": bytes_}}
 
 
+# Errors epsilon (Eq. errorDef) at T = 2 that the paper reports for its own
+# workload (Tables 1 and 2: 40 x 40 cells, C_f = 0.2, N_sound = 4,
+# nu_f = 0.005, nu_c = 0.1), per (C_c, N_p) for N_it = 1, 2, ...
+PAPER_TABLE_EPS = {(2.0, 4): [1.3e-1, 2.8e-2], (2.0, 6): [1.4e-1, 5.0e-2, 1.1e-2],
+                   (2.0, 8): [1.6e-1, 6.7e-2, 1.7e-2, 3.2e-3], (4.0, 4): [1.8e-1, 1.7e-1],
+                   (4.0, 6): [1.9e-1, 8.6e-2, 3.7e-2], (4.0, 8): [2.0e-1, 9.3e-2, 3.4e-2, 3.0e-2]}
+
+
+def paper_tables(P, torch, stream):
+    """The paper's own workload (solid-body rotation, c_s = 30, 40 x 40 cells,
+    T = 2 = one revolution, cosine bell in u at (0.5, 0.65)) run as in its
+    Tables 1-2: N_p slices of one coarse step per parallel step, 2 / (N_p dt_g)
+    parallel steps, N_it iterations each, plain FP64.  epsilon against the
+    sequential fine solution (F applied 12000 times), with the GPU time of
+    each whole run; the paper's epsilon (and its CPU times, Tables 1-2) are
+    context, not a target: its readings of the unstated details may differ."""
+    q0 = W.paper_rotation_initial_value(40).ravel()
+    u0 = torch.from_numpy(q0).cuda()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # sequential fine reference: 12000 RK-3 steps of dt = 0.2 dx / c_s
+    pr = W.paper_rotation(40, 2.0, 4)
+    s = P.Solver(pr, stream=stream, K_max=1)
+    nsl = int(round(2.0 / pr.dt_g))
+    q = u0.clone()
+    nxt = torch.empty_like(q)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(nsl):
+        P.parareal_fine_sweep(s.h, q, nxt, 1)
+        q, nxt = nxt, q
+    e1.record(stream)
+    torch.cuda.synchronize()
+    qseq = q.clone()
+    out = {"workload": "solid-body rotation pi (y - 1/2, -(x - 1/2)), c_s = 30, 40 x 40, T = 2, FP64",
+           "sequential_fine_ms": e0.elapsed_time(e1), "fine_steps": nsl * pr.n_f, "runs": []}
+    s.close()
+    for (C_c, N_p), eps_paper in PAPER_TABLE_EPS.items():
+        p = W.paper_rotation(40, C_c, N_p)
+        M = int(round(2.0 / p.T))
+        for K, ep in enumerate(eps_paper, start=1):
+            sv = P.Solver(p, stream=stream, K_max=K, n_windows=M)
+            qT = torch.empty_like(u0)
+            P.parareal_solve(sv.h, u0, K, qT=qT, report=False)     # warm-up
+            torch.cuda.synchronize()
+            e0.record(stream)
+            P.parareal_solve(sv.h, u0, K, qT=qT, report=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out["runs"].append({"C_c": C_c, "N_p": N_p, "N_it": K, "parallel_steps": M,
+                                "eps": rel_l2(qT, qseq), "eps_paper": ep, "ms": e0.elapsed_time(e1)})
+            sv.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -557,6 +611,7 @@ def run_ours(args):
     line = None
     if rank == 0:
         fine32 = fine_sweep_fp32(P, torch, stream)
+        tables = paper_tables(P, torch, stream)
         precision = precision_workload(P, torch, stream)
         batching = batching_workload(P, torch)
         serving = serving_workload(P, torch) if not args.no_serving else None
@@ -604,6 +659,7 @@ def run_ours(args):
             "clocks": clk,
             "fp64_fma_tflops": peak,
             "fine_sweep_fp32": fine32,
+            "paper_workload": tables,
             "mixed": mixed,
             "fp64_tensor_core_projection": fp64_tc,
             "precision_workload": precision,
