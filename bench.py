@@ -67,10 +67,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream sweep")
-    ap.add_argument("--case", choices=["fine", "fine32", "solve", "solve_mixed"], default=None,
+    ap.add_argument("--case", choices=["fine", "fine32", "fine32x", "solve", "solve_mixed"], default=None,
                     help="small isolated case for profiler captures: 'fine' = three fine sweeps over all "
                          "32 slices of the 256x128 workload; 'fine32' = three FP32 fine sweeps over the 64 "
-                         "slices of the 512x256 workload; 'solve' = two solves of the 256x128 workload's "
+                         "slices of the 512x256 workload ('fine32x': FP32 stages on an FP64 state); 'solve' = "
+                         "two solves of the 256x128 workload's "
                          "first IC; 'solve_mixed' = the same in mixed precision with the tensor-core projections")
     return ap.parse_args()
 
@@ -680,16 +681,16 @@ def run_case(args):
 
     import paper_1510_02237_gb300 as P
     torch.cuda.set_device(0)
-    wl = W.workload_large() if args.case == "fine32" else W.workload_medium()
+    wl = W.workload_large() if args.case in ("fine32", "fine32x") else W.workload_medium()
     p = wl.problem
     opt = {}
-    if args.case == "fine32":
-        opt = {"fine_prec": P.PR_FP32}
+    if args.case in ("fine32", "fine32x"):
+        opt = {"fine_prec": P.PR_FP32 if args.case == "fine32" else P.PR_FP32X}
     if args.case == "solve_mixed":
         opt = {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32, "proj_prec": P.PR_PROJ_SPLIT_BF16}
     s = P.Solver(p, stream=torch.cuda.current_stream(), K_max=wl.K, krylov_cap=wl.krylov_cap, **opt)
     q0 = torch.from_numpy(wl.ics[0][1]().ravel()).cuda()
-    if args.case in ("fine", "fine32"):
+    if args.case in ("fine", "fine32", "fine32x"):
         X = q0.repeat(p.n_slices)
         Y = torch.empty_like(X)
         for _ in range(3):
