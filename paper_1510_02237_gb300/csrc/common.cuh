@@ -135,13 +135,10 @@ long tswork_elems(long nrows, int ccap, int mmax);
 cudaError_t gemm_tn(const double* A, long lda, const int* c0_dev, const int* c1_dev, int ccap,
                     const double* X, long ldx, int m, long nrows, double* C, int ldc, const TsWork& w,
                     cudaStream_t s);
-// Y[:, j] = B[:, j] + sgn * sum_c A[:, c0 + c] C[c, j]   (B may alias Y; B == NULL means 0).
-// yoff_dev (optional): B and Y start that many columns in; mcap_dev
-// (optional): only columns j < *mcap_dev are written.
+// Y[:, j] = B[:, j] + sgn * sum_c A[:, c0 + c] C[c, j]   (B may alias Y; B == NULL means 0)
 cudaError_t gemm_nn(const double* A, long lda, const int* c0_dev, const int* c1_dev, int ccap,
                     const double* C, int ldc, const double* B, long ldb, double* Y, long ldy, int m,
-                    long nrows, double sgn, cudaStream_t s, const int* yoff_dev = nullptr,
-                    const int* mcap_dev = nullptr);
+                    long nrows, double sgn, cudaStream_t s);
 // out[j] = sum_rows X[row, j]^2
 cudaError_t colnorm2(const double* X, long ldx, int m, long nrows, double* out, const TsWork& w,
                      cudaStream_t s);
@@ -184,13 +181,9 @@ struct GridBar {
 // max_blocks > 0 caps the cooperative grid (one CTA per SM).
 // compact: the kept columns (normalised) are written in order to the first
 // slots of wv (and wz) instead of Q[:, *r_dev] (and D); *r_dev still counts them.
-// T (optional, 64 x 64, only with wz == NULL): kept column c = W T[:, c] with
-// W the m columns as they entered (rows i < m of the first *r_dev - *r_old_dev
-// columns are written).
 cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2, const int* r_old_dev,
                         int* r_dev, int cap, double eta, double* Q, double* D, int* kept, double* ratio,
-                        const TsWork& w, GridBar* gb, cudaStream_t s, int max_blocks = 0, bool compact = false,
-                        double* T = nullptr);
+                        const TsWork& w, GridBar* gb, cudaStream_t s, int max_blocks = 0, bool compact = false);
 // Re-orthonormalisation of n = *nk_dev <= m <= 64 nearly orthonormal columns
 // W = Q1 - Q C2 (ld d; Q1 orthonormal, C2 = Q^T Q1 with *r2_dev rows, ld ldc2)
 // by Cholesky QR: G = W^T W = I - C2^T C2 = R^T R (G, Rinv: 64 x 64 scratch),
@@ -199,15 +192,6 @@ cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2,
 cudaError_t cholqr_block(double* W, double* Z, long d, int m, const int* nk_dev, const double* C2, int ldc2,
                          const int* r2_dev, double* G, double* Rinv, double* Q, double* D, const int* off_dev,
                          cudaStream_t s);
-// D-images of the n = *nk_dev columns a block appended at Q[:, *r_old_dev]
-// (block Gram-Schmidt: first pass coefficients C1, in-block transform T,
-// second pass coefficients C2, Cholesky factor inverse Rinv):
-// D[:, r_old + k] = (Z S - D[:, :r_old] E)_k with S = T Rinv and
-// E = (C1 T + C2) Rinv (S: 64 x 64 scratch; E: lde >= cap rows x 64 scratch).
-// Z: the block's m original images F(V) - G(V), ld d.
-cudaError_t image_update(const double* Z, long d, int m, const double* T, const double* Rinv, const double* C1,
-                         int ldc1, const double* C2, int ldc2, const int* r_old_dev, const int* nk_dev, double* S,
-                         double* E, int lde, int cap, double* D, cudaStream_t s);
 cudaError_t sub_int(const int* a, const int* b, int* out, cudaStream_t s);
 
 

@@ -116,27 +116,17 @@ __global__ void k_reduce_chunks(const double* __restrict__ partial, int nchunk, 
     out[c + (long)j * ldo] = s;
 }
 
-// Y[:, j] = B[:, j] + sgn * sum_{c < ncols} A[:, c0 + c] C[c, j] for
-// j < min(m, *mcap_dev); B and Y start *yoff_dev columns in when yoff_dev is
-// given (A may be the same array, on columns before them)
+// Y[:, j] = B[:, j] + sgn * sum_{c < ncols} A[:, c0 + c] C[c, j]
 __global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ A, long lda,
                                                  const int* c0_dev, const int* c1_dev,
                                                  const double* __restrict__ C, int ldc,
                                                  const double* B, long ldb, double* Y, long ldy,
-                                                 int m, long nrows, double sgn, const int* yoff_dev,
-                                                 const int* mcap_dev) {
+                                                 int m, long nrows, double sgn) {
     extern __shared__ double Cs[];   // ncap x NN_JB
     const int ncols = cols_avail(c0_dev, c1_dev);
     const int c0 = c0_dev ? *c0_dev : 0;
-    if (mcap_dev) m = min(m, *mcap_dev);
-    if (yoff_dev) {
-        const long yo = *yoff_dev;
-        if (B) B += yo * ldb;
-        Y += yo * ldy;
-    }
     const int jb = blockIdx.y * NN_JB;
     const int nj = min(NN_JB, m - jb);
-    if (nj <= 0) return;   // the same for every thread of the CTA
     for (int e = threadIdx.x; e < ncols * NN_JB; e += 256) {
         int c = e / NN_JB, jj = e - c * NN_JB;
         Cs[e] = (jj < nj) ? sgn * C[c + (long)(jb + jj) * ldc] : 0.0;
@@ -305,18 +295,13 @@ __global__ void k_fill_int(int* p, int v, int n) {
 // CTA sums the CTA partials in the same order, so all CTAs hold identical
 // coefficients and take identical decisions.  Partial buffers alternate
 // between two halves, so one barrier per reduction suffices.
-// With Tm (and no wz) CTA 0 records the block's transform instead of
-// repeating every column operation on the images: kept column c equals
-// W t_c, W the m columns as they entered, t_c = (e_j - T_{<c} s) / res with s
-// the coefficients of both passes summed, written to Tm[i + 64 c] (i < m).
 constexpr int IB_NT = 512;
 __global__ void __launch_bounds__(IB_NT) k_intra_block(double* wv, double* wz, long d, int m,
                                                       const double* __restrict__ a2, const int* r_old_dev,
                                                       int* r_dev, int cap, double eta, double* Qb, double* Db,
                                                       int* kept, double* ratio, double* __restrict__ part,
-                                                      int pstride, GridBar* gb, bool compact, double* Tm) {
+                                                      int pstride, GridBar* gb, bool compact) {
     __shared__ double cs[64];
-    __shared__ double csum[64];   // coefficients of both passes, summed (CTA 0, with Tm)
     __shared__ double sred[IB_NT / 32][17];
     __shared__ double s_res2;   // pstride >= 64: slot 63 carries ||v||^2 partials (nn <= 63)
     const unsigned nb = gridDim.x;
@@ -345,8 +330,6 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* wv, double* wz, l
         // Without earlier columns only ||v||^2 is reduced.
         const int npass = nn > 0 ? 2 : 1;
         double res2 = 0.0;
-        const bool track = Tm != nullptr && b == 0;
-        if (track && (int)threadIdx.x < 64) csum[threadIdx.x] = 0.0;   // read after the barriers below
         for (int pass = 0; pass < npass; ++pass) {
             double* P = buf ? P1 : P0;
             const bool last = pass == npass - 1;
@@ -438,7 +421,6 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* wv, double* wz, l
             }
             buf ^= 1;
             __syncthreads();
-            if (track && (int)threadIdx.x < nn) csum[threadIdx.x] += cs[threadIdx.x];
             if (last) {
                 double c2 = 0.0;
                 for (int l = 0; l < nn; ++l) c2 += cs[l] * cs[l];
@@ -468,13 +450,6 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* wv, double* wz, l
             for (long row = r0 + threadIdx.x; row < r1; row += IB_NT) {
                 Q[row + (long)rl * d] = v[row] * inv;
                 if (z) D[row + (long)rl * d] = z[row] * inv;
-            }
-            if (track && (int)threadIdx.x < m) {
-                // column nn of T; row i of T stays with thread i across columns
-                const int i = threadIdx.x;
-                double t = i == j ? 1.0 : 0.0;
-                for (int l = 0; l < nn; ++l) t -= Tm[i + 64 * l] * csum[l];
-                Tm[i + 64 * nn] = t * inv;
             }
             ++rl;
         }
@@ -531,50 +506,6 @@ __global__ void k_cholqr(const double* __restrict__ G, int ldg, const int* n_dev
     }
 }
 
-// Coefficients of the D-images of a block appended by block Gram-Schmidt
-// (two projection passes around an in-block pass, then Cholesky QR).  With
-// W = V - Q C1 (first pass), the kept in-block columns W T, C2 = Q^T (W T)
-// (second pass) and R^-1 of the Cholesky QR, the appended columns are
-//   Q_new = (W T - Q C2) R^-1 = V S - Q E,  S = T R^-1,  E = (C1 T + C2) R^-1,
-// so by linearity their images are Z S - D E with Z = F(V) - G(V) and
-// D = F(Q) - G(Q).  T, R^-1, S: 64 x 64, column-major (ld 64); n = *n_dev
-// kept columns of m; E: r = *r_dev rows (ld lde), n columns.  The last CTA
-// writes all of S (zero outside m x n); the others take 64 rows of E each.
-__global__ void __launch_bounds__(256) k_image_coef(const double* __restrict__ T, const double* __restrict__ Rinv,
-                                                    const double* __restrict__ C1, int ldc1,
-                                                    const double* __restrict__ C2, int ldc2, const int* r_dev,
-                                                    const int* n_dev, int m, double* __restrict__ S,
-                                                    double* __restrict__ E, int lde) {
-    __shared__ double F[64][65];   // rows of C1 T + C2
-    const int n = min(*n_dev, 64), r = *r_dev;
-    const int li = threadIdx.x & 63, kq = threadIdx.x >> 6;
-    if (blockIdx.x == gridDim.x - 1) {
-        for (int k = kq; k < 64; k += 4) {
-            double t = 0.0;
-            if (li < m && k < n)
-                for (int kk = 0; kk <= k; ++kk) t += T[li + 64 * kk] * Rinv[kk + 64 * k];
-            S[li + 64 * k] = t;
-        }
-        return;
-    }
-    const int l = blockIdx.x * 64 + li;
-    for (int k = kq; k < n; k += 4) {
-        double f = 0.0;
-        if (l < r) {
-            f = C2[l + (long)ldc2 * k];
-            for (int i = 0; i < m; ++i) f += C1[l + (long)ldc1 * i] * T[i + 64 * k];
-        }
-        F[li][k] = f;
-    }
-    __syncthreads();
-    if (l >= r) return;
-    for (int k = kq; k < n; k += 4) {
-        double e = 0.0;
-        for (int kk = 0; kk <= k; ++kk) e += F[li][kk] * Rinv[kk + 64 * k];
-        E[l + (long)lde * k] = e;
-    }
-}
-
 // Gram matrix of the reprojected block W = Q1 - Q C (Q1: in-block
 // orthonormal columns, Q: the orthonormal basis, C = Q^T Q1 with *r_dev rows):
 // W^T W = Q1^T Q1 - C^T C = I - C^T C up to rounding, because Q1^T Q1 = I and
@@ -597,7 +528,7 @@ __global__ void k_gram_c(const double* __restrict__ C, int ldc, const int* r_dev
 // out[:, *off_dev + j] = sum_{i <= j} W[:, i] Rinv[i, j] for j < *n_dev
 // (Rinv upper, ld 64): one row per thread, 16 output columns at a time.
 __global__ void k_apply_upper(const double* __restrict__ W, long d, const double* __restrict__ Rinv,
-                              const int* n_dev, double* out, const int* off_dev, int full_rows) {
+                              const int* n_dev, double* out, const int* off_dev) {
     __shared__ double Rs[64 * 64];
     const int n = min(*n_dev, 64);
     for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) Rs[idx] = Rinv[idx];
@@ -608,7 +539,7 @@ __global__ void k_apply_upper(const double* __restrict__ W, long d, const double
             double acc[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) acc[k] = 0.0;
-            const int iend = full_rows > 0 ? full_rows : min(n, j0 + 16);
+            const int iend = min(n, j0 + 16);
             for (int i = 0; i < iend; ++i) {
                 const double w = W[row + (long)i * d];
 #pragma unroll
@@ -670,14 +601,13 @@ cudaError_t gemm_tn(const double* A, long lda, const int* c0_dev, const int* c1_
 
 cudaError_t gemm_nn(const double* A, long lda, const int* c0_dev, const int* c1_dev, int ccap,
                     const double* C, int ldc, const double* B, long ldb, double* Y, long ldy, int m,
-                    long nrows, double sgn, cudaStream_t s, const int* yoff_dev, const int* mcap_dev) {
+                    long nrows, double sgn, cudaStream_t s) {
     if (m <= 0 || ccap <= 0) return cudaSuccess;
     const size_t smem = sizeof(double) * (size_t)ccap * NN_JB;
     cudaError_t e = cudaFuncSetAttribute(k_gemm_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(cdiv(nrows, 256), cdiv(m, NN_JB));
-    k_gemm_nn<<<grid, 256, smem, s>>>(A, lda, c0_dev, c1_dev, C, ldc, B, ldb, Y, ldy, m, nrows, sgn, yoff_dev,
-                                      mcap_dev);
+    k_gemm_nn<<<grid, 256, smem, s>>>(A, lda, c0_dev, c1_dev, C, ldc, B, ldb, Y, ldy, m, nrows, sgn);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -768,8 +698,7 @@ int intra_block_grid() {
 
 cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2, const int* r_old_dev,
                         int* r_dev, int cap, double eta, double* Q, double* D, int* kept, double* ratio,
-                        const TsWork& w, GridBar* gb, cudaStream_t s, int max_blocks, bool compact, double* T) {
-    if (T && wz) return cudaErrorInvalidValue;
+                        const TsWork& w, GridBar* gb, cudaStream_t s, int max_blocks, bool compact) {
     if (compact) {
         Q = wv;
         D = wz;
@@ -785,7 +714,7 @@ cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2,
     if (e != cudaSuccess) return e;
     double* part = w.partial;
     void* args[] = {&wv, &wz, &d, &m, (void*)&a2, (void*)&r_old_dev, &r_dev, &cap, &eta, &Q, &D, &kept, &ratio,
-                    &part, &pstride, &gb, &compact, &T};
+                    &part, &pstride, &gb, &compact};
     e = cudaLaunchCooperativeKernel((const void*)k_intra_block, dim3(nb), dim3(IB_NT), args, 0, s);
     count_launches(1);
     return e;
@@ -822,31 +751,13 @@ cudaError_t cholqr_block(double* W, double* Z, long d, int m, const int* nk_dev,
     count_launches(1);
     int nb = cdiv(d, 256);
     if (nb > 4 * 152) nb = 4 * 152;
-    k_apply_upper<<<nb, 256, 0, s>>>(W, d, Rinv, nk_dev, Q, off_dev, 0);
+    k_apply_upper<<<nb, 256, 0, s>>>(W, d, Rinv, nk_dev, Q, off_dev);
     count_launches(2);
     if (Z) {
-        k_apply_upper<<<nb, 256, 0, s>>>(Z, d, Rinv, nk_dev, D, off_dev, 0);
+        k_apply_upper<<<nb, 256, 0, s>>>(Z, d, Rinv, nk_dev, D, off_dev);
         count_launches(1);
     }
     return cudaGetLastError();
-}
-
-cudaError_t image_update(const double* Z, long d, int m, const double* T, const double* Rinv, const double* C1,
-                         int ldc1, const double* C2, int ldc2, const int* r_old_dev, const int* nk_dev, double* S,
-                         double* E, int lde, int cap, double* D, cudaStream_t s) {
-    if (m < 1 || m > 64 || lde < cap) return cudaErrorInvalidValue;
-    k_image_coef<<<cdiv(cap, 64) + 1, 256, 0, s>>>(T, Rinv, C1, ldc1, C2, ldc2, r_old_dev, nk_dev, m, S, E, lde);
-    count_launches(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    int nb = cdiv(d, 256);
-    if (nb > 4 * 152) nb = 4 * 152;
-    k_apply_upper<<<nb, 256, 0, s>>>(Z, d, S, nk_dev, D, r_old_dev, m);   // D[:, r_old + k] = (Z S)_k
-    count_launches(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // D[:, r_old + k] -= D[:, :r_old] E[:, k]
-    return gemm_nn(D, d, nullptr, r_old_dev, cap, E, lde, D, d, D, d, m, d, -1.0, s, r_old_dev, nk_dev);
 }
 
 cudaError_t sub_int(const int* a, const int* b, int* out, cudaStream_t s) {

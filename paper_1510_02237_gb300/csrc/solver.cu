@@ -68,9 +68,6 @@ struct pr_solver {
     int* r_it = nullptr;
     int *r = nullptr, *r_old = nullptr, *kept = nullptr, *ranks = nullptr, *zero = nullptr, *nk = nullptr;
     double *G = nullptr, *Rinv = nullptr;   // 64 x 64 Gram matrix and R^-1 of the block Cholesky QR
-    double *Tm = nullptr, *Sm = nullptr;    // 64 x 64 in-block transform and image coefficients
-    double *C1 = nullptr, *Eim = nullptr;   // first-pass coefficients and image coefficients, ldi x 64
-    int ldi = 0;                            // cap rounded up to 32 (>= the ld of either coefficient array)
     int* kept_hist = nullptr;                       // PR_MAX_ITERS x N kept flags
     int M_hist[PR_MAX_ITERS] = {};
     GridBar* gbar = nullptr;
@@ -119,8 +116,6 @@ struct Sizes {
     size_t bytes;
 };
 
-static int ldi_of(int cap) { return (cap + 31) / 32 * 32; }
-
 static Sizes compute_sizes(int nx, int ny, int N, int K_max, const pr_options& o) {
     Sizes s{};
     s.d = 3L * nx * ny;
@@ -148,8 +143,7 @@ static Sizes compute_sizes(int nx, int ny, int N, int K_max, const pr_options& o
         b += sizeof(float) * ((size_t)s.cap * s.d * 2 + (size_t)s.d * 3);   // Q32, D32, delta, ping-pong
     b += dd * (size_t)chain_resp_elems(N);
     b += dd * ((size_t)s.cap * N + s.cap);     // C, cvec
-    b += dd * 4 * 64 * 64;                     // G, Rinv, in-block transform, image coefficients S
-    b += dd * 2 * (size_t)ldi_of(s.cap) * 64;  // first-pass and image coefficients C1, E
+    b += dd * 2 * 64 * 64;                     // G, Rinv
     b += dd * (size_t)s.partial;
     b += dd * (size_t)(N + (N + 1) + PR_MAX_ITERS + 1);
     b += sizeof(int) * (size_t)(3 + N + PR_MAX_ITERS);
@@ -247,24 +241,24 @@ static pr_status coarse_apply(pr_solver* h, const double* in, double* out, int n
 
 // ------------------------------------------------------------------ subspace update
 
-// One classical Gram-Schmidt pass of the mm columns v against the basis
-// columns [0, *r_old): C = Q^T v, v <- v - Q C, on the FP64 units or with the
-// tensor-core projections (C left in pass_coef()).
-static pr_status block_pass(pr_solver* h, double* v, int mm) {
+// One classical Gram-Schmidt pass of the mm columns v (and their D-images z)
+// against the basis columns [0, *r_old): C = Q^T v, v <- v - Q C, z <- z - D C,
+// on the FP64 units or with the tensor-core projections.
+static pr_status block_pass(pr_solver* h, double* v, double* z, int mm) {
     const long d = h->d;
     const int cap = h->cap;
     cudaStream_t s = h->stream;
     TsWork w{h->partial, h->partial_elems};
     if (h->use_sg) {
         CKC(sg_cgs_pass(&h->sg, v, d, mm, h->r_old, s));
+        if (z) CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->sg.C, h->sg.cap_pad, z, d, z, d, mm, d, -1.0, s));
     } else {
         CKC(gemm_tn(h->Q, d, nullptr, h->r_old, cap, v, d, mm, d, h->C, cap, w, s));
         CKC(gemm_nn(h->Q, d, nullptr, h->r_old, cap, h->C, cap, v, d, v, d, mm, d, -1.0, s));
+        if (z) CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->C, cap, z, d, z, d, mm, d, -1.0, s));
     }
     return PR_OK;
 }
-static double* pass_coef(pr_solver* h) { return h->use_sg ? h->sg.C : h->C; }
-static int pass_ldc(pr_solver* h) { return h->use_sg ? h->sg.cap_pad : h->cap; }
 
 // Append the m columns V (with fine images FV and coarse images GV) to the
 // subspace, in order (Eq. subspaceUpdate), by block Gram-Schmidt with
@@ -282,10 +276,8 @@ static int pass_ldc(pr_solver* h) { return h->use_sg ? h->sg.cap_pad : h->cap; }
 // block's own columns are nearly dependent (in-block ratios of 1e-6 leave
 // components of size eps / 1e-6 along the old basis, and they compound from
 // block to block); the drop decisions and ratios come from step 2.  The
-// D-images Z = FV - GV receive the same linear map, so D = F(Q) - G(Q): the
-// appended columns are V S - Q E with S, E composed from the two passes'
-// coefficients, the in-block transform and R^-1, and their images
-// Z S - D E take one product with D instead of two.
+// D-images Z = FV - GV receive exactly the same transformations, so
+// D = F(Q) - G(Q).
 template <typename Mark, typename SubMark>
 static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, const double* GV, int m, Mark mark,
                               SubMark sub_mark, double* ratio = nullptr) {
@@ -303,20 +295,15 @@ static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, c
         double* v = h->wv + (long)j0 * d;
         double* z = images ? h->wz + (long)j0 * d : nullptr;
         CKC(cudaMemcpyAsync(h->r_old, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
-        CKS(block_pass(h, v, mm));
-        if (z) CKC(cudaMemcpyAsync(h->C1, pass_coef(h), sizeof(double) * pass_ldc(h) * mm, cudaMemcpyDeviceToDevice, s));
+        CKS(block_pass(h, v, z, mm));
         CKC(sub_mark(0));
-        CKC(intra_block(v, nullptr, d, mm, h->anorm2 + j0, h->r_old, h->r, cap, h->opt.drop_tol, h->Q, nullptr,
-                        h->kept + j0, ratio ? ratio + j0 : nullptr, w, h->gbar, s, h->opt.sm_limit, true,
-                        z ? h->Tm : nullptr));
+        CKC(intra_block(v, z, d, mm, h->anorm2 + j0, h->r_old, h->r, cap, h->opt.drop_tol, h->Q, h->D,
+                        h->kept + j0, ratio ? ratio + j0 : nullptr, w, h->gbar, s, h->opt.sm_limit, true));
         CKC(sub_mark(1));
         CKC(sub_int(h->r, h->r_old, h->nk, s));
-        CKS(block_pass(h, v, mm));
-        CKC(cholqr_block(v, nullptr, d, mm, h->nk, pass_coef(h), pass_ldc(h), h->r_old, h->G, h->Rinv, h->Q,
-                         nullptr, h->r_old, s));
-        if (z)
-            CKC(image_update(z, d, mm, h->Tm, h->Rinv, h->C1, pass_ldc(h), pass_coef(h), pass_ldc(h), h->r_old,
-                             h->nk, h->Sm, h->Eim, h->ldi, cap, h->D, s));
+        CKS(block_pass(h, v, z, mm));
+        CKC(cholqr_block(v, z, d, mm, h->nk, h->use_sg ? h->sg.C : h->C, h->use_sg ? h->sg.cap_pad : cap, h->r_old,
+                         h->G, h->Rinv, h->Q, h->D, h->r_old, s));
         if (h->use_sg) CKC(sg_append(&h->sg, h->Q, d, h->r_old, h->r, 0, mm, s));
     }
     CKC(mark());
@@ -760,11 +747,6 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     chk(cudaMalloc((void**)&h->r, sizeof(int) * 8));
     chk(dalloc(&h->G, 64 * 64));
     chk(dalloc(&h->Rinv, 64 * 64));
-    chk(dalloc(&h->Tm, 64 * 64));
-    chk(dalloc(&h->Sm, 64 * 64));
-    h->ldi = ldi_of(h->cap);
-    chk(dalloc(&h->C1, (size_t)h->ldi * 64));
-    chk(dalloc(&h->Eim, (size_t)h->ldi * 64));
     if (o.corr_prec == PR_FP32) {
         chk(cudaMalloc((void**)&h->Q32, sizeof(float) * (size_t)h->cap * d));
         chk(cudaMalloc((void**)&h->D32, sizeof(float) * (size_t)h->cap * d));
@@ -806,7 +788,7 @@ pr_status parareal_destroy(pr_solver* h) {
     if (h->stream || h->q) cudaStreamSynchronize(h->stream);
     double* ds[] = {h->q, h->qt, h->gv, h->kold, h->Q, h->D, h->wv, h->wz, h->fb0, h->fb1, h->fb2, h->cb0, h->cb1,
                     h->gtmp, h->C, h->cvec, h->partial, h->anorm2, h->res2, h->rhist, h->nres2,
-                    h->gbuf, h->resp, h->ratios, h->G, h->Rinv, h->Tm, h->Sm, h->C1, h->Eim};
+                    h->gbuf, h->resp, h->ratios, h->G, h->Rinv};
     for (double* p : ds) if (p) cudaFree(p);
     float* fs[] = {h->Q32, h->D32, h->dlt, h->gbuf32};
     for (float* p : fs) if (p) cudaFree(p);
