@@ -40,8 +40,9 @@ __device__ __forceinline__ void stage_seg(const double* in, const double* qn,
         Rp3 = (long)wrapp(y + 3, ny) * nx;
     }
     // advection coefficients of this row (x) and, below, of each column (y):
-    // constant, or varying with the solid-body rotation (Eq. adVel)
-    const double A = c.adx[k] + c.aomx[k] * ((y + 0.5) * c.dy - c.hly);
+    // constant, or varying with the solid-body rotation (Eq. adVel), which
+    // the host runs as HV (a rotation has both components)
+    const double A = HV ? c.adx[k] + c.aomx[k] * ((y + 0.5) * c.dy - c.hly) : c.adx[k];
     const double Bx = c.csx[k], By = c.csy[k];
     const double Cx = c.dxx[k], Ex = c.dxy1[k], Cy = c.dyy[k], Ey = c.dxy2[k];
     const double* qu = qn + base;
