@@ -108,3 +108,27 @@ def test_mixed_and_direct_images_accuracy(ref, ic):
     budget = {0: 1e-5, 1: 10 * R["eps"], 2: 1e-4}[ic]
     assert abs(e64 - emx) <= budget, (e64, emx)
     assert list(rep64.rank[:wl.K]) == list(repmx.rank[:wl.K]) == R["rank"]
+
+
+def test_large_workload_images_by_linearity():
+    """512x256, N = 64, K = 5 in FP64: the first iteration's 64 columns are
+    nearly dependent (kept ratios down to 1e-6, condition number ~1e15 after
+    column scaling), the hardest case for images by linearity.  Any FP64
+    evaluation of Eq. Genhance that keeps each step at the scale of a
+    normalised column stays finite there and takes the same drop decisions as
+    direct images (ratios far from the 1e-10 threshold); an evaluation that
+    multiplies the images by the block's inverse triangular factor (entries
+    up to 1/sigma_min) loses them entirely and the solve breaks down."""
+    wl = W.workload_large()
+    p = wl.problem
+    q0 = wl.ics[0][1]().ravel()
+    glin, qs, rlin = _solve(p, q0, wl.K, 0)
+    gdir, _, rdir = _solve(p, q0, wl.K, 0, images=P.PR_IMAGES_DIRECT)
+    assert np.all(np.isfinite(glin)) and np.all(np.isfinite(gdir))
+    ranks = list(rlin.rank[:wl.K])
+    assert ranks == list(rdir.rank[:wl.K])
+    # every iteration adds most of its N - k new columns
+    assert all(ranks[k] - (ranks[k - 1] if k else 0) > (p.n_slices - k) // 2 for k in range(wl.K)), ranks
+    elin = np.linalg.norm(glin - qs) / np.linalg.norm(qs)
+    edir = np.linalg.norm(gdir - qs) / np.linalg.norm(qs)
+    assert elin < 1.0 and edir < 1.0 and 0.25 < elin / edir < 4.0, (elin, edir)
