@@ -142,16 +142,6 @@ cudaError_t gemm_nn(const double* A, long lda, const int* c0_dev, const int* c1_
 // out[j] = sum_rows X[row, j]^2
 cudaError_t colnorm2(const double* X, long ldx, int m, long nrows, double* out, const TsWork& w,
                      cudaStream_t s);
-// Append v / ||v|| and z / ||v|| as column *r of Q and D if ||v|| > eta ||a|| and *r < cap;
-// *kept receives the decision and *r is incremented when kept.
-cudaError_t krylov_append(const double* v, const double* z, const double* res2, const double* a2,
-                          double eta, int cap, int* r, double* Q, double* D, long ld, long nrows,
-                          int* kept, cudaStream_t s);
-// Serial correction of Alg. 2 for one slice: q <- qt + ((g + D c) - kold),
-// *res2_slot = ||q_new - q_old||^2.
-cudaError_t chain_update(const double* qt, const double* g, const double* D, long ldd, const int* c1_dev,
-                         int ccap, const double* c, const double* kold, double* q, long nrows,
-                         double* res2_slot, const TsWork& w, cudaStream_t s);
 // dst <- src with *res2 = ||src - dst_old||^2 (and delta = src - dst_old in FP32 if non-NULL)
 cudaError_t copy_resid(const double* src, double* dst, long n, double* res2, const TsWork& w, cudaStream_t s,
                        float* delta = nullptr);

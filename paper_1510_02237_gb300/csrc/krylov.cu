@@ -177,51 +177,6 @@ __global__ void __launch_bounds__(256) k_colnorm2_partial(const double* __restri
     if (threadIdx.x == 0) partial[(long)blockIdx.x * m + j] = s;
 }
 
-__global__ void k_krylov_append(const double* __restrict__ v, const double* __restrict__ z,
-                                const double* res2, const double* a2, double eta, int cap, const int* r,
-                                double* Q, double* D, long ld, long nrows, int* kept) {
-    const double res = sqrt(*res2), an = sqrt(*a2);
-    const int slot = *r;
-    const bool keep = (res > eta * an) && (an > 0.0) && (slot < cap);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && kept) *kept = keep ? 1 : 0;
-    if (!keep) return;
-    const double inv = 1.0 / res;
-    for (long row = (long)blockIdx.x * blockDim.x + threadIdx.x; row < nrows; row += (long)gridDim.x * blockDim.x) {
-        Q[row + (long)slot * ld] = v[row] * inv;
-        D[row + (long)slot * ld] = z[row] * inv;
-    }
-}
-
-__global__ void k_bump_rank(int* r, const int* kept) {
-    if (*kept) *r += 1;
-}
-
-// q_new = qt + ((g + D c) - kold); partial res2 over the chunk
-__global__ void __launch_bounds__(256) k_chain_update(const double* __restrict__ qt, const double* __restrict__ g,
-                                                      const double* __restrict__ D, long ldd,
-                                                      const int* c1_dev, const double* __restrict__ cvec,
-                                                      const double* __restrict__ kold, double* q, long nrows,
-                                                      double* __restrict__ partial) {
-    extern __shared__ double cs[];
-    __shared__ double red[8];
-    const int ncols = c1_dev ? *c1_dev : 0;
-    for (int e = threadIdx.x; e < ncols; e += 256) cs[e] = cvec[e];
-    __syncthreads();
-    const long row = (long)blockIdx.x * 256 + threadIdx.x;
-    double s = 0.0;
-    if (row < nrows) {
-        double acc = 0.0;
-        for (int c = 0; c < ncols; ++c) acc += D[row + (long)c * ldd] * cs[c];
-        double knew = g[row] + acc;
-        double y = qt[row] + (knew - kold[row]);
-        double e = y - q[row];
-        s = e * e;
-        q[row] = y;
-    }
-    s = block_sum256(s, red);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
 __global__ void k_copy_resid(const double* __restrict__ src, double* __restrict__ dst, long n,
                              double* __restrict__ partial, float* __restrict__ delta) {
     __shared__ double red[8];
@@ -621,37 +576,6 @@ cudaError_t colnorm2(const double* X, long ldx, int m, long nrows, double* out, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_chunks<<<cdiv(m, 256), 256, 0, s>>>(w.partial, nchunk, m, nullptr, nullptr, m, out, 1);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t krylov_append(const double* v, const double* z, const double* res2, const double* a2,
-                          double eta, int cap, int* r, double* Q, double* D, long ld, long nrows,
-                          int* kept, cudaStream_t s) {
-    int nb = cdiv(nrows, 256);
-    if (nb > 1024) nb = 1024;
-    k_krylov_append<<<nb, 256, 0, s>>>(v, z, res2, a2, eta, cap, r, Q, D, ld, nrows, kept);
-    count_launches(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_bump_rank<<<1, 1, 0, s>>>(r, kept);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t chain_update(const double* qt, const double* g, const double* D, long ldd, const int* c1_dev,
-                         int ccap, const double* c, const double* kold, double* q, long nrows,
-                         double* res2_slot, const TsWork& w, cudaStream_t s) {
-    const int nb = cdiv(nrows, 256);
-    if (nb > w.elems) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(double) * (size_t)(ccap > 0 ? ccap : 1);
-    cudaError_t e = cudaFuncSetAttribute(k_chain_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_chain_update<<<nb, 256, smem, s>>>(qt, g, D, ldd, c1_dev, c, kold, q, nrows, w.partial);
-    count_launches(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_sum_partials<<<1, 256, 0, s>>>(w.partial, nb, res2_slot);
     count_launches(1);
     return cudaGetLastError();
 }
