@@ -52,6 +52,26 @@ __device__ __forceinline__ double warp_sum_strided(const double* base, unsigned 
     return s;
 }
 
+// Warp sums of 16 per-lane values by recursive halving: at each step a lane
+// keeps half of its values and adds its partner's copy of them (16 shuffles
+// instead of 80).  Returns kof; afterwards acc[0] of every even lane holds the
+// warp sum of value kof, summed in a fixed order.
+__device__ __forceinline__ int warp_sum16(double (&acc)[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double send = up ? acc[i] : acc[i + h];
+            const double keep = up ? acc[i + h] : acc[i];
+            acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
 // Dot product of a and b over rows [r0, r1) by one warp: lane j takes rows
 // r0 + j + 32 t in order, four rows per iteration with their loads issued
 // together, then a fixed xor-shuffle tree.  Deterministic.

@@ -327,24 +327,10 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* wv, double* wz, l
                     for (int k = 0; k < 16; ++k)
                         if (k < lc) acc[k] += q[(long)k * d] * x;
                 }
-                // warp sums of the 16 accumulators by recursive halving: at
-                // each step a lane keeps half of its values and adds its
-                // partner's copy of them (16 shuffles instead of 80); lane L
+                // warp sums of the 16 accumulators (recursive halving); lane L
                 // ends with the sum for column kof(L), in a fixed order
-#pragma unroll
-                for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
-                    const bool up = (lane & o) != 0;
-#pragma unroll
-                    for (int i = 0; i < h; ++i) {
-                        const double send = up ? acc[i] : acc[i + h];
-                        const double keep = up ? acc[i + h] : acc[i];
-                        acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-                    }
-                }
-                acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
                 {
-                    const int kof = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
-                                    ((lane >> 1) & 1);
+                    const int kof = warp_sum16(acc);
                     if ((lane & 1) == 0 && kof < lc) sred[wid][kof] = acc[0];
                 }
                 if (norm) {
