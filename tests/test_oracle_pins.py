@@ -8,7 +8,9 @@ property K = N, and a dense brute-force restatement of Alg. 2 on tiny grids.
 from __future__ import annotations
 
 import dataclasses
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -471,3 +473,28 @@ def test_kse_error_decreases_on_small_workload():
         errs.append(oracle.rel_error(rr["q"][-1], qs[-1]))
     assert all(errs[i + 1] < errs[i] for i in range(4)), errs
     assert list(r["rank"]) == [8, 15, 21, 26]
+
+
+@pytest.mark.slow
+def test_paper_table1_errors_np4():
+    """The paper's printed errors (Table 1, C_c = 2.0, N_p = 4; fixture
+    tests/golden/paper_tables_1_2.json): the oracle's KSE-Parareal on the
+    solid-body rotation workload over one revolution, against its own
+    sequential fine solution.  The paper leaves details unstated (the forward-
+    backward order, the damping discretisation), so the pin is the magnitude:
+    within a factor 2 of the printed value for N_it = 1 and 2, and the second
+    iteration reducing the error by more than half."""
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_tables_1_2.json")) as fh:
+        paper = json.load(fh)["eps"]["C_c=2.0"]["N_p=4"]
+    q0 = W.paper_rotation_initial_value(40).ravel()
+    p = W.paper_rotation(40, 2.0, 4)
+    n_coarse = int(round(2.0 / p.dt_g))                # 600 coarse intervals over [0, 2]
+    qs = oracle.fine_steps(p, q0, n_coarse * p.n_f)    # 12000 fine steps
+    M = int(round(2.0 / p.T))                          # 150 parallel steps
+    eps = []
+    for K in (1, 2):
+        res = oracle.parareal_windows(dataclasses.replace(p, T=M * p.T), q0, K, M)
+        eps.append(float(np.linalg.norm(res["qT"] - qs) / np.linalg.norm(qs)))
+    for e, ep in zip(eps, paper):
+        assert 0.5 * ep < e < 2.0 * ep, (eps, paper)
+    assert eps[1] < 0.5 * eps[0], eps
