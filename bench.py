@@ -39,11 +39,13 @@ import workloads as W  # noqa: E402
 METRIC = "Parareal solves/s & fine cell-steps/s vs plain FP64 on GB300; p50/p99 latency"
 
 # Floating-point operations of one fine cell-step (three RK-3 stages) as the
-# fine kernel evaluates them with V = 0, counting an FMA as 2: per stage and
-# cell the 6th-order x-advection difference of three fields (3 x 7), its
-# scaling (3), the acoustic terms (12), the divergence damping (18) and the
-# stage update (6) = 60.
-FINE_FLOPS_PER_CELL_STEP = 180.0
+# fine kernel evaluates them with V = 0 and the stage length folded into the
+# coefficients, counting an FMA as 2: per stage and cell the 6th-order
+# x-advection differences of three fields (3 x 7), the four acoustic
+# differences (4), the four damping differences (12) and eight coefficient
+# FMAs for the acoustic and damping terms (16), plus the three FMAs that add
+# the scaled advection to q^n (6) = 59.
+FINE_FLOPS_PER_CELL_STEP = 177.0
 # One fine cell-step reads and writes the three FP64 fields once (M1 model).
 FINE_BYTES_PER_CELL_STEP_F64 = 48.0
 
