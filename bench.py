@@ -200,6 +200,24 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 
+def max_over_ranks(x, device):
+    """x maximised over all ranks of the default process group (the slowest
+    rank's time); x itself without a group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units processed by all ranks (each rank the same number) per second of
+    the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def serial_fine_gpu(P, s, u0, n):
     """q_seq(T): n fine sweeps of one slice each through the C ABI (FP64 handle)."""
     import torch
@@ -511,16 +529,11 @@ def run_ours(args):
         dist.barrier()
     launches = P.parareal_kernel_launches() - launches0
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), "cuda")
     tm = P.parareal_timing_read(s.h)
     lat = sorted(a.elapsed_time(b) for row in lat_events for a, b in row)
 
-    solves = args.steps * nsol * world
-    value = solves / (ms / 1e3)
+    value = whole_job_rate(args.steps * nsol, world, ms / 1e3)
     fine_cell_steps = tm["fine_cell_steps"] * world
     n = tm["n_solves"]
 
@@ -535,12 +548,8 @@ def run_ours(args):
     for _ in range(args.steps):
         for j in range(nsol):
             P.parareal_solve_host(s.h, hin[j], K, hout[j], report=False)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": solves / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": nsol * p.d * 8,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
+    e2e = {"value": whole_job_rate(args.steps * nsol, world, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": nsol * p.d * 8,
            "d2h_bytes_per_step": nsol * p.d * 8}
 
     # ---- other arithmetic on the same workload, timed the same way:
@@ -567,15 +576,11 @@ def run_ours(args):
             step_v()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms_v = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms_v], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_v = float(t.item())
+        ms_v = max_over_ranks(e0.elapsed_time(e1), "cuda")
         tv = P.parareal_timing_read(sv.h)
         ph = {k: tv[k] / tv["n_solves"] for k in ("ms_init", "ms_fine", "ms_coarse", "ms_krylov", "ms_gs_block",
                                                    "ms_gs_intra", "ms_kold", "ms_chain")}
-        return sv, outs_v, solves / (ms_v / 1e3), ph
+        return sv, outs_v, whole_job_rate(args.steps * nsol, world, ms_v / 1e3), ph
 
     def per_ic_errors(outs_v):
         per_ic = {}
