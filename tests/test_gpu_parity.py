@@ -178,6 +178,33 @@ def test_coarse_apply(name, spec, order):
         assert rel(got[i], oracle.coarse_prop(p, X[i])) < TOL64
 
 
+# Batches large enough for the 64 x 32 coarse tiles (at least two per SM on
+# a 152-SM GPU), with full and ragged tiles
+BIG_COARSE = [
+    ("256x128_N32", dict(nx=256, ny=128, N=32)),
+    ("ragged200x72_N64", dict(nx=200, ny=72, N=64)),
+]
+
+
+@pytest.mark.parametrize("variant", ["split_o1", "split_o3", "rk3", "rotation"])
+@pytest.mark.parametrize("name,spec", BIG_COARSE, ids=[g[0] for g in BIG_COARSE])
+def test_coarse_apply_large_batch(name, spec, variant):
+    p = _prob(spec)
+    if variant == "split_o3":
+        p = dataclasses.replace(p, adv_order_c=3)
+    elif variant == "rk3":
+        p = _rk3_coarse(p)
+    elif variant == "rotation":
+        p = _rot(spec)
+    X = states(p, p.n_slices, 90)
+    with solver(p) as s:
+        out = torch.empty(p.n_slices * p.d, dtype=torch.float64, device="cuda")
+        P.parareal_coarse_apply(s.h, dev(X), out, p.n_slices)
+        got = host(out).reshape(p.n_slices, p.d)
+    for i in range(p.n_slices):
+        assert rel(got[i], oracle.coarse_prop(p, X[i])) < TOL64
+
+
 def _rk3_coarse(p, order=1):
     """The RK-3 coarse propagator with a coarse step of two fine steps."""
     return dataclasses.replace(p, adv_order_c=order, coarse_scheme=1, dt_g=2 * p.dt_f, n_g=p.n_f // 2)
