@@ -321,11 +321,18 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* wv, double* wz, l
                 double nv = 0.0;
                 for (long row = r0 + threadIdx.x; row < r1; row += IB_NT) {
                     const double x = v[row];
-                    nv += x * x;
+                    if (norm) nv += x * x;
                     const double* q = Q + (long)(c0 + l0) * d + row;
+                    // groups of 4 columns behind uniform branches: at most 3
+                    // predicated-off products per row instead of 16 - lc
 #pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        if (k < lc) acc[k] += q[(long)k * d] * x;
+                    for (int g = 0; g < 16; g += 4) {
+                        if (g < lc) {
+#pragma unroll
+                            for (int k = g; k < g + 4; ++k)
+                                if (k < lc) acc[k] += q[(long)k * d] * x;
+                        }
+                    }
                 }
                 // warp sums of the 16 accumulators (recursive halving); lane L
                 // ends with the sum for column kof(L), in a fixed order
