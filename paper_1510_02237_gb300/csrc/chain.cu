@@ -64,15 +64,20 @@ __device__ __forceinline__ float warp_dot_f32(const float* __restrict__ a, const
     return t;
 }
 
-// DELTA = false: the literal correction in FP64,
-//   q_{i+1} = q~_{i+1} + ((G(q_i) + D Q^T q_i) - K_old_i).
-// DELTA = true: the same correction through linearity in FP32,
+// DELTA = false: the literal correction in FP64 (T = double),
+//   q_{i+1} = q~_{i+1} + ((G(q_i) + D Q^T q_i) - K_old_i)
+// (K_old = G(q_i^k) for the original Parareal, or no basis and no K_old: the
+// serial coarse sweep).
+// DELTA = true: the KSE correction through the linearity of K,
 //   q_{i+1} = q~_{i+1} + (G(delta_i) + D Q^T delta_i),  delta_i = q_i^{k+1} - q_i^k,
-// with FP32 copies of Q and D; delta_{i+1} is produced by the update itself.
-// Its rounding scales with ||delta||, not ||q||; the sum into q stays FP64.
-template <bool DELTA>
+// in T = float (FP32 copies of Q and D) or T = double; delta_{i+1} is
+// produced by the update itself.  Its rounding scales with ||delta||, not
+// ||q||, a converged slice (delta = 0) gets exactly no correction, and the
+// sum into q stays FP64.
+template <bool DELTA, typename T>
 __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
-    using T = typename std::conditional<DELTA, float, double>::type;
+    static_assert(DELTA || std::is_same<T, double>::value, "the literal form is FP64");
+    constexpr bool F32 = std::is_same<T, float>::value;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
     __shared__ double red[CH_NT / 32];
@@ -85,22 +90,24 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
     const int ncols = A.r_dev ? *A.r_dev : 0;
     const int ntx = (A.nx + CH_TX - 1) / CH_TX, nty = (A.ny + CH_TY - 1) / CH_TY, ntiles = ntx * nty;
     const int cpb = (ncols + (int)nb - 1) / (int)nb;
-    const T* Qm = DELTA ? reinterpret_cast<const T*>(A.Q32) : reinterpret_cast<const T*>(A.Q);
-    const T* Dm = DELTA ? reinterpret_cast<const T*>(A.D32) : reinterpret_cast<const T*>(A.D);
-    T* gbuf = DELTA ? reinterpret_cast<T*>(A.gbuf32) : reinterpret_cast<T*>(A.gbuf);
+    const T* Qm = F32 ? reinterpret_cast<const T*>(A.Q32) : reinterpret_cast<const T*>(A.Q);
+    const T* Dm = F32 ? reinterpret_cast<const T*>(A.D32) : reinterpret_cast<const T*>(A.D);
+    T* gbuf = F32 ? reinterpret_cast<T*>(A.gbuf32) : reinterpret_cast<T*>(A.gbuf);
+    T* dlt = F32 ? reinterpret_cast<T*>(A.dlt) : reinterpret_cast<T*>(A.dlt64);
 
     for (int i = A.i_begin; i < A.i_end; ++i) {
         const double* qi = A.q + (long)i * d;
         double* qn = A.q + (long)(i + 1) * d;
-        const T* x = DELTA ? reinterpret_cast<const T*>(A.dlt) : reinterpret_cast<const T*>(qi);
+        const T* x = DELTA ? dlt : reinterpret_cast<const T*>(qi);
         // phase A: this CTA's partial dot products c_l = sum_rows Q[row, l] x[row]
         for (int l = wid; l < ncols; l += nw) {
             double s;
-            if (DELTA) {
+            if (F32) {
                 s = (double)warp_dot_f32(reinterpret_cast<const float*>(Qm) + (long)l * d,
                                          reinterpret_cast<const float*>(x), r0, r1, (d & 3) == 0);
             } else {
-                s = warp_dot(reinterpret_cast<const double*>(Qm) + (long)l * d, qi, r0, r1);
+                s = warp_dot(reinterpret_cast<const double*>(Qm) + (long)l * d, reinterpret_cast<const double*>(x),
+                             r0, r1);
             }
             if (lane == 0) A.part[(long)b * A.ccap + l] = s;
         }
@@ -132,7 +139,7 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
         const double* qt = A.qt ? A.qt + (long)i * d : nullptr;
         const double* ko = A.kold ? A.kold + (long)i * d : nullptr;
         double s = 0.0;
-        if (DELTA && (d & 3) == 0) {
+        if (F32 && (d & 3) == 0) {
             // four consecutive rows per thread: 16-byte loads of D32, eight
             // basis columns in flight
             const float* gq = reinterpret_cast<const float*>(gin);
@@ -157,7 +164,7 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
                     const double e = y - qn[rw];
                     s += e * e;
                     qn[rw] = y;
-                    A.dlt[rw] = (float)e;
+                    dlt[rw] = (T)e;
                 }
             }
         } else
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
             const double e = y - qn[row];
             s += e * e;
             qn[row] = y;
-            if (DELTA) A.dlt[row] = (float)e;
+            if (DELTA) dlt[row] = (T)e;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -197,8 +204,8 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
     }
 }
 
-size_t chain_smem_bytes(int H, int ccap, bool delta) {
-    const size_t el = delta ? sizeof(float) : sizeof(double);
+size_t chain_smem_bytes(int H, int ccap, bool f32) {
+    const size_t el = f32 ? sizeof(float) : sizeof(double);
     size_t a = el * coarse_tile_smem_elems<CH_TX, CH_TY>(H);
     size_t c = el * (size_t)(ccap > 0 ? ccap : 1);
     return a > c ? a : c;
@@ -206,18 +213,18 @@ size_t chain_smem_bytes(int H, int ccap, bool delta) {
 
 }  // namespace
 
-template <bool DELTA>
+template <bool DELTA, typename T>
 int chain_grid(int H, int ccap) {
     static int cached[64][2] = {};   // [device] -> (key, blocks)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    const int key = (int)chain_smem_bytes(H, ccap, DELTA);
+    const int key = (int)chain_smem_bytes(H, ccap, std::is_same<T, float>::value);
     if (cached[dev][0] != key) {
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaFuncSetAttribute(k_chain<DELTA>, cudaFuncAttributeMaxDynamicSharedMemorySize, key) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_chain<DELTA, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, key) != cudaSuccess)
             return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain<DELTA>, CH_NT, key);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain<DELTA, T>, CH_NT, key);
         cached[dev][0] = key;
         cached[dev][1] = per >= 1 ? sms : 0;
     }
@@ -228,12 +235,15 @@ long chain_resp_elems(int n_slices) { return (long)(n_slices + 1) * 1024; }
 
 cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s) {
     if (a.i_end <= a.i_begin) return cudaSuccess;
-    const bool delta = a.dlt != nullptr;
-    int nb = delta ? chain_grid<true>(a.H, a.ccap) : chain_grid<false>(a.H, a.ccap);
+    if (a.dlt && a.dlt64) return cudaErrorInvalidValue;
+    const bool f32 = a.dlt != nullptr, d64 = a.dlt64 != nullptr;
+    int nb = f32 ? chain_grid<true, float>(a.H, a.ccap)
+                 : (d64 ? chain_grid<true, double>(a.H, a.ccap) : chain_grid<false, double>(a.H, a.ccap));
     if (a.max_blocks > 0 && nb > a.max_blocks) nb = a.max_blocks;
     if (nb < 1 || nb > 1024) return cudaErrorInvalidConfiguration;
-    const size_t smem = chain_smem_bytes(a.H, a.ccap, delta);
-    const void* fn = delta ? (const void*)k_chain<true> : (const void*)k_chain<false>;
+    const size_t smem = chain_smem_bytes(a.H, a.ccap, f32);
+    const void* fn = f32 ? (const void*)k_chain<true, float>
+                         : (d64 ? (const void*)k_chain<true, double> : (const void*)k_chain<false, double>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(&a.gb->count, 0, sizeof(unsigned), s);

@@ -142,9 +142,10 @@ cudaError_t gemm_nn(const double* A, long lda, const int* c0_dev, const int* c1_
 // out[j] = sum_rows X[row, j]^2
 cudaError_t colnorm2(const double* X, long ldx, int m, long nrows, double* out, const TsWork& w,
                      cudaStream_t s);
-// dst <- src with *res2 = ||src - dst_old||^2 (and delta = src - dst_old in FP32 if non-NULL)
+// dst <- src with *res2 = ||src - dst_old||^2 (and delta = src - dst_old in FP32,
+// delta64 the same in FP64, where non-NULL)
 cudaError_t copy_resid(const double* src, double* dst, long n, double* res2, const TsWork& w, cudaStream_t s,
-                       float* delta = nullptr);
+                       float* delta = nullptr, double* delta64 = nullptr);
 // FP32 copies of basis columns [*c0_dev, *c1_dev) of Q and D (at most maxcols columns)
 cudaError_t to_fp32_cols(const double* Q, const double* D, float* Q32, float* D32, long d, const int* c0_dev,
                          const int* c1_dev, int maxcols, cudaStream_t s);
@@ -213,6 +214,8 @@ struct ChainArgs {
     const float* Q32;     // FP32 copies of Q and D
     const float* D32;
     float* gbuf32;        // 2 x d FP32 coarse ping-pong
+    // FP64 delta form (dlt64 != NULL): the same with Q, D, gbuf and delta in FP64
+    double* dlt64;
     int max_blocks;       // > 0: cap on the cooperative grid (one CTA per SM)
 };
 cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s);

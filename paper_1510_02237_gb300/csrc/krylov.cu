@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(256) k_colnorm2_partial(const double* __restri
 }
 
 __global__ void k_copy_resid(const double* __restrict__ src, double* __restrict__ dst, long n,
-                             double* __restrict__ partial, float* __restrict__ delta) {
+                             double* __restrict__ partial, float* __restrict__ delta, double* __restrict__ delta64) {
     __shared__ double red[8];
     const long row = (long)blockIdx.x * 256 + threadIdx.x;
     double s = 0.0;
@@ -188,6 +188,7 @@ __global__ void k_copy_resid(const double* __restrict__ src, double* __restrict_
         s = e * e;
         dst[row] = y;
         if (delta) delta[row] = (float)e;
+        if (delta64) delta64[row] = e;
     }
     s = block_sum256(s, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -574,10 +575,10 @@ cudaError_t colnorm2(const double* X, long ldx, int m, long nrows, double* out, 
 }
 
 cudaError_t copy_resid(const double* src, double* dst, long n, double* res2, const TsWork& w, cudaStream_t s,
-                       float* delta) {
+                       float* delta, double* delta64) {
     const int nb = cdiv(n, 256);
     if (nb > w.elems) return cudaErrorInvalidValue;
-    k_copy_resid<<<nb, 256, 0, s>>>(src, dst, n, w.partial, delta);
+    k_copy_resid<<<nb, 256, 0, s>>>(src, dst, n, w.partial, delta, delta64);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -5,9 +5,10 @@
 //   q    (N+1) x d   iterates q_n^k, updated in place by the serial correction
 //   qt   N x d       fine images q~_{i+1}^k = F(q_i^k)   (slot i)
 //   gv   N x d       coarse images G(q_i^k)              (slot i)
-//   kold N x d       K(q_i^k) with the current subspace   (slot i)
+//   dlt64 d          delta_i = q_i^{k+1} - q_i^k of the serial correction
 //   Q, D d x cap     orthonormal basis of S^k and D = F(Q) - G(Q); by linearity
-//                    K(q) = G(q - Q Q^T q) + F(Q) Q^T q = G(q) + D (Q^T q)
+//                    K(q) = G(q - Q Q^T q) + F(Q) Q^T q = G(q) + D (Q^T q), so
+//                    K(q_i^{k+1}) - K(q_i^k) = G(delta_i) + D (Q^T delta_i)
 //   wv, wz N x d     Gram-Schmidt work columns and their D-images
 //   fine/coarse ping-pong buffers (FP64, and FP32 when the fine sweep runs in FP32)
 #include <cmath>
@@ -57,7 +58,7 @@ struct pr_solver {
     FineCoefK fck{};
     double* fb2 = nullptr;
     CoarseCoef cc{};
-    double *q = nullptr, *qt = nullptr, *gv = nullptr, *kold = nullptr;
+    double *q = nullptr, *qt = nullptr, *gv = nullptr, *dlt64 = nullptr;
     double *Q = nullptr, *D = nullptr, *wv = nullptr, *wz = nullptr;
     double *fb0 = nullptr, *fb1 = nullptr, *cb0 = nullptr, *cb1 = nullptr, *gtmp = nullptr;
     float *f32a = nullptr, *f32b = nullptr;
@@ -128,7 +129,8 @@ static Sizes compute_sizes(int nx, int ny, int N, int K_max, const pr_options& o
     size_t dd = sizeof(double);
     size_t b = 0;
     b += dd * (size_t)(N + 1) * s.d;           // q
-    b += dd * (size_t)N * s.d * 4;             // qt, gv, kold, wv
+    b += dd * (size_t)N * s.d * 3;             // qt, gv, wv
+    b += dd * (size_t)s.d;                     // FP64 delta of the serial correction
     b += dd * (size_t)N * s.d;                 // wz
     b += dd * (size_t)s.cap * s.d * 2;         // Q, D
     b += dd * (size_t)N * s.d * 2;             // coarse ping-pong
@@ -410,9 +412,10 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
         CKS(fine_apply(h, qa, h->qt + (long)a * d, M));
         if (ev) h->tr.fine_launches[h->tr.n - 1] += (long)(parareal_kernel_launches() - l0);
         CKC(mark());
-        // coarse images G(q_i^k) (subspace images and K(q_i^k)); the FP32
-        // correction needs neither
-        if (!mixed) CKS(coarse_apply(h, qa, h->gv + (long)a * d, M));   // also K(q_i^k) for FP64
+        // coarse images G(q_i^k): the images by linearity of the KSE columns,
+        // and K_old of the original Parareal in FP64; corrections in delta
+        // form and direct images need none
+        if ((kse && !direct) || (!kse && !mixed)) CKS(coarse_apply(h, qa, h->gv + (long)a * d, M));
         CKC(mark());
         if (kse) {
             CKC(cudaMemcpyAsync(h->r_it, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
@@ -423,23 +426,6 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
             h->M_hist[rbase + k] = M;
             CKC(mark());
             if (direct) CKS(direct_images(h, mixed, M));
-            if (!mixed && M > 1) {
-                // K(q_i^k) = G(q_i^k) + D Q^T q_i^k for i = k+1..N-1 with the updated S^k
-                if (h->use_sg) {
-                    // projection coefficients Q^T q on the tensor cores, 16 slices at a time
-                    for (int j0 = 0; j0 < M - 1; j0 += SG_N) {
-                        const int mm = M - 1 - j0 < SG_N ? M - 1 - j0 : SG_N;
-                        const long off = (long)(a + 1 + j0) * d;
-                        CKC(sg_project(&h->sg, h->q + off, d, mm, h->r, s));
-                        CKC(gemm_nn(h->D, d, nullptr, h->r, cap, h->sg.C, h->sg.cap_pad, h->gv + off, d,
-                                    h->kold + off, d, mm, d, 1.0, s));
-                    }
-                } else {
-                    CKC(gemm_tn(h->Q, d, nullptr, h->r, cap, h->q + (long)(a + 1) * d, d, M - 1, d, h->C, cap, w, s));
-                    CKC(gemm_nn(h->D, d, nullptr, h->r, cap, h->C, cap, h->gv + (long)(a + 1) * d, d,
-                                h->kold + (long)(a + 1) * d, d, M - 1, d, 1.0, s));
-                }
-            }
             CKC(cudaMemcpyAsync(h->ranks + rbase + k, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
         } else {
             CKC(mark());
@@ -448,15 +434,24 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
         CKC(mark());
         // serial correction
         CKC(cudaMemsetAsync(h->res2, 0, sizeof(double) * (N + 1), s));
+        // q_{i+1}^{k+1} = q~_{i+1}^k + K(q_i^{k+1}) - K(q_i^k) (Alg. 2; K = G
+        // for Alg. 1) evaluated through the linearity of K as
+        // q~ + G(delta) + D Q^T delta, delta = q_i^{k+1} - q_i^k: in FP32 with
+        // FP32 copies of Q and D in mixed precision, in FP64 for the KSE
+        // correction otherwise; the FP64 original Parareal subtracts
+        // K_old = G(q_i^k) literally
+        const bool d64 = kse && !mixed;
         CKC(copy_resid(h->qt + (long)a * d, h->q + (long)(a + 1) * d, d, h->res2 + a + 1, w, s,
-                       mixed ? h->dlt : nullptr));
-        ChainArgs ca = chain_args(h, a + 1, N, h->qt, kse ? h->kold : h->gv, kse ? h->r : nullptr, h->res2);
+                       mixed ? h->dlt : nullptr, d64 ? h->dlt64 : nullptr));
+        ChainArgs ca = chain_args(h, a + 1, N, h->qt, kse || mixed ? nullptr : h->gv, kse ? h->r : nullptr,
+                                  h->res2);
         if (mixed) {
-            ca.kold = nullptr;
             ca.dlt = h->dlt;
             ca.Q32 = h->Q32;
             ca.D32 = h->D32;
             ca.gbuf32 = h->gbuf32;
+        } else if (d64) {
+            ca.dlt64 = h->dlt64;
         }
         CKC(chain_coop(ca, s));
         CKC(max_sqrt(h->res2 + 1, N, h->rhist + rbase + k, s));
@@ -715,7 +710,7 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
     chk(dalloc(&h->q, (size_t)(N + 1) * d));
     chk(dalloc(&h->qt, (size_t)N * d));
     chk(dalloc(&h->gv, (size_t)N * d));
-    chk(dalloc(&h->kold, (size_t)N * d));
+    chk(dalloc(&h->dlt64, (size_t)d));
     chk(dalloc(&h->wv, (size_t)N * d));
     chk(dalloc(&h->wz, (size_t)N * d));
     chk(dalloc(&h->Q, (size_t)h->cap * d));
@@ -786,7 +781,7 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
 pr_status parareal_destroy(pr_solver* h) {
     if (!h) return PR_EINVAL;
     if (h->stream || h->q) cudaStreamSynchronize(h->stream);
-    double* ds[] = {h->q, h->qt, h->gv, h->kold, h->Q, h->D, h->wv, h->wz, h->fb0, h->fb1, h->fb2, h->cb0, h->cb1,
+    double* ds[] = {h->q, h->qt, h->gv, h->dlt64, h->Q, h->D, h->wv, h->wz, h->fb0, h->fb1, h->fb2, h->cb0, h->cb1,
                     h->gtmp, h->C, h->cvec, h->partial, h->anorm2, h->res2, h->rhist, h->nres2,
                     h->gbuf, h->resp, h->ratios, h->G, h->Rinv};
     for (double* p : ds) if (p) cudaFree(p);
