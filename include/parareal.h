@@ -159,17 +159,19 @@ typedef struct {
 /* Phase timing of solves, measured with CUDA events on the handle's stream
  * (no synchronisation while solving).  Phases follow Alg. 2: the serial
  * coarse initialisation, then per iteration the parallel fine predictor, the
- * coarse images G(q_i^k), the subspace update with K(q_i^k), and the serial
- * correction. */
+ * coarse images G(q_i^k), the subspace update, and the serial correction
+ * (K(q_i^{k+1}) - K(q_i^k) through the linearity of K, so K(q_i^k) itself is
+ * not formed). */
 typedef struct {
     int32_t n_solves;        /* solves accumulated since the last reset           */
     double ms_init;          /* serial coarse initialisation                      */
     double ms_fine;          /* fine predictor F (all RK-3 step launches)         */
     double ms_coarse;        /* coarse images G(q_i^k)                            */
-    double ms_krylov;        /* subspace update and K(q_i^k) (sum of the next 3)  */
+    double ms_krylov;        /* subspace update (sum of the next 3)               */
     double ms_gs_block;      /*   Gram-Schmidt against the existing basis         */
     double ms_gs_intra;      /*   Gram-Schmidt within the new columns, appends    */
-    double ms_kold;          /*   K(q_i^k) for the correction                     */
+    double ms_kold;          /*   direct images F(Q_j) - G(Q_j) of the new columns
+                              *   (PR_IMAGES_DIRECT, FP32 fine sweeps); ~0 else   */
     double ms_chain;         /* serial correction                                 */
     double ms_total;         /* sum of the solves' device time                    */
     double fine_cell_steps;  /* cells x RK-3 steps computed by the fine predictor */
