@@ -6,7 +6,7 @@ slices, K = 6 iterations and a Krylov cap of 192, solved for each of its
 three seeded initial conditions (Gaussian bump + noise, 8 random-phase
 Fourier modes, filtered noise) -- 3 solves per step.  Inputs are resident in
 HBM when the timed region starts; each solve's working set (basis Q and D,
-302 MB, plus ~1.1 GB of buffers) is larger than the 129 MB L2, so no
+302 MB, plus ~0.27 GB of other buffers) is larger than the 129 MB L2, so no
 explicit L2 flush is used between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
