@@ -347,6 +347,33 @@ def test_basis_projector_identities():
     assert _rel(FQ[:, 5], oracle.fine_prop(p, Q[:, 5])) < 1e-12
 
 
+def test_modified_coarse_is_linear_and_exact_on_the_subspace():
+    """K of Eq. modifiedCoarse, built from the oracle's basis and images:
+    for a fixed subspace it is linear, so K(q1) - K(q2) = K(q1 - q2) = G(d) +
+    F(P d) - G(P d) with d = q1 - q2 (the difference the serial correction of
+    Alg. 2 needs); and on vectors of the subspace it is F."""
+    p = _prob(16, 8)
+    d = p.d
+    rng = np.random.default_rng(12)
+    B = oracle.Basis(d, 20)
+    cols = [rng.standard_normal(d) for _ in range(8)]
+    for a in cols:
+        assert B.add(a, oracle.fine_prop(p, a))[0]
+
+    def K(q):
+        Pq, FPq = B.project(q)
+        return oracle.coarse_prop(p, q - Pq) + FPq
+
+    q1, q2 = rng.standard_normal(d), rng.standard_normal(d)
+    dq = q1 - q2
+    Pd, FPd = B.project(dq)
+    assert _rel(K(q1) - K(q2), K(dq)) < 1e-12
+    assert _rel(K(dq), oracle.coarse_prop(p, dq) + FPd - oracle.coarse_prop(p, Pd)) < 1e-12
+    # on S, K is F: the correction's two K terms differ from F only off S
+    v = 0.7 * cols[2] - 1.3 * cols[5]
+    assert _rel(K(v), oracle.fine_prop(p, v)) < 1e-12
+
+
 def test_basis_cap_freezes():
     d = 50
     B = oracle.Basis(d, 3)
