@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
         __syncthreads();
         const double* qt = A.qt ? A.qt + (long)i * d : nullptr;
         const double* ko = A.kold ? A.kold + (long)i * d : nullptr;
+        double* ga = (DELTA && !F32 && A.gacc) ? A.gacc + (long)i * d : nullptr;
         double s = 0.0;
         if (F32 && (d & 3) == 0) {
             // four consecutive rows per thread: 16-byte loads of D32, eight
@@ -184,6 +185,7 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
             s += e * e;
             qn[row] = y;
             if (DELTA) dlt[row] = (T)e;
+            if (ga) ga[row] += (double)gin[row];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);

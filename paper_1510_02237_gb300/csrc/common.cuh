@@ -216,6 +216,9 @@ struct ChainArgs {
     float* gbuf32;        // 2 x d FP32 coarse ping-pong
     // FP64 delta form (dlt64 != NULL): the same with Q, D, gbuf and delta in FP64
     double* dlt64;
+    // with the FP64 delta form, optional: slot i holds G(q_i^k) on entry and
+    // receives G(q_i^{k+1}) = G(q_i^k) + G(delta_i) (linearity of G)
+    double* gacc;
     int max_blocks;       // > 0: cap on the cooperative grid (one CTA per SM)
 };
 cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s);

@@ -396,6 +396,12 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
     // initialisation: q_{i+1}^0 = G(q_i^0), serially (q[0] already holds u0)
     CKC(chain_coop(chain_args(h, 0, N, nullptr, nullptr, nullptr, nullptr), s));
     CKC(fill_int(h->r, 0, 1, s));
+    // The FP64 KSE path with images by linearity needs the coarse images
+    // G(q_i^k) of the new columns.  G(q_i^0) = q_{i+1}^0 bit for bit; later
+    // the delta-form correction adds G(delta_i) to them (linearity of G), so
+    // no coarse sweep over the columns is needed.
+    const bool gacc = kse && !mixed && !direct;
+    if (gacc) CKC(cudaMemcpyAsync(h->gv, h->q + d, sizeof(double) * (size_t)N * d, cudaMemcpyDeviceToDevice, s));
     CKC(mark());
 
     if (ev)
@@ -412,10 +418,9 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
         CKS(fine_apply(h, qa, h->qt + (long)a * d, M));
         if (ev) h->tr.fine_launches[h->tr.n - 1] += (long)(parareal_kernel_launches() - l0);
         CKC(mark());
-        // coarse images G(q_i^k): the images by linearity of the KSE columns,
-        // and K_old of the original Parareal in FP64; corrections in delta
-        // form and direct images need none
-        if ((kse && !direct) || (!kse && !mixed)) CKS(coarse_apply(h, qa, h->gv + (long)a * d, M));
+        // coarse images G(q_i^k): K_old of the FP64 original Parareal (the
+        // KSE images by linearity have them from the correction, above)
+        if (!kse && !mixed) CKS(coarse_apply(h, qa, h->gv + (long)a * d, M));
         CKC(mark());
         if (kse) {
             CKC(cudaMemcpyAsync(h->r_it, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
@@ -452,6 +457,7 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
             ca.gbuf32 = h->gbuf32;
         } else if (d64) {
             ca.dlt64 = h->dlt64;
+            if (gacc) ca.gacc = h->gv;
         }
         CKC(chain_coop(ca, s));
         CKC(max_sqrt(h->res2 + 1, N, h->rhist + rbase + k, s));
