@@ -2,14 +2,17 @@
 // slices in one cooperative launch:
 //
 //   for i = i_begin .. i_end-1:
-//     c         = Q^T q_i                                 (Eq. modifiedCoarse, P q = Q c)
-//     K(q_i)    = G(q_i) + D c,   D = F(Q) - G(Q)          (Eq. Genhance by linearity)
-//     q_{i+1}   = q~_{i+1} + (K(q_i) - K_old_i)            (Alg. 2)
+//     c         = Q^T x_i                                 (Eq. modifiedCoarse, P x = Q c)
+//     K(x_i)    = G(x_i) + D c,   D = F(Q) - G(Q)          (Eq. Genhance by linearity)
+//     q_{i+1}   = q~_{i+1} + K(x_i) [- K_old_i]            (Alg. 2)
 //     res2[i+1] = ||q_{i+1}^{new} - q_{i+1}^{old}||^2       (for r^k, Sec. 2.1)
 //
-// With no basis, no fine images and no K_old it is the serial coarse sweep
-// q_{i+1} = G(q_i) of the initialisation; with K_old = G(q_i^k) and no basis
-// it is the correction of the original Parareal (Alg. 1).
+// KSE correction: x_i = delta_i = q_i^{k+1} - q_i^k (K is linear, so
+// K(q_i^{k+1}) - K(q_i^k) = K(delta_i)), and the update produces delta_{i+1}.
+// Literal form (x_i = q_i): with no basis, no fine images and no K_old it is
+// the serial coarse sweep q_{i+1} = G(q_i) of the initialisation; with
+// K_old = G(q_i^k) and no basis it is the correction of the original
+// Parareal (Alg. 1).
 //
 // Every CTA owns a fixed range of rows for the dot products and the update
 // and a set of 16 x 16 tiles for the coarse steps.  Per slice: phase A
