@@ -60,6 +60,13 @@ def test_footprint_grows_with_basis():
     (dict(n_sound=9), "n_sound"),
     (dict(fine_prec=7), "fine_prec"),
     (dict(K_max=9), "K_max"),
+    (dict(omega=float("nan")), "omega"),
+    (dict(coarse_scheme=5), "coarse_scheme"),
+    (dict(variant=3), "variant"),
+    (dict(corr_prec=9), "corr_prec"),
+    (dict(n_windows=0), "n_windows"),
+    (dict(images=4), "images"),
+    (dict(proj_prec=6), "proj_prec"),
 ])
 def test_create_rejects_invalid_arguments(kw, msg):
     """Validation happens on the host before any CUDA call."""
