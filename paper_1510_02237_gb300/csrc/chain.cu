@@ -220,20 +220,20 @@ size_t chain_smem_bytes(int H, int ccap, bool f32) {
 
 template <bool DELTA, typename T>
 int chain_grid(int H, int ccap) {
-    static int cached[64][2] = {};   // [device] -> (key, blocks)
+    static DevMemo memo;   // [device] -> (shared-memory bytes, blocks)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     const int key = (int)chain_smem_bytes(H, ccap, std::is_same<T, float>::value);
-    if (cached[dev][0] != key) {
-        int sms = 0, per = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaFuncSetAttribute(k_chain<DELTA, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, key) != cudaSuccess)
-            return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain<DELTA, T>, CH_NT, key);
-        cached[dev][0] = key;
-        cached[dev][1] = per >= 1 ? sms : 0;
-    }
-    return cached[dev][1];
+    int k0 = -1, blocks = 0;
+    if (memo.get(dev, &k0, &blocks) && k0 == key) return blocks;
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(k_chain<DELTA, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, key) != cudaSuccess)
+        return 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain<DELTA, T>, CH_NT, key);
+    blocks = per >= 1 ? sms : 0;
+    memo.put(dev, key, blocks);
+    return blocks;
 }
 
 long chain_resp_elems(int n_slices) { return (long)(n_slices + 1) * 1024; }

@@ -44,18 +44,14 @@ cudaError_t launch_shape(const double* in, double* out, long stride, int n, int 
 
 // SMs and opt-in shared memory per block of the current device
 bool device_limits(int* sms, int* smem_optin) {
-    static int cached[64][2] = {};
+    static DevMemo memo;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
-    if (!cached[dev][0]) {
-        if (cudaDeviceGetAttribute(&cached[dev][0], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&cached[dev][1], cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
-            cached[dev][0] = 0;
-            return false;
-        }
-    }
-    *sms = cached[dev][0];
-    *smem_optin = cached[dev][1];
+    if (memo.get(dev, sms, smem_optin)) return true;
+    if (cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return false;
+    memo.put(dev, *sms, *smem_optin);
     return true;
 }
 

@@ -5,10 +5,32 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace pr {
 
 // Count n kernel launches (process-wide, reported by parareal_kernel_launches).
 void count_launches(int n);
+
+// Per-device memo of a pair of small non-negative launch parameters (a, b),
+// one atomic 64-bit word per device so that concurrent host threads (one
+// handle per thread) read either nothing or a consistent pair.
+struct DevMemo {
+    std::atomic<unsigned long long> w[64];
+    bool get(int dev, int* a, int* b) const {
+        if (dev < 0 || dev >= 64) return false;
+        const unsigned long long x = w[dev].load(std::memory_order_acquire);
+        if (!(x >> 63)) return false;
+        *a = (int)((x >> 32) & 0x7fffffffu);
+        *b = (int)(x & 0xffffffffu);
+        return true;
+    }
+    void put(int dev, int a, int b) {
+        if (dev < 0 || dev >= 64 || a < 0 || b < 0) return;
+        w[dev].store((1ull << 63) | ((unsigned long long)(unsigned)a << 32) | (unsigned)b,
+                     std::memory_order_release);
+    }
+};
 
 // Periodic index for offsets that may exceed one period (tiny grids).
 __host__ __device__ __forceinline__ int pwrap(int i, int n) {

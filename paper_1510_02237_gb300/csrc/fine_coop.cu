@@ -126,19 +126,18 @@ __global__ void __launch_bounds__(FC_NT) k_fine_coop(FineSweepArgs a) {
 
 template <bool HV>
 int coop_blocks(int max_sms) {
-    static int cached[64][2] = {};   // [device] -> (SMs, CTAs per SM)
+    static DevMemo memo;   // [device] -> (SMs, CTAs per SM)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    if (!cached[dev][0]) {
-        int sms = 0, per = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int nsm = 0, per = 0;
+    if (!memo.get(dev, &nsm, &per)) {
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fine_coop<HV>, FC_NT, 0);
-        cached[dev][0] = sms;
-        cached[dev][1] = per;
+        memo.put(dev, nsm, per);
     }
-    if (cached[dev][1] < 1) return -1;
-    const int sms = max_sms > 0 && max_sms < cached[dev][0] ? max_sms : cached[dev][0];
-    return sms * cached[dev][1];
+    if (per < 1) return -1;
+    const int sms = max_sms > 0 && max_sms < nsm ? max_sms : nsm;
+    return sms * per;
 }
 
 }  // namespace

@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(32 * NW, (NW >= 8 ? 1 : 12 / NW))
 template <int NW, typename Tin, typename Tout>
 cudaError_t launch_nw(const Tin* in, long instride, Tout* out, long outstride, int n, int nx, int ny,
                       const RowCoef& k, cudaStream_t s, const SliceMap& map, int min_rows) {
-    static int cached[64][2] = {};   // [device] -> (SMs, CTAs per SM)
+    static DevMemo memo;   // [device] -> (SMs, CTAs per SM)
     constexpr int R = ring_rows<Tin>();
     const size_t smem = (size_t)R * 3 * nx * sizeof(Tin) + 8 * R;
     int dev = 0;
@@ -462,18 +462,12 @@ cudaError_t launch_nw(const Tin* in, long instride, Tout* out, long outstride, i
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int sms = 0, per = 0;
-    if (dev >= 0 && dev < 64 && cached[dev][0]) {
-        sms = cached[dev][0];
-        per = cached[dev][1];
-    } else {
+    if (!memo.get(dev, &sms, &per)) {
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * NW, smem);
         if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) {
-            cached[dev][0] = sms;
-            cached[dev][1] = per;
-        }
+        memo.put(dev, sms, per);
     }
     if (per < 1) return cudaErrorInvalidConfiguration;
     // at least min_rows rows per CTA (default 16) keep the 6 halo rows of a range cheap

@@ -602,16 +602,16 @@ cudaError_t sub(const double* a, const double* b, double* out, long n, cudaStrea
 }
 
 int intra_block_grid() {
-    static int cached[64] = {};
+    static DevMemo memo;   // [device] -> (SMs, CTAs per SM)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    if (!cached[dev]) {
-        int sms = 0, per = 0;
+    int sms = 0, per = 0;
+    if (!memo.get(dev, &sms, &per)) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_intra_block, IB_NT, 0);
-        cached[dev] = sms * (per < 1 ? 0 : 1);
+        memo.put(dev, sms, per);
     }
-    return cached[dev];
+    return sms * (per < 1 ? 0 : 1);
 }
 
 cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2, const int* r_old_dev,
