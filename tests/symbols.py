@@ -76,29 +76,64 @@ def fine_amplification(p, kx, ky, nsteps):
     return np.linalg.matrix_power(R, nsteps)
 
 
-def coarse_amplification(p, kx, ky, nsteps):
+def damping_symbol(stencil, tx, ty, dx, dy):
+    """2x2 symbol of grad(div u) on (u, w): 'compact' (3-point second
+    differences plus the 4-point cross difference), or 'wide' (the centred
+    divergence followed by the centred gradient, which misses the 2 dx mode)."""
+    sx, sy = np.sin(tx), np.sin(ty)
+    cross = -sx * sy / (dx * dy)
+    if stencil == "compact":
+        hx, hy = np.sin(tx / 2) ** 2, np.sin(ty / 2) ** 2
+        return np.array([[-4 * hx / dx ** 2, cross], [cross, -4 * hy / dy ** 2]], dtype=complex)
+    return np.array([[-sx ** 2 / dx ** 2, cross], [cross, -sy ** 2 / dy ** 2]], dtype=complex)
+
+
+def coarse_amplification(p, kx, ky, nsteps, *, order="velocity_first", damping="old", stencil="compact",
+                         slow="frozen", n_sound=None):
     """Split forward-Euler / forward-backward coarse step as a product of
-    substep matrices on z = (q, q^n) -- the slow tendency is frozen at q^n."""
+    substep matrices on z = (q, q^n) -- the slow tendency is frozen at q^n.
+
+    The keywords select readings of what Sec. 3.2 leaves open (defaults: the
+    implemented one): ``order`` -- velocities first, then the pressure from the
+    new velocities, or the pressure first; ``damping`` -- grad-div damping from
+    the velocities at the start of the substep ('old') or applied to the
+    velocities just updated ('new'); ``stencil`` -- see damping_symbol;
+    ``slow`` -- 'frozen' adds the frozen slow tendency in every substep
+    (partially split), 'advect_first' takes one forward-Euler advective step of
+    Delta t and then the acoustic substeps (not partially split)."""
     nx, ny = p.nx, p.ny
     dx, dy = p.lx / nx, p.ly / ny
     tx, ty = 2 * np.pi * kx / nx, 2 * np.pi * ky / ny
-    tau = p.dt_g / p.n_sound
+    ns = p.n_sound if n_sound is None else n_sound
+    tau = p.dt_g / ns
     a1 = p.nu_c * dx * dx / tau
     a2 = p.nu_c * dy * dy / tau
     s = adv_symbol(p.adv_order_c, p.U, p.V, tx, ty, dx, dy)
-    F = fast_symbol(p.c_s, a1, a2, tx, ty, dx, dy)
-    # forward part: (u, w) <- (u, w) + tau (s q^n + F[0:2,:] q)
-    Mf = np.eye(6, dtype=complex)
-    Mf[0:2, 0:3] += tau * F[0:2, :]
-    Mf[0:2, 3:5] += tau * s * np.eye(2)
+    F = fast_symbol(p.c_s, 0.0, 0.0, tx, ty, dx, dy)   # acoustics only
+    Dm = np.diag([a1, a2]) @ damping_symbol(stencil, tx, ty, dx, dy)
+    sf = s if slow == "frozen" else 0.0
+    # forward part: (u, w) <- (u, w) + tau (s q^n + F[0:2,:] q [+ damping])
+    def vel(with_damping):
+        M = np.eye(6, dtype=complex)
+        M[0:2, 0:3] += tau * F[0:2, :]
+        M[0:2, 3:5] += tau * sf * np.eye(2)
+        if with_damping:
+            M[0:2, 0:2] += tau * Dm
+        return M
     # backward part: p <- p + tau (s p^n + F[2, :] q_new)
     Mb = np.eye(6, dtype=complex)
     Mb[2, 0:3] += tau * F[2, :]
-    Mb[2, 5] += tau * s
-    sub = Mb @ Mf
-    Msub = np.linalg.matrix_power(sub, p.n_sound)
+    Mb[2, 5] += tau * sf
+    Md = np.eye(6, dtype=complex)
+    Md[0:2, 0:2] += tau * Dm
+    Mv = vel(True) if damping == "old" else Md @ vel(False)
+    sub = Mb @ Mv if order == "velocity_first" else Mv @ Mb
+    Msub = np.linalg.matrix_power(sub, ns)
     # start from z = (q, q): big step map is Msub[0:3,0:3] + Msub[0:3,3:6]
-    step = Msub[0:3, 0:3] + Msub[0:3, 3:6]
+    if slow == "frozen":
+        step = Msub[0:3, 0:3] + Msub[0:3, 3:6]
+    else:
+        step = Msub[0:3, 0:3] @ ((1.0 + p.dt_g * s) * np.eye(3))
     return np.linalg.matrix_power(step, nsteps)
 
 
