@@ -197,7 +197,8 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
 pr_status parareal_destroy(pr_solver* h);
 
 /* Message of the last error on h ("" if none).  Valid until the next call on h.
- * h == NULL returns the message of the last failed parareal_create. */
+ * h == NULL returns the message of the calling host thread's last failed
+ * parareal_create. */
 const char* parareal_last_error(const pr_solver* h);
 
 /* Bytes of device memory a handle with these parameters holds. */
@@ -332,12 +333,15 @@ pr_status parareal_batch_destroy(pr_batch* b);
  * where they need F: code running while a stream is captured into a CUDA
  * graph (cudaMalloc is not permitted there), runtimes that route every
  * device allocation through their own pool, and hosts that may not allocate
- * after start-up.  The paper has no counterpart; it computes exactly what
- * parareal_fine_sweep computes (n_steps RK-3 steps of the fine tendency on n
- * independent states) without a handle: every input and output comes from
- * the caller and the RK-3 intermediates live in a file-scope device array of
+ * after start-up.  The paper has no counterpart.  For constant advection
+ * velocity (U, V) in PR_FP64 or PR_FP32 it computes what parareal_fine_sweep
+ * computes on a handle with the same parameters (n_steps RK-3 steps of the
+ * fine tendency on n independent states); it has no rotation (omega) and no
+ * PR_FP32X mode.  It needs no handle: every input and output comes from the
+ * caller and the RK-3 intermediates live in a file-scope device array of
  * 32 MiB (two 16 MiB halves) that every GPU loading the library holds until
- * the process exits.
+ * the process exits.  It always runs the shared-memory tile kernel, which
+ * has no device-side waits, so nothing is left to report after it returns.
  *   g, U, V, c_s, nu_f, dt_f: as for parareal_create (nx, ny >= 4).
  *   n_steps: RK-3 steps (>= 1); fine_prec: PR_FP64 or PR_FP32.
  *   q_in_dev / q_out_dev: device, n*d doubles each, not overlapping.
@@ -346,7 +350,8 @@ pr_status parareal_batch_destroy(pr_batch* b);
  *      PR_EINVAL and print the limit to stderr.
  *   stream: cudaStream_t or NULL.  Returns after enqueueing.
  * The first call on each device looks up the array's device address (with
- * that device current) and must come before any stream capture.  Calls share
+ * that device current) and must come before any stream capture; later calls
+ * made outside capture look it up again.  Calls share
  * the array: calls whose work overlaps on the GPU race and must be
  * serialised by the caller.  No allocation of any kind is made. */
 pr_status parareal_fine_sweep_static(const pr_grid* g, double U, double V, double c_s, double nu_f,

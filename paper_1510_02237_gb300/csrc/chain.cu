@@ -36,7 +36,7 @@ constexpr int CH_NT = 512, CH_TX = 16, CH_TY = 16;
 // FP32 in a fixed order (deterministic).  With vec (both columns 16-byte
 // aligned at r0, r0 a multiple of 4) four float4 loads per operand are in
 // flight per lane.
-__device__ __forceinline__ float warp_dot_f32(const float* __restrict__ a, const float* __restrict__ x, long r0,
+__device__ __forceinline__ float warp_dot_f32(const float* __restrict__ a, const float* x, long r0,
                                               long r1, bool vec) {
     const int lane = threadIdx.x & 31;
     float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
@@ -228,8 +228,7 @@ int chain_grid(int H, int ccap) {
     if (memo.get(dev, &k0, &blocks) && k0 == key) return blocks;
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(k_chain<DELTA, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, key) != cudaSuccess)
-        return 0;
+    if (allow_max_dynamic_smem((const void*)k_chain<DELTA, T>) != cudaSuccess) return 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain<DELTA, T>, CH_NT, key);
     blocks = per >= 1 ? sms : 0;
     memo.put(dev, key, blocks);
@@ -249,7 +248,7 @@ cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s) {
     const size_t smem = chain_smem_bytes(a.H, a.ccap, f32);
     const void* fn = f32 ? (const void*)k_chain<true, float>
                          : (d64 ? (const void*)k_chain<true, double> : (const void*)k_chain<false, double>);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(fn);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(&a.gb->count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;

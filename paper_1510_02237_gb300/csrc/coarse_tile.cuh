@@ -43,8 +43,10 @@ __host__ __device__ constexpr int coarse_tile_smem_elems(int H) {
 // out tile (tx0, ty0) = one coarse step of in, in arithmetic T (double or
 // float, loaded from Tin and stored as Tout); NT threads cooperate; sm holds
 // coarse_tile_smem_elems<TX,TY>(H) elements of T.  Contains __syncthreads().
+// src is read with plain (coherent) loads: the serial chain passes states
+// that other CTAs wrote earlier in the same launch.
 template <int TX, int TY, int NT, typename T = double, typename Tin = double, typename Tout = double>
-__device__ __forceinline__ void coarse_tile(const Tin* __restrict__ src, Tout* __restrict__ dst, int nx, int ny,
+__device__ __forceinline__ void coarse_tile(const Tin* src, Tout* __restrict__ dst, int nx, int ny,
                                             const CoarseCoef& cd, int H, int tx0, int ty0, T* __restrict__ sm) {
     const int RX = TX + 2 * H, RY = TY + 2 * H, NR = RX * RY;
     T* u = sm;

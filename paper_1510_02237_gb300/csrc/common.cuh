@@ -6,8 +6,37 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
+#include <set>
+#include <utility>
 
 namespace pr {
+
+// Raise kernel fn's dynamic shared-memory limit to the current device's
+// opt-in maximum, once per (kernel, device).  The limit is process-wide per
+// kernel; setting it to one fixed value (instead of each launch's own size)
+// means no host thread can lower it between another thread's set and launch.
+inline cudaError_t allow_max_dynamic_smem(const void* fn) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({fn, dev})) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    int stat = 0;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    stat = (int)fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - stat);
+    if (e != cudaSuccess) return e;
+    done.insert({fn, dev});
+    return cudaSuccess;
+}
 
 // Count n kernel launches (process-wide, reported by parareal_kernel_launches).
 void count_launches(int n);
@@ -102,6 +131,7 @@ struct SliceMap {
 struct FineLaunch {
     int tile = -1;
     int min_rows = 16;
+    bool rows = true;   // false: never the row-streamed kernel (it has bounded waits)
 };
 constexpr int kFineTiles = 4;
 extern const int fine_tile_shapes[kFineTiles][2];

@@ -179,8 +179,7 @@ cudaError_t launch_tile(const Tin* in, long instride, Tout* out, long outstride,
     constexpr int RX = TX + 18, RY = TY + 6 * RYH;
     constexpr size_t smem = sizeof(T) * 6 * RX * RY;
     auto kern = k_fine_step<T, Tin, Tout, RYH, TX, TY, NT, ACC64>;
-    // idempotent; set on every launch so it holds on whichever device is current
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem((const void*)kern);
     if (e != cudaSuccess) return e;
     dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, n);
     kern<<<grid, NT, smem, s>>>(in, instride, out, outstride, nx, ny, c, map);
@@ -223,7 +222,8 @@ cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outst
                              const FineLaunch& fl) {
     if constexpr (std::is_same<T, float>::value) {
         cudaError_t e = cudaSuccess;
-        if (launch_fine_rows<Tin, Tout>(in, instride, out, outstride, n, nx, ny, has_v, c, s, map, &e, fl.min_rows))
+        if (fl.rows &&
+            launch_fine_rows<Tin, Tout>(in, instride, out, outstride, n, nx, ny, has_v, c, s, map, &e, fl.min_rows))
             return e;
     }
     return launch_tiles<T, Tin, Tout, false>(in, instride, out, outstride, n, nx, ny, has_v, c, s, map, fl);

@@ -458,8 +458,7 @@ cudaError_t launch_nw(const Tin* in, long instride, Tout* out, long outstride, i
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     auto kern = k_fine_rows<NW, Tin, Tout>;
-    // idempotent; set on every launch so it holds on whichever device is current
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_max_dynamic_smem((const void*)kern);
     if (e != cudaSuccess) return e;
     int sms = 0, per = 0;
     if (!memo.get(dev, &sms, &per)) {

@@ -75,7 +75,7 @@ __device__ __forceinline__ int warp_sum16(double (&acc)[16]) {
 // Dot product of a and b over rows [r0, r1) by one warp: lane j takes rows
 // r0 + j + 32 t in order, four rows per iteration with their loads issued
 // together, then a fixed xor-shuffle tree.  Deterministic.
-__device__ __forceinline__ double warp_dot(const double* __restrict__ a, const double* __restrict__ b, long r0,
+__device__ __forceinline__ double warp_dot(const double* a, const double* b, long r0,
                                            long r1) {
     const int lane = threadIdx.x & 31;
     double s = 0.0;

@@ -82,7 +82,7 @@ struct pr_solver {
     std::string err;
 };
 
-static std::string g_create_err;
+static thread_local std::string g_create_err;   // per host thread: concurrent creates do not race
 
 static pr_status set_err(pr_solver* h, pr_status st, const std::string& msg) {
     if (h) h->err = msg; else g_create_err = msg;

@@ -658,11 +658,7 @@ int sm_count() {
 }
 
 cudaError_t launch_mma(const CUtensorMap* A, const CUtensorMap& B2, const SgArgs& a, dim3 grid, cudaStream_t s) {
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(k_split_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, SG_DSMEM);
-    });
+    const cudaError_t attr = allow_max_dynamic_smem((const void*)k_split_mma);
     if (attr != cudaSuccess) return attr;
     k_split_mma<<<grid, SG_THREADS, SG_DSMEM, s>>>(A[0], A[1], A[2], A[3], B2, a);
     count_launches(1);
@@ -724,11 +720,7 @@ cudaError_t sg_init(SplitGemm* g, long d, int cap) {
     SG_ALLOC(g->ws, sizeof(double) * (size_t)g->grid * cp * SG_N);
     SG_ALLOC(g->C, sizeof(double) * (size_t)SG_N * cp);
 #undef SG_ALLOC
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * (int)sizeof(double));
-    });
+    const cudaError_t attr = allow_max_dynamic_smem((const void*)k_finish);
     if (attr != cudaSuccess) {
         sg_free(g);
         return attr;

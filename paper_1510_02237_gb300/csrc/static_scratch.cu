@@ -11,12 +11,14 @@
 //
 // The array is 32 MiB, split into two halves of 16 MiB; every GPU on which
 // the library's device code is loaded holds it until the process exits.
-// Host code cannot use the array's name as a device address, so on the first
-// call on each device (with that device current) the address is looked up
-// once with cudaGetSymbolAddress and cached; make that first call before any
-// stream capture begins.  All calls share the array: calls whose work
-// overlaps on the GPU (other streams, other host threads) race on it and
-// must be serialised by the caller.  Nothing in it needs to start at zero --
+// Host code cannot use the array's name as a device address, so the first
+// call on each device (with that device current) looks the address up with
+// cudaGetSymbolAddress and caches it; make that first call before any stream
+// capture begins.  Later calls outside capture look it up again (cheap).
+// The sweep runs the shared-memory tile kernel, which has no device-side
+// waits, so a call has no deferred error to report.  All calls share the
+// array: calls whose work overlaps on the GPU (other streams, other host
+// threads) race on it and must be serialised by the caller.  Nothing in it needs to start at zero --
 // every step overwrites the whole part of the half it uses before reading it.
 #include <cmath>
 #include <cstdio>
@@ -37,12 +39,17 @@ static __device__ __align__(256) unsigned char g_fine_scratch[2 * kHalfBytes];
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of g_fine_scratch on the current device (set-up on first use).
-pr_status scratch_for_current_device(void** out) {
+// Device address of g_fine_scratch on the current device.  Set up on the
+// first call on each device; looked up again on every call made outside
+// stream capture (cheap), so a module reloaded after cudaDeviceReset is
+// followed; during capture the cached address is used.
+pr_status scratch_for_current_device(cudaStream_t s, void** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PR_ECUDA;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return PR_ECUDA;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (!g_scratch_ptr[dev] || cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_fine_scratch);
         if (e != cudaSuccess || !p) {
@@ -83,18 +90,26 @@ template <typename T>
 pr_status sweep(const double* in, double* out, int n, int nx, int ny, int nsteps, bool hv, const FineCoef<T>& c,
                 unsigned char* scratch, cudaStream_t s) {
     const long d = 3L * nx * ny;
+    // shared-memory tile kernel only: the row-streamed FP32 kernel's bounded
+    // waits report through a process-wide word that this call cannot return
+    FineLaunch fl;
+    fl.rows = false;
+    const SliceMap all;
     if (nsteps == 1)
-        return launch_fine_step<T, double, double>(in, d, out, d, n, nx, ny, hv, c, s) == cudaSuccess ? PR_OK : PR_ECUDA;
+        return launch_fine_step<T, double, double>(in, d, out, d, n, nx, ny, hv, c, s, all, fl) == cudaSuccess
+                   ? PR_OK
+                   : PR_ECUDA;
     T* a = reinterpret_cast<T*>(scratch);
     T* b = reinterpret_cast<T*>(scratch + kHalfBytes);
-    if (launch_fine_step<T, double, T>(in, d, a, d, n, nx, ny, hv, c, s) != cudaSuccess) return PR_ECUDA;
+    if (launch_fine_step<T, double, T>(in, d, a, d, n, nx, ny, hv, c, s, all, fl) != cudaSuccess) return PR_ECUDA;
     for (int st = 1; st < nsteps - 1; ++st) {
-        if (launch_fine_step<T, T, T>(a, d, b, d, n, nx, ny, hv, c, s) != cudaSuccess) return PR_ECUDA;
+        if (launch_fine_step<T, T, T>(a, d, b, d, n, nx, ny, hv, c, s, all, fl) != cudaSuccess) return PR_ECUDA;
         T* t = a;
         a = b;
         b = t;
     }
-    return launch_fine_step<T, T, double>(a, d, out, d, n, nx, ny, hv, c, s) == cudaSuccess ? PR_OK : PR_ECUDA;
+    return launch_fine_step<T, T, double>(a, d, out, d, n, nx, ny, hv, c, s, all, fl) == cudaSuccess ? PR_OK
+                                                                                         : PR_ECUDA;
 }
 
 }  // namespace
@@ -116,13 +131,13 @@ extern "C" pr_status parareal_fine_sweep_static(const pr_grid* g, double U, doub
     if ((double)n * (double)d * (double)elem > (double)kHalfBytes)
         return reject("n * 3 * nx * ny intermediate values exceed the 16 MiB static scratch half "
                       "(2097152 doubles or 4194304 floats)");
+    cudaStream_t s = (cudaStream_t)stream;
     void* scratch = nullptr;
-    pr_status st = scratch_for_current_device(&scratch);
+    pr_status st = scratch_for_current_device(s, &scratch);
     if (st != PR_OK) return st;
     const double lx = g->lx > 0 ? g->lx : 1.0, ly = g->ly > 0 ? g->ly : 1.0;
     const double dx = lx / g->nx, dy = ly / g->ny;
     const bool hv = V != 0.0;
-    cudaStream_t s = (cudaStream_t)stream;
     unsigned char* sc = static_cast<unsigned char*>(scratch);
     if (fine_prec == PR_FP64)
         return sweep<double>(q_in_dev, q_out_dev, n, g->nx, g->ny, n_steps, hv,
