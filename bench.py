@@ -56,8 +56,8 @@ def _sha(path):
 
 
 # DRAM traffic of one FP64 fine-sweep launch from an ncu capture of the same
-# kernel source (profiles/fine_coop_fp64_256x128.md: 25.3 MB read + 634.3 MB
-# written for 31 slices x 32768 cells x 20 steps); null once fine_coop.cu changes.
+# kernel source (25.3 MB read + 634.3 MB written for 31 slices x 32768 cells
+# x 20 steps); null once fine_coop.cu changes.
 FINE_TRAFFIC = {"source_sha": "665cf23bcceb", "bytes_per_cell_step": 32.46}
 
 

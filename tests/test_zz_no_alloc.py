@@ -13,6 +13,7 @@ from __future__ import annotations
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -21,6 +22,7 @@ P = pytest.importorskip("paper_1510_02237_gb300")
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
+TOL32 = 1e-5   # FP32 fine sweep against the FP64 oracle, as in the parity tests
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -34,9 +36,12 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
 
 
+@pytest.mark.parametrize("V", [0.0, 0.05], ids=["V0", "V005"])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
-def test_static_fine_sweep_matches_handle_twice(prec):
-    p = W.make_problem(256, 128, 8)
+def test_static_fine_sweep_matches_handle_twice(prec, V):
+    """Two calls in a row (sharing the static scratch) against the handle's
+    sweep and against the oracle's F on a few of the states."""
+    p = W.make_problem(256, 128, 8, V=V)
     n = 8
     stream = torch.cuda.current_stream()
     X = [torch.from_numpy(np.stack([W.ic_random(p.nx, p.ny, seed=s + i).ravel() for i in range(n)])).cuda()
@@ -49,6 +54,7 @@ def test_static_fine_sweep_matches_handle_twice(prec):
             want.append(y)
         torch.cuda.synchronize()
         want = [w.cpu().numpy() for w in want]
+    tol_oracle = TOL64 if prec == 0 else TOL32
     for call in range(2):                      # two calls in a row share the static scratch
         x = X[call]
         y = torch.full_like(x, float("nan"))
@@ -58,6 +64,10 @@ def test_static_fine_sweep_matches_handle_twice(prec):
         got = y.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert _rel(got, want[call]) < TOL64
+        xin = x.cpu().numpy()
+        for i in (0, n - 1):
+            ref = oracle.fine_prop(p, xin[i])
+            assert _rel(got[i], ref) < tol_oracle
 
 
 def test_static_fine_sweep_rejects_oversize():
