@@ -130,40 +130,51 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- CPU oracle timing
 
-def oracle_sample(budget_s: float, wl):
-    """Time the oracle on a bounded sample of the workload on the host cores.
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
-    Sample: one KSE-Parareal iteration (K = 1) of the first IC -- the serial
-    coarse initialisation, the fine predictor on all N slices, the Householder
-    subspace update and the serial correction.  A K-iteration solve repeats
-    the iteration K times (the oracle propagates every slice in every
-    iteration), so K * t(sample) is a lower bound of the oracle's solve time
-    (the update and the correction grow with the basis); the throughput
-    reported is therefore an upper bound for the oracle.  If the budget is
-    below one sample, the sample shrinks to fine propagations of single slices
-    and is scaled by the fine share of the work (K * N slice propagations).
-    """
+
+def oracle_solve_seconds(wl, threads: int) -> float:
+    """Wall time of one complete oracle solve of the workload (IC 0, K
+    iterations, the workload's Krylov cap): serial coarse initialisation, then
+    per iteration the parallel predictor on ``threads`` host threads (OpenMP
+    over slices, the paper's own parallel structure, Sec. 2.1), the Householder
+    subspace update and the serial correction."""
     import oracle
     p = wl.problem
     q0 = wl.ics[0][1]().ravel()
-    t0 = time.perf_counter()
-    oracle.fine_prop(p, q0)
-    t_slice = time.perf_counter() - t0
-    est_iter = t_slice * p.n_slices * 1.5
-    if budget_s >= est_iter:
+    old = oracle.set_threads(threads)
+    try:
         t0 = time.perf_counter()
-        oracle.parareal(p, q0, 1)
-        t = time.perf_counter() - t0
-        return {"value": 1.0 / (wl.K * t), "sample": f"one K=1 iteration of the {wl.name} solve (IC 0) = "
-                f"{t:.2f} s; solve time estimated as K={wl.K} x that (lower bound)", "seconds": t}
-    n = max(1, int(budget_s / max(t_slice, 1e-3)))
-    t0 = time.perf_counter()
-    for _ in range(n):
-        oracle.fine_prop(p, q0)
-    t = (time.perf_counter() - t0) / n
-    return {"value": 1.0 / (wl.K * p.n_slices * t), "sample": f"{n} fine slice propagations of {wl.name} "
-            f"({t:.3f} s each); solve time estimated as K*N of them (fine work only, lower bound)",
-            "seconds": t * n}
+        oracle.parareal(p, q0, wl.K, cap=wl.krylov_cap)
+        return time.perf_counter() - t0
+    finally:
+        oracle.set_threads(old)
+
+
+def oracle_baseline(wl, n_solves: int = 1) -> dict:
+    """cpu_baseline object: n_solves complete oracle solves on all host cores."""
+    cores = host_cores()
+    ts = [oracle_solve_seconds(wl, cores) for _ in range(max(1, n_solves))]
+    t = float(np.mean(ts))
+    return {"value": 1.0 / t, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(ts)} complete oracle solve(s) of {wl.name} (IC 0, K={wl.K}, cap {wl.krylov_cap}), "
+                      f"{t:.1f} s each; fine predictor OpenMP over slices on {cores} threads, the rest serial",
+            "seconds": ts}
+
+
+def workload_config(wl, world: int, K: int, nsol: int) -> dict:
+    """The config object of the bench line (the same for both arms)."""
+    p = wl.problem
+    return {"workload": wl.name, "grid": f"{p.nx}x{p.ny}", "N_slices": p.n_slices, "K": K,
+            "krylov_cap": wl.krylov_cap, "n_f": p.n_f, "n_g": p.n_g, "ics": [nm for nm, _ in wl.ics],
+            "solves_per_step": nsol, "fine_prec": "f64",
+            "l2": "no flush: per-solve working set (Q, D 302 MB + buffers) > 129 MB L2",
+            "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args):
@@ -171,27 +182,31 @@ def run_reference(args):
     if rank != 0:
         return 0
     wl = W.workload_medium()
-    # warm-up steps: one fine slice each (untimed); timed steps share a ~150 s budget
     import oracle
     p = wl.problem
     q0 = wl.ics[0][1]().ravel()
-    for _ in range(args.warmup):
+    for _ in range(args.warmup):          # untimed: one fine slice each
         oracle.fine_prop(p, q0)
-    per_step = 150.0 / max(1, args.steps)
-    vals, secs, samples = [], 0.0, None
-    for _ in range(args.steps):
-        r = oracle_sample(per_step, wl)
-        vals.append(r["value"])
-        secs += r["seconds"]
-        samples = r["sample"]
-    value = float(np.mean(vals))
+    # complete solves, as many as fit a ~180 s budget (at least one)
+    cores = host_cores()
+    t_first = oracle_solve_seconds(wl, cores)
+    ts = [t_first]
+    n_more = min(args.steps, int(180.0 / max(t_first, 1e-3))) - 1
+    for _ in range(max(0, n_more)):
+        ts.append(oracle_solve_seconds(wl, cores))
+    t = float(np.mean(ts))
+    value = 1.0 / t
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t * len(wl.ics),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "grid": f"{p.nx}x{p.ny}", "N_slices": p.n_slices, "K": wl.K,
-                   "krylov_cap": wl.krylov_cap, "ics": [n for n, _ in wl.ics]},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": samples},
+        "config": workload_config(wl, world, wl.K, len(wl.ics)),
+        "solves_timed": len(ts),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{len(ts)} complete oracle solve(s) of {wl.name} (IC 0), {t:.1f} s each; "
+                                   f"fine predictor OpenMP over slices on {cores} threads, the rest serial; "
+                                   f"ms_per_step = 3 solves"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -645,17 +660,12 @@ def run_ours(args):
                 / (tm["ms_fine"] / 1e3) / 1e9}
         cpu = None
         if not args.no_cpu_baseline:
-            cb = oracle_sample(25.0, wl)
-            cpu = {"value": cb["value"], "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": cb["sample"]}
+            cpu = oracle_baseline(wl, 1)
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "grid": f"{p.nx}x{p.ny}", "N_slices": p.n_slices, "K": K,
-                       "krylov_cap": wl.krylov_cap, "n_f": p.n_f, "n_g": p.n_g, "ics": [nm for nm, _ in wl.ics],
-                       "solves_per_step": nsol, "fine_prec": "f64",
-                       "l2": "no flush: per-solve working set (Q, D 302 MB + buffers) > 129 MB L2",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(wl, world, K, nsol),
             "fine_cell_steps_per_s": fine_cell_steps / (ms / 1e3),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "what": "device time of one solve, CUDA events"},

@@ -16,6 +16,7 @@ Functions and the passages they follow:
   parareal                            -- Alg. 2 (KSE-Parareal) and Alg. 1 (original)
   serial_fine                         -- the sequential fine solution q_seq
   rel_error                           -- Eq. errorDef
+  set_threads                         -- OpenMP threads of Alg. 2's parallel predictor
 """
 from __future__ import annotations
 
@@ -67,6 +68,8 @@ def lib():
         L.orc_parareal.argtypes = [pp, _P, C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, _P, _P, _I, _I, _P]
         L.orc_parareal.restype = C.c_int
         L.orc_serial_fine.argtypes = [pp, _P, _P]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = C.c_int
         _lib = L
     return _lib
 
@@ -210,6 +213,12 @@ def parareal_windows(p, q0, K: int, n_windows: int, **kw):
         wins.append(r)
         q = r["q"][-1].copy()
     return dict(qT=q, windows=wins)
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the parallel predictor (OpenMP over slices, Sec. 2.1);
+    1 runs it serially.  Results do not depend on it.  Returns the previous value."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def serial_fine(p, q0, **over):

@@ -22,6 +22,10 @@
  *   - the subspace update is a Householder QR of the columns in insertion
  *     order that drops column j when |R_jj| <= eta * ||a_j|| (the paper uses
  *     pivoted DGEQP3 without stating a rank rule) -- Sec. 2.2, Eq. subspaceUpdate.
+ *
+ * The parallel predictor can run on several host threads (OpenMP over
+ * slices, the paper's own parallel structure, Sec. 2.1); everything else is
+ * serial, as in the paper, and the results do not depend on the threads.
  */
 #include "oracle.h"
 
@@ -403,6 +407,14 @@ static void kse_coarse(const orc_problem* pb, const orc_basis* b, const double* 
 
 /* ------------------------------------------------------------------ Parareal */
 
+static int g_threads = 1;
+
+int orc_set_threads(int n) {
+    const int old = g_threads;
+    g_threads = n > 0 ? n : 1;
+    return old;
+}
+
 int orc_parareal(const orc_problem* pb, const double* q0, int K, int variant,
                  double eta, int cap, double r_tol, double* q_all, double* r_hist, int* rank_hist,
                  int* kept, double* ratio) {
@@ -423,7 +435,9 @@ int orc_parareal(const orc_problem* pb, const double* q0, int K, int variant,
     for (int i = 0; i < N; ++i) orc_coarse_prop(pb, q_all + (long)i * d, q_all + (long)(i + 1) * d);
 
     for (int k = 0; k < K; ++k) {
-        /* parallel predictor: q~_{i+1}^k = F(q_i^k) */
+        /* parallel predictor: q~_{i+1}^k = F(q_i^k), one slice per iteration of
+         * an OpenMP loop as in the paper's implementation when threads > 1 */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads) if (g_threads > 1)
         for (int i = 0; i < N; ++i) orc_fine_prop(pb, q_all + (long)i * d, qt + (long)i * d);
         /* subspace update S^{k-1} -> S^k with q_i^k and their images */
         if (variant == 0) {

@@ -67,6 +67,12 @@ int orc_parareal(const orc_problem* pb, const double* q0, int K, int variant,
 /* q_all[n] = F^n(q0), n = 0..N (serial fine reference). */
 void orc_serial_fine(const orc_problem* pb, const double* q0, double* q_all);
 
+/* Threads for the parallel predictor of Alg. 2 (the loop over slices that
+ * the paper runs with OpenMP, Sec. 2.1 and Sec. 3.2): 1 (the default) runs it
+ * serially.  Each slice's fine propagation is independent, so the results do
+ * not depend on the thread count.  Returns the previous value. */
+int orc_set_threads(int n);
+
 #ifdef __cplusplus
 }
 #endif

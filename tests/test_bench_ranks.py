@@ -69,3 +69,14 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_config_matches_gpu_arm():
+    """Both arms describe the workload with the same config object."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    wl = W.workload_medium()
+    c = bench.workload_config(wl, 1, wl.K, len(wl.ics))
+    assert c["workload"] == wl.name and c["K"] == wl.K and c["solves_per_step"] == 3
+    assert {"grid", "N_slices", "krylov_cap", "n_f", "n_g", "ics", "fine_prec", "l2", "parallelism"} <= set(c)

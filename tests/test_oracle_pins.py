@@ -624,3 +624,17 @@ def test_paper_table2_needs_short_acoustic_steps():
         eps[ns] = float(np.linalg.norm(res["qT"] - qs) / np.linalg.norm(qs))
     assert eps[4] > 2.0, eps
     assert 0.5 * printed < eps[16] < 2.0 * printed, (eps, printed)
+
+
+def test_parallel_predictor_threads_do_not_change_results():
+    """The OpenMP loop over slices of the parallel predictor (Sec. 2.1) gives
+    the serial oracle's iterates bit for bit."""
+    p = W.make_problem(64, 32, 8)
+    q0 = W.ic_gaussian(64, 32, seed=0).ravel()
+    a = oracle.parareal(p, q0, 3)
+    old = oracle.set_threads(4)
+    try:
+        b = oracle.parareal(p, q0, 3)
+    finally:
+        oracle.set_threads(old)
+    assert np.array_equal(a["q"], b["q"]) and np.array_equal(a["r"], b["r"])
