@@ -63,7 +63,9 @@ def test_static_fine_sweep_matches_handle_twice(prec, V):
         torch.cuda.synchronize()
         got = y.cpu().numpy()
         assert np.all(np.isfinite(got))
-        assert _rel(got, want[call]) < TOL64
+        # FP64: the same kernel arithmetic; FP32: the handle may run the
+        # row-streamed kernel (packed pair arithmetic, other rounding order)
+        assert _rel(got, want[call]) < (TOL64 if prec == 0 else TOL32)
         xin = x.cpu().numpy()
         for i in (0, n - 1):
             ref = oracle.fine_prop(p, xin[i])
