@@ -90,7 +90,11 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
     const long rpb = ((d + nb - 1) / nb + 31) / 32 * 32;   // rows per CTA, a multiple of 32
     const long r0 = min(d, (long)b * rpb), r1 = min(d, r0 + rpb);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = CH_NT / 32;
-    const int ncols = A.r_dev ? *A.r_dev : 0;
+    int ncols = A.r_dev ? *A.r_dev : 0;
+    if (ncols < 0 || ncols > A.ccap) {   // cannot happen: the rank never exceeds the cap
+        if (threadIdx.x == 0) atomicExch(&A.gb->err, 2);
+        return;
+    }
     const int ntx = (A.nx + CH_TX - 1) / CH_TX, nty = (A.ny + CH_TY - 1) / CH_TY, ntiles = ntx * nty;
     const int cpb = (ncols + (int)nb - 1) / (int)nb;
     const T* Qm = F32 ? reinterpret_cast<const T*>(A.Q32) : reinterpret_cast<const T*>(A.Q);

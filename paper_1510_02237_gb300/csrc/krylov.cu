@@ -20,9 +20,12 @@ constexpr int TN_KT = 32;     // rows per shared-memory tile
 constexpr int GV_CB = 64;     // columns of A per CTA (gemv_tn)
 constexpr int NN_JB = 16;     // output columns per thread (gemm_nn)
 
-__device__ __forceinline__ int cols_avail(const int* c0_dev, const int* c1_dev) {
+// Columns [c0, c1) read from device memory, clamped to [0, ccap] (the
+// buffers and shared-memory tiles hold ccap columns).
+__device__ __forceinline__ int cols_avail(const int* c0_dev, const int* c1_dev, int ccap) {
     int c0 = c0_dev ? *c0_dev : 0;
-    return *c1_dev - c0;
+    const int n = *c1_dev - c0;
+    return n < 0 ? 0 : (n > ccap ? ccap : n);
 }
 
 // partial[chunk][c * m + j] = sum over the chunk's rows of A[row, c0 + c] * X[row, j]
@@ -33,7 +36,7 @@ __global__ void __launch_bounds__(256) k_gemm_tn_partial(const double* __restric
                                                          double* __restrict__ partial) {
     __shared__ double As[TN_KT][TN_CB + 1];
     __shared__ double Xs[TN_KT][TN_JB + 1];
-    const int ncols = cols_avail(c0_dev, c1_dev);
+    const int ncols = cols_avail(c0_dev, c1_dev, ccap);
     const int c0 = c0_dev ? *c0_dev : 0;
     const int cb = blockIdx.y * TN_CB, jb = blockIdx.z * TN_JB;
     if (cb >= ncols) return;
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(256) k_gemv_tn_partial(const double* __restric
                                                          const double* __restrict__ x, long nrows,
                                                          int rpc, int ccap, double* __restrict__ partial) {
     extern __shared__ double xs[];
-    const int ncols = cols_avail(c0_dev, c1_dev);
+    const int ncols = cols_avail(c0_dev, c1_dev, ccap);
     const int c0 = c0_dev ? *c0_dev : 0;
     const int cb = blockIdx.y * GV_CB;
     if (cb >= ncols) return;
@@ -106,8 +109,8 @@ __global__ void __launch_bounds__(256) k_gemv_tn_partial(const double* __restric
 // out[idx] = sum_chunk partial[chunk][idx], idx < n_dev_cols * m (fixed chunk order)
 __global__ void k_reduce_chunks(const double* __restrict__ partial, int nchunk, long pstride,
                                 const int* c0_dev, const int* c1_dev, int m, double* __restrict__ out,
-                                int ldo) {
-    const int ncols = c1_dev ? cols_avail(c0_dev, c1_dev) : 1;
+                                int ldo, int ccap) {
+    const int ncols = c1_dev ? cols_avail(c0_dev, c1_dev, ccap) : 1;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= ncols * m) return;
     double s = 0.0;
@@ -121,9 +124,9 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ A, l
                                                  const int* c0_dev, const int* c1_dev,
                                                  const double* __restrict__ C, int ldc,
                                                  const double* B, long ldb, double* Y, long ldy,
-                                                 int m, long nrows, double sgn) {
-    extern __shared__ double Cs[];   // ncap x NN_JB
-    const int ncols = cols_avail(c0_dev, c1_dev);
+                                                 int m, long nrows, double sgn, int ccap) {
+    extern __shared__ double Cs[];   // ccap x NN_JB
+    const int ncols = cols_avail(c0_dev, c1_dev, ccap);
     const int c0 = c0_dev ? *c0_dev : 0;
     const int jb = blockIdx.y * NN_JB;
     const int nj = min(NN_JB, m - jb);
@@ -531,7 +534,7 @@ cudaError_t gemm_tn(const double* A, long lda, const int* c0_dev, const int* c1_
         count_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_reduce_chunks<<<cdiv(ccap, 256), 256, 0, s>>>(w.partial, nchunk, ccap, c0_dev, c1_dev, 1, C, ldc);
+        k_reduce_chunks<<<cdiv(ccap, 256), 256, 0, s>>>(w.partial, nchunk, ccap, c0_dev, c1_dev, 1, C, ldc, ccap);
         count_launches(1);
         return cudaGetLastError();
     }
@@ -543,7 +546,7 @@ cudaError_t gemm_tn(const double* A, long lda, const int* c0_dev, const int* c1_
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_chunks<<<cdiv((long)ccap * m, 256), 256, 0, s>>>(w.partial, nchunk, (long)ccap * m, c0_dev,
-                                                            c1_dev, m, C, ldc);
+                                                            c1_dev, m, C, ldc, ccap);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -556,7 +559,7 @@ cudaError_t gemm_nn(const double* A, long lda, const int* c0_dev, const int* c1_
     cudaError_t e = allow_max_dynamic_smem((const void*)k_gemm_nn);
     if (e != cudaSuccess) return e;
     dim3 grid(cdiv(nrows, 256), cdiv(m, NN_JB));
-    k_gemm_nn<<<grid, 256, smem, s>>>(A, lda, c0_dev, c1_dev, C, ldc, B, ldb, Y, ldy, m, nrows, sgn);
+    k_gemm_nn<<<grid, 256, smem, s>>>(A, lda, c0_dev, c1_dev, C, ldc, B, ldb, Y, ldy, m, nrows, sgn, ccap);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -569,7 +572,7 @@ cudaError_t colnorm2(const double* X, long ldx, int m, long nrows, double* out, 
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_reduce_chunks<<<cdiv(m, 256), 256, 0, s>>>(w.partial, nchunk, m, nullptr, nullptr, m, out, 1);
+    k_reduce_chunks<<<cdiv(m, 256), 256, 0, s>>>(w.partial, nchunk, m, nullptr, nullptr, m, out, 1, 1);
     count_launches(1);
     return cudaGetLastError();
 }

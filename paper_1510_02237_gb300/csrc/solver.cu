@@ -484,6 +484,7 @@ static void timing_free(pr_solver* h) {
 static pr_status check_device_waits(pr_solver* h) {
     int err = 0;
     CKC(cudaMemcpy(&err, &h->gbar->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err == 2) return set_err(h, PR_ECUDA, "the serial chain read a basis rank above the cap; results invalid");
     if (err) return set_err(h, PR_ETIMEOUT, "a grid barrier wait gave up; results of this handle are invalid");
     if (h->opt.fine_prec != PR_FP64 && fine_rows_wait_error(false) > 0)
         return set_err(h, PR_ETIMEOUT, "a fine-sweep row-load wait gave up; FP32 fine sweeps since then are invalid");
