@@ -232,8 +232,11 @@ int chain_grid(int H, int ccap) {
     if (memo.get(dev, &k0, &blocks) && k0 == key) return blocks;
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (allow_max_dynamic_smem((const void*)k_chain<DELTA, T>) != cudaSuccess) return 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain<DELTA, T>, CH_NT, key);
+    {
+        std::lock_guard<std::mutex> lk(smem_launch_lock());
+        if (set_dynamic_smem((const void*)k_chain<DELTA, T>, key) != cudaSuccess) return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain<DELTA, T>, CH_NT, key);
+    }
     blocks = per >= 1 ? sms : 0;
     memo.put(dev, key, blocks);
     return blocks;
@@ -252,12 +255,13 @@ cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s) {
     const size_t smem = chain_smem_bytes(a.H, a.ccap, f32);
     const void* fn = f32 ? (const void*)k_chain<true, float>
                          : (d64 ? (const void*)k_chain<true, double> : (const void*)k_chain<false, double>);
-    cudaError_t e = allow_max_dynamic_smem(fn);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(&a.gb->count, 0, sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(&a.gb->count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     ChainArgs arg = a;
     void* args[] = {&arg};
+    std::lock_guard<std::mutex> lk(smem_launch_lock());
+    e = set_dynamic_smem(fn, smem);
+    if (e != cudaSuccess) return e;
     e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(CH_NT), args, smem, s);
     count_launches(1);
     return e;

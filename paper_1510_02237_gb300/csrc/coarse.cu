@@ -34,7 +34,8 @@ cudaError_t launch_shape(const double* in, double* out, long stride, int n, int 
                          int H, cudaStream_t s, const SliceMap& map) {
     const dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, n);
     const size_t smem = sizeof(T) * coarse_tile_smem_elems<TX, TY>(H);
-    cudaError_t e = allow_max_dynamic_smem((const void*)k_coarse_step<TX, TY, NT, T>);
+    std::lock_guard<std::mutex> lk(smem_launch_lock());
+    cudaError_t e = set_dynamic_smem((const void*)k_coarse_step<TX, TY, NT, T>, smem);
     if (e != cudaSuccess) return e;
     k_coarse_step<TX, TY, NT, T><<<grid, NT, smem, s>>>(in, out, stride, nx, ny, c, H, map);
     count_launches(1);

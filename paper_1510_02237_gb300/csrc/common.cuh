@@ -7,35 +7,20 @@
 
 #include <atomic>
 #include <mutex>
-#include <set>
-#include <utility>
 
 namespace pr {
 
-// Raise kernel fn's dynamic shared-memory limit to the current device's
-// opt-in maximum, once per (kernel, device).  The limit is process-wide per
-// kernel; setting it to one fixed value (instead of each launch's own size)
-// means no host thread can lower it between another thread's set and launch.
-inline cudaError_t allow_max_dynamic_smem(const void* fn) {
-    static std::mutex mu;
-    static std::set<std::pair<const void*, int>> done;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lock(mu);
-    if (done.count({fn, dev})) return cudaSuccess;
-    int optin = 0;
-    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
-    int stat = 0;
-    cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, fn);
-    if (e != cudaSuccess) return e;
-    stat = (int)fa.sharedSizeBytes;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - stat);
-    if (e != cudaSuccess) return e;
-    done.insert({fn, dev});
-    return cudaSuccess;
+// Kernels whose dynamic shared memory depends on the problem set the
+// process-wide per-kernel limit to the launch's own size right before the
+// launch.  Both happen under this lock, so a concurrent host thread (one
+// handle per thread) cannot lower the limit between another thread's set and
+// its launch.
+inline std::mutex& smem_launch_lock() {
+    static std::mutex m;
+    return m;
+}
+inline cudaError_t set_dynamic_smem(const void* fn, size_t bytes) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 // Count n kernel launches (process-wide, reported by parareal_kernel_launches).

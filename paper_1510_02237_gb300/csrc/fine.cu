@@ -179,7 +179,8 @@ cudaError_t launch_tile(const Tin* in, long instride, Tout* out, long outstride,
     constexpr int RX = TX + 18, RY = TY + 6 * RYH;
     constexpr size_t smem = sizeof(T) * 6 * RX * RY;
     auto kern = k_fine_step<T, Tin, Tout, RYH, TX, TY, NT, ACC64>;
-    cudaError_t e = allow_max_dynamic_smem((const void*)kern);
+    std::lock_guard<std::mutex> lk(smem_launch_lock());
+    cudaError_t e = set_dynamic_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, n);
     kern<<<grid, NT, smem, s>>>(in, instride, out, outstride, nx, ny, c, map);

@@ -8,8 +8,19 @@
 //   6th-order centred advection difference, 2nd-order centred acoustics and
 //   the compact grad-div damping (Sec. 3.2, Eq. dampingCoeff).
 // c_k is folded into every coefficient, so each term costs one FMA.
-// Work items are 32-cell segments of grid rows, one per warp (lanes along x,
-// coalesced); each CTA owns a contiguous range of them.
+//
+// GB300 issues FP64 arithmetic at 1/64 of the FP32 rate (one warp
+// instruction per ~64 cycles per SM sub-partition), while shuffles, loads and
+// integer work issue at full rate: the FP64 instruction count per cell is the
+// cost, everything else is nearly free.  Constant velocity with V = 0 (the
+// benchmark problems) runs k_fine_march: every warp walks down a contiguous
+// range of rows of 32-column segments (lane = column), x-neighbours come by
+// shuffles from the lane values and a 6-cell halo held by lanes 0..5, and
+// the x-differences of u and w are computed once per row and reused by the
+// rows above and below (the cross terms of the damping are differences of
+// them), 33 FP64 instructions per cell and stage.  Rows are split evenly over
+// all warps of the grid, so every SM sub-partition gets the same work.
+// V != 0 and the rotation run k_fine_coop<true> on 32-cell work items.
 #include "grid_barrier.cuh"
 
 namespace pr {
@@ -124,6 +135,177 @@ __global__ void __launch_bounds__(FC_NT) k_fine_coop(FineSweepArgs a) {
     }
 }
 
+// ------------------------------------------------------------ V = 0 marching
+
+constexpr int FM_NT = 256;   // 8 warps per CTA, one CTA per SM
+
+// One field of one row around the lane's column: the lane's own value and a
+// halo value (lanes 0..2: columns x0-3..x0-1, lanes 3..5: x0+nv..x0+nv+2,
+// periodic); at(k) is the value at column x+k, k = -3..3.
+struct Fld {
+    double own, halo;
+};
+struct RowV {
+    Fld u, w, p;
+};
+
+__device__ __forceinline__ double at(const Fld& f, int lane, int k, int nv) {
+    const int src = lane + k;
+    const double a = __shfl_sync(0xffffffffu, f.own, src & 31);
+    const double h = __shfl_sync(0xffffffffu, f.halo, (src < 0 ? src + 3 : src - nv + 3) & 31);
+    return (src >= 0 && src < nv) ? a : h;
+}
+
+__device__ __forceinline__ RowV load_row(const double* in, long r, long ncell, int xo, int xh, bool hl) {
+    RowV v;
+    v.u.own = in[r + xo];
+    v.w.own = in[ncell + r + xo];
+    v.p.own = in[2 * ncell + r + xo];
+    v.u.halo = hl ? in[r + xh] : 0.0;
+    v.w.halo = hl ? in[ncell + r + xh] : 0.0;
+    v.p.halo = hl ? in[2 * ncell + r + xh] : 0.0;
+    return v;
+}
+
+// Stage k on the rows [g0, g1) of the batch's row segments (index
+// ((slice * nseg) + segment) * ny + y): out = qn + c_k L(in).  in, qn and out
+// are written by other CTAs earlier in the same launch (ordered by the grid
+// barriers), so they are read through the coherent path: no __restrict__.
+__device__ __forceinline__ void stage_march(const double* in, const double* qn, double* out, long d, int nx, int ny,
+                                            int nseg, long g0, long g1, const FineCoefK& c, int k) {
+    const int lane = threadIdx.x & 31;
+    const long ncell = (long)nx * ny;
+    const double A = c.adx[k], Bx = c.csx[k], By = c.csy[k], Cx = c.dxx[k], Ex = c.dxy1[k], Cy = c.dyy[k],
+                 Ey = c.dxy2[k];
+    // u's x-terms on raw neighbours: A (6-point difference) + Cx (u[x+1] - 2u + u[x-1])
+    const double up1 = 45.0 * A + Cx, um1 = Cx - 45.0 * A, up2 = -9.0 * A, um2 = 9.0 * A, u00 = -2.0 * Cx;
+    const double A45 = 45.0 * A, Am9 = -9.0 * A, Cy2 = -2.0 * Cy;
+    for (long g = g0; g < g1;) {
+        const long col = g / ny;
+        const int y0 = (int)(g - col * ny);
+        const int y1 = (int)min((long)ny, (long)y0 + (g1 - g));
+        g += y1 - y0;
+        const int z = (int)(col / nseg), sg = (int)(col - (long)z * nseg);
+        const int x0 = 32 * sg, nv = min(32, nx - x0);
+        const int xo = x0 + (lane < nv ? lane : 0);
+        const bool hl = lane < 6;
+        const int xh = lane < 3 ? pwrap(x0 - 3 + lane, nx) : pwrap(x0 + nv + lane - 3, nx);
+        const double* src = in + (long)z * d;
+        const double* qz = qn + (long)z * d;
+        double* dz = out + (long)z * d;
+        // row above the range (only its x-differences and w, p are used) and the first row
+        const RowV m = load_row(src, (long)pwrap(y0 - 1, ny) * nx, ncell, xo, xh, hl);
+        double d1u_m = at(m.u, lane, 1, nv) - at(m.u, lane, -1, nv);
+        double d1w_m = at(m.w, lane, 1, nv) - at(m.w, lane, -1, nv);
+        double w_m = m.w.own, p_m = m.p.own;
+        RowV cr = load_row(src, (long)y0 * nx, ncell, xo, xh, hl);
+        double d1u_c = at(cr.u, lane, 1, nv) - at(cr.u, lane, -1, nv);
+        double d1w_c = at(cr.w, lane, 1, nv) - at(cr.w, lane, -1, nv);
+        // loads run one row ahead of their use: the row below the centre row
+        // and q^n of the centre row are in registers when an iteration starts
+        RowV nx_ = load_row(src, (long)(y0 + 1 < ny ? y0 + 1 : y0 + 1 - ny) * nx, ncell, xo, xh, hl);
+        long rc = (long)y0 * nx + xo;
+        double qu = qz[rc], qw = qz[ncell + rc], qp = qz[2 * ncell + rc];
+        for (int y = y0; y < y1; ++y) {
+            const int y2 = pwrap(y + 2, ny);
+            const RowV nn = load_row(src, (long)y2 * nx, ncell, xo, xh, hl);
+            const long rn = (long)(y + 1 < ny ? y + 1 : y + 1 - ny) * nx + xo;
+            const double qu_n = qz[rn], qw_n = qz[ncell + rn], qp_n = qz[2 * ncell + rn];
+            const double d1u_n = at(nx_.u, lane, 1, nv) - at(nx_.u, lane, -1, nv);
+            const double d1w_n = at(nx_.w, lane, 1, nv) - at(nx_.w, lane, -1, nv);
+            // x-windows of the centre row
+            const double u1 = at(cr.u, lane, 1, nv), um1v = at(cr.u, lane, -1, nv);
+            const double u2 = at(cr.u, lane, 2, nv), um2v = at(cr.u, lane, -2, nv);
+            const double u3 = at(cr.u, lane, 3, nv), um3v = at(cr.u, lane, -3, nv);
+            const double d1p = at(cr.p, lane, 1, nv) - at(cr.p, lane, -1, nv);
+            const double d2p = at(cr.p, lane, 2, nv) - at(cr.p, lane, -2, nv);
+            const double d3p = at(cr.p, lane, 3, nv) - at(cr.p, lane, -3, nv);
+            const double d2w = at(cr.w, lane, 2, nv) - at(cr.w, lane, -2, nv);
+            const double d3w = at(cr.w, lane, 3, nv) - at(cr.w, lane, -3, nv);
+            const double dwy = nx_.w.own - w_m, dpy = nx_.p.own - p_m;
+            const double crw = d1w_n - d1w_m, cru = d1u_n - d1u_m;
+            double nu = fma(up1, u1, qu);
+            nu = fma(um1, um1v, nu);
+            nu = fma(up2, u2, nu);
+            nu = fma(um2, um2v, nu);
+            nu = fma(A, u3, nu);
+            nu = fma(-A, um3v, nu);
+            nu = fma(u00, cr.u.own, nu);
+            nu = fma(Bx, d1p, nu);
+            nu = fma(Ex, crw, nu);
+            double nw = fma(A45, d1w_c, qw);
+            nw = fma(Am9, d2w, nw);
+            nw = fma(A, d3w, nw);
+            nw = fma(By, dpy, nw);
+            nw = fma(Cy, nx_.w.own, nw);
+            nw = fma(Cy, w_m, nw);
+            nw = fma(Cy2, cr.w.own, nw);
+            nw = fma(Ey, cru, nw);
+            double np = fma(A45, d1p, qp);
+            np = fma(Am9, d2p, np);
+            np = fma(A, d3p, np);
+            np = fma(Bx, d1u_c, np);
+            np = fma(By, dwy, np);
+            if (lane < nv) {
+                dz[rc] = nu;
+                dz[ncell + rc] = nw;
+                dz[2 * ncell + rc] = np;
+            }
+            w_m = cr.w.own;
+            p_m = cr.p.own;
+            d1u_m = d1u_c;
+            d1w_m = d1w_c;
+            cr = nx_;
+            nx_ = nn;
+            d1u_c = d1u_n;
+            d1w_c = d1w_n;
+            rc = rn;
+            qu = qu_n;
+            qw = qw_n;
+            qp = qp_n;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(FM_NT) k_fine_march(FineSweepArgs a) {
+    const unsigned nb = gridDim.x;
+    const long d = 3L * a.nx * a.ny;
+    const int nseg = (a.nx + 31) >> 5;
+    const long rows = (long)a.n * nseg * a.ny;
+    const long W = (long)gridDim.x * (FM_NT / 32);
+    const long gw = (long)blockIdx.x * (FM_NT / 32) + (threadIdx.x >> 5);
+    const long g0 = rows * gw / W, g1 = rows * (gw + 1) / W;
+    const double* cur = a.in;
+    for (int t = 0; t < a.nsteps; ++t) {
+        double* s1 = (cur == a.w1) ? a.w2 : a.w1;
+        double* s2 = a.w3;
+        double* dst = (t == a.nsteps - 1) ? a.out : s1;
+        const double* srcs[3] = {cur, s1, s2};
+        double* dsts[3] = {s1, s2, dst};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            stage_march(srcs[k], cur, dsts[k], d, a.nx, a.ny, nseg, g0, g1, a.c, k);
+            if (t == a.nsteps - 1 && k == 2) break;   // kernel end publishes the result
+            if (!grid_barrier(a.gb, nb)) return;
+        }
+        cur = dst;
+    }
+}
+
+int march_blocks(int max_sms) {
+    static DevMemo memo;   // [device] -> (SMs, CTAs per SM)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int nsm = 0, per = 0;
+    if (!memo.get(dev, &nsm, &per)) {
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fine_march, FM_NT, 0);
+        memo.put(dev, nsm, per);
+    }
+    if (per < 1) return -1;
+    return max_sms > 0 && max_sms < nsm ? max_sms : nsm;   // one CTA per SM
+}
+
 template <bool HV>
 int coop_blocks(int max_sms) {
     static DevMemo memo;   // [device] -> (SMs, CTAs per SM)
@@ -167,14 +349,14 @@ FineCoefK make_fine_coef_k(double U, double V, double cs, double dx, double dy, 
 }
 
 cudaError_t fine_sweep_coop(const FineSweepArgs& a, bool has_v, cudaStream_t s) {
-    const int nb = has_v ? coop_blocks<true>(a.max_sms) : coop_blocks<false>(a.max_sms);
+    const int nb = has_v ? coop_blocks<true>(a.max_sms) : march_blocks(a.max_sms);
     if (nb < 1) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaMemsetAsync(&a.gb->count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     FineSweepArgs arg = a;
     void* args[] = {&arg};
-    const void* fn = has_v ? (const void*)k_fine_coop<true> : (const void*)k_fine_coop<false>;
-    e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(FC_NT), args, 0, s);
+    const void* fn = has_v ? (const void*)k_fine_coop<true> : (const void*)k_fine_march;
+    e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(has_v ? FC_NT : FM_NT), args, 0, s);
     count_launches(1);
     return e;
 }

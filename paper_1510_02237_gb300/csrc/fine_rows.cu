@@ -458,7 +458,8 @@ cudaError_t launch_nw(const Tin* in, long instride, Tout* out, long outstride, i
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     auto kern = k_fine_rows<NW, Tin, Tout>;
-    e = allow_max_dynamic_smem((const void*)kern);
+    std::lock_guard<std::mutex> lk(smem_launch_lock());
+    e = set_dynamic_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
     int sms = 0, per = 0;
     if (!memo.get(dev, &sms, &per)) {

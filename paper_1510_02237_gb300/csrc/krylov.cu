@@ -556,7 +556,8 @@ cudaError_t gemm_nn(const double* A, long lda, const int* c0_dev, const int* c1_
                     long nrows, double sgn, cudaStream_t s) {
     if (m <= 0 || ccap <= 0) return cudaSuccess;
     const size_t smem = sizeof(double) * (size_t)ccap * NN_JB;
-    cudaError_t e = allow_max_dynamic_smem((const void*)k_gemm_nn);
+    std::lock_guard<std::mutex> lk(smem_launch_lock());
+    cudaError_t e = set_dynamic_smem((const void*)k_gemm_nn, smem);
     if (e != cudaSuccess) return e;
     dim3 grid(cdiv(nrows, 256), cdiv(m, NN_JB));
     k_gemm_nn<<<grid, 256, smem, s>>>(A, lda, c0_dev, c1_dev, C, ldc, B, ldb, Y, ldy, m, nrows, sgn, ccap);

@@ -658,7 +658,8 @@ int sm_count() {
 }
 
 cudaError_t launch_mma(const CUtensorMap* A, const CUtensorMap& B2, const SgArgs& a, dim3 grid, cudaStream_t s) {
-    const cudaError_t attr = allow_max_dynamic_smem((const void*)k_split_mma);
+    std::lock_guard<std::mutex> lk(smem_launch_lock());
+    const cudaError_t attr = set_dynamic_smem((const void*)k_split_mma, SG_DSMEM);
     if (attr != cudaSuccess) return attr;
     k_split_mma<<<grid, SG_THREADS, SG_DSMEM, s>>>(A[0], A[1], A[2], A[3], B2, a);
     count_launches(1);
@@ -720,7 +721,7 @@ cudaError_t sg_init(SplitGemm* g, long d, int cap) {
     SG_ALLOC(g->ws, sizeof(double) * (size_t)g->grid * cp * SG_N);
     SG_ALLOC(g->C, sizeof(double) * (size_t)SG_N * cp);
 #undef SG_ALLOC
-    const cudaError_t attr = allow_max_dynamic_smem((const void*)k_finish);
+    const cudaError_t attr = set_dynamic_smem((const void*)k_finish, 16384 * sizeof(double));
     if (attr != cudaSuccess) {
         sg_free(g);
         return attr;

@@ -1,16 +1,18 @@
 """The benchmark workload (256x128, N = 32, K = 6, cap 192, three seeded ICs)
-against oracle reference values stored by tests/golden/make_oracle_reference.py.
+against the oracle's stored results (tests/golden/make_oracle_reference.py).
 
-Forming F(Q) by linearity (Eq. Genhance) divides rounding errors by the
-residual ratios |R_jj|/||a_j|| of the new columns, and the errors compound
-from column to column.  Where every kept ratio of the iterations that feed a
-correction is >= 1e-3 (the Gaussian IC) the GPU's FP64 solve must reproduce
-the oracle: r^k to 1e-9 relative, q_N^K samples to 1e-11 of ||q_N||.  The
-filtered-noise IC's last iterations keep ratios down to 3e-4 (r^k to 1e-6).
-The Fourier IC keeps ratios down to 5e-6 from the first iteration on, so two
-correct FP64 evaluations of the method legitimately drift apart; for it the
-results must be finite, of the oracle's size, and the error against the
-serial fine solution within a decade of the oracle's.
+The element-by-element bound is derived from the oracle itself.  Forming
+F(Q) by linearity (Eq. Genhance) divides rounding errors by the residual
+ratios |R_jj|/||a_j|| of the new columns, and the errors compound from
+column to column, so how well FP64 arithmetic determines q_N^K depends on
+the initial value.  The golden file records the oracle's own spread: the
+relative l2 change of q_N^K when every entry of the initial value moves by
+one unit in the last place (1.5e-13 for the Gaussian IC, 8e-11 for the
+filtered noise, 9e-4 for the 8-mode Fourier IC, whose iterates are nearly
+dependent).  The GPU evaluates the same formulas with its own rounding in
+every operation and its own summation order; its q_N^K must agree with the
+oracle's, over all 98 304 entries, to 10 times that spread or to 1e-12
+relative, whichever is larger.  Ranks must agree exactly.
 """
 from __future__ import annotations
 
@@ -52,6 +54,9 @@ def _solve(p, q0, K, cap, **opt):
         return out.cpu().numpy(), qs.cpu().numpy(), rep
 
 
+QN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_256x128_N32_K6_qN.npz")
+
+
 @pytest.mark.parametrize("proj", [0, 1], ids=["proj_fp64", "proj_split_bf16"])
 @pytest.mark.parametrize("ic", [0, 1, 2], ids=["gaussian+noise", "fourier8", "filtered_noise16"])
 def test_fp64_solve_against_oracle_reference(ref, ic, proj):
@@ -61,27 +66,16 @@ def test_fp64_solve_against_oracle_reference(ref, ic, proj):
     p = wl.problem
     name, f = wl.ics[ic]
     R = ref["ics"][name]
+    want = np.load(QN)[name]
     idx = np.array(ref["sample_indices"])
     got, qs, rep = _solve(p, f().ravel(), wl.K, wl.krylov_cap, proj_prec=proj)
-    r = np.array(rep.r[:wl.K])
     assert list(rep.rank[:wl.K]) == R["rank"]
     # the serial fine solution is well conditioned: always within 1e-12
     assert np.max(np.abs(qs[idx] - np.array(R["qseq_sample"]))) < 1e-12 * R["qseq_norm"]
-    # the first iteration's columns (the coarse chain) are the oracle's: same conditioning
-    assert abs(rep.min_ratio[0] - R["min_kept_ratio"][0]) < 1e-4 * R["min_kept_ratio"][0]
-    worst = min(R["min_kept_ratio"][:wl.K - 1])
-    if worst >= 1e-4:
-        assert np.allclose(np.array(rep.min_ratio[:wl.K]), R["min_kept_ratio"], rtol=1e-3)
-    if worst >= 1e-3:
-        assert np.allclose(r, R["r"], rtol=1e-9, atol=0)
-        assert np.max(np.abs(got[idx] - np.array(R["qN_sample"]))) < 1e-11 * R["qN_norm"]
-    elif worst >= 1e-4:
-        assert np.allclose(r, R["r"], rtol=1e-6, atol=0)
-        assert np.max(np.abs(got[idx] - np.array(R["qN_sample"]))) < 1e-7 * R["qN_norm"]
-    else:
-        assert np.all(np.isfinite(got)) and np.linalg.norm(got) < 10 * R["qN_norm"]
-        eps = np.linalg.norm(got - qs) / np.linalg.norm(qs)
-        assert 0.1 * R["eps"] < eps < 10 * R["eps"]
+    assert np.array_equal(want[idx], np.array(R["qN_sample"]))          # the two golden files agree
+    spread = max(s["qN_rel_l2"] for s in R["spread_1ulp"])
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= max(1e-12, 10.0 * spread), (err, spread)
 
 
 @pytest.mark.parametrize("ic", [0, 1, 2], ids=["gaussian+noise", "fourier8", "filtered_noise16"])
