@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream sweep")
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="requests of the saturated serving rate (the others use 300)")
     ap.add_argument("--case", choices=["fine", "fine32", "fine32x", "solve", "solve_mixed"], default=None,
                     help="small isolated case for profiler captures: 'fine' = three fine sweeps over all "
                          "32 slices of the 256x128 workload; 'fine32' = three FP32 fine sweeps over the 64 "
@@ -325,19 +327,56 @@ def batching_workload(P, torch):
     return res
 
 
-def serving_workload(P, torch, rates=(10, 30, 100, 300, 1000), n_req=120):
+def served_accuracy(P, torch, reqs, results, max_shapes=8):
+    """Equal-accuracy check of served results: for one request of each of up
+    to max_shapes problem shapes, the plain FP64 solve of the same request on
+    a handle of its own, both errors against the serial fine solution (N FP64
+    fine sweeps, Eq. errorDef) and |eps_served - eps_fp64|."""
+    seen, out = set(), []
+    for (t, inst), r in zip(reqs, results):
+        p = inst.problem
+        key = (p.nx, p.ny, p.n_slices)
+        if key in seen or r is None:
+            continue
+        seen.add(key)
+        q0 = torch.from_numpy(inst.initial_value().ravel()).cuda()
+        with P.Solver(p, stream=torch.cuda.current_stream(), K_max=inst.K) as s:
+            ref = torch.empty_like(q0)
+            P.parareal_solve(s.h, q0, inst.K, qT=ref, report=False)
+            qs = serial_fine_gpu(P, s, q0, p.n_slices)
+            torch.cuda.synchronize()
+        got = torch.from_numpy(r.qT).cuda()
+        e_s, e_r = rel_l2(got, qs), rel_l2(ref, qs)
+        out.append({"shape": f"{p.nx}x{p.ny}_N{p.n_slices}_K{inst.K}", "ic": inst.ic, "eps_served": e_s,
+                    "eps_fp64": e_r, "abs_diff": abs(e_s - e_r), "qT_rel_diff": rel_l2(got, ref)})
+        if len(out) >= max_shapes:
+            break
+    return {"per_shape": out, "max_abs_eps_diff": max(o["abs_diff"] for o in out) if out else None}
+
+
+def serving_workload(P, torch, n_sat=2000, n_low=300):
     """Poisson request streams (seed 7) of solves with grids 64x32..512x256,
-    N 8..64, K 1..5, served in mixed precision with continuous batching under a
-    150 GB footprint budget; per rate the p50/p99 latency (arrival to result in
-    host memory) and the completed solves per second."""
+    N 8..64, K 1..5, served with continuous batching under a 150 GB footprint
+    budget; per rate the p50/p99 latency (arrival to result in host memory)
+    and the completed solves per second.  Mode 'fp64_tc' (the equal-accuracy
+    served form: FP64 fine sweep and correction, subspace products on the BF16
+    tensor cores with exact split digits) at 10, 100 and 1000 requests/s
+    (n_low, n_low and n_sat requests); mode 'mixed' (FP32 tendencies and
+    correction in addition) at 1000 requests/s.  Each mode reports the
+    equal-accuracy check of a sample of its served results."""
     from paper_1510_02237_gb300 import serve
-    out = {"requests_per_rate": n_req, "budget_bytes": 150e9, "mode": "mixed", "rates": {}}
-    srv = serve.Server(budget_bytes=150e9, max_inflight=16, mode="mixed")
-    srv.run(W.request_stream(1000.0, 8, seed=99))          # create slots untimed
-    for lam in rates:
-        _, st = srv.run(W.request_stream(float(lam), n_req, seed=7))
-        out["rates"][str(lam)] = st.summary()
-    srv.close()
+    out = {"budget_bytes": 150e9, "modes": {}}
+    for mode, plan in (("fp64_tc", ((10, n_low), (100, n_low), (1000, n_sat))), ("mixed", ((1000, n_low),))):
+        srv = serve.Server(budget_bytes=150e9, max_inflight=16, mode=mode)
+        srv.run(W.request_stream(1000.0, 8, seed=99))          # create slots untimed
+        res = {"rates": {}}
+        for lam, n_req in plan:
+            reqs = W.request_stream(float(lam), n_req, seed=7)
+            results, st = srv.run(reqs)
+            res["rates"][str(lam)] = dict(st.summary(), requests=n_req)
+        srv.close()
+        res["accuracy"] = served_accuracy(P, torch, reqs, results)
+        out["modes"][mode] = res
     return out
 
 
@@ -637,7 +676,7 @@ def run_ours(args):
         tables = paper_tables(P, torch, stream)
         precision = precision_workload(P, torch, stream)
         batching = batching_workload(P, torch)
-        serving = serving_workload(P, torch) if not args.no_serving else None
+        serving = serving_workload(P, torch, n_sat=args.serving_requests) if not args.no_serving else None
         # ---- roofline of the dominant phase's kernel
         phases = {k: tm[k] / n for k in ("ms_init", "ms_fine", "ms_coarse", "ms_krylov", "ms_gs_block",
                                           "ms_gs_intra", "ms_kold", "ms_chain")}

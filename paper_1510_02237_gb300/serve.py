@@ -82,6 +82,8 @@ class Server:
     def __init__(self, budget_bytes: float = 150e9, max_inflight: int = 16, mode: str = "mixed",
                  sm_limit=default_sm_limit, autotune: bool = True):
         import torch
+        if mode not in self.MODES:
+            raise ValueError(f"mode must be one of {self.MODES}")
         self.torch = torch
         self.budget = float(budget_bytes)
         self.max_inflight = int(max_inflight)
@@ -93,14 +95,23 @@ class Server:
         self.bytes = 0
 
     # ---------------------------------------------------------------- slots
+    MODES = ("fp64", "fp64_tc", "mixed")
+
     def solver_options(self, p) -> dict:
         """Options of the handles this server creates for problem p (also what
-        reproduces a served result with a handle of one's own)."""
+        reproduces a served result with a handle of one's own).
+
+        mode 'fp64': plain FP64.  'fp64_tc': FP64 fine sweep and correction,
+        the subspace products Q^T V and V - Q C on the BF16 tensor cores with
+        FP32 accumulation and exact split digits (FP64-accurate, so the final
+        accuracy equals the plain FP64 solve's).  'mixed': additionally FP32
+        tendencies in the fine sweep and an FP32 correction (fastest; its
+        accuracy depends on the input's conditioning)."""
         opt = {}
         if self.mode == "mixed":
             opt.update(fine_prec=PR_FP32X, corr_prec=PR_FP32)
-            if (3 * p.nx * p.ny) % 8 == 0:
-                opt.update(proj_prec=PR_PROJ_SPLIT_BF16)
+        if self.mode in ("mixed", "fp64_tc") and (3 * p.nx * p.ny) % 8 == 0:
+            opt.update(proj_prec=PR_PROJ_SPLIT_BF16)
         if self.sm_limit:
             opt["sm_limit"] = self.sm_limit(p.d, self.sms)
         return opt
