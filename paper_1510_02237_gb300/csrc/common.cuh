@@ -267,6 +267,10 @@ long chain_resp_elems(int n_slices);
 // and signed as they enter q^n + c_k L.
 struct FineCoefK {
     double adx[3], ady[3], csx[3], csy[3], dxx[3], dxy1[3], dyy[3], dxy2[3];
+    // products of the above used by the V = 0 marching kernel, formed on the
+    // host so the kernel reads them as constant operands: u's x-terms on raw
+    // neighbours (45 A + Cx, Cx - 45 A, -9 A, 9 A, -A, -2 Cx), 45 A, -9 A, -2 Cy
+    double up1[3], um1[3], up2[3], um2[3], um3[3], u00[3], a45[3], am9[3], cy2[3];
     // rotation (Eq. adVel): row j advects with adx + aomx yc(j), column i with
     // ady + aomy xc(i); yc, xc cell-centre coordinates about the domain centre
     double aomx[3], aomy[3];

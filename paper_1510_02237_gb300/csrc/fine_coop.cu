@@ -175,11 +175,12 @@ __device__ __forceinline__ void stage_march(const double* in, const double* qn, 
                                             int nseg, long g0, long g1, const FineCoefK& c, int k) {
     const int lane = threadIdx.x & 31;
     const long ncell = (long)nx * ny;
-    const double A = c.adx[k], Bx = c.csx[k], By = c.csy[k], Cx = c.dxx[k], Ex = c.dxy1[k], Cy = c.dyy[k],
-                 Ey = c.dxy2[k];
+    // k is a compile-time constant after unrolling: the coefficients are
+    // constant operands of the FMAs, not registers
+    const double A = c.adx[k], Bx = c.csx[k], By = c.csy[k], Ex = c.dxy1[k], Cy = c.dyy[k], Ey = c.dxy2[k];
     // u's x-terms on raw neighbours: A (6-point difference) + Cx (u[x+1] - 2u + u[x-1])
-    const double up1 = 45.0 * A + Cx, um1 = Cx - 45.0 * A, up2 = -9.0 * A, um2 = 9.0 * A, u00 = -2.0 * Cx;
-    const double A45 = 45.0 * A, Am9 = -9.0 * A, Cy2 = -2.0 * Cy;
+    const double up1 = c.up1[k], um1 = c.um1[k], up2 = c.up2[k], um2 = c.um2[k], um3 = c.um3[k], u00 = c.u00[k];
+    const double A45 = c.a45[k], Am9 = c.am9[k], Cy2 = c.cy2[k];
     for (long g = g0; g < g1;) {
         const long col = g / ny;
         const int y0 = (int)(g - col * ny);
@@ -229,7 +230,7 @@ __device__ __forceinline__ void stage_march(const double* in, const double* qn, 
             nu = fma(up2, u2, nu);
             nu = fma(um2, um2v, nu);
             nu = fma(A, u3, nu);
-            nu = fma(-A, um3v, nu);
+            nu = fma(um3, um3v, nu);
             nu = fma(u00, cr.u.own, nu);
             nu = fma(Bx, d1p, nu);
             nu = fma(Ex, crw, nu);
@@ -344,6 +345,16 @@ FineCoefK make_fine_coef_k(double U, double V, double cs, double dx, double dy, 
         c.dxy1[k] = ck[k] * (a1 / (4.0 * dx * dy));
         c.dyy[k] = ck[k] * (a2 / (dy * dy));
         c.dxy2[k] = ck[k] * (a2 / (4.0 * dx * dy));
+        const double A = c.adx[k], Cx = c.dxx[k];
+        c.up1[k] = 45.0 * A + Cx;
+        c.um1[k] = Cx - 45.0 * A;
+        c.up2[k] = -9.0 * A;
+        c.um2[k] = 9.0 * A;
+        c.um3[k] = -A;
+        c.u00[k] = -2.0 * Cx;
+        c.a45[k] = 45.0 * A;
+        c.am9[k] = -9.0 * A;
+        c.cy2[k] = -2.0 * c.dyy[k];
     }
     return c;
 }
