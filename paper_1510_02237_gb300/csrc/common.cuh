@@ -265,6 +265,30 @@ long chain_resp_elems(int n_slices);
 // FP64 fine sweep in one cooperative launch (fine_coop.cu).  Coefficients
 // already multiplied by the stage length c_k (k = 0, 1, 2: dt/3, dt/2, dt)
 // and signed as they enter q^n + c_k L.
+// One handle's fine sweep inside a batched launch (FP32 tendencies on FP64
+// states, V = 0, no rotation): n states from in to out in nf RK-3 steps
+// through the ping-pong buffers w0, w1 (step t writes out when t = nf - 1,
+// else w0 for even t and w1 for odd t), with the slice maps of its first and
+// of its later steps; d = 3 nx ny; its tiles are the work indices
+// [tile0, tile0 + n * tiles).
+struct FineBatchItem {
+    const double* in;
+    double* out;
+    double *w0, *w1;
+    SliceMap first, rest;
+    FineCoef<float> c;
+    long d;
+    int nx, ny, n, nf;
+    int tiles_x, tiles;
+    long tile0;
+};
+// Output tiles per state of the batched sweep's tile shape.
+void fine_batch_tiles(int nx, int ny, int* tiles_x, int* tiles);
+// All nf steps of all items in one cooperative launch with a bounded grid
+// barrier between steps (items sorted by tile0; total = sum of n * tiles).
+cudaError_t fine_batch_coop(const FineBatchItem* items_dev, int nitems, long total, int max_nf, GridBar* gb,
+                            cudaStream_t s);
+
 struct FineCoefK {
     double adx[3], ady[3], csx[3], csy[3], dxx[3], dxy1[3], dyy[3], dxy2[3];
     // products of the above used by the V = 0 marching kernel, formed on the

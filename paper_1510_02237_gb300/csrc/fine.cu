@@ -20,6 +20,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "grid_barrier.cuh"
 
 namespace pr {
 namespace {
@@ -67,28 +68,21 @@ __device__ __forceinline__ void fine_tend(const T* __restrict__ u, const T* __re
           c.dxy2 * ((u[i + 1 + S1] - u[i - 1 + S1]) - (u[i + 1 - S1] - u[i - 1 - S1]));
 }
 
-// ACC64: the state is FP64 in memory and the last stage adds dt L(q**) to
-// the FP64 q^n (the tendencies and the intermediate stages stay in T).
-template <typename T, typename Tin, typename Tout, int RYH, int TX, int TY, int NT, bool ACC64 = false>
-__global__ void __launch_bounds__(NT) k_fine_step(const Tin* __restrict__ in, long instride,
-                                                   Tout* __restrict__ out, long outstride, int nx,
-                                                   int ny, FineCoef<T> c, SliceMap map) {
+// One RK-3 step of the TX x TY output tile at (tx0, ty0) of one state:
+// src -> dst (both already offset to the state), in arithmetic T, with the
+// three stages in shared memory (smem_raw: 6 (TX + 18) (TY + 6 RYH) values of
+// T).  ACC64: the state is FP64 in memory and the last stage adds dt L(q**)
+// to the FP64 q^n (the tendencies and the intermediate stages stay in T).
+// src is read with plain loads (the batched sweep passes states that other
+// CTAs wrote earlier in the same launch).  Contains __syncthreads().
+template <typename T, typename Tin, typename Tout, int RYH, int TX, int TY, int NT, bool ACC64>
+__device__ __forceinline__ void fine_tile(const Tin* src, Tout* __restrict__ dst, int nx, int ny,
+                                          const FineCoef<T>& c, int tx0, int ty0, unsigned char* smem_raw) {
     constexpr int HX = 9, HY = 3 * RYH;
     constexpr int RX = TX + 2 * HX, RY = TY + 2 * HY, NR = RX * RY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* q = reinterpret_cast<T*>(smem_raw);
     T* s = q + 3 * NR;
     const long ncell = (long)nx * ny;
-    long zi = blockIdx.z, zo = blockIdx.z;
-    if (map.end) {
-        const int b0 = *map.beg;
-        if ((int)blockIdx.z >= *map.end - b0) return;
-        if (map.in_map) zi += b0;
-        if (map.out_map) zo += b0;
-    }
-    const Tin* src = in + zi * instride;
-    Tout* dst = out + zo * outstride;
-    const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
 
     // load the haloed region (periodic wrap)
     for (int idx = threadIdx.x; idx < NR; idx += NT) {
@@ -171,6 +165,23 @@ __global__ void __launch_bounds__(NT) k_fine_step(const Tin* __restrict__ in, lo
             }
         }
     }
+    __syncthreads();   // the shared buffers may be reused right after
+}
+
+template <typename T, typename Tin, typename Tout, int RYH, int TX, int TY, int NT, bool ACC64 = false>
+__global__ void __launch_bounds__(NT) k_fine_step(const Tin* __restrict__ in, long instride,
+                                                   Tout* __restrict__ out, long outstride, int nx,
+                                                   int ny, FineCoef<T> c, SliceMap map) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    long zi = blockIdx.z, zo = blockIdx.z;
+    if (map.end) {
+        const int b0 = *map.beg;
+        if ((int)blockIdx.z >= *map.end - b0) return;
+        if (map.in_map) zi += b0;
+        if (map.out_map) zo += b0;
+    }
+    fine_tile<T, Tin, Tout, RYH, TX, TY, NT, ACC64>(in + zi * instride, out + zo * outstride, nx, ny, c,
+                                                    blockIdx.x * TX, blockIdx.y * TY, smem_raw);
 }
 
 template <typename T, typename Tin, typename Tout, int RYH, int TX, int TY, int NT, bool ACC64 = false>
@@ -208,6 +219,50 @@ cudaError_t launch_tiles(const Tin* in, long instride, Tout* out, long outstride
     } else {   // FP64 tile steps (slice-mapped sweeps) keep the fixed shapes
         if (big) return launch_tile<T, Tin, Tout, 1, 64, 16, 256, ACC64>(in, instride, out, outstride, n, nx, ny, c, s, map);
         return launch_tile<T, Tin, Tout, 1, 32, 8, 256, ACC64>(in, instride, out, outstride, n, nx, ny, c, s, map);
+    }
+}
+
+// ------------------------------------------------------------ batched sweep
+
+constexpr int FB_TX = 32, FB_TY = 8, FB_NT = 256;
+constexpr size_t FB_SMEM = sizeof(float) * 6 * (FB_TX + 18) * (FB_TY + 6);
+
+// The fine sweeps of many handles (uneven grids, slice counts and step
+// counts) in one cooperative launch: per step t, every CTA takes work
+// indices (item, state, tile) in a grid-stride loop, items whose nf <= t
+// are done; a bounded grid barrier separates the steps.  Each tile runs the
+// same per-cell arithmetic as the per-handle tile kernel (fine_tile), so the
+// results are those of the handles' own sweeps bit for bit.
+__global__ void __launch_bounds__(FB_NT) k_fine_batch(const FineBatchItem* __restrict__ items, int nitems,
+                                                      long total, int max_nf, GridBar* gb) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const unsigned nb = gridDim.x;
+    for (int t = 0; t < max_nf; ++t) {
+        for (long w = blockIdx.x; w < total; w += nb) {
+            int lo = 0, hi = nitems - 1;   // last item with tile0 <= w
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (items[mid].tile0 <= w) lo = mid; else hi = mid - 1;
+            }
+            const FineBatchItem& it = items[lo];
+            if (t >= it.nf) continue;
+            const long lw = w - it.tile0;
+            const int z = (int)(lw / it.tiles), tt = (int)(lw - (long)z * it.tiles);
+            const int ty = tt / it.tiles_x, tx = tt - ty * it.tiles_x;
+            const SliceMap& map = t == 0 ? it.first : it.rest;
+            long zi = z, zo = z;
+            if (map.end) {
+                const int b0 = *map.beg;
+                if (z >= *map.end - b0) continue;
+                if (map.in_map) zi += b0;
+                if (map.out_map) zo += b0;
+            }
+            const double* a = t == 0 ? it.in : ((t - 1) % 2 == 0 ? it.w0 : it.w1);
+            double* b = t == it.nf - 1 ? it.out : (t % 2 == 0 ? it.w0 : it.w1);
+            fine_tile<float, double, double, 1, FB_TX, FB_TY, FB_NT, true>(a + zi * it.d, b + zo * it.d, it.nx, it.ny,
+                                                                          it.c, tx * FB_TX, ty * FB_TY, smem_raw);
+        }
+        if (t + 1 < max_nf && !grid_barrier(gb, nb)) return;
     }
 }
 
@@ -251,5 +306,42 @@ template cudaError_t launch_fine_step<float, float, double>(const float*, long, 
 template cudaError_t launch_fine_step<float, double, double>(const double*, long, double*, long, int,
                                                              int, int, bool, const FineCoef<float>&,
                                                              cudaStream_t, const SliceMap&, const FineLaunch&);
+
+void fine_batch_tiles(int nx, int ny, int* tiles_x, int* tiles) {
+    *tiles_x = (nx + FB_TX - 1) / FB_TX;
+    *tiles = *tiles_x * ((ny + FB_TY - 1) / FB_TY);
+}
+
+cudaError_t fine_batch_coop(const FineBatchItem* items_dev, int nitems, long total, int max_nf, GridBar* gb,
+                            cudaStream_t s) {
+    if (nitems < 1 || total < 1 || max_nf < 1) return cudaSuccess;
+    static DevMemo memo;   // [device] -> (SMs, CTAs per SM)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int sms = 0, per = 0;
+    if (!memo.get(dev, &sms, &per)) {
+        std::lock_guard<std::mutex> lk(smem_launch_lock());
+        e = set_dynamic_smem((const void*)k_fine_batch, FB_SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fine_batch, FB_NT, FB_SMEM);
+        if (e != cudaSuccess) return e;
+        memo.put(dev, sms, per);
+    }
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    long nb = (long)sms * per;
+    if (nb > total) nb = total;
+    e = cudaMemsetAsync(&gb->count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&items_dev, &nitems, &total, &max_nf, &gb};
+    std::lock_guard<std::mutex> lk(smem_launch_lock());
+    e = set_dynamic_smem((const void*)k_fine_batch, FB_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaLaunchCooperativeKernel((const void*)k_fine_batch, dim3((unsigned)nb), dim3(FB_NT), args, FB_SMEM, s);
+    count_launches(1);
+    return e;
+}
 
 }  // namespace pr

@@ -312,26 +312,6 @@ static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, c
     return PR_OK;
 }
 
-// Images of the columns appended since *r_it computed directly as
-// D_j = F(Q_j) - G(Q_j) (the quantity Eq. Genhance forms by linearity, here
-// without dividing rounding errors by small residuals |R_jj|).  Mixed
-// precision uses the FP32 propagators and refreshes the FP32 copies of Q
-// and D used by the serial correction.
-static pr_status direct_images(pr_solver* h, bool mixed, int maxn) {
-    const long d = h->d;
-    cudaStream_t s = h->stream;
-    // columns [*r_it, *r) of Q: at most maxn, the exact count known only on the device
-    SliceMap first, rest;
-    first.beg = rest.beg = h->r_it;
-    first.end = rest.end = h->r;
-    first.in_map = true;
-    CKS(fine_apply(h, h->Q, h->wv, maxn, &first, &rest));
-    CKS(coarse_apply(h, h->Q, h->wz, maxn, mixed, &first, &rest));
-    CKC(sub_mapped(h->wv, h->wz, h->D, d, maxn, h->r_it, h->r, s));
-    if (mixed) CKC(to_fp32_cols(h->Q, h->D, h->Q32, h->D32, d, h->r_it, h->r, maxn, s));
-    return PR_OK;
-}
-
 static cudaError_t no_mark() { return cudaSuccess; }
 static cudaError_t no_sub_mark(int) { return cudaSuccess; }
 
@@ -365,76 +345,127 @@ static ChainArgs chain_args(pr_solver* h, int i_begin, int i_end, const double* 
     return a;
 }
 
-static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
-    const long d = h->d;
-    const int N = h->N, cap = h->cap;
-    cudaStream_t s = h->stream;
-    TsWork w{h->partial, h->partial_elems};
-    const bool kse = h->opt.variant == PR_KSE;
-    const bool mixed = h->opt.corr_prec == PR_FP32;
-    // FP32 fine images cannot be divided by small residuals: non-FP64 fine sweeps use direct images
-    const bool direct = mixed || h->opt.images == PR_IMAGES_DIRECT || h->opt.fine_prec != PR_FP64;
+// One solve of Alg. 2 / Alg. 1 (one parallel step), split into the phases
+// between which a batch runs the fine sweeps of all its handles in one
+// launch: begin (the serial coarse initialisation), then per iteration
+// fine (the parallel predictor), update (the subspace update), images_fine
+// (the fine images of the new basis columns, where they are formed
+// directly), correct (their coarse images, the serial correction, r^k).  The
+// solo solve runs the phases in this order on the handle's stream; a batch
+// runs exactly the same phases, so its results are the solo results bit for
+// bit.
+struct SolveRun {
+    pr_solver* h;
+    int K, rbase, k = 0, iter = 0, evi = 0;
+    bool kse, mixed, direct, gacc, d64;
     cudaEvent_t* ev = nullptr;
-    if (h->tr.n < h->tr.max_solves) {
-        ev = h->tr.ev.data() + (size_t)h->tr.n * h->tr.per_solve;
-        h->tr.K[h->tr.n] = K;
-        h->tr.fine_launches[h->tr.n] = 0;
-        h->tr.n += 1;
+    SliceMap img_first, img_rest;   // slice maps of the images sweep
+
+    SolveRun(pr_solver* h_, int K_, int rbase_, bool timing) : h(h_), K(K_), rbase(rbase_) {
+        kse = h->opt.variant == PR_KSE;
+        mixed = h->opt.corr_prec == PR_FP32;
+        // FP32 fine images cannot be divided by small residuals: non-FP64 fine sweeps use direct images
+        direct = mixed || h->opt.images == PR_IMAGES_DIRECT || h->opt.fine_prec != PR_FP64;
+        // The FP64 KSE path with images by linearity needs the coarse images
+        // G(q_i^k) of the new columns.  G(q_i^0) = q_{i+1}^0 bit for bit; later
+        // the delta-form correction adds G(delta_i) to them (linearity of G), so
+        // no coarse sweep over the columns is needed.
+        gacc = kse && !mixed && !direct;
+        d64 = kse && !mixed;
+        img_first.beg = img_rest.beg = h->r_it;
+        img_first.end = img_rest.end = h->r;
+        img_first.in_map = true;
+        if (timing && h->tr.n < h->tr.max_solves) {
+            ev = h->tr.ev.data() + (size_t)h->tr.n * h->tr.per_solve;
+            h->tr.K[h->tr.n] = K;
+            h->tr.fine_launches[h->tr.n] = 0;
+            h->tr.n += 1;
+        }
     }
-    int evi = 0;
-    auto mark = [&]() -> cudaError_t { return ev ? cudaEventRecord(ev[evi++], s) : cudaSuccess; };
-    int iter = 0;
-    auto sub_mark = [&](int) -> cudaError_t {
+    cudaError_t mark() { return ev ? cudaEventRecord(ev[evi++], h->stream) : cudaSuccess; }
+    cudaError_t sub_mark(int) {
         if (!ev) return cudaSuccess;
         const size_t base = ((size_t)(h->tr.n - 1) * h->K_max + iter) * (size_t)h->tr.sub_per_iter;
         int& ns = h->tr.nsub[(size_t)(h->tr.n - 1) * h->K_max + iter];
         if (ns >= 2 * h->tr.sub_per_iter) return cudaSuccess;
-        return cudaEventRecord(h->tr.sub[2 * base + ns++], s);
-    };
-    CKC(mark());
+        return cudaEventRecord(h->tr.sub[2 * base + ns++], h->stream);
+    }
+    int M() const { return h->N - k; }       // active slices of iteration k (slices i < k are converged)
+    double* qa() const { return h->q + (long)k * h->d; }
+    double* qta() const { return h->qt + (long)k * h->d; }
+    bool has_images_fine() const { return kse && direct; }
 
-    // initialisation: q_{i+1}^0 = G(q_i^0), serially (q[0] already holds u0)
-    CKC(chain_coop(chain_args(h, 0, N, nullptr, nullptr, nullptr, nullptr), s));
-    CKC(fill_int(h->r, 0, 1, s));
-    // The FP64 KSE path with images by linearity needs the coarse images
-    // G(q_i^k) of the new columns.  G(q_i^0) = q_{i+1}^0 bit for bit; later
-    // the delta-form correction adds G(delta_i) to them (linearity of G), so
-    // no coarse sweep over the columns is needed.
-    const bool gacc = kse && !mixed && !direct;
-    if (gacc) CKC(cudaMemcpyAsync(h->gv, h->q + d, sizeof(double) * (size_t)N * d, cudaMemcpyDeviceToDevice, s));
-    CKC(mark());
-
-    if (ev)
-        for (int k = 0; k < h->K_max; ++k) h->tr.nsub[(size_t)(h->tr.n - 1) * h->K_max + k] = 0;
-    for (int k = 0; k < K; ++k) {
-        iter = k;
-        // Slices i < k satisfy q_i^{k} = q_i^{k-1} bit for bit (the correction
-        // of a converged slice is K(q) - K(q) = 0), so their fine images, their
-        // columns (already in S) and their corrections are skipped.
-        const int a = k, M = N - k;
-        double* qa = h->q + (long)a * d;
-        // parallel predictor: q~_{i+1}^k = F(q_i^k)
-        const uint64_t l0 = parareal_kernel_launches();
-        CKS(fine_apply(h, qa, h->qt + (long)a * d, M));
-        if (ev) h->tr.fine_launches[h->tr.n - 1] += (long)(parareal_kernel_launches() - l0);
+    pr_status begin() {
+        const long d = h->d;
+        const int N = h->N;
+        cudaStream_t s = h->stream;
         CKC(mark());
+        // initialisation: q_{i+1}^0 = G(q_i^0), serially (q[0] already holds u0)
+        CKC(chain_coop(chain_args(h, 0, N, nullptr, nullptr, nullptr, nullptr), s));
+        CKC(fill_int(h->r, 0, 1, s));
+        if (gacc) CKC(cudaMemcpyAsync(h->gv, h->q + d, sizeof(double) * (size_t)N * d, cudaMemcpyDeviceToDevice, s));
+        CKC(mark());
+        if (ev)
+            for (int j = 0; j < h->K_max; ++j) h->tr.nsub[(size_t)(h->tr.n - 1) * h->K_max + j] = 0;
+        return PR_OK;
+    }
+    // parallel predictor: q~_{i+1}^k = F(q_i^k).  Slices i < k satisfy
+    // q_i^{k} = q_i^{k-1} bit for bit (the correction of a converged slice is
+    // K(q) - K(q) = 0), so their fine images, their columns (already in S)
+    // and their corrections are skipped.
+    pr_status fine() {
+        iter = k;
+        const uint64_t l0 = parareal_kernel_launches();
+        CKS(fine_apply(h, qa(), qta(), M()));
+        if (ev) h->tr.fine_launches[h->tr.n - 1] += (long)(parareal_kernel_launches() - l0);
+        return PR_OK;
+    }
+    pr_status update() {
+        const long d = h->d;
+        const int N = h->N;
+        cudaStream_t s = h->stream;
         // coarse images G(q_i^k): K_old of the FP64 original Parareal (the
         // KSE images by linearity have them from the correction, above)
-        if (!kse && !mixed) CKS(coarse_apply(h, qa, h->gv + (long)a * d, M));
+        if (!kse && !mixed) CKS(coarse_apply(h, qa(), h->gv + (long)k * d, M()));
         CKC(mark());
         if (kse) {
             CKC(cudaMemcpyAsync(h->r_it, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
-            CKS(krylov_block(h, qa, direct ? nullptr : h->qt + (long)a * d, h->gv + (long)a * d, M, mark, sub_mark,
+            auto mk = [&]() { return mark(); };
+            auto smk = [&](int i) { return sub_mark(i); };
+            CKS(krylov_block(h, qa(), direct ? nullptr : qta(), h->gv + (long)k * d, M(), mk, smk,
                              h->ratios + (long)(rbase + k) * N));
-            CKC(cudaMemcpyAsync(h->kept_hist + (long)(rbase + k) * N, h->kept, sizeof(int) * M,
+            CKC(cudaMemcpyAsync(h->kept_hist + (long)(rbase + k) * N, h->kept, sizeof(int) * M(),
                                 cudaMemcpyDeviceToDevice, s));
-            h->M_hist[rbase + k] = M;
+            h->M_hist[rbase + k] = M();
             CKC(mark());
-            if (direct) CKS(direct_images(h, mixed, M));
-            CKC(cudaMemcpyAsync(h->ranks + rbase + k, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
         } else {
             CKC(mark());
             CKC(mark());
+        }
+        return PR_OK;
+    }
+    // Images of the columns appended since *r_it computed directly as
+    // D_j = F(Q_j) - G(Q_j) (the quantity Eq. Genhance forms by linearity,
+    // here without dividing rounding errors by small residuals |R_jj|):
+    // images_fine forms F(Q_j) (at most M columns, the exact count known only
+    // on the device), correct forms G(Q_j) and D.  Mixed precision uses the
+    // FP32 propagators and refreshes the FP32 copies of Q and D used by the
+    // serial correction.
+    pr_status images_fine() { return fine_apply(h, h->Q, h->wv, M(), &img_first, &img_rest); }
+    pr_status correct(int* K_done) {
+        const long d = h->d;
+        const int N = h->N;
+        const int a = k;
+        cudaStream_t s = h->stream;
+        TsWork w{h->partial, h->partial_elems};
+        if (kse) {
+            if (direct) {
+                // D_j = F(Q_j) - G(Q_j) for the new columns
+                CKS(coarse_apply(h, h->Q, h->wz, M(), mixed, &img_first, &img_rest));
+                CKC(sub_mapped(h->wv, h->wz, h->D, d, M(), h->r_it, h->r, s));
+                if (mixed) CKC(to_fp32_cols(h->Q, h->D, h->Q32, h->D32, d, h->r_it, h->r, M(), s));
+            }
+            CKC(cudaMemcpyAsync(h->ranks + rbase + k, h->r, sizeof(int), cudaMemcpyDeviceToDevice, s));
         }
         CKC(mark());
         // serial correction
@@ -445,7 +476,6 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
         // FP32 copies of Q and D in mixed precision, in FP64 for the KSE
         // correction otherwise; the FP64 original Parareal subtracts
         // K_old = G(q_i^k) literally
-        const bool d64 = kse && !mixed;
         CKC(copy_resid(h->qt + (long)a * d, h->q + (long)(a + 1) * d, d, h->res2 + a + 1, w, s,
                        mixed ? h->dlt : nullptr, d64 ? h->dlt64 : nullptr));
         ChainArgs ca = chain_args(h, a + 1, N, h->qt, kse || mixed ? nullptr : h->gv, kse ? h->r : nullptr,
@@ -463,11 +493,26 @@ static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
         CKC(max_sqrt(h->res2 + 1, N, h->rhist + rbase + k, s));
         CKC(mark());
         *K_done = k + 1;
+        ++k;
+        return PR_OK;
+    }
+};
+
+static pr_status solve_impl(pr_solver* h, int K, int rbase, int* K_done) {
+    SolveRun run(h, K, rbase, true);
+    CKS(run.begin());
+    while (run.k < K) {
+        CKS(run.fine());
+        CKC(run.mark());
+        CKS(run.update());
+        if (run.has_images_fine()) CKS(run.images_fine());
+        const int k = run.k;
+        CKS(run.correct(K_done));
         if (h->opt.r_tol > 0) {
             // stopping rule of Sec. 2.1 (one synchronisation per iteration)
             double r = 0.0;
-            CKC(cudaMemcpyAsync(&r, h->rhist + rbase + k, sizeof(double), cudaMemcpyDeviceToHost, s));
-            CKC(cudaStreamSynchronize(s));
+            CKC(cudaMemcpyAsync(&r, h->rhist + rbase + k, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            CKC(cudaStreamSynchronize(h->stream));
             if (r <= h->opt.r_tol) break;
         }
     }
@@ -1112,16 +1157,159 @@ struct pr_batch {
     cudaStream_t stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    std::vector<cudaEvent_t> ev;   // fork + one join per handle
+    std::vector<cudaEvent_t> ev;   // fork + one join per handle (+ one for the batched launches)
+    bool lockstep = false;         // fine sweeps of all handles in one launch per phase
+    GridBar* gb = nullptr;         // grid barrier of the batched fine sweeps
+    FineBatchItem* items = nullptr;   // device: the work tables of all batched launches
+    std::vector<long> first, count, total;   // per batched launch: its items and work indices
+    std::vector<int> maxnf;
 };
 
 static void batch_free(pr_batch* b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->gb) cudaFree(b->gb);
+    if (b->items) cudaFree(b->items);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
     delete b;
+}
+
+// A batch whose handles all run the FP32-tendency fine sweep (PR_FP32X) of
+// constant velocity with V = 0 and KSE-Parareal in one parallel step is
+// captured in lockstep: the handles' solves advance phase by phase (see
+// SolveRun), and at each fine phase (the predictor of iteration k, the fine
+// images of the new basis columns) the sweeps of every handle still
+// iterating run as one persistent cooperative launch over all their
+// (state, tile) items, forked from and joined back into the handles' streams.
+static bool batch_lockstep_ok(pr_solver* const* hs, int n) {
+    for (int i = 0; i < n; ++i) {
+        const pr_solver* h = hs[i];
+        if (h->opt.fine_prec != PR_FP32X || h->V != 0.0 || h->opt.omega != 0.0 || h->opt.variant != PR_KSE ||
+            h->opt.n_windows != 1)
+            return false;
+    }
+    return true;
+}
+
+static FineBatchItem batch_item(pr_solver* h, const double* in, double* out, int n, const SliceMap* first,
+                                const SliceMap* rest) {
+    FineBatchItem it{};
+    it.in = in;
+    it.out = out;
+    it.w0 = h->fb0;
+    it.w1 = h->fb1;
+    if (first) it.first = *first;
+    if (rest) it.rest = *rest;
+    it.c = h->fc32;
+    it.d = h->d;
+    it.nx = h->nx;
+    it.ny = h->ny;
+    it.n = n;
+    it.nf = h->n_f;
+    fine_batch_tiles(h->nx, h->ny, &it.tiles_x, &it.tiles);
+    return it;
+}
+
+// Work tables of a lockstep batch, built and uploaded before capture: per
+// iteration k the predictor (q_i^k -> q~_{i+1}^k, N - k states) and the fine
+// images of the new basis columns (Q[:, *r_it ..] -> wv, at most N - k), one
+// item per handle still iterating.
+static cudaError_t batch_tables(pr_batch* b, const int32_t* K) {
+    const int n = (int)b->hs.size();
+    int Kmax = 0;
+    for (int i = 0; i < n; ++i) Kmax = K[i] > Kmax ? K[i] : Kmax;
+    std::vector<FineBatchItem> tab;
+    for (int k = 0; k < Kmax; ++k) {
+        for (int images = 0; images < 2; ++images) {
+            b->first.push_back((long)tab.size());
+            long tile0 = 0;
+            int mnf = 0;
+            for (int i = 0; i < n; ++i) {
+                if (k >= K[i]) continue;
+                pr_solver* h = b->hs[i];
+                const int M = h->N - k;
+                FineBatchItem it;
+                if (images) {
+                    SliceMap first, rest;
+                    first.beg = rest.beg = h->r_it;
+                    first.end = rest.end = h->r;
+                    first.in_map = true;
+                    it = batch_item(h, h->Q, h->wv, M, &first, &rest);
+                } else {
+                    it = batch_item(h, h->q + (long)k * h->d, h->qt + (long)k * h->d, M, nullptr, nullptr);
+                }
+                it.tile0 = tile0;
+                tile0 += (long)it.n * it.tiles;
+                mnf = it.nf > mnf ? it.nf : mnf;
+                tab.push_back(it);
+            }
+            b->count.push_back((long)tab.size() - b->first.back());
+            b->total.push_back(tile0);
+            b->maxnf.push_back(mnf);
+        }
+    }
+    cudaError_t e = cudaMalloc((void**)&b->items, sizeof(FineBatchItem) * (tab.empty() ? 1 : tab.size()));
+    if (e == cudaSuccess && !tab.empty())
+        e = cudaMemcpy(b->items, tab.data(), sizeof(FineBatchItem) * tab.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// Capture body of a lockstep batch (the caller has begun capture on b->stream
+// and recorded b->ev[0] there).
+static pr_status batch_capture_lockstep(pr_batch* b, const double* const* u0_dev, const int32_t* K,
+                                        double* const* qT_dev) {
+    pr_solver* h = b->hs[0];   // errors are reported on the first handle
+    const int n = (int)b->hs.size();
+    int Kmax = 0;
+    for (int i = 0; i < n; ++i) Kmax = K[i] > Kmax ? K[i] : Kmax;
+    cudaEvent_t eb = b->ev[n + 1];
+    std::vector<SolveRun> runs;
+    runs.reserve(n);
+    for (int i = 0; i < n; ++i) {
+        pr_solver* hi = b->hs[i];
+        CKC(cudaStreamWaitEvent(hi->stream, b->ev[0], 0));
+        CKC(cudaEventRecord(hi->ev0, hi->stream));
+        CKC(cudaMemcpyAsync(hi->q, u0_dev[i], sizeof(double) * hi->d, cudaMemcpyDeviceToDevice, hi->stream));
+        runs.emplace_back(hi, K[i], 0, false);
+        CKS(runs.back().begin());
+    }
+    // a batched fine phase: join the handles still iterating, one launch, fork
+    auto batched = [&](int k, int li) -> pr_status {
+        for (int i = 0; i < n; ++i) {
+            if (k >= K[i]) continue;
+            CKC(cudaEventRecord(b->ev[i + 1], b->hs[i]->stream));
+            CKC(cudaStreamWaitEvent(b->stream, b->ev[i + 1], 0));
+        }
+        CKC(fine_batch_coop(b->items + b->first[li], (int)b->count[li], b->total[li], b->maxnf[li], b->gb,
+                            b->stream));
+        CKC(cudaEventRecord(eb, b->stream));
+        for (int i = 0; i < n; ++i)
+            if (k < K[i]) CKC(cudaStreamWaitEvent(b->hs[i]->stream, eb, 0));
+        return PR_OK;
+    };
+    for (int k = 0; k < Kmax; ++k) {
+        CKS(batched(k, 2 * k));
+        for (int i = 0; i < n; ++i) {
+            if (k >= K[i]) continue;
+            CKC(runs[i].mark());
+            CKS(runs[i].update());
+        }
+        CKS(batched(k, 2 * k + 1));
+        int done = 0;
+        for (int i = 0; i < n; ++i)
+            if (k < K[i]) CKS(runs[i].correct(&done));
+    }
+    for (int i = 0; i < n; ++i) {
+        pr_solver* hi = b->hs[i];
+        CKC(cudaEventRecord(hi->ev1, hi->stream));
+        CKC(cudaMemcpyAsync(qT_dev[i], hi->q + (long)hi->N * hi->d, sizeof(double) * hi->d,
+                            cudaMemcpyDeviceToDevice, hi->stream));
+        CKC(cudaEventRecord(b->ev[i + 1], hi->stream));
+        CKC(cudaStreamWaitEvent(b->stream, b->ev[i + 1], 0));
+    }
+    return PR_OK;
 }
 
 extern "C" {
@@ -1145,24 +1333,34 @@ pr_status parareal_batch_create(pr_solver* const* hs, int32_t n, const double* c
     if (!b) return set_err(h, PR_ENOMEM, "host allocation failed");
     b->hs.assign(hs, hs + n);
     b->stream = (cudaStream_t)stream;
-    b->ev.assign((size_t)n + 1, nullptr);
+    b->lockstep = batch_lockstep_ok(hs, n);
+    b->ev.assign((size_t)n + 2, nullptr);
     cudaError_t e = cudaSuccess;
     for (auto& x : b->ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (e == cudaSuccess && b->lockstep) {
+        e = cudaMalloc((void**)&b->gb, sizeof(GridBar));
+        if (e == cudaSuccess) e = cudaMemset(b->gb, 0, sizeof(GridBar));
+        if (e == cudaSuccess) e = batch_tables(b, K);
+    }
     if (e != cudaSuccess) {
         batch_free(b);
-        return set_err(h, PR_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+        return set_err(h, PR_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
     }
     e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev[0], b->stream);
     pr_status st = PR_OK;
-    for (int i = 0; i < n && e == cudaSuccess && st == PR_OK; ++i) {
-        e = cudaStreamWaitEvent(hs[i]->stream, b->ev[0], 0);
-        if (e != cudaSuccess) break;
-        st = parareal_solve(hs[i], u0_dev[i], K[i], nullptr, qT_dev[i], nullptr);
-        if (st != PR_OK) break;
-        e = cudaEventRecord(b->ev[i + 1], hs[i]->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev[i + 1], 0);
+    if (b->lockstep && e == cudaSuccess) {
+        st = batch_capture_lockstep(b, u0_dev, K, qT_dev);
+    } else {
+        for (int i = 0; i < n && e == cudaSuccess && st == PR_OK; ++i) {
+            e = cudaStreamWaitEvent(hs[i]->stream, b->ev[0], 0);
+            if (e != cudaSuccess) break;
+            st = parareal_solve(hs[i], u0_dev[i], K[i], nullptr, qT_dev[i], nullptr);
+            if (st != PR_OK) break;
+            e = cudaEventRecord(b->ev[i + 1], hs[i]->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev[i + 1], 0);
+        }
     }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);

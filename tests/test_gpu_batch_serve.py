@@ -35,10 +35,14 @@ def _alone(inst, **opt):
         return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "fp32x"])
 def test_batch_equals_alone(mode):
+    """'mixed' and 'fp32x' (FP32 tendencies, FP32 or FP64 correction) batches
+    run their fine sweeps as one persistent launch per phase over all
+    handles (lockstep capture); 'fp64' forks the handles' own solves."""
     insts = W.workload_batch(6, seed=2000)
-    opt = {} if mode == "fp64" else {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32}
+    opt = {"fp64": {}, "mixed": {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32},
+           "fp32x": {"fine_prec": P.PR_FP32X}}[mode]
     want = [_alone(i, sm_limit=8, **opt) for i in insts]
     streams = [P.new_stream() for _ in insts]
     solvers = [P.Solver(i.problem, stream=st, K_max=i.K, sm_limit=8, **opt) for i, st in zip(insts, streams)]
