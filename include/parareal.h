@@ -320,9 +320,18 @@ typedef struct pr_batch pr_batch;
 /* Capture the n solves of parareal_solve_batch (same arguments, which stay
  * bound to the batch: refill u0_dev[i] before each launch) into one CUDA
  * graph that forks from `stream` into the handles' streams and joins back.
- * Handles must be distinct, with non-NULL streams other than `stream`;
- * handles sharing a stream run one after the other.  Requires r_tol = 0 on
- * every handle.  Allocates the graph only. */
+ * When every handle runs the FP32-tendency fine sweep (PR_FP32X) with V = 0,
+ * no rotation, KSE-Parareal and one parallel step, the handles are grouped
+ * by problem shape (grid, slices, fine steps per slice) and each group's
+ * fine sweeps (the predictor of every iteration and the fine images of the
+ * new basis columns) run as one persistent cooperative launch over all the
+ * (state, tile) items of its handles still iterating; the rest of each
+ * solve runs on the handle's stream.  Results equal the handles' solo
+ * solves bit for bit either way.  Handles must be distinct, with non-NULL
+ * streams other than `stream`; handles sharing a stream run one after the
+ * other.  Requires r_tol = 0 on every handle.  Allocates the graph, and for
+ * batched fine sweeps one stream, one barrier word and the work tables per
+ * group. */
 pr_status parareal_batch_create(pr_solver* const* hs, int32_t n, const double* const* u0_dev, const int32_t* K,
                                 double* const* qT_dev, void* stream, pr_batch** out);
 /* Enqueue one replay of the batch graph on its stream (asynchronous). */

@@ -1158,18 +1158,28 @@ struct pr_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaEvent_t> ev;   // fork + one join per handle (+ one for the batched launches)
-    bool lockstep = false;         // fine sweeps of all handles in one launch per phase
-    GridBar* gb = nullptr;         // grid barrier of the batched fine sweeps
+    bool lockstep = false;         // fine sweeps batched per group of handles of one shape
+    struct Group {
+        std::vector<int> idx;              // handles of the group
+        cudaStream_t stream = nullptr;     // the group's batched fine launches
+        GridBar* gb = nullptr;
+        cudaEvent_t ev = nullptr;
+        std::vector<long> first, count, total;   // per batched launch: its items and work indices
+        std::vector<int> maxnf;
+    };
+    std::vector<Group> groups;
     FineBatchItem* items = nullptr;   // device: the work tables of all batched launches
-    std::vector<long> first, count, total;   // per batched launch: its items and work indices
-    std::vector<int> maxnf;
 };
 
 static void batch_free(pr_batch* b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    if (b->gb) cudaFree(b->gb);
+    for (auto& g : b->groups) {
+        if (g.gb) cudaFree(g.gb);
+        if (g.ev) cudaEventDestroy(g.ev);
+        if (g.stream) cudaStreamDestroy(g.stream);
+    }
     if (b->items) cudaFree(b->items);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
@@ -1177,12 +1187,15 @@ static void batch_free(pr_batch* b) {
 }
 
 // A batch whose handles all run the FP32-tendency fine sweep (PR_FP32X) of
-// constant velocity with V = 0 and KSE-Parareal in one parallel step is
-// captured in lockstep: the handles' solves advance phase by phase (see
-// SolveRun), and at each fine phase (the predictor of iteration k, the fine
-// images of the new basis columns) the sweeps of every handle still
-// iterating run as one persistent cooperative launch over all their
-// (state, tile) items, forked from and joined back into the handles' streams.
+// constant velocity with V = 0 and KSE-Parareal in one parallel step runs
+// its fine sweeps batched: the handles are grouped by problem shape (grid,
+// slices, fine steps per slice), and within a group the solves advance in
+// lockstep phase by phase (see SolveRun); at each fine phase (the predictor
+// of iteration k, the fine images of the new basis columns) the sweeps of
+// every handle of the group still iterating run as one persistent
+// cooperative launch over all their (state, tile) items, forked from and
+// joined back into the handles' streams.  Groups progress independently, so
+// a short solve never waits for the serial chain of a longer one.
 static bool batch_lockstep_ok(pr_solver* const* hs, int n) {
     for (int i = 0; i < n; ++i) {
         const pr_solver* h = hs[i];
@@ -1212,42 +1225,65 @@ static FineBatchItem batch_item(pr_solver* h, const double* in, double* out, int
     return it;
 }
 
-// Work tables of a lockstep batch, built and uploaded before capture: per
-// iteration k the predictor (q_i^k -> q~_{i+1}^k, N - k states) and the fine
-// images of the new basis columns (Q[:, *r_it ..] -> wv, at most N - k), one
-// item per handle still iterating.
-static cudaError_t batch_tables(pr_batch* b, const int32_t* K) {
+// Groups, their streams and barriers, and the work tables (per group and
+// iteration k: the predictor q_i^k -> q~_{i+1}^k over N - k states and the
+// fine images Q[:, *r_it ..] -> wv of at most N - k columns, one item per
+// handle of the group still iterating), built and uploaded before capture.
+static cudaError_t batch_setup(pr_batch* b, const int32_t* K) {
     const int n = (int)b->hs.size();
-    int Kmax = 0;
-    for (int i = 0; i < n; ++i) Kmax = K[i] > Kmax ? K[i] : Kmax;
-    std::vector<FineBatchItem> tab;
-    for (int k = 0; k < Kmax; ++k) {
-        for (int images = 0; images < 2; ++images) {
-            b->first.push_back((long)tab.size());
-            long tile0 = 0;
-            int mnf = 0;
-            for (int i = 0; i < n; ++i) {
-                if (k >= K[i]) continue;
-                pr_solver* h = b->hs[i];
-                const int M = h->N - k;
-                FineBatchItem it;
-                if (images) {
-                    SliceMap first, rest;
-                    first.beg = rest.beg = h->r_it;
-                    first.end = rest.end = h->r;
-                    first.in_map = true;
-                    it = batch_item(h, h->Q, h->wv, M, &first, &rest);
-                } else {
-                    it = batch_item(h, h->q + (long)k * h->d, h->qt + (long)k * h->d, M, nullptr, nullptr);
-                }
-                it.tile0 = tile0;
-                tile0 += (long)it.n * it.tiles;
-                mnf = it.nf > mnf ? it.nf : mnf;
-                tab.push_back(it);
+    for (int i = 0; i < n; ++i) {
+        const pr_solver* h = b->hs[i];
+        bool found = false;
+        for (auto& g : b->groups) {
+            const pr_solver* f = b->hs[g.idx[0]];
+            if (f->nx == h->nx && f->ny == h->ny && f->N == h->N && f->n_f == h->n_f) {
+                g.idx.push_back(i);
+                found = true;
+                break;
             }
-            b->count.push_back((long)tab.size() - b->first.back());
-            b->total.push_back(tile0);
-            b->maxnf.push_back(mnf);
+        }
+        if (!found) {
+            b->groups.emplace_back();
+            b->groups.back().idx.push_back(i);
+        }
+    }
+    std::vector<FineBatchItem> tab;
+    for (auto& g : b->groups) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&g.gb, sizeof(GridBar));
+        if (e == cudaSuccess) e = cudaMemset(g.gb, 0, sizeof(GridBar));
+        if (e != cudaSuccess) return e;
+        int Kmax = 0;
+        for (int i : g.idx) Kmax = K[i] > Kmax ? K[i] : Kmax;
+        for (int k = 0; k < Kmax; ++k) {
+            for (int images = 0; images < 2; ++images) {
+                g.first.push_back((long)tab.size());
+                long tile0 = 0;
+                int mnf = 0;
+                for (int i : g.idx) {
+                    if (k >= K[i]) continue;
+                    pr_solver* h = b->hs[i];
+                    const int M = h->N - k;
+                    FineBatchItem it;
+                    if (images) {
+                        SliceMap first, rest;
+                        first.beg = rest.beg = h->r_it;
+                        first.end = rest.end = h->r;
+                        first.in_map = true;
+                        it = batch_item(h, h->Q, h->wv, M, &first, &rest);
+                    } else {
+                        it = batch_item(h, h->q + (long)k * h->d, h->qt + (long)k * h->d, M, nullptr, nullptr);
+                    }
+                    it.tile0 = tile0;
+                    tile0 += (long)it.n * it.tiles;
+                    mnf = it.nf > mnf ? it.nf : mnf;
+                    tab.push_back(it);
+                }
+                g.count.push_back((long)tab.size() - g.first.back());
+                g.total.push_back(tile0);
+                g.maxnf.push_back(mnf);
+            }
         }
     }
     cudaError_t e = cudaMalloc((void**)&b->items, sizeof(FineBatchItem) * (tab.empty() ? 1 : tab.size()));
@@ -1261,53 +1297,56 @@ static cudaError_t batch_tables(pr_batch* b, const int32_t* K) {
 static pr_status batch_capture_lockstep(pr_batch* b, const double* const* u0_dev, const int32_t* K,
                                         double* const* qT_dev) {
     pr_solver* h = b->hs[0];   // errors are reported on the first handle
-    const int n = (int)b->hs.size();
-    int Kmax = 0;
-    for (int i = 0; i < n; ++i) Kmax = K[i] > Kmax ? K[i] : Kmax;
-    cudaEvent_t eb = b->ev[n + 1];
-    std::vector<SolveRun> runs;
-    runs.reserve(n);
-    for (int i = 0; i < n; ++i) {
-        pr_solver* hi = b->hs[i];
-        CKC(cudaStreamWaitEvent(hi->stream, b->ev[0], 0));
-        CKC(cudaEventRecord(hi->ev0, hi->stream));
-        CKC(cudaMemcpyAsync(hi->q, u0_dev[i], sizeof(double) * hi->d, cudaMemcpyDeviceToDevice, hi->stream));
-        runs.emplace_back(hi, K[i], 0, false);
-        CKS(runs.back().begin());
-    }
-    // a batched fine phase: join the handles still iterating, one launch, fork
-    auto batched = [&](int k, int li) -> pr_status {
-        for (int i = 0; i < n; ++i) {
-            if (k >= K[i]) continue;
-            CKC(cudaEventRecord(b->ev[i + 1], b->hs[i]->stream));
+    for (auto& g : b->groups) {
+        int Kmax = 0;
+        for (int i : g.idx) Kmax = K[i] > Kmax ? K[i] : Kmax;
+        CKC(cudaStreamWaitEvent(g.stream, b->ev[0], 0));
+        std::vector<SolveRun> runs;
+        runs.reserve(g.idx.size());
+        for (int i : g.idx) {
+            pr_solver* hi = b->hs[i];
+            CKC(cudaStreamWaitEvent(hi->stream, b->ev[0], 0));
+            CKC(cudaEventRecord(hi->ev0, hi->stream));
+            CKC(cudaMemcpyAsync(hi->q, u0_dev[i], sizeof(double) * hi->d, cudaMemcpyDeviceToDevice, hi->stream));
+            runs.emplace_back(hi, K[i], 0, false);
+            CKS(runs.back().begin());
+        }
+        // a batched fine phase: join the handles still iterating, one launch, fork
+        auto batched = [&](int k, int li) -> pr_status {
+            for (int i : g.idx) {
+                if (k >= K[i]) continue;
+                CKC(cudaEventRecord(b->ev[i + 1], b->hs[i]->stream));
+                CKC(cudaStreamWaitEvent(g.stream, b->ev[i + 1], 0));
+            }
+            CKC(fine_batch_coop(b->items + g.first[li], (int)g.count[li], g.total[li], g.maxnf[li], g.gb,
+                                g.stream));
+            CKC(cudaEventRecord(g.ev, g.stream));
+            for (int i : g.idx)
+                if (k < K[i]) CKC(cudaStreamWaitEvent(b->hs[i]->stream, g.ev, 0));
+            return PR_OK;
+        };
+        for (int k = 0; k < Kmax; ++k) {
+            CKS(batched(k, 2 * k));
+            for (size_t j = 0; j < g.idx.size(); ++j) {
+                if (k >= K[g.idx[j]]) continue;
+                CKC(runs[j].mark());
+                CKS(runs[j].update());
+            }
+            CKS(batched(k, 2 * k + 1));
+            int done = 0;
+            for (size_t j = 0; j < g.idx.size(); ++j)
+                if (k < K[g.idx[j]]) CKS(runs[j].correct(&done));
+        }
+        for (int i : g.idx) {
+            pr_solver* hi = b->hs[i];
+            CKC(cudaEventRecord(hi->ev1, hi->stream));
+            CKC(cudaMemcpyAsync(qT_dev[i], hi->q + (long)hi->N * hi->d, sizeof(double) * hi->d,
+                                cudaMemcpyDeviceToDevice, hi->stream));
+            CKC(cudaEventRecord(b->ev[i + 1], hi->stream));
             CKC(cudaStreamWaitEvent(b->stream, b->ev[i + 1], 0));
         }
-        CKC(fine_batch_coop(b->items + b->first[li], (int)b->count[li], b->total[li], b->maxnf[li], b->gb,
-                            b->stream));
-        CKC(cudaEventRecord(eb, b->stream));
-        for (int i = 0; i < n; ++i)
-            if (k < K[i]) CKC(cudaStreamWaitEvent(b->hs[i]->stream, eb, 0));
-        return PR_OK;
-    };
-    for (int k = 0; k < Kmax; ++k) {
-        CKS(batched(k, 2 * k));
-        for (int i = 0; i < n; ++i) {
-            if (k >= K[i]) continue;
-            CKC(runs[i].mark());
-            CKS(runs[i].update());
-        }
-        CKS(batched(k, 2 * k + 1));
-        int done = 0;
-        for (int i = 0; i < n; ++i)
-            if (k < K[i]) CKS(runs[i].correct(&done));
-    }
-    for (int i = 0; i < n; ++i) {
-        pr_solver* hi = b->hs[i];
-        CKC(cudaEventRecord(hi->ev1, hi->stream));
-        CKC(cudaMemcpyAsync(qT_dev[i], hi->q + (long)hi->N * hi->d, sizeof(double) * hi->d,
-                            cudaMemcpyDeviceToDevice, hi->stream));
-        CKC(cudaEventRecord(b->ev[i + 1], hi->stream));
-        CKC(cudaStreamWaitEvent(b->stream, b->ev[i + 1], 0));
+        CKC(cudaEventRecord(g.ev, g.stream));
+        CKC(cudaStreamWaitEvent(b->stream, g.ev, 0));
     }
     return PR_OK;
 }
@@ -1334,15 +1373,11 @@ pr_status parareal_batch_create(pr_solver* const* hs, int32_t n, const double* c
     b->hs.assign(hs, hs + n);
     b->stream = (cudaStream_t)stream;
     b->lockstep = batch_lockstep_ok(hs, n);
-    b->ev.assign((size_t)n + 2, nullptr);
+    b->ev.assign((size_t)n + 1, nullptr);
     cudaError_t e = cudaSuccess;
     for (auto& x : b->ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
-    if (e == cudaSuccess && b->lockstep) {
-        e = cudaMalloc((void**)&b->gb, sizeof(GridBar));
-        if (e == cudaSuccess) e = cudaMemset(b->gb, 0, sizeof(GridBar));
-        if (e == cudaSuccess) e = batch_tables(b, K);
-    }
+    if (e == cudaSuccess && b->lockstep) e = batch_setup(b, K);
     if (e != cudaSuccess) {
         batch_free(b);
         return set_err(h, PR_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
