@@ -285,9 +285,11 @@ struct FineBatchItem {
 // Output tiles per state of the batched sweep's tile shape.
 void fine_batch_tiles(int nx, int ny, int* tiles_x, int* tiles);
 // All nf steps of all items in one cooperative launch with a bounded grid
-// barrier between steps (items sorted by tile0; total = sum of n * tiles).
+// barrier between steps (items sorted by tile0; total = sum of n * tiles),
+// on max_sms SMs (0: all), so that several batched launches can run side by
+// side.
 cudaError_t fine_batch_coop(const FineBatchItem* items_dev, int nitems, long total, int max_nf, GridBar* gb,
-                            cudaStream_t s);
+                            cudaStream_t s, int max_sms);
 
 struct FineCoefK {
     double adx[3], ady[3], csx[3], csy[3], dxx[3], dxy1[3], dyy[3], dxy2[3];

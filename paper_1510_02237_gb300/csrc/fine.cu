@@ -313,7 +313,7 @@ void fine_batch_tiles(int nx, int ny, int* tiles_x, int* tiles) {
 }
 
 cudaError_t fine_batch_coop(const FineBatchItem* items_dev, int nitems, long total, int max_nf, GridBar* gb,
-                            cudaStream_t s) {
+                            cudaStream_t s, int max_sms) {
     if (nitems < 1 || total < 1 || max_nf < 1) return cudaSuccess;
     static DevMemo memo;   // [device] -> (SMs, CTAs per SM)
     int dev = 0;
@@ -331,6 +331,7 @@ cudaError_t fine_batch_coop(const FineBatchItem* items_dev, int nitems, long tot
         memo.put(dev, sms, per);
     }
     if (per < 1) return cudaErrorInvalidConfiguration;
+    if (max_sms > 0 && max_sms < sms) sms = max_sms;
     long nb = (long)sms * per;
     if (nb > total) nb = total;
     e = cudaMemsetAsync(&gb->count, 0, sizeof(unsigned), s);

@@ -1164,6 +1164,7 @@ struct pr_batch {
         cudaStream_t stream = nullptr;     // the group's batched fine launches
         GridBar* gb = nullptr;
         cudaEvent_t ev = nullptr;
+        int sm_limit = 0;                  // SMs of its batched launches: the sum of its handles' limits
         std::vector<long> first, count, total;   // per batched launch: its items and work indices
         std::vector<int> maxnf;
     };
@@ -1249,6 +1250,16 @@ static cudaError_t batch_setup(pr_batch* b, const int32_t* K) {
     }
     std::vector<FineBatchItem> tab;
     for (auto& g : b->groups) {
+        // the group's batched sweeps take the SMs its handles would use side by
+        // side (no limit if any handle has none)
+        for (int i : g.idx) {
+            const int l = b->hs[i]->opt.sm_limit;
+            if (l <= 0) {
+                g.sm_limit = 0;
+                break;
+            }
+            g.sm_limit += l;
+        }
         cudaError_t e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMalloc((void**)&g.gb, sizeof(GridBar));
@@ -1319,7 +1330,7 @@ static pr_status batch_capture_lockstep(pr_batch* b, const double* const* u0_dev
                 CKC(cudaStreamWaitEvent(g.stream, b->ev[i + 1], 0));
             }
             CKC(fine_batch_coop(b->items + g.first[li], (int)g.count[li], g.total[li], g.maxnf[li], g.gb,
-                                g.stream));
+                                g.stream, g.sm_limit));
             CKC(cudaEventRecord(g.ev, g.stream));
             for (int i : g.idx)
                 if (k < K[i]) CKC(cudaStreamWaitEvent(b->hs[i]->stream, g.ev, 0));
