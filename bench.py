@@ -291,36 +291,47 @@ def batching_workload(P, torch):
     ms_seq = e0.elapsed_time(e1)
     for s in seq:
         s.close()
-    # one graph, per-instance streams and SM limits
-    streams = [P.new_stream() for _ in insts]
-    bat = [P.Solver(i.problem, stream=st, K_max=i.K, sm_limit=default_sm_limit(i.problem.d, sms), **opt)
-           for i, st in zip(insts, streams)]
-    for s in bat:
-        P.parareal_autotune(s.h)
-    outs_b = [torch.empty_like(u) for u in u0s]
-    side = P.new_stream()
-    g = P.parareal_batch_create([s.h for s in bat], u0s, [i.K for i in insts], outs_b, side)
-    for rep in range(2):
-        torch.cuda.synchronize()
-        e0.record(side)
-        P.parareal_batch_launch(g)
-        e1.record(side)
-        torch.cuda.synchronize()
-    ms_bat = e0.elapsed_time(e1)
-    P.parareal_batch_destroy(g)
-    # the same SM limits without concurrency, for the bitwise comparison
-    same = 0
-    for s, i, u, o in zip(bat, insts, u0s, outs_b):
-        ref = torch.empty_like(u)
-        P.parareal_solve(s.h, u, i.K, qT=ref, report=False)
-        torch.cuda.synchronize()
-        same += int(torch.equal(ref, o))
-    for s in bat:
-        s.close()
+    # one graph: per-instance streams and SM limits, the fine sweeps either on
+    # the instances' streams or as one persistent launch per phase over all
+    def graph_run(persistent):
+        streams = [P.new_stream() for _ in insts]
+        extra = {"batch_fine": P.PR_BATCH_PERSISTENT} if persistent else {}
+        bat = [P.Solver(i.problem, stream=st, K_max=i.K, sm_limit=default_sm_limit(i.problem.d, sms), **opt,
+                        **extra) for i, st in zip(insts, streams)]
+        for s in bat:
+            P.parareal_autotune(s.h)
+        outs_b = [torch.empty_like(u) for u in u0s]
+        side = P.new_stream()
+        g = P.parareal_batch_create([s.h for s in bat], u0s, [i.K for i in insts], outs_b, side)
+        for rep in range(2):
+            torch.cuda.synchronize()
+            e0.record(side)
+            P.parareal_batch_launch(g)
+            e1.record(side)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        P.parareal_batch_destroy(g)
+        # the same SM limits without concurrency, for the bitwise comparison
+        same = 0
+        for s, i, u, o in zip(bat, insts, u0s, outs_b):
+            ref = torch.empty_like(u)
+            P.parareal_solve(s.h, u, i.K, qT=ref, report=False)
+            torch.cuda.synchronize()
+            same += int(torch.equal(ref, o))
+        for s in bat:
+            s.close()
+        return ms, same
+    ms_bat, same = graph_run(False)
+    ms_pers, same_p = graph_run(True)
     res.update({"ms_sequential": ms_seq, "ms_batched_graph": ms_bat,
                 "solves_per_s_sequential": len(insts) / (ms_seq / 1e3),
                 "solves_per_s_batched": len(insts) / (ms_bat / 1e3), "speedup": ms_seq / ms_bat,
                 "results_bitwise_equal_alone": f"{same}/{len(insts)}",
+                "persistent_fine": {"ms": ms_pers, "solves_per_s": len(insts) / (ms_pers / 1e3),
+                                    "speedup": ms_seq / ms_pers,
+                                    "results_bitwise_equal_alone": f"{same_p}/{len(insts)}",
+                                    "what": "the same graph with the fine sweeps of all 64 instances as one "
+                                            "persistent cooperative launch per phase (solves in lockstep)"},
                 "autotune": {"what": "FP32X fine step: tile shape of the shared-memory kernel (TX x TY: "
                                      "0 = 32x8, 1 = 64x8, 2 = 64x16, 3 = 128x8), timed per problem shape",
                              "per_shape": tuned}})

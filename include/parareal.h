@@ -60,6 +60,7 @@ enum { PR_PROJ_FP64 = 0, PR_PROJ_SPLIT_BF16 = 1 };  /* arithmetic of the project
                                                       the BF16 tensor cores (each
                                                       FP64 column split into 8
                                                       exact 7-bit digit slices)     */
+enum { PR_BATCH_STREAMS = 0, PR_BATCH_PERSISTENT = 1 };  /* fine sweeps of a batch graph */
 enum { PR_COARSE_SPLIT_FE = 0, PR_COARSE_RK3 = 1 };  /* coarse propagator G: partially
                                                       split forward Euler with
                                                       forward-backward acoustic
@@ -140,6 +141,13 @@ typedef struct {
                               the column's y-velocity.  0 (default): constant
                               (U, V).  The paper's workload: U = V = 0,
                               omega = pi, c_s = 30                              */
+    int32_t batch_fine;    /* in batch graphs (parareal_batch_create):
+                              PR_BATCH_STREAMS (default) runs this handle's
+                              solve on its own stream; PR_BATCH_PERSISTENT puts
+                              its fine sweeps into the batch's persistent
+                              launches (used when every handle of the batch asks
+                              for it and runs PR_FP32X with V = 0, no rotation,
+                              KSE-Parareal in one parallel step)               */
 } pr_options;
 
 typedef struct {
@@ -320,18 +328,18 @@ typedef struct pr_batch pr_batch;
 /* Capture the n solves of parareal_solve_batch (same arguments, which stay
  * bound to the batch: refill u0_dev[i] before each launch) into one CUDA
  * graph that forks from `stream` into the handles' streams and joins back.
- * When every handle runs the FP32-tendency fine sweep (PR_FP32X) with V = 0,
- * no rotation, KSE-Parareal and one parallel step, the handles are grouped
- * by problem shape (grid, slices, fine steps per slice) and each group's
- * fine sweeps (the predictor of every iteration and the fine images of the
- * new basis columns) run as one persistent cooperative launch over all the
- * (state, tile) items of its handles still iterating; the rest of each
- * solve runs on the handle's stream.  Results equal the handles' solo
- * solves bit for bit either way.  Handles must be distinct, with non-NULL
- * streams other than `stream`; handles sharing a stream run one after the
- * other.  Requires r_tol = 0 on every handle.  Allocates the graph, and for
- * batched fine sweeps one stream, one barrier word and the work tables per
- * group. */
+ * When every handle has batch_fine = PR_BATCH_PERSISTENT and runs the
+ * FP32-tendency fine sweep (PR_FP32X) with V = 0, no rotation, KSE-Parareal
+ * and one parallel step, the solves advance in lockstep phase by phase and
+ * their fine sweeps (the predictor of every iteration and the fine images of
+ * the new basis columns) run as one persistent cooperative launch per phase
+ * over all the (state, tile) items of the handles still iterating; the rest
+ * of each solve runs on the handle's stream.  Results equal the handles'
+ * solo solves bit for bit either way.  Handles must be distinct, with
+ * non-NULL streams other than `stream`; handles sharing a stream run one
+ * after the other.  Requires r_tol = 0 on every handle.  Allocates the
+ * graph, and for persistent fine sweeps one stream, one barrier word and the
+ * work tables. */
 pr_status parareal_batch_create(pr_solver* const* hs, int32_t n, const double* const* u0_dev, const int32_t* K,
                                 double* const* qT_dev, void* stream, pr_batch** out);
 /* Enqueue one replay of the batch graph on its stream (asynchronous). */

@@ -20,6 +20,7 @@ PR_KSE, PR_ORIGINAL = 0, 1
 PR_IMAGES_LINEARITY, PR_IMAGES_DIRECT = 0, 1
 PR_PROJ_FP64, PR_PROJ_SPLIT_BF16 = 0, 1
 PR_COARSE_SPLIT_FE, PR_COARSE_RK3 = 0, 1
+PR_BATCH_STREAMS, PR_BATCH_PERSISTENT = 0, 1
 PR_MAX_ITERS = 128
 _STATUS = {0: "PR_OK", -1: "PR_EINVAL", -2: "PR_ENOMEM", -3: "PR_ECUDA", -4: "PR_ETIMEOUT",
            -5: "PR_ESTATE", -6: "PR_ECANCELLED"}
@@ -36,7 +37,7 @@ class pr_options(C.Structure):
                 ("fine_prec", C.c_int32), ("variant", C.c_int32), ("corr_prec", C.c_int32),
                 ("r_tol", C.c_double), ("n_windows", C.c_int32), ("images", C.c_int32),
                 ("sm_limit", C.c_int32), ("stream", C.c_void_p), ("proj_prec", C.c_int32),
-                ("coarse_scheme", C.c_int32), ("omega", C.c_double)]
+                ("coarse_scheme", C.c_int32), ("omega", C.c_double), ("batch_fine", C.c_int32)]
 
 
 class pr_report(C.Structure):

@@ -35,14 +35,16 @@ def _alone(inst, **opt):
         return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed", "fp32x"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "mixed_persistent", "fp32x_persistent"])
 def test_batch_equals_alone(mode):
-    """'mixed' and 'fp32x' (FP32 tendencies, FP32 or FP64 correction) batches
+    """The '_persistent' batches (FP32 tendencies, FP32 or FP64 correction)
     run their fine sweeps as one persistent launch per phase over all
-    handles (lockstep capture); 'fp64' forks the handles' own solves."""
+    handles (lockstep capture); the others fork the handles' own solves."""
     insts = W.workload_batch(6, seed=2000)
+    pers = {"batch_fine": P.PR_BATCH_PERSISTENT}
     opt = {"fp64": {}, "mixed": {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32},
-           "fp32x": {"fine_prec": P.PR_FP32X}}[mode]
+           "mixed_persistent": {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32, **pers},
+           "fp32x_persistent": {"fine_prec": P.PR_FP32X, **pers}}[mode]
     want = [_alone(i, sm_limit=8, **opt) for i in insts]
     streams = [P.new_stream() for _ in insts]
     solvers = [P.Solver(i.problem, stream=st, K_max=i.K, sm_limit=8, **opt) for i, st in zip(insts, streams)]
