@@ -408,6 +408,14 @@ pr_status parareal_selftest_wait_timeout(void* stream, double* seconds);
 /* Process-wide number of CUDA kernels this library has launched. */
 uint64_t parareal_kernel_launches(void);
 
+/* Synchronise the handle's stream and report whether the work enqueued on
+ * it so far completed cleanly: PR_OK, PR_ETIMEOUT if a bounded device-side
+ * wait gave up (a grid barrier, a tensor-core pipeline or row-ring wait;
+ * results since then are invalid and the handle should be destroyed), or
+ * PR_ECUDA.  For callers of the asynchronous calls (parareal_solve without a
+ * report, batches, servers); the paper has no counterpart. */
+pr_status parareal_status(pr_solver* h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,7 +78,7 @@ EXPORTS = ["parareal_default_options", "parareal_create", "parareal_destroy", "p
            "krylov_project", "parareal_timing_enable", "parareal_timing_read", "parareal_kernel_launches",
            "parareal_alu_probe", "parareal_fine_sweep_static", "parareal_selftest_wait_timeout",
            "parareal_solve_batch", "parareal_batch_create", "parareal_batch_launch", "parareal_batch_destroy",
-           "parareal_split_gemm_tn", "parareal_split_gemm_nn", "parareal_autotune"]
+           "parareal_split_gemm_tn", "parareal_split_gemm_nn", "parareal_autotune", "parareal_status"]
 
 _lib = None
 
@@ -128,6 +128,8 @@ def lib():
     L.parareal_timing_read.restype = st
     L.parareal_autotune.argtypes = [P, C.POINTER(pr_tuning)]
     L.parareal_autotune.restype = st
+    L.parareal_status.argtypes = [P]
+    L.parareal_status.restype = st
     L.parareal_kernel_launches.argtypes = []
     L.parareal_kernel_launches.restype = C.c_uint64
     L.parareal_alu_probe.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_double)]
@@ -218,6 +220,11 @@ def parareal_solve_host(h, u0_host, K, qT_host, report=True):
     _check(h, lib().parareal_solve_host(h, _ptr(u0_host), int(K), _ptr(qT_host),
                                         C.byref(rep) if rep is not None else None))
     return rep
+
+
+def parareal_status(h):
+    """Synchronise the handle's stream; raise if a device-side wait gave up."""
+    _check(h, lib().parareal_status(h))
 
 
 def parareal_fine_sweep(h, q_in, q_out, n):

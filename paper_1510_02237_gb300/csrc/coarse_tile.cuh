@@ -171,6 +171,11 @@ __device__ __forceinline__ void coarse_tile(const Tin* src, Tout* __restrict__ d
     // slow (advective) tendency on the region shrunk by ra
     {
         const int W1 = RX - 2 * ra, H1 = RY - 2 * ra, N1 = W1 * H1;
+        // first order: both x-interfaces of a cell move with the row's velocity
+        // and both y-interfaces with the column's, so the flux difference is the
+        // velocity times the upwind difference of the field (y skipped when
+        // the advection has no y-component anywhere)
+        const bool ynone = cd.V == 0.0 && cd.omega == 0.0;
         for (int t = threadIdx.x; t < N1; t += NT) {
             int r = t / W1;
             int i = (r + ra) * RX + (t - r * W1) + ra;
@@ -178,12 +183,25 @@ __device__ __forceinline__ void coarse_tile(const Tin* src, Tout* __restrict__ d
             T* ss[3] = {su, sw, sp};
             T Ur, Vc;
             vel(r + ra, t - r * W1 + ra, Ur, Vc);
+            if (c.order == 1) {
+                const T ax = -Ur * c.inv_dx, ay = -Vc * c.inv_dy;
+                const int sx = Ur >= T(0) ? -1 : 1, sy = Vc >= T(0) ? -RX : RX;
 #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                const T* a = fs[f];
-                T Fe = upwind_flux<T>(c.order, Ur, a, i, 1), Fw = upwind_flux<T>(c.order, Ur, a, i - 1, 1);
-                T Gn = upwind_flux<T>(c.order, Vc, a, i, RX), Gs = upwind_flux<T>(c.order, Vc, a, i - RX, RX);
-                ss[f][i] = -(Fe - Fw) * c.inv_dx - (Gn - Gs) * c.inv_dy;
+                for (int f = 0; f < 3; ++f) {
+                    const T* a = fs[f];
+                    const T dx_ = sx < 0 ? a[i] - a[i - 1] : a[i + 1] - a[i];
+                    T v = ax * dx_;
+                    if (!ynone) v += ay * (sy < 0 ? a[i] - a[i - RX] : a[i + RX] - a[i]);
+                    ss[f][i] = v;
+                }
+            } else {
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    const T* a = fs[f];
+                    T Fe = upwind_flux<T>(c.order, Ur, a, i, 1), Fw = upwind_flux<T>(c.order, Ur, a, i - 1, 1);
+                    T Gn = upwind_flux<T>(c.order, Vc, a, i, RX), Gs = upwind_flux<T>(c.order, Vc, a, i - RX, RX);
+                    ss[f][i] = -(Fe - Fw) * c.inv_dx - (Gn - Gs) * c.inv_dy;
+                }
             }
         }
     }

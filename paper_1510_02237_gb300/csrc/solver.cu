@@ -1034,6 +1034,12 @@ pr_status parareal_timing_read(pr_solver* h, pr_timing* t, int32_t reset) {
 
 uint64_t parareal_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+pr_status parareal_status(pr_solver* h) {
+    if (!h) return PR_EINVAL;
+    CKC(cudaStreamSynchronize(h->stream));
+    return check_device_waits(h);
+}
+
 // ------------------------------------------------------------------ autotuning
 
 }  // extern "C"

@@ -3,8 +3,11 @@
 Requests (an initial value, a problem and K) arrive over time.  A request is
 admitted as soon as a solver slot for its problem shape is free, or can be
 created within the device-memory budget (slot footprint from
-``parareal_footprint_bytes``: iterates, fine images and the Krylov basis) and
-the in-flight limit.  Each slot owns a solver handle with its own CUDA
+``parareal_footprint_bytes``: iterates, fine images and the Krylov basis),
+the in-flight limit and the SM budget (the grid-synchronised kernels of the
+solves in flight, each on its slot's SM limit, fit on the GPU side by side).
+Every completed solve's handle is asked whether a device-side wait gave up
+(counted in ``device_errors``).  Each slot owns a solver handle with its own CUDA
 stream, device input/output buffers and pinned host staging buffers, so
 admitted requests run side by side on the device while later ones keep
 arriving.  A request's latency runs from its arrival to the moment its
@@ -21,8 +24,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (PR_FP32, PR_FP32X, PR_FP64, PR_PROJ_SPLIT_BF16, Solver, new_stream, parareal_autotune,
-               parareal_footprint_bytes, parareal_solve)
+from . import (PR_FP32, PR_FP32X, PR_FP64, PR_PROJ_SPLIT_BF16, PararealError, Solver, new_stream,
+               parareal_autotune, parareal_footprint_bytes, parareal_solve, parareal_status)
 
 
 @dataclass
@@ -48,6 +51,7 @@ class _Slot:
     u0_host: object
     qT_host: object
     bytes: int
+    sms: int = 0            # SMs its grid-synchronised kernels use
     busy: bool = False
 
 
@@ -58,6 +62,7 @@ class ServeStats:
     peak_inflight: int = 0
     peak_bytes: int = 0
     slots_created: int = 0
+    device_errors: int = 0   # completed solves whose handle reported a device-side wait that gave up
     latencies_s: list = field(default_factory=list)
 
     def summary(self) -> dict:
@@ -67,7 +72,7 @@ class ServeStats:
                 "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
                 "mean_ms": float(lat.mean()) if len(lat) else None, "makespan_s": self.makespan_s,
                 "peak_inflight": self.peak_inflight, "peak_device_bytes": self.peak_bytes,
-                "slots_created": self.slots_created}
+                "slots_created": self.slots_created, "device_errors": self.device_errors}
 
 
 def default_sm_limit(d: int, sms: int) -> int:
@@ -123,14 +128,19 @@ class Server:
         p = inst.problem
         return (p.nx, p.ny, p.n_slices, p.n_f, p.n_g, p.U, p.V, p.c_s, p.nu_f, p.nu_c, p.n_sound)
 
-    def _acquire(self, inst, inflight: int):
+    def _acquire(self, inst, inflight: int, sms_used: int = 0):
         if inflight >= self.max_inflight:
+            return None
+        # SM admission: the grid-synchronised kernels of all solves in flight
+        # fit on the GPU side by side
+        p = inst.problem
+        need = self.solver_options(p).get("sm_limit", 0) or self.sms
+        if inflight and sms_used + need > self.sms:
             return None
         key = self._key(inst)
         for s in self.slots[key]:
             if not s.busy:
                 return s
-        p = inst.problem
         K_max = min(p.n_slices, 8)
         opt = self._options(p, K_max)
         nbytes = parareal_footprint_bytes(p.nx, p.ny, p.n_slices, **opt)
@@ -146,7 +156,7 @@ class Server:
         slot = _Slot(key, solver, stream, torch.empty(p.d, dtype=torch.float64, device="cuda"),
                      torch.empty(p.d, dtype=torch.float64, device="cuda"),
                      torch.empty(p.d, dtype=torch.float64).pin_memory(),
-                     torch.empty(p.d, dtype=torch.float64).pin_memory(), nbytes)
+                     torch.empty(p.d, dtype=torch.float64).pin_memory(), nbytes, need)
         self.slots[key].append(slot)
         self.bytes += nbytes
         self.stats.slots_created += 1
@@ -191,6 +201,10 @@ class Server:
             for (i, slot, ev, t_adm) in inflight:
                 if ev.query():
                     t_done = now() if realtime else 0.0
+                    try:
+                        parareal_status(slot.solver.h)   # the stream is idle: no wait
+                    except PararealError:
+                        self.stats.device_errors += 1
                     results[i] = Result(i, requests[i][0], t_adm, t_done, slot.qT_host.numpy().copy())
                     slot.busy = False
                     self.stats.completed += 1
@@ -202,7 +216,7 @@ class Server:
             while waiting:
                 i = waiting[0]
                 inst = requests[i][1]
-                slot = self._acquire(inst, len(inflight))
+                slot = self._acquire(inst, len(inflight), sum(sl.sms for (_, sl, _, _) in inflight))
                 if slot is None:
                     break
                 waiting.popleft()
