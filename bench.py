@@ -387,11 +387,13 @@ def serving_workload(P, torch, n_req=2000):
     with exact split digits) at 1000 requests/s (saturated: its throughput)
     and at 12 requests/s with n_req requests (below saturation, so the
     percentiles measure service, not an unbounded queue); mode 'mixed' (FP32
-    tendencies and correction in addition) at 1000 requests/s.  Each mode reports the
+    tendencies and correction in addition) at 1000 requests/s; and plain
+    'fp64' at 1000 requests/s, the baseline for the same request stream.  Each mode reports the
     equal-accuracy check of a sample of its served results."""
     from paper_1510_02237_gb300 import serve
     out = {"budget_bytes": 150e9, "modes": {}}
-    for mode, plan in (("fp64_tc", ((1000, 300), (12, n_req))), ("mixed", ((1000, 300),))):
+    for mode, plan in (("fp64", ((1000, 300),)), ("fp64_tc", ((1000, 300), (12, n_req))),
+                       ("mixed", ((1000, 300),))):
         srv = serve.Server(budget_bytes=150e9, max_inflight=16, mode=mode)
         srv.run(W.request_stream(1000.0, 8, seed=99))          # create slots untimed
         res = {"rates": {}}
