@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream sweep")
+    ap.add_argument("--serving-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests of the equal-accuracy serving stream (12 requests/s)")
     ap.add_argument("--case", choices=["fine", "fine32", "fine32x", "solve", "solve_mixed"], default=None,
@@ -407,6 +408,34 @@ def serving_workload(P, torch, n_req=2000):
     return out
 
 
+def serving_subprocess(n_req, torch):
+    """The request-stream sweep in a process of its own (its 16 concurrent
+    solves are the most concurrent scenario of the bench): its JSON result,
+    or the reason it did not produce one -- a failure there cannot take the
+    rest of the bench line with it."""
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    cmd = [sys.executable, os.path.abspath(__file__), "--serving-only", "--serving-requests", str(n_req)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=1200)
+    except subprocess.TimeoutExpired:
+        return {"error": "request-stream sweep did not finish within 1200 s"}
+    for line in reversed(r.stdout.strip().splitlines()):
+        if line.startswith("{"):
+            return json.loads(line)
+    return {"error": f"request-stream sweep exited {r.returncode}: " + (r.stderr.strip().splitlines() or ["?"])[-1][:300]}
+
+
+def run_serving_only(args):
+    import torch
+
+    import paper_1510_02237_gb300 as P
+    torch.cuda.set_device(0)
+    P.lib()
+    print(json.dumps(serving_workload(P, torch, n_req=args.serving_requests)))
+    return 0
+
+
 def precision_workload(P, torch, stream):
     """512x256, N = 64, K = 5, power-law Fourier IC: one solve each in plain FP64
     (images by linearity, as in the paper), FP64 with direct images, FP64 with
@@ -703,7 +732,7 @@ def run_ours(args):
         tables = paper_tables(P, torch, stream)
         precision = precision_workload(P, torch, stream)
         batching = batching_workload(P, torch)
-        serving = serving_workload(P, torch, n_req=args.serving_requests) if not args.no_serving else None
+        serving = serving_subprocess(args.serving_requests, torch) if not args.no_serving else None
         # ---- roofline of the dominant phase's kernel
         phases = {k: tm[k] / n for k in ("ms_init", "ms_fine", "ms_coarse", "ms_krylov", "ms_gs_block",
                                           "ms_gs_intra", "ms_kold", "ms_chain")}
@@ -790,6 +819,8 @@ def run_case(args):
 
 def main():
     args = parse()
+    if args.serving_only:
+        return run_serving_only(args)
     if args.case:
         return run_case(args)
     if args.impl == "reference":
