@@ -56,9 +56,9 @@ def _sha(path):
 
 
 # DRAM traffic of one FP64 fine-sweep launch from an ncu capture of the same
-# kernel source (25.6 MB read + 712.4 MB written for 32 slices x 32768 cells
+# kernel source (26.2 MB read + 709.8 MB written for 32 slices x 32768 cells
 # x 20 steps: the stage buffers leave L2); null once fine_coop.cu changes.
-FINE_TRAFFIC = {"source_sha": "ffc670714459", "bytes_per_cell_step": 35.19}
+FINE_TRAFFIC = {"source_sha": "8e96352a0fbe", "bytes_per_cell_step": 35.10}
 
 
 def parse():
@@ -261,43 +261,50 @@ def batching_workload(P, torch):
     solved one after another on one stream with every SM available, then all
     together as one CUDA graph whose branches run on per-instance streams with
     SM-limited grid-synchronised kernels.  Each is timed with CUDA events after
-    one untimed pass; the results of the two are compared bit for bit."""
-    from paper_1510_02237_gb300.serve import default_sm_limit
+    one untimed pass; the results of the two are compared bit for bit.  The
+    same again with the subspace products on the tensor cores (FP64-accurate
+    split digits), and the graph with all fine sweeps as one persistent
+    launch per phase."""
+    from paper_1510_02237_gb300.serve import batch_sm_limit
     insts = W.workload_batch(64)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    opt = {"fine_prec": P.PR_FP32X}
+    base_opt = {"fine_prec": P.PR_FP32X}
     u0s = [torch.from_numpy(i.initial_value().ravel()).cuda() for i in insts]
     res = {"instances": len(insts), "solves": len(insts), "fine_prec": "f32 tendencies, f64 state",
            "corr_prec": "f64", "cells_total": int(sum(i.problem.ncell for i in insts)),
            "fine_cell_steps_total": float(sum(sum(i.problem.n_slices - k for k in range(i.K)) * i.problem.n_f
-                                              * i.problem.ncell for i in insts))}
+                                              * i.problem.ncell for i in insts)),
+           "sm_limit": "per instance max(4, min(SMs, d / 2048))"}
     main = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # sequential, all SMs per solve; fine-step launch shapes autotuned per
-    # problem shape (cached, untimed)
-    seq = [P.Solver(i.problem, stream=main, K_max=i.K, **opt) for i in insts]
     tuned = {}
-    for s, i in zip(seq, insts):
-        t = P.parareal_autotune(s.h)
-        if not t["cached"]:
-            tuned[f"{i.problem.nx}x{i.problem.ny}_N{i.problem.n_slices}"] = t
-    outs_a = [torch.empty_like(u) for u in u0s]
-    for rep in range(2):
-        torch.cuda.synchronize()
-        e0.record(main)
-        for s, i, u, o in zip(seq, insts, u0s, outs_a):
-            P.parareal_solve(s.h, u, i.K, qT=o, report=False)
-        e1.record(main)
-        torch.cuda.synchronize()
-    ms_seq = e0.elapsed_time(e1)
-    for s in seq:
-        s.close()
-    # one graph: per-instance streams and SM limits, the fine sweeps either on
-    # the instances' streams or as one persistent launch per phase over all
-    def graph_run(persistent):
+
+    def sequential(opt):
+        # one after another, all SMs per solve; fine-step launch shapes
+        # autotuned per problem shape (cached, untimed)
+        seq = [P.Solver(i.problem, stream=main, K_max=i.K, **opt) for i in insts]
+        for s, i in zip(seq, insts):
+            t = P.parareal_autotune(s.h)
+            if not t["cached"]:
+                tuned[f"{i.problem.nx}x{i.problem.ny}_N{i.problem.n_slices}"] = t
+        outs = [torch.empty_like(u) for u in u0s]
+        for rep in range(2):
+            torch.cuda.synchronize()
+            e0.record(main)
+            for s, i, u, o in zip(seq, insts, u0s, outs):
+                P.parareal_solve(s.h, u, i.K, qT=o, report=False)
+            e1.record(main)
+            torch.cuda.synchronize()
+        for s in seq:
+            s.close()
+        return e0.elapsed_time(e1)
+
+    def graph_run(opt, persistent):
+        # one graph: per-instance streams and SM limits, the fine sweeps either
+        # on the instances' streams or as one persistent launch per phase
         streams = [P.new_stream() for _ in insts]
         extra = {"batch_fine": P.PR_BATCH_PERSISTENT} if persistent else {}
-        bat = [P.Solver(i.problem, stream=st, K_max=i.K, sm_limit=default_sm_limit(i.problem.d, sms), **opt,
+        bat = [P.Solver(i.problem, stream=st, K_max=i.K, sm_limit=batch_sm_limit(i.problem.d, sms), **opt,
                         **extra) for i, st in zip(insts, streams)]
         for s in bat:
             P.parareal_autotune(s.h)
@@ -322,8 +329,23 @@ def batching_workload(P, torch):
         for s in bat:
             s.close()
         return ms, same
-    ms_bat, same = graph_run(False)
-    ms_pers, same_p = graph_run(True)
+
+    ms_seq = sequential(base_opt)
+    ms_bat, same = graph_run(base_opt, False)
+    ms_pers, same_p = graph_run(base_opt, True)
+    tc_opt = dict(base_opt, proj_prec=P.PR_PROJ_SPLIT_BF16)
+    tc_ok = all((3 * i.problem.nx * i.problem.ny) % 8 == 0 for i in insts)
+    tc = None
+    if tc_ok:
+        ms_seq_tc = sequential(tc_opt)
+        ms_bat_tc, same_tc = graph_run(tc_opt, False)
+        tc = {"ms_sequential": ms_seq_tc, "ms_batched_graph": ms_bat_tc,
+              "solves_per_s_sequential": len(insts) / (ms_seq_tc / 1e3),
+              "solves_per_s_batched": len(insts) / (ms_bat_tc / 1e3), "speedup": ms_seq_tc / ms_bat_tc,
+              "speedup_vs_fp64_products_sequential": ms_seq / ms_bat_tc,
+              "results_bitwise_equal_alone": f"{same_tc}/{len(insts)}",
+              "what": "the subspace products Q^T V and V - Q C on the BF16 tensor cores with exact split "
+                      "digits (FP64-accurate)"}
     res.update({"ms_sequential": ms_seq, "ms_batched_graph": ms_bat,
                 "solves_per_s_sequential": len(insts) / (ms_seq / 1e3),
                 "solves_per_s_batched": len(insts) / (ms_bat / 1e3), "speedup": ms_seq / ms_bat,
@@ -333,6 +355,7 @@ def batching_workload(P, torch):
                                     "results_bitwise_equal_alone": f"{same_p}/{len(insts)}",
                                     "what": "the same graph with the fine sweeps of all 64 instances as one "
                                             "persistent cooperative launch per phase (solves in lockstep)"},
+                "tensor_core_products": tc,
                 "autotune": {"what": "FP32X fine step: tile shape of the shared-memory kernel (TX x TY: "
                                      "0 = 32x8, 1 = 64x8, 2 = 64x16, 3 = 128x8), timed per problem shape",
                              "per_shape": tuned}})

@@ -139,38 +139,24 @@ __global__ void __launch_bounds__(FC_NT) k_fine_coop(FineSweepArgs a) {
 
 constexpr int FM_NT = 256;   // 8 warps per CTA, one CTA per SM
 
-// One field of one row around the lane's column: the lane's own value and a
-// halo value (lanes 0..2: columns x0-3..x0-1, lanes 3..5: x0+nv..x0+nv+2,
-// periodic); at(k) is the value at column x+k, k = -3..3.
-struct Fld {
-    double own, halo;
-};
-struct RowV {
-    Fld u, w, p;
-};
-
-__device__ __forceinline__ double at(const Fld& f, int lane, int k, int nv) {
-    const int src = lane + k;
-    const double a = __shfl_sync(0xffffffffu, f.own, src & 31);
-    const double h = __shfl_sync(0xffffffffu, f.halo, (src < 0 ? src + 3 : src - nv + 3) & 31);
-    return (src >= 0 && src < nv) ? a : h;
-}
-
-__device__ __forceinline__ RowV load_row(const double* in, long r, long ncell, int xo, int xh, bool hl) {
-    RowV v;
-    v.u.own = in[r + xo];
-    v.w.own = in[ncell + r + xo];
-    v.p.own = in[2 * ncell + r + xo];
-    v.u.halo = hl ? in[r + xh] : 0.0;
-    v.w.halo = hl ? in[ncell + r + xh] : 0.0;
-    v.p.halo = hl ? in[2 * ncell + r + xh] : 0.0;
-    return v;
-}
+// a - b as one FMA by a 1.0 held in a register: exactly the rounded
+// difference.  DADD and DFMA take the same FP64 pipe slot; in this kernel the
+// FMA form measured 4 % faster, but only with the 1.0 in a register -- as a
+// constant-bank operand of the FMAs (a literal or a kernel parameter) it was
+// 5 % slower than that.  The 1.0 is therefore read from device memory, which
+// the compiler cannot fold.
+__device__ double g_march_one = 1.0;
+__device__ __forceinline__ double dsub(double a, double b, double one) { return fma(a, one, -b); }
 
 // Stage k on the rows [g0, g1) of the batch's row segments (index
-// ((slice * nseg) + segment) * ny + y): out = qn + c_k L(in).  in, qn and out
-// are written by other CTAs earlier in the same launch (ordered by the grid
-// barriers), so they are read through the coherent path: no __restrict__.
+// ((slice * nseg) + segment) * ny + y): out = qn + c_k L(in).  A warp marches
+// down its rows with 32 columns per row (one per lane): each row's own values
+// are loaded one row ahead of their use, its x-neighbours (periodic offsets
+// -3..3 precomputed per lane) are loaded where they are used, from lines the
+// row's own loads brought into L1, and the x-differences of a row are reused
+// by the rows above and below it.  in, qn and out are written by other CTAs
+// earlier in the same launch (ordered by the grid barriers), so they are read
+// through the coherent path: no __restrict__, no __ldg.
 __device__ __forceinline__ void stage_march(const double* in, const double* qn, double* out, long d, int nx, int ny,
                                             int nseg, long g0, long g1, const FineCoefK& c, int k) {
     const int lane = threadIdx.x & 31;
@@ -181,6 +167,7 @@ __device__ __forceinline__ void stage_march(const double* in, const double* qn, 
     // u's x-terms on raw neighbours: A (6-point difference) + Cx (u[x+1] - 2u + u[x-1])
     const double up1 = c.up1[k], um1 = c.um1[k], up2 = c.up2[k], um2 = c.um2[k], um3 = c.um3[k], u00 = c.u00[k];
     const double A45 = c.a45[k], Am9 = c.am9[k], Cy2 = c.cy2[k];
+    const double one = g_march_one;
     for (long g = g0; g < g1;) {
         const long col = g / ny;
         const int y0 = (int)(g - col * ny);
@@ -188,59 +175,59 @@ __device__ __forceinline__ void stage_march(const double* in, const double* qn, 
         g += y1 - y0;
         const int z = (int)(col / nseg), sg = (int)(col - (long)z * nseg);
         const int x0 = 32 * sg, nv = min(32, nx - x0);
-        const int xo = x0 + (lane < nv ? lane : 0);
-        const bool hl = lane < 6;
-        const int xh = lane < 3 ? pwrap(x0 - 3 + lane, nx) : pwrap(x0 + nv + lane - 3, nx);
+        const int xo = x0 + (lane < nv ? lane : 0);   // lanes past a ragged edge compute, never store
+        const int xm1 = pwrap(xo - 1, nx), xp1 = pwrap(xo + 1, nx), xm2 = pwrap(xo - 2, nx);
+        const int xp2 = pwrap(xo + 2, nx), xm3 = pwrap(xo - 3, nx), xp3 = pwrap(xo + 3, nx);
         const double* src = in + (long)z * d;
         const double* qz = qn + (long)z * d;
         double* dz = out + (long)z * d;
-        // row above the range (only its x-differences and w, p are used) and the first row
-        const RowV m = load_row(src, (long)pwrap(y0 - 1, ny) * nx, ncell, xo, xh, hl);
-        double d1u_m = at(m.u, lane, 1, nv) - at(m.u, lane, -1, nv);
-        double d1w_m = at(m.w, lane, 1, nv) - at(m.w, lane, -1, nv);
-        double w_m = m.w.own, p_m = m.p.own;
-        RowV cr = load_row(src, (long)y0 * nx, ncell, xo, xh, hl);
-        double d1u_c = at(cr.u, lane, 1, nv) - at(cr.u, lane, -1, nv);
-        double d1w_c = at(cr.w, lane, 1, nv) - at(cr.w, lane, -1, nv);
-        // loads run one row ahead of their use: the row below the centre row
-        // and q^n of the centre row are in registers when an iteration starts
-        RowV nx_ = load_row(src, (long)(y0 + 1 < ny ? y0 + 1 : y0 + 1 - ny) * nx, ncell, xo, xh, hl);
-        long rc = (long)y0 * nx + xo;
-        double qu = qz[rc], qw = qz[ncell + rc], qp = qz[2 * ncell + rc];
+        // the row above the range (only its x-differences and w, p are used)
+        const double* rm = src + (long)pwrap(y0 - 1, ny) * nx;
+        double d1u_m = dsub(rm[xp1], rm[xm1], one);
+        double d1w_m = dsub(rm[ncell + xp1], rm[ncell + xm1], one);
+        double w_m = rm[ncell + xo], p_m = rm[2 * ncell + xo];
+        // the centre row and the row below: own values in registers
+        const double* rc = src + (long)y0 * nx;
+        double d1u_c = dsub(rc[xp1], rc[xm1], one);
+        double d1w_c = dsub(rc[ncell + xp1], rc[ncell + xm1], one);
+        double cu = rc[xo], cw = rc[ncell + xo], cp = rc[2 * ncell + xo];
+        const double* rb = src + (long)(y0 + 1 < ny ? y0 + 1 : y0 + 1 - ny) * nx;
+        double bu = rb[xo], bw = rb[ncell + xo], bp = rb[2 * ncell + xo];
+        long rcx = (long)y0 * nx + xo;
+        double qu = qz[rcx], qw = qz[ncell + rcx], qp = qz[2 * ncell + rcx];
         for (int y = y0; y < y1; ++y) {
-            const int y2 = pwrap(y + 2, ny);
-            const RowV nn = load_row(src, (long)y2 * nx, ncell, xo, xh, hl);
-            const long rn = (long)(y + 1 < ny ? y + 1 : y + 1 - ny) * nx + xo;
-            const double qu_n = qz[rn], qw_n = qz[ncell + rn], qp_n = qz[2 * ncell + rn];
-            const double d1u_n = at(nx_.u, lane, 1, nv) - at(nx_.u, lane, -1, nv);
-            const double d1w_n = at(nx_.w, lane, 1, nv) - at(nx_.w, lane, -1, nv);
-            // x-windows of the centre row
-            const double u1 = at(cr.u, lane, 1, nv), um1v = at(cr.u, lane, -1, nv);
-            const double u2 = at(cr.u, lane, 2, nv), um2v = at(cr.u, lane, -2, nv);
-            const double u3 = at(cr.u, lane, 3, nv), um3v = at(cr.u, lane, -3, nv);
-            const double d1p = at(cr.p, lane, 1, nv) - at(cr.p, lane, -1, nv);
-            const double d2p = at(cr.p, lane, 2, nv) - at(cr.p, lane, -2, nv);
-            const double d3p = at(cr.p, lane, 3, nv) - at(cr.p, lane, -3, nv);
-            const double d2w = at(cr.w, lane, 2, nv) - at(cr.w, lane, -2, nv);
-            const double d3w = at(cr.w, lane, 3, nv) - at(cr.w, lane, -3, nv);
-            const double dwy = nx_.w.own - w_m, dpy = nx_.p.own - p_m;
-            const double crw = d1w_n - d1w_m, cru = d1u_n - d1u_m;
+            const double* rn = src + (long)pwrap(y + 2, ny) * nx;
+            const double nu_ = rn[xo], nw_ = rn[ncell + xo], np_ = rn[2 * ncell + xo];
+            const long rnx = (long)(y + 1 < ny ? y + 1 : y + 1 - ny) * nx + xo;
+            const double qu_n = qz[rnx], qw_n = qz[ncell + rnx], qp_n = qz[2 * ncell + rnx];
+            const double d1u_n = dsub(rb[xp1], rb[xm1], one);
+            const double d1w_n = dsub(rb[ncell + xp1], rb[ncell + xm1], one);
+            const double u1 = rc[xp1], um1v = rc[xm1], u2 = rc[xp2], um2v = rc[xm2], u3 = rc[xp3], um3v = rc[xm3];
+            const double* rcw = rc + ncell;
+            const double* rcp = rc + 2 * ncell;
+            const double d1p = dsub(rcp[xp1], rcp[xm1], one);
+            const double d2p = dsub(rcp[xp2], rcp[xm2], one);
+            const double d3p = dsub(rcp[xp3], rcp[xm3], one);
+            const double d2w = dsub(rcw[xp2], rcw[xm2], one);
+            const double d3w = dsub(rcw[xp3], rcw[xm3], one);
+            const double dwy = dsub(bw, w_m, one), dpy = dsub(bp, p_m, one);
+            const double crw = dsub(d1w_n, d1w_m, one), cru = dsub(d1u_n, d1u_m, one);
             double nu = fma(up1, u1, qu);
             nu = fma(um1, um1v, nu);
             nu = fma(up2, u2, nu);
             nu = fma(um2, um2v, nu);
             nu = fma(A, u3, nu);
             nu = fma(um3, um3v, nu);
-            nu = fma(u00, cr.u.own, nu);
+            nu = fma(u00, cu, nu);
             nu = fma(Bx, d1p, nu);
             nu = fma(Ex, crw, nu);
             double nw = fma(A45, d1w_c, qw);
             nw = fma(Am9, d2w, nw);
             nw = fma(A, d3w, nw);
             nw = fma(By, dpy, nw);
-            nw = fma(Cy, nx_.w.own, nw);
+            nw = fma(Cy, bw, nw);
             nw = fma(Cy, w_m, nw);
-            nw = fma(Cy2, cr.w.own, nw);
+            nw = fma(Cy2, cw, nw);
             nw = fma(Ey, cru, nw);
             double np = fma(A45, d1p, qp);
             np = fma(Am9, d2p, np);
@@ -248,19 +235,25 @@ __device__ __forceinline__ void stage_march(const double* in, const double* qn, 
             np = fma(Bx, d1u_c, np);
             np = fma(By, dwy, np);
             if (lane < nv) {
-                dz[rc] = nu;
-                dz[ncell + rc] = nw;
-                dz[2 * ncell + rc] = np;
+                dz[rcx] = nu;
+                dz[ncell + rcx] = nw;
+                dz[2 * ncell + rcx] = np;
             }
-            w_m = cr.w.own;
-            p_m = cr.p.own;
+            w_m = cw;
+            p_m = cp;
             d1u_m = d1u_c;
             d1w_m = d1w_c;
-            cr = nx_;
-            nx_ = nn;
+            rc = rb;
+            cu = bu;
+            cw = bw;
+            cp = bp;
+            rb = rn;
+            bu = nu_;
+            bw = nw_;
+            bp = np_;
             d1u_c = d1u_n;
             d1w_c = d1w_n;
-            rc = rn;
+            rcx = rnx;
             qu = qu_n;
             qw = qw_n;
             qp = qp_n;
@@ -268,7 +261,10 @@ __device__ __forceinline__ void stage_march(const double* in, const double* qn, 
     }
 }
 
-__global__ void __launch_bounds__(FM_NT) k_fine_march(FineSweepArgs a) {
+// One CTA per SM, stated as the minimum-blocks bound: the compiler then uses
+// up to 140 registers and keeps more loads in flight (without the bound it
+// chose 104 and the sweep was 5 % slower)
+__global__ void __launch_bounds__(FM_NT, 1) k_fine_march(FineSweepArgs a) {
     const unsigned nb = gridDim.x;
     const long d = 3L * a.nx * a.ny;
     const int nseg = (a.nx + 31) >> 5;
