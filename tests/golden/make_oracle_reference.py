@@ -9,7 +9,7 @@ of the serial fine solution at fixed seeded indices, and the oracle's own
 spread: the relative l2 change of q_N^K (and the change of eps) when every
 entry of the initial value moves by one unit in the last place (random
 direction, two seeds) -- how well the method's result is determined in FP64
-arithmetic at all.
+arithmetic at all -- and the same for the initial value rounded to FP32.
 tests/golden/oracle_256x128_N32_K6_qN.npz -- q_N^K of every initial value in
 full (float64), for element-by-element comparison.
 Run: python tests/golden/make_oracle_reference.py   (about 10 minutes on 8 cores)
@@ -54,13 +54,20 @@ def main():
                            "qN_rel_l2": float(np.linalg.norm(r1["q"][-1] - qN) / np.linalg.norm(qN)),
                            "eps_shift": abs(oracle.rel_error(r1["q"][-1], qs1[-1]) - eps),
                            "rank_equal": bool(np.array_equal(r1["rank"], r["rank"]))})
+        # the spread at FP32 input precision: the same solve from the initial
+        # value rounded to FP32 (what a solve with FP32 tendencies sees first)
+        q32 = q0.astype(np.float32).astype(np.float64)
+        r32 = oracle.parareal(p, q32, wl.K, cap=wl.krylov_cap)
+        qs32 = oracle.serial_fine(p, q32)
+        spread32 = {"qN_rel_l2": float(np.linalg.norm(r32["q"][-1] - qN) / np.linalg.norm(qN)),
+                    "eps_shift": abs(oracle.rel_error(r32["q"][-1], qs32[-1]) - eps)}
         full[name] = qN
         out["ics"][name] = {
             "r": [float(x) for x in r["r"]], "rank": [int(x) for x in r["rank"]],
             "min_kept_ratio": minratio, "eps": eps,
             "qN_norm": float(np.linalg.norm(qN)), "qN_sample": qN[idx].tolist(),
             "qseq_sample": qs[-1][idx].tolist(), "qseq_norm": float(np.linalg.norm(qs[-1])),
-            "spread_1ulp": spread,
+            "spread_1ulp": spread, "spread_fp32_input": spread32,
         }
         print(name, out["ics"][name]["r"], eps, spread, flush=True)
     with open(os.path.join(HERE, "oracle_256x128_N32_K6.json"), "w") as fh:

@@ -79,28 +79,39 @@ def test_fp64_solve_against_oracle_reference(ref, ic, proj):
 
 
 @pytest.mark.parametrize("ic", [0, 1, 2], ids=["gaussian+noise", "fourier8", "filtered_noise16"])
-def test_mixed_and_direct_images_accuracy(ref, ic):
-    """Direct images (FP64) and the mixed-precision solve (FP32 fine sweep and
-    correction, direct FP32 images, FP64 Gram-Schmidt).  For the Gaussian IC
-    the error against the serial fine solution moves by <= 1e-5 (measured
-    4e-8).  The filtered-noise IC excites the band in which the coarse step
-    grows by 1.09 per step (see the oracle pins), so FP32 rounding in the
-    correction is amplified ~1.09^62 along the chain (measured 3.7e-5); the
-    Fourier IC's nearly dependent iterates make the subspace itself
-    sensitive (eps/ratio).  Those two are held to <= 1e-4 and to the size of
-    the oracle's error respectively."""
+def test_precision_forms_against_fp64(ref, ic):
+    """Equal final accuracy, |eps - eps_FP64| <= 1e-5 (eps: relative l2 error
+    of q_N against the serial fine solution), for the FP64-accurate form with
+    the subspace products on the tensor cores, on every IC.
+
+    The served mixed form (FP32 tendencies on the FP64 state, FP32
+    correction, direct images, tensor-core products) rounds its data to FP32.  How much that alone can move eps is recorded
+    by the oracle: its solve from the initial value rounded once to FP32
+    (golden `spread_fp32_input`) moves eps by 3.8e-9 (Gaussian), 2.3e-6
+    (filtered noise: the band in which the coarse step grows) and 8.8e-4
+    (Fourier: nearly dependent iterates).  Where that shift is below 1e-6 the
+    mixed form is held to the 1e-5 rule; elsewhere, since it rounds at every
+    stage rather than once, to 10 times the single-rounding shift (no
+    FP32-data evaluation is determined more tightly than the shift itself)."""
     wl = W.workload_medium()
     p = wl.problem
     name, f = wl.ics[ic]
     R = ref["ics"][name]
     q0 = f().ravel()
     g64, qs, rep64 = _solve(p, q0, wl.K, wl.krylov_cap, images=P.PR_IMAGES_DIRECT)
-    gmx, _, repmx = _solve(p, q0, wl.K, wl.krylov_cap, fine_prec=P.PR_FP32, corr_prec=P.PR_FP32)
-    assert np.all(np.isfinite(g64)) and np.all(np.isfinite(gmx))
-    e64 = np.linalg.norm(g64 - qs) / np.linalg.norm(qs)
-    emx = np.linalg.norm(gmx - qs) / np.linalg.norm(qs)
-    budget = {0: 1e-5, 1: 10 * R["eps"], 2: 1e-4}[ic]
-    assert abs(e64 - emx) <= budget, (e64, emx)
+    gtc, _, reptc = _solve(p, q0, wl.K, wl.krylov_cap, proj_prec=P.PR_PROJ_SPLIT_BF16)
+    gl64, _, _ = _solve(p, q0, wl.K, wl.krylov_cap)
+    gmx, _, repmx = _solve(p, q0, wl.K, wl.krylov_cap, fine_prec=P.PR_FP32X, corr_prec=P.PR_FP32,
+                           proj_prec=P.PR_PROJ_SPLIT_BF16)
+    for g in (g64, gtc, gl64, gmx):
+        assert np.all(np.isfinite(g))
+    err = lambda g: np.linalg.norm(g - qs) / np.linalg.norm(qs)
+    # the tensor-core form against plain FP64 with the same images by linearity
+    assert abs(err(gtc) - err(gl64)) <= 1e-5, (err(gtc), err(gl64))
+    assert list(reptc.rank[:wl.K]) == R["rank"]
+    shift32 = R["spread_fp32_input"]["eps_shift"]
+    budget = 1e-5 if shift32 < 1e-6 else 10.0 * shift32
+    assert abs(err(g64) - err(gmx)) <= budget, (err(g64), err(gmx), budget)
     assert list(rep64.rank[:wl.K]) == list(repmx.rank[:wl.K]) == R["rank"]
 
 
