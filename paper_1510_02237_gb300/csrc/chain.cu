@@ -14,8 +14,10 @@
 // K_old = G(q_i^k) and no basis it is the correction of the original
 // Parareal (Alg. 1).
 //
-// Every CTA owns a fixed range of rows for the dot products and the update
-// and a set of 16 x 16 tiles for the coarse steps.  Per slice: phase A
+// k_chain (below) serves every form; the FP64 delta form with the split
+// coarse step runs in k_chain_split (further below).  In k_chain every CTA
+// owns a fixed range of rows for the dot products and the update and a set
+// of 16 x 16 tiles for the coarse steps.  Per slice: phase A
 // computes the CTA's partial dot products and the first coarse step; after a
 // barrier the coefficients are reduced (each CTA sums a share of them over
 // all CTA partials in a fixed order) while the second coarse step runs;
@@ -213,6 +215,244 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
     }
 }
 
+// ------------------------------------------------------------ split groups
+// The FP64 KSE correction (delta form) with the partially split coarse step,
+// with the coarse steps and the products in two thread groups of every CTA
+// that run side by side.  CTA b owns the cells [c0, c1) of the grid (and the
+// rows of those cells in all three fields):
+//   coarse group (warps 0..3): the n_g coarse steps of delta_i on the CTA's
+//     cells with no halo recomputation -- every acoustic substep's forward
+//     (velocities) and backward (pressure) half is one phase over all cells,
+//     the phases separated by the group's own grid barrier; two work states
+//     alternate, the slow tendencies of the CTA's cells stay in shared memory;
+//   product group (warps 4..15): the partial dot products Q^T delta_i over a
+//     fixed row range, the group's grid barrier, the CTA's share of the
+//     coefficient sums, the group's grid barrier, and D c on the CTA's rows.
+// The groups join (CTA barrier), every thread updates the CTA's rows, and a
+// full grid barrier ends the slice.  Each cell's arithmetic is the tile
+// kernel's (the shared fb_new_* helpers) and each dot product, coefficient
+// sum and D c row is summed in the tile kernel's order, so the iterates are
+// the same bit for bit; only the order of the residual partial sums differs.
+constexpr int CS_NT = 512, CS_CW = 4, CS_CT = 32 * CS_CW, CS_PT = CS_NT - CS_CT, CS_PW = CS_PT / 32;
+
+// periodic neighbour indices of cell c (pp = (x+1, y+1), pm = (x+1, y-1), ...)
+struct CellNb {
+    long i, xp, xm, yp, ym, pp, pm, mp, mm;
+    int x, y;
+};
+__device__ __forceinline__ CellNb cell_nb(long c, int nx, int ny) {
+    const int y = (int)(c / nx), x = (int)(c - (long)y * nx);
+    const long r = (long)y * nx, rp = (long)pwrap(y + 1, ny) * nx, rm = (long)pwrap(y - 1, ny) * nx;
+    const int xp = pwrap(x + 1, nx), xm = pwrap(x - 1, nx);
+    return {c, r + xp, r + xm, rp + x, rm + x, rp + xp, rm + xp, rp + xm, rm + xm, x, y};
+}
+
+__device__ __forceinline__ double ldg2(const double* p) { return __ldcg(p); }   // written by other CTAs
+
+// warp_dot with x read from L2 (x's rows were written by other CTAs)
+__device__ __forceinline__ double warp_dot_x_l2(const double* a, const double* x, long r0, long r1) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    long row = r0 + lane;
+    for (; row + 96 < r1; row += 128) {
+        const double a0 = a[row], a1 = a[row + 32], a2 = a[row + 64], a3 = a[row + 96];
+        const double b0 = __ldcg(x + row), b1 = __ldcg(x + row + 32), b2 = __ldcg(x + row + 64),
+                     b3 = __ldcg(x + row + 96);
+        s += a0 * b0;
+        s += a1 * b1;
+        s += a2 * b2;
+        s += a3 * b3;
+    }
+    for (; row < r1; row += 32) s += a[row] * __ldcg(x + row);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// slow tendency of field a at cell n (the tile kernel's formulas)
+__device__ __forceinline__ double slow_cell(const CoarseCoef& cd, const CoarseT<double>& c, const double* a,
+                                            const CellNb& n, int nx, int ny, bool ynone) {
+    double Ur = c.U, Vc = c.V;
+    if (cd.omega != 0.0) {
+        Ur += (double)(cd.omega * ((n.y + 0.5) * cd.dy - cd.hly));
+        Vc -= (double)(cd.omega * ((n.x + 0.5) * cd.dx - cd.hlx));
+    }
+    const double a0 = ldg2(a + n.i);
+    if (c.order == 1) {
+        const double ax = -Ur * c.inv_dx, ay = -Vc * c.inv_dy;
+        const double dx_ = Ur >= 0.0 ? a0 - ldg2(a + n.xm) : ldg2(a + n.xp) - a0;
+        const double dy_ = ynone ? 0.0 : (Vc >= 0.0 ? a0 - ldg2(a + n.ym) : ldg2(a + n.yp) - a0);
+        return slow_first_order<double>(ax, ay, dx_, dy_, ynone);
+    }
+    const long r = (long)n.y * nx;
+    const double xm2 = ldg2(a + r + pwrap(n.x - 2, nx)), xp2 = ldg2(a + r + pwrap(n.x + 2, nx));
+    const double ym2 = ldg2(a + (long)pwrap(n.y - 2, ny) * nx + n.x), yp2 = ldg2(a + (long)pwrap(n.y + 2, ny) * nx + n.x);
+    const double xm = ldg2(a + n.xm), xp = ldg2(a + n.xp), ym = ldg2(a + n.ym), yp = ldg2(a + n.yp);
+    const double Fe = upwind_flux3_pts<double>(Ur, xm, a0, xp, xp2), Fw = upwind_flux3_pts<double>(Ur, xm2, xm, a0, xp);
+    const double Gn = upwind_flux3_pts<double>(Vc, ym, a0, yp, yp2), Gs = upwind_flux3_pts<double>(Vc, ym2, ym, a0, yp);
+    return -(Fe - Fw) * c.inv_dx - (Gn - Gs) * c.inv_dy;
+}
+
+__global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[CS_NT / 32];
+    __shared__ int s_okc, s_okp, s_fail;
+    const unsigned nb = gridDim.x;
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const long d = A.d, ncell = d / 3;
+    const int nx = A.nx, ny = A.ny;
+    const long c0 = ncell * b / nb, c1 = ncell * (b + 1) / nb;
+    const int ncl = (int)(c1 - c0), cmax = (int)((ncell + nb - 1) / nb);
+    double* S = reinterpret_cast<double*>(smraw);   // [3][cmax] slow tendencies of the CTA's cells
+    double* dc = S + 3 * cmax;                      // [3][cmax] D c on the CTA's rows
+    double* cs = dc + 3 * cmax;                     // [ccap] coefficients
+    const int ncols = A.r_dev ? *A.r_dev : 0;
+    if (ncols < 0 || ncols > A.ccap) {   // cannot happen: the rank never exceeds the cap
+        if (tid == 0) atomicExch(&A.gb->err, 2);
+        return;
+    }
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    // rows of the dot products: the tile kernel's contiguous ranges
+    const long rpb = ((d + nb - 1) / nb + 31) / 32 * 32;
+    const long r0 = min(d, (long)b * rpb), r1 = min(d, r0 + rpb);
+    const CoarseT<double> cc = coarse_t<double>(A.cc);
+    const bool ynone = A.cc.V == 0.0 && A.cc.omega == 0.0;
+    double* bufA = A.gbuf;
+    double* bufB = A.gbuf + d;
+
+    // the buffer holding G(delta_i) after the coarse group: every step starts
+    // in the buffer other than its input and alternates with each substep
+    const double* R = A.dlt64;
+    for (int st = 0; st < A.n_g; ++st) {
+        const double* n0 = (R == bufA) ? bufB : bufA;
+        R = (cc.n_sound & 1) ? n0 : ((n0 == bufA) ? bufB : bufA);
+    }
+
+    for (int i = A.i_begin; i < A.i_end; ++i) {
+        if (wid < CS_CW) {
+            // ---------------------------------------------------- coarse group
+            const int ct = tid;
+            const double* X = A.dlt64;
+            bool ok = true;
+            for (int st = 0; st < A.n_g && ok; ++st) {
+                const double* cur = X;
+                double* nxt = (X == bufA) ? bufB : bufA;
+                for (int m = 0; m < cc.n_sound && ok; ++m) {
+                    // forward: velocities from cur (slow tendency from X at the first substep)
+                    for (long c = c0 + ct; c < c1; c += CS_CT) {
+                        const CellNb n = cell_nb(c, nx, ny);
+                        const int k = (int)(c - c0);
+                        const double* u = cur;
+                        const double* w = cur + ncell;
+                        const double* p = cur + 2 * ncell;
+                        if (m == 0) {
+#pragma unroll
+                            for (int f = 0; f < 3; ++f) S[f * cmax + k] = slow_cell(A.cc, cc, X + f * ncell, n, nx, ny, ynone);
+                        }
+                        const double nu = fb_new_u<double>(cc, S[k], ldg2(u + n.i), ldg2(u + n.xp), ldg2(u + n.xm),
+                                                           ldg2(p + n.xp), ldg2(p + n.xm), ldg2(w + n.pp), ldg2(w + n.pm),
+                                                           ldg2(w + n.mp), ldg2(w + n.mm));
+                        const double nw = fb_new_w<double>(cc, S[cmax + k], ldg2(w + n.i), ldg2(w + n.yp), ldg2(w + n.ym),
+                                                           ldg2(p + n.yp), ldg2(p + n.ym), ldg2(u + n.pp), ldg2(u + n.mp),
+                                                           ldg2(u + n.pm), ldg2(u + n.mm));
+                        nxt[c] = nu;
+                        nxt[ncell + c] = nw;
+                    }
+                    if (!grid_barrier_group(A.gb, 0, nb, 1, CS_CT, ct == 0, &s_okc)) {
+                        ok = false;
+                        break;
+                    }
+                    // backward: pressure with the new velocities
+                    for (long c = c0 + ct; c < c1; c += CS_CT) {
+                        const CellNb n = cell_nb(c, nx, ny);
+                        const int k = (int)(c - c0);
+                        nxt[2 * ncell + c] = fb_new_p<double>(cc, S[2 * cmax + k], ldg2(cur + 2 * ncell + c),
+                                                              ldg2(nxt + n.xp), ldg2(nxt + n.xm),
+                                                              ldg2(nxt + ncell + n.yp), ldg2(nxt + ncell + n.ym));
+                    }
+                    const bool last = st == A.n_g - 1 && m == cc.n_sound - 1;
+                    if (!last && !grid_barrier_group(A.gb, 0, nb, 1, CS_CT, ct == 0, &s_okc)) {
+                        ok = false;
+                        break;
+                    }
+                    cur = nxt;
+                    nxt = (nxt == bufA) ? bufB : bufA;
+                }
+                X = cur;
+            }
+            if (!ok) s_fail = 1;
+        } else {
+            // ---------------------------------------------------- product group
+            const int pt = tid - CS_CT, pw = pt >> 5;
+            const double* x = A.dlt64;
+            bool ok = true;
+            for (int l = pw; l < ncols; l += CS_PW) {
+                const double s = warp_dot_x_l2(A.Q + (long)l * d, x, r0, r1);
+                if (lane == 0) A.part[(long)b * A.ccap + l] = s;
+            }
+            ok = grid_barrier_group(A.gb, 1, nb, 2, CS_PT, pt == 0, &s_okp);
+            if (ok && ncols > 0) {
+                const int cpb = (ncols + (int)nb - 1) / (int)nb;
+                const int l1 = min(ncols, (b + 1) * cpb);
+                for (int l = b * cpb + pw; l < l1; l += CS_PW) {
+                    const double s = warp_sum_strided(A.part + l, nb, A.ccap);
+                    if (lane == 0) A.cvec[l] = s;
+                }
+            }
+            if (ok) ok = grid_barrier_group(A.gb, 1, nb, 2, CS_PT, pt == 0, &s_okp);
+            if (ok) {
+                for (int l = pt; l < ncols; l += CS_PT) cs[l] = __ldcg(A.cvec + l);
+                named_barrier(2, CS_PT);
+                for (int k = pt; k < 3 * ncl; k += CS_PT) {
+                    const int f = k / ncl;
+                    const long row = (long)f * ncell + c0 + (k - f * ncl);
+                    const double* Dr = A.D + row;
+                    double acc = 0.0;
+#pragma unroll 8
+                    for (int l = 0; l < ncols; ++l) acc += __ldg(Dr + (long)l * d) * cs[l];
+                    dc[f * cmax + (k - f * ncl)] = acc;
+                }
+            }
+            if (!ok) s_fail = 1;
+        }
+        __syncthreads();   // join: G(delta_i) and D c of the CTA's rows are complete
+        if (s_fail) return;
+        const double* qt = A.qt + (long)i * d;
+        double* qn = A.q + (long)(i + 1) * d;
+        double* dl = A.dlt64;
+        double* ga = A.gacc ? A.gacc + (long)i * d : nullptr;
+        double s = 0.0;
+        for (int k = tid; k < 3 * ncl; k += CS_NT) {
+            const int f = k / ncl;
+            const long row = (long)f * ncell + c0 + (k - f * ncl);
+            const double gin = R[row];
+            const double y = qt[row] + (gin + dc[f * cmax + (k - f * ncl)]);
+            const double e = y - qn[row];
+            s += e * e;
+            qn[row] = y;
+            dl[row] = e;
+            if (ga) ga[row] += gin;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[wid] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int k = 0; k < CS_NT / 32; ++k) t += red[k];
+            A.resp[(long)i * nb + b] = t;
+        }
+        if (!grid_barrier(A.gb, nb)) return;
+    }
+    if (A.res2 && b == 0) {
+        for (int i = A.i_begin + wid; i < A.i_end; i += CS_NT / 32) {
+            const double t = warp_sum_strided(A.resp + (long)i * nb, nb, 1);
+            if (lane == 0) A.res2[i + 1] = t;
+        }
+    }
+}
+
 size_t chain_smem_bytes(int H, int ccap, bool f32) {
     const size_t el = f32 ? sizeof(float) : sizeof(double);
     size_t a = el * coarse_tile_smem_elems<CH_TX, CH_TY>(H);
@@ -244,9 +484,59 @@ int chain_grid(int H, int ccap) {
 
 long chain_resp_elems(int n_slices) { return (long)(n_slices + 1) * 1024; }
 
+namespace {
+
+size_t split_smem_bytes(long ncell, int nb, int ccap) {
+    const long cmax = (ncell + nb - 1) / nb;
+    return sizeof(double) * (size_t)(6 * cmax + (ccap > 0 ? ccap : 1));
+}
+
+// CTAs of the split-group chain (one per SM), or 0 when it does not fit
+int split_grid(size_t smem) {
+    static DevMemo memo;   // [device] -> (shared-memory bytes, blocks)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int k0 = -1, blocks = 0;
+    if (memo.get(dev, &k0, &blocks) && k0 == (int)smem) return blocks;
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    {
+        std::lock_guard<std::mutex> lk(smem_launch_lock());
+        if (set_dynamic_smem((const void*)k_chain_split, smem) != cudaSuccess) return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain_split, CS_NT, smem);
+    }
+    blocks = per >= 1 ? sms : 0;
+    memo.put(dev, (int)smem, blocks);
+    return blocks;
+}
+
+}  // namespace
+
 cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s) {
     if (a.i_end <= a.i_begin) return cudaSuccess;
     if (a.dlt && a.dlt64) return cudaErrorInvalidValue;
+    if (a.dlt64 && a.cc.scheme == 0 && a.cc.n_sound >= 1 && a.n_g >= 1 && a.qt) {
+        // FP64 delta form with the split coarse step: coarse steps and
+        // products side by side in two thread groups (one CTA per SM)
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int nb = a.max_blocks > 0 && a.max_blocks < sms ? a.max_blocks : sms;
+        const size_t smem = split_smem_bytes(a.d / 3, nb, a.ccap);
+        if (nb >= 1 && smem <= 200 * 1024 && split_grid(smem) >= nb) {
+            cudaError_t e = cudaMemsetAsync(&a.gb->count, 0, sizeof(unsigned), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(a.gb->gcount, 0, sizeof(a.gb->gcount), s);
+            if (e != cudaSuccess) return e;
+            ChainArgs arg = a;
+            void* args[] = {&arg};
+            std::lock_guard<std::mutex> lk(smem_launch_lock());
+            e = set_dynamic_smem((const void*)k_chain_split, smem);
+            if (e != cudaSuccess) return e;
+            e = cudaLaunchCooperativeKernel((const void*)k_chain_split, dim3(nb), dim3(CS_NT), args, smem, s);
+            count_launches(1);
+            return e;
+        }
+    }
     const bool f32 = a.dlt != nullptr, d64 = a.dlt64 != nullptr;
     int nb = f32 ? chain_grid<true, float>(a.H, a.ccap)
                  : (d64 ? chain_grid<true, double>(a.H, a.ccap) : chain_grid<false, double>(a.H, a.ccap));

@@ -34,6 +34,57 @@ __device__ __forceinline__ T upwind_flux(int order, T U, const T* f, int i, int 
            aU * ((f[i + 2 * st] - f[i - st]) - T(3) * (f[i + st] - f[i])) * (T(1) / T(12));
 }
 
+// The same flux from the four values along the stencil line (f_{i-1}, f_i,
+// f_{i+1}, f_{i+2}): one expression for both, so both round alike.
+template <typename T>
+__device__ __forceinline__ T upwind_flux3_pts(T U, T fm1, T f0, T fp1, T fp2) {
+    const T aU = U >= T(0) ? U : -U;
+    return U * (T(7) * (fp1 + f0) - (fp2 + fm1)) * (T(1) / T(12)) +
+           aU * ((fp2 - fm1) - T(3) * (fp1 - f0)) * (T(1) / T(12));
+}
+
+// Coefficients of the split coarse step in arithmetic T.
+template <typename T>
+struct CoarseT {
+    T U, V, inv_dx, inv_dy, tau, csx, csy, dxx, dxy1, dyy, dxy2;
+    int n_sound, order;
+};
+template <typename T>
+__device__ __forceinline__ CoarseT<T> coarse_t(const CoarseCoef& cd) {
+    return {(T)cd.U, (T)cd.V, (T)cd.inv_dx, (T)cd.inv_dy, (T)cd.tau, (T)cd.csx, (T)cd.csy,
+            (T)cd.dxx, (T)cd.dxy1, (T)cd.dyy, (T)cd.dxy2, cd.n_sound, cd.order};
+}
+
+// Forward-backward acoustic substep of one cell from its neighbourhood (x+-1
+// and y+-1 of each field, the corners of the other velocity for the damping
+// cross terms; ab names x then y offsets, p = +1, m = -1).  Written once and
+// used by the tile kernel and the distributed serial chain alike.
+template <typename T>
+__device__ __forceinline__ T fb_new_u(const CoarseT<T>& c, T su, T u0, T uxp, T uxm, T pxp, T pxm, T wpp, T wpm,
+                                      T wmp, T wmm) {
+    const T du = su - c.csx * (pxp - pxm) + c.dxx * (uxp - T(2) * u0 + uxm) + c.dxy1 * ((wpp - wpm) - (wmp - wmm));
+    return u0 + c.tau * du;
+}
+template <typename T>
+__device__ __forceinline__ T fb_new_w(const CoarseT<T>& c, T sw, T w0, T wyp, T wym, T pyp, T pym, T upp, T ump,
+                                      T upm, T umm) {
+    const T dw = sw - c.csy * (pyp - pym) + c.dyy * (wyp - T(2) * w0 + wym) + c.dxy2 * ((upp - ump) - (upm - umm));
+    return w0 + c.tau * dw;
+}
+template <typename T>
+__device__ __forceinline__ T fb_new_p(const CoarseT<T>& c, T sp, T p0, T uxp, T uxm, T wyp, T wym) {
+    return p0 + c.tau * (sp - (c.csx * (uxp - uxm) + c.csy * (wyp - wym)));
+}
+
+// First-order slow tendency of one field from its upwind differences (the
+// y-difference skipped when the advection has no y-component anywhere).
+template <typename T>
+__device__ __forceinline__ T slow_first_order(T ax, T ay, T dxu, T dyu, bool ynone) {
+    T v = ax * dxu;
+    if (!ynone) v += ay * dyu;
+    return v;
+}
+
 // Shared memory (elements) of one tile: 6 arrays of (TX + 2H) x (TY + 2H).
 template <int TX, int TY>
 __host__ __device__ constexpr int coarse_tile_smem_elems(int H) {
@@ -56,11 +107,7 @@ __device__ __forceinline__ void coarse_tile(const Tin* src, Tout* __restrict__ d
     T* sw = su + NR;
     T* sp = sw + NR;
     const long ncell = (long)nx * ny;
-    struct {
-        T U, V, inv_dx, inv_dy, tau, csx, csy, dxx, dxy1, dyy, dxy2;
-        int n_sound, order;
-    } c = {(T)cd.U, (T)cd.V, (T)cd.inv_dx, (T)cd.inv_dy, (T)cd.tau, (T)cd.csx, (T)cd.csy,
-           (T)cd.dxx, (T)cd.dxy1, (T)cd.dyy, (T)cd.dxy2, cd.n_sound, cd.order};
+    const CoarseT<T> c = coarse_t<T>(cd);
     // advection velocity of the cell at local (lr, lc): constant, or with the
     // solid-body rotation (Eq. adVel) at the cell's periodic position -- the
     // x-velocity is that of the row, the y-velocity that of the column
@@ -190,16 +237,17 @@ __device__ __forceinline__ void coarse_tile(const Tin* src, Tout* __restrict__ d
                 for (int f = 0; f < 3; ++f) {
                     const T* a = fs[f];
                     const T dx_ = sx < 0 ? a[i] - a[i - 1] : a[i + 1] - a[i];
-                    T v = ax * dx_;
-                    if (!ynone) v += ay * (sy < 0 ? a[i] - a[i - RX] : a[i + RX] - a[i]);
-                    ss[f][i] = v;
+                    const T dy_ = ynone ? T(0) : (sy < 0 ? a[i] - a[i - RX] : a[i + RX] - a[i]);
+                    ss[f][i] = slow_first_order<T>(ax, ay, dx_, dy_, ynone);
                 }
             } else {
 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
                     const T* a = fs[f];
-                    T Fe = upwind_flux<T>(c.order, Ur, a, i, 1), Fw = upwind_flux<T>(c.order, Ur, a, i - 1, 1);
-                    T Gn = upwind_flux<T>(c.order, Vc, a, i, RX), Gs = upwind_flux<T>(c.order, Vc, a, i - RX, RX);
+                    const T Fe = upwind_flux3_pts<T>(Ur, a[i - 1], a[i], a[i + 1], a[i + 2]);
+                    const T Fw = upwind_flux3_pts<T>(Ur, a[i - 2], a[i - 1], a[i], a[i + 1]);
+                    const T Gn = upwind_flux3_pts<T>(Vc, a[i - RX], a[i], a[i + RX], a[i + 2 * RX]);
+                    const T Gs = upwind_flux3_pts<T>(Vc, a[i - 2 * RX], a[i - RX], a[i], a[i + RX]);
                     ss[f][i] = -(Fe - Fw) * c.inv_dx - (Gn - Gs) * c.inv_dy;
                 }
             }
@@ -218,14 +266,10 @@ __device__ __forceinline__ void coarse_tile(const Tin* src, Tout* __restrict__ d
             if (t < N2) {
                 int r = t / W2;
                 int i = (r + sh) * RX + (t - r * W2) + sh;
-                T du = su[i] - c.csx * (p[i + 1] - p[i - 1]) +
-                            c.dxx * (u[i + 1] - T(2) * u[i] + u[i - 1]) +
-                            c.dxy1 * ((w[i + 1 + RX] - w[i + 1 - RX]) - (w[i - 1 + RX] - w[i - 1 - RX]));
-                T dw = sw[i] - c.csy * (p[i + RX] - p[i - RX]) +
-                            c.dyy * (w[i + RX] - T(2) * w[i] + w[i - RX]) +
-                            c.dxy2 * ((u[i + 1 + RX] - u[i - 1 + RX]) - (u[i + 1 - RX] - u[i - 1 - RX]));
-                nu[k] = u[i] + c.tau * du;
-                nw[k] = w[i] + c.tau * dw;
+                nu[k] = fb_new_u<T>(c, su[i], u[i], u[i + 1], u[i - 1], p[i + 1], p[i - 1], w[i + 1 + RX],
+                                    w[i + 1 - RX], w[i - 1 + RX], w[i - 1 - RX]);
+                nw[k] = fb_new_w<T>(c, sw[i], w[i], w[i + RX], w[i - RX], p[i + RX], p[i - RX], u[i + 1 + RX],
+                                    u[i - 1 + RX], u[i + 1 - RX], u[i - 1 - RX]);
             }
         }
         __syncthreads();
@@ -246,7 +290,7 @@ __device__ __forceinline__ void coarse_tile(const Tin* src, Tout* __restrict__ d
         for (int t = threadIdx.x; t < N3; t += NT) {
             int r = t / W3;
             int i = (r + sp1) * RX + (t - r * W3) + sp1;
-            p[i] = p[i] + c.tau * (sp[i] - (c.csx * (u[i + 1] - u[i - 1]) + c.csy * (w[i + RX] - w[i - RX])));
+            p[i] = fb_new_p<T>(c, sp[i], p[i], u[i + 1], u[i - 1], w[i + RX], w[i - RX]);
         }
         __syncthreads();
     }

@@ -39,6 +39,47 @@ __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned nblocks) {
     return s_ok != 0;
 }
 
+// The same barrier over one group of nthr threads (a multiple of 32, calling
+// it together) in every CTA, on the group counter gb->gcount[slot]: the
+// group meets at named barrier bar_id (1..15), its first thread (leader)
+// arrives and waits for the other CTAs' groups, the group meets again.  Two
+// groups of a CTA can thus synchronise with their peers independently.
+// Bounded like grid_barrier, on the same error word; s_ok is a shared-memory
+// word of the group.
+__device__ __forceinline__ void named_barrier(int bar_id, int nthr) {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthr) : "memory");
+}
+__device__ __forceinline__ bool grid_barrier_group(GridBar* gb, int slot, unsigned nblocks, int bar_id, int nthr,
+                                                   bool leader, volatile int* s_ok) {
+    named_barrier(bar_id, nthr);
+    if (leader) {
+        volatile unsigned* vgen = &gb->ggen[slot];
+        volatile int* verr = &gb->err;
+        if (*verr == 0) {
+            const unsigned g = *vgen;
+            __threadfence();
+            if (atomicAdd(&gb->gcount[slot], 1u) == nblocks - 1) {
+                atomicExch(&gb->gcount[slot], 0u);
+                __threadfence();
+                atomicAdd(&gb->ggen[slot], 1u);
+            } else {
+                unsigned long long it = 0;
+                while (*vgen == g) {
+                    if (++it > (1ull << 22) || *verr != 0) {
+                        atomicExch(&gb->err, 1);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        *s_ok = *verr == 0;
+    }
+    named_barrier(bar_id, nthr);
+    return *s_ok != 0;
+}
+
 // Sum of the nb values base[k * stride], k = 0..nb-1, by one warp: lane j adds
 // k = j, j+32, ... in order, then a fixed xor-shuffle tree combines the lanes.
 // Deterministic, the same in every CTA; the loads are independent, so they
