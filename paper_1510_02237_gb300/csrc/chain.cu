@@ -296,7 +296,7 @@ __device__ __forceinline__ double slow_cell(const CoarseCoef& cd, const CoarseT<
 __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double red[CS_NT / 32];
-    __shared__ int s_okc, s_okp, s_fail;
+    __shared__ int s_okc, s_okp, s_okf, s_fail;
     const unsigned nb = gridDim.x;
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long d = A.d, ncell = d / 3;
@@ -339,37 +339,65 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
                 const double* cur = X;
                 double* nxt = (X == bufA) ? bufB : bufA;
                 for (int m = 0; m < cc.n_sound && ok; ++m) {
-                    // forward: velocities from cur (slow tendency from X at the first substep)
-                    for (long c = c0 + ct; c < c1; c += CS_CT) {
-                        const CellNb n = cell_nb(c, nx, ny);
-                        const int k = (int)(c - c0);
+                    // forward: velocities from cur (slow tendency from X at the first
+                    // substep); two cells per thread at a time, their loads in flight together
+                    for (long ca = c0 + ct; ca < c1; ca += 2 * CS_CT) {
+                        const bool two = ca + CS_CT < c1;
+                        const long cb = two ? ca + CS_CT : ca;
+                        const CellNb na = cell_nb(ca, nx, ny), nb2 = cell_nb(cb, nx, ny);
+                        const int ka = (int)(ca - c0), kb = (int)(cb - c0);
                         const double* u = cur;
                         const double* w = cur + ncell;
                         const double* p = cur + 2 * ncell;
                         if (m == 0) {
 #pragma unroll
-                            for (int f = 0; f < 3; ++f) S[f * cmax + k] = slow_cell(A.cc, cc, X + f * ncell, n, nx, ny, ynone);
+                            for (int f = 0; f < 3; ++f) {
+                                const double sa = slow_cell(A.cc, cc, X + f * ncell, na, nx, ny, ynone);
+                                const double sb = slow_cell(A.cc, cc, X + f * ncell, nb2, nx, ny, ynone);
+                                S[f * cmax + ka] = sa;
+                                if (two) S[f * cmax + kb] = sb;
+                            }
                         }
-                        const double nu = fb_new_u<double>(cc, S[k], ldg2(u + n.i), ldg2(u + n.xp), ldg2(u + n.xm),
-                                                           ldg2(p + n.xp), ldg2(p + n.xm), ldg2(w + n.pp), ldg2(w + n.pm),
-                                                           ldg2(w + n.mp), ldg2(w + n.mm));
-                        const double nw = fb_new_w<double>(cc, S[cmax + k], ldg2(w + n.i), ldg2(w + n.yp), ldg2(w + n.ym),
-                                                           ldg2(p + n.yp), ldg2(p + n.ym), ldg2(u + n.pp), ldg2(u + n.mp),
-                                                           ldg2(u + n.pm), ldg2(u + n.mm));
-                        nxt[c] = nu;
-                        nxt[ncell + c] = nw;
+                        const double nua = fb_new_u<double>(cc, S[ka], ldg2(u + na.i), ldg2(u + na.xp), ldg2(u + na.xm),
+                                                            ldg2(p + na.xp), ldg2(p + na.xm), ldg2(w + na.pp),
+                                                            ldg2(w + na.pm), ldg2(w + na.mp), ldg2(w + na.mm));
+                        const double nub = fb_new_u<double>(cc, S[kb], ldg2(u + nb2.i), ldg2(u + nb2.xp),
+                                                            ldg2(u + nb2.xm), ldg2(p + nb2.xp), ldg2(p + nb2.xm),
+                                                            ldg2(w + nb2.pp), ldg2(w + nb2.pm), ldg2(w + nb2.mp),
+                                                            ldg2(w + nb2.mm));
+                        const double nwa = fb_new_w<double>(cc, S[cmax + ka], ldg2(w + na.i), ldg2(w + na.yp),
+                                                            ldg2(w + na.ym), ldg2(p + na.yp), ldg2(p + na.ym),
+                                                            ldg2(u + na.pp), ldg2(u + na.mp), ldg2(u + na.pm),
+                                                            ldg2(u + na.mm));
+                        const double nwb = fb_new_w<double>(cc, S[cmax + kb], ldg2(w + nb2.i), ldg2(w + nb2.yp),
+                                                            ldg2(w + nb2.ym), ldg2(p + nb2.yp), ldg2(p + nb2.ym),
+                                                            ldg2(u + nb2.pp), ldg2(u + nb2.mp), ldg2(u + nb2.pm),
+                                                            ldg2(u + nb2.mm));
+                        nxt[ca] = nua;
+                        nxt[ncell + ca] = nwa;
+                        if (two) {
+                            nxt[cb] = nub;
+                            nxt[ncell + cb] = nwb;
+                        }
                     }
                     if (!grid_barrier_group(A.gb, 0, nb, 1, CS_CT, ct == 0, &s_okc)) {
                         ok = false;
                         break;
                     }
                     // backward: pressure with the new velocities
-                    for (long c = c0 + ct; c < c1; c += CS_CT) {
-                        const CellNb n = cell_nb(c, nx, ny);
-                        const int k = (int)(c - c0);
-                        nxt[2 * ncell + c] = fb_new_p<double>(cc, S[2 * cmax + k], ldg2(cur + 2 * ncell + c),
-                                                              ldg2(nxt + n.xp), ldg2(nxt + n.xm),
-                                                              ldg2(nxt + ncell + n.yp), ldg2(nxt + ncell + n.ym));
+                    for (long ca = c0 + ct; ca < c1; ca += 2 * CS_CT) {
+                        const bool two = ca + CS_CT < c1;
+                        const long cb = two ? ca + CS_CT : ca;
+                        const CellNb na = cell_nb(ca, nx, ny), nb2 = cell_nb(cb, nx, ny);
+                        const int ka = (int)(ca - c0), kb = (int)(cb - c0);
+                        const double pa = fb_new_p<double>(cc, S[2 * cmax + ka], ldg2(cur + 2 * ncell + ca),
+                                                           ldg2(nxt + na.xp), ldg2(nxt + na.xm),
+                                                           ldg2(nxt + ncell + na.yp), ldg2(nxt + ncell + na.ym));
+                        const double pb = fb_new_p<double>(cc, S[2 * cmax + kb], ldg2(cur + 2 * ncell + cb),
+                                                           ldg2(nxt + nb2.xp), ldg2(nxt + nb2.xm),
+                                                           ldg2(nxt + ncell + nb2.yp), ldg2(nxt + ncell + nb2.ym));
+                        nxt[2 * ncell + ca] = pa;
+                        if (two) nxt[2 * ncell + cb] = pb;
                     }
                     const bool last = st == A.n_g - 1 && m == cc.n_sound - 1;
                     if (!last && !grid_barrier_group(A.gb, 0, nb, 1, CS_CT, ct == 0, &s_okc)) {
@@ -443,7 +471,7 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
             for (int k = 0; k < CS_NT / 32; ++k) t += red[k];
             A.resp[(long)i * nb + b] = t;
         }
-        if (!grid_barrier(A.gb, nb)) return;
+        if (!grid_barrier_group(A.gb, 2, nb, 0, CS_NT, tid == 0, &s_okf)) return;
     }
     if (A.res2 && b == 0) {
         for (int i = A.i_begin + wid; i < A.i_end; i += CS_NT / 32) {

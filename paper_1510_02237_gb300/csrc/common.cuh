@@ -199,7 +199,7 @@ struct GridBar {
     unsigned count;
     unsigned gen;
     int err;   // set to 1 when a barrier wait gave up
-    unsigned gcount[2], ggen[2];   // barriers of thread groups (grid_barrier_group)
+    unsigned gcount[3];   // monotonic counters of grid_barrier_group (zeroed before a launch using them)
 };
 // In-order Gram-Schmidt (twice) within a block of m <= 64 columns that are
 // already orthogonal to the basis columns [0, *r_old_dev), the drop rule
