@@ -218,33 +218,64 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
 // ------------------------------------------------------------ split groups
 // The FP64 KSE correction (delta form) with the partially split coarse step,
 // with the coarse steps and the products in two thread groups of every CTA
-// that run side by side.  CTA b owns the cells [c0, c1) of the grid (and the
-// rows of those cells in all three fields):
-//   coarse group (warps 0..3): the n_g coarse steps of delta_i on the CTA's
-//     cells with no halo recomputation -- every acoustic substep's forward
-//     (velocities) and backward (pressure) half is one phase over all cells,
-//     the phases separated by the group's own grid barrier; two work states
-//     alternate, the slow tendencies of the CTA's cells stay in shared memory;
+// that run side by side.  CTA b owns one tile of the grid (16 columns by th
+// rows, th chosen so that the tiles fit on the CTAs; CTAs past the last tile
+// own none) and the rows of its cells in all three fields:
+//   coarse group (warps 0..3): the n_g coarse steps of delta_i on the tile,
+//     one phase per acoustic substep: the state on the tile and a 2-cell ring
+//     (3 for third-order fluxes) is loaded into shared memory, the forward
+//     half (velocities) is computed on the tile and a 1-cell ring, the
+//     backward half (pressure) on the tile, the tile is written out, and the
+//     group's grid barrier separates the phases; the slow tendencies of the
+//     tile and ring stay in shared memory through a step; two states
+//     alternate in memory;
 //   product group (warps 4..15): the partial dot products Q^T delta_i over a
 //     fixed row range, the group's grid barrier, the CTA's share of the
-//     coefficient sums, the group's grid barrier, and D c on the CTA's rows.
-// The groups join (CTA barrier), every thread updates the CTA's rows, and a
+//     coefficient sums, the group's grid barrier, and D c on the tile's rows.
+// The groups join (CTA barrier), every thread updates the tile's rows, and a
 // full grid barrier ends the slice.  Each cell's arithmetic is the tile
-// kernel's (the shared fb_new_* helpers) and each dot product, coefficient
-// sum and D c row is summed in the tile kernel's order, so the iterates are
-// the same bit for bit; only the order of the residual partial sums differs.
+// kernel's (the shared fb_new_* helpers; a ring cell's forward values are
+// those its owner computes), and each dot product, coefficient sum and D c
+// row is summed in the tile kernel's order, so the iterates are the same bit
+// for bit; only the order of the residual partial sums differs.
 constexpr int CS_NT = 512, CS_CW = 4, CS_CT = 32 * CS_CW, CS_PT = CS_NT - CS_CT, CS_PW = CS_PT / 32;
+constexpr int CS_TW = 16;   // tile width
 
-// periodic neighbour indices of cell c (pp = (x+1, y+1), pm = (x+1, y-1), ...)
-struct CellNb {
-    long i, xp, xm, yp, ym, pp, pm, mp, mm;
-    int x, y;
+// Tiling of an nx x ny grid on nb CTAs: tiles of tw0 x th0 (the last column
+// and row of tiles may be narrower), tw0 = 16, 32, 64 or 128 columns (nx if
+// narrower), whichever gives the smallest loaded region (tile + ring) with at
+// most nb tiles; ntx = 0 when no width fits.
+struct SplitTiles {
+    int tw0, th0, ntx, nty, LR;
 };
-__device__ __forceinline__ CellNb cell_nb(long c, int nx, int ny) {
-    const int y = (int)(c / nx), x = (int)(c - (long)y * nx);
-    const long r = (long)y * nx, rp = (long)pwrap(y + 1, ny) * nx, rm = (long)pwrap(y - 1, ny) * nx;
-    const int xp = pwrap(x + 1, nx), xm = pwrap(x - 1, nx);
-    return {c, r + xp, r + xm, rp + x, rm + x, rp + xp, rm + xp, rp + xm, rm + xm, x, y};
+__host__ __device__ inline SplitTiles split_tiles(int nx, int ny, int nb, int order) {
+    SplitTiles best{};
+    best.LR = order == 3 ? 3 : 2;
+    long best_area = -1;
+    for (int w = CS_TW; w <= 8 * CS_TW; w *= 2) {
+        SplitTiles t{};
+        t.LR = best.LR;
+        t.tw0 = nx < w ? nx : w;
+        t.ntx = (nx + t.tw0 - 1) / t.tw0;
+        const int ntymax = t.ntx <= nb ? nb / t.ntx : 0;
+        if (ntymax < 1) continue;
+        t.th0 = (ny + ntymax - 1) / ntymax;
+        t.nty = (ny + t.th0 - 1) / t.th0;
+        const long area = (long)(t.tw0 + 2 * t.LR) * (t.th0 + 2 * t.LR);
+        if (best_area < 0 || area < best_area) {
+            best = t;
+            best_area = area;
+        }
+        if (nx <= w) break;
+    }
+    return best;
+}
+// shared-memory doubles: the loaded state (3 fields, tile + ring LR), the slow
+// tendencies and the forward velocities (tile + ring 1), D c of the tile's
+// rows, the coefficients
+__host__ __device__ inline long split_smem_doubles(const SplitTiles& t, int ccap) {
+    const long rw = t.tw0 + 2 * t.LR, rh = t.th0 + 2 * t.LR, hw = t.tw0 + 2, hh = t.th0 + 2;
+    return 3 * rw * rh + 5 * hw * hh + 3L * t.tw0 * t.th0 + (ccap > 0 ? ccap : 1);
 }
 
 __device__ __forceinline__ double ldg2(const double* p) { return __ldcg(p); }   // written by other CTAs
@@ -269,30 +300,6 @@ __device__ __forceinline__ double warp_dot_x_l2(const double* a, const double* x
     return s;
 }
 
-// slow tendency of field a at cell n (the tile kernel's formulas)
-__device__ __forceinline__ double slow_cell(const CoarseCoef& cd, const CoarseT<double>& c, const double* a,
-                                            const CellNb& n, int nx, int ny, bool ynone) {
-    double Ur = c.U, Vc = c.V;
-    if (cd.omega != 0.0) {
-        Ur += (double)(cd.omega * ((n.y + 0.5) * cd.dy - cd.hly));
-        Vc -= (double)(cd.omega * ((n.x + 0.5) * cd.dx - cd.hlx));
-    }
-    const double a0 = ldg2(a + n.i);
-    if (c.order == 1) {
-        const double ax = -Ur * c.inv_dx, ay = -Vc * c.inv_dy;
-        const double dx_ = Ur >= 0.0 ? a0 - ldg2(a + n.xm) : ldg2(a + n.xp) - a0;
-        const double dy_ = ynone ? 0.0 : (Vc >= 0.0 ? a0 - ldg2(a + n.ym) : ldg2(a + n.yp) - a0);
-        return slow_first_order<double>(ax, ay, dx_, dy_, ynone);
-    }
-    const long r = (long)n.y * nx;
-    const double xm2 = ldg2(a + r + pwrap(n.x - 2, nx)), xp2 = ldg2(a + r + pwrap(n.x + 2, nx));
-    const double ym2 = ldg2(a + (long)pwrap(n.y - 2, ny) * nx + n.x), yp2 = ldg2(a + (long)pwrap(n.y + 2, ny) * nx + n.x);
-    const double xm = ldg2(a + n.xm), xp = ldg2(a + n.xp), ym = ldg2(a + n.ym), yp = ldg2(a + n.yp);
-    const double Fe = upwind_flux3_pts<double>(Ur, xm, a0, xp, xp2), Fw = upwind_flux3_pts<double>(Ur, xm2, xm, a0, xp);
-    const double Gn = upwind_flux3_pts<double>(Vc, ym, a0, yp, yp2), Gs = upwind_flux3_pts<double>(Vc, ym2, ym, a0, yp);
-    return -(Fe - Fw) * c.inv_dx - (Gn - Gs) * c.inv_dy;
-}
-
 __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double red[CS_NT / 32];
@@ -301,11 +308,24 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long d = A.d, ncell = d / 3;
     const int nx = A.nx, ny = A.ny;
-    const long c0 = ncell * b / nb, c1 = ncell * (b + 1) / nb;
-    const int ncl = (int)(c1 - c0), cmax = (int)((ncell + nb - 1) / nb);
-    double* S = reinterpret_cast<double*>(smraw);   // [3][cmax] slow tendencies of the CTA's cells
-    double* dc = S + 3 * cmax;                      // [3][cmax] D c on the CTA's rows
-    double* cs = dc + 3 * cmax;                     // [ccap] coefficients
+    const SplitTiles T = split_tiles(nx, ny, (int)nb, A.cc.order);
+    int tx0 = 0, ty0 = 0, tw = 0, th = 0;
+    if (b < T.ntx * T.nty) {
+        const int ty = b / T.ntx, tx = b - ty * T.ntx;
+        tx0 = tx * T.tw0;
+        ty0 = ty * T.th0;
+        tw = min(T.tw0, nx - tx0);
+        th = min(T.th0, ny - ty0);
+    }
+    const int ncl = tw * th, nclx = T.tw0 * T.th0;
+    const int LR = T.LR, RW = tw + 2 * LR, RH = th + 2 * LR, HW = tw + 2, HH = th + 2;
+    const int RSZ = (T.tw0 + 2 * LR) * (T.th0 + 2 * LR), HSZ = (T.tw0 + 2) * (T.th0 + 2);
+    double* st = reinterpret_cast<double*>(smraw);   // [3][RSZ] state on the tile + ring LR
+    double* S = st + 3 * RSZ;                        // [3][HSZ] slow tendencies, tile + ring 1
+    double* fu = S + 3 * HSZ;                        // [HSZ] forward u, tile + ring 1
+    double* fw = fu + HSZ;                           // [HSZ] forward w
+    double* dc = fw + HSZ;                           // [3][nclx] D c on the tile's rows
+    double* cs = dc + 3 * nclx;                      // [ccap] coefficients
     const int ncols = A.r_dev ? *A.r_dev : 0;
     if (ncols < 0 || ncols > A.ccap) {   // cannot happen: the rank never exceeds the cap
         if (tid == 0) atomicExch(&A.gb->err, 2);
@@ -320,11 +340,16 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
     const bool ynone = A.cc.V == 0.0 && A.cc.omega == 0.0;
     double* bufA = A.gbuf;
     double* bufB = A.gbuf + d;
+    // global row of local cell k of the tile, field f
+    auto tile_row = [&](int f, int k) {
+        const int ly = k / tw, lx = k - ly * tw;
+        return (long)f * ncell + (long)(ty0 + ly) * nx + tx0 + lx;
+    };
 
     // the buffer holding G(delta_i) after the coarse group: every step starts
     // in the buffer other than its input and alternates with each substep
     const double* R = A.dlt64;
-    for (int st = 0; st < A.n_g; ++st) {
+    for (int st_ = 0; st_ < A.n_g; ++st_) {
         const double* n0 = (R == bufA) ? bufB : bufA;
         R = (cc.n_sound & 1) ? n0 : ((n0 == bufA) ? bufB : bufA);
     }
@@ -335,71 +360,81 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
             const int ct = tid;
             const double* X = A.dlt64;
             bool ok = true;
-            for (int st = 0; st < A.n_g && ok; ++st) {
+            for (int gs = 0; gs < A.n_g && ok; ++gs) {
                 const double* cur = X;
                 double* nxt = (X == bufA) ? bufB : bufA;
                 for (int m = 0; m < cc.n_sound && ok; ++m) {
-                    // forward: velocities from cur (slow tendency from X at the first
-                    // substep); two cells per thread at a time, their loads in flight together
-                    for (long ca = c0 + ct; ca < c1; ca += 2 * CS_CT) {
-                        const bool two = ca + CS_CT < c1;
-                        const long cb = two ? ca + CS_CT : ca;
-                        const CellNb na = cell_nb(ca, nx, ny), nb2 = cell_nb(cb, nx, ny);
-                        const int ka = (int)(ca - c0), kb = (int)(cb - c0);
-                        const double* u = cur;
-                        const double* w = cur + ncell;
-                        const double* p = cur + 2 * ncell;
-                        if (m == 0) {
+                    // the state on the tile and its ring (periodic)
+                    for (int e = ct; e < RW * RH; e += CS_CT) {
+                        const int ly = e / RW, lx = e - ly * RW;
+                        const long g = (long)pwrap(ty0 - LR + ly, ny) * nx + pwrap(tx0 - LR + lx, nx);
+                        st[e] = ldg2(cur + g);
+                        st[RSZ + e] = ldg2(cur + ncell + g);
+                        st[2 * RSZ + e] = ldg2(cur + 2 * ncell + g);
+                    }
+                    named_barrier(1, CS_CT);
+                    if (m == 0) {
+                        // slow tendencies of the step's input (cur == X) on the tile + ring 1
+                        for (int e = ct; e < HW * HH; e += CS_CT) {
+                            const int hy = e / HW, hx = e - hy * HW;
+                            const int si = (hy + LR - 1) * RW + hx + LR - 1;
+                            double Ur = cc.U, Vc = cc.V;
+                            if (A.cc.omega != 0.0) {
+                                const int gy = pwrap(ty0 - 1 + hy, ny), gx = pwrap(tx0 - 1 + hx, nx);
+                                Ur += (double)(A.cc.omega * ((gy + 0.5) * A.cc.dy - A.cc.hly));
+                                Vc -= (double)(A.cc.omega * ((gx + 0.5) * A.cc.dx - A.cc.hlx));
+                            }
 #pragma unroll
                             for (int f = 0; f < 3; ++f) {
-                                const double sa = slow_cell(A.cc, cc, X + f * ncell, na, nx, ny, ynone);
-                                const double sb = slow_cell(A.cc, cc, X + f * ncell, nb2, nx, ny, ynone);
-                                S[f * cmax + ka] = sa;
-                                if (two) S[f * cmax + kb] = sb;
+                                const double* a = st + f * RSZ;
+                                double v;
+                                if (cc.order == 1) {
+                                    const double ax = -Ur * cc.inv_dx, ay = -Vc * cc.inv_dy;
+                                    const double dx_ = Ur >= 0.0 ? a[si] - a[si - 1] : a[si + 1] - a[si];
+                                    const double dy_ = ynone ? 0.0 : (Vc >= 0.0 ? a[si] - a[si - RW] : a[si + RW] - a[si]);
+                                    v = slow_first_order<double>(ax, ay, dx_, dy_, ynone);
+                                } else {
+                                    const double Fe = upwind_flux3_pts<double>(Ur, a[si - 1], a[si], a[si + 1], a[si + 2]);
+                                    const double Fw = upwind_flux3_pts<double>(Ur, a[si - 2], a[si - 1], a[si], a[si + 1]);
+                                    const double Gn = upwind_flux3_pts<double>(Vc, a[si - RW], a[si], a[si + RW],
+                                                                               a[si + 2 * RW]);
+                                    const double Gs = upwind_flux3_pts<double>(Vc, a[si - 2 * RW], a[si - RW], a[si],
+                                                                               a[si + RW]);
+                                    v = -(Fe - Fw) * cc.inv_dx - (Gn - Gs) * cc.inv_dy;
+                                }
+                                S[f * HSZ + e] = v;
                             }
                         }
-                        const double nua = fb_new_u<double>(cc, S[ka], ldg2(u + na.i), ldg2(u + na.xp), ldg2(u + na.xm),
-                                                            ldg2(p + na.xp), ldg2(p + na.xm), ldg2(w + na.pp),
-                                                            ldg2(w + na.pm), ldg2(w + na.mp), ldg2(w + na.mm));
-                        const double nub = fb_new_u<double>(cc, S[kb], ldg2(u + nb2.i), ldg2(u + nb2.xp),
-                                                            ldg2(u + nb2.xm), ldg2(p + nb2.xp), ldg2(p + nb2.xm),
-                                                            ldg2(w + nb2.pp), ldg2(w + nb2.pm), ldg2(w + nb2.mp),
-                                                            ldg2(w + nb2.mm));
-                        const double nwa = fb_new_w<double>(cc, S[cmax + ka], ldg2(w + na.i), ldg2(w + na.yp),
-                                                            ldg2(w + na.ym), ldg2(p + na.yp), ldg2(p + na.ym),
-                                                            ldg2(u + na.pp), ldg2(u + na.mp), ldg2(u + na.pm),
-                                                            ldg2(u + na.mm));
-                        const double nwb = fb_new_w<double>(cc, S[cmax + kb], ldg2(w + nb2.i), ldg2(w + nb2.yp),
-                                                            ldg2(w + nb2.ym), ldg2(p + nb2.yp), ldg2(p + nb2.ym),
-                                                            ldg2(u + nb2.pp), ldg2(u + nb2.mp), ldg2(u + nb2.pm),
-                                                            ldg2(u + nb2.mm));
-                        nxt[ca] = nua;
-                        nxt[ncell + ca] = nwa;
-                        if (two) {
-                            nxt[cb] = nub;
-                            nxt[ncell + cb] = nwb;
+                        named_barrier(1, CS_CT);
+                    }
+                    // forward: velocities on the tile + ring 1
+                    {
+                        const double* u = st;
+                        const double* w = st + RSZ;
+                        const double* p = st + 2 * RSZ;
+                        for (int e = ct; e < HW * HH; e += CS_CT) {
+                            const int hy = e / HW, hx = e - hy * HW;
+                            const int si = (hy + LR - 1) * RW + hx + LR - 1;
+                            fu[e] = fb_new_u<double>(cc, S[e], u[si], u[si + 1], u[si - 1], p[si + 1], p[si - 1],
+                                                     w[si + 1 + RW], w[si + 1 - RW], w[si - 1 + RW], w[si - 1 - RW]);
+                            fw[e] = fb_new_w<double>(cc, S[HSZ + e], w[si], w[si + RW], w[si - RW], p[si + RW],
+                                                     p[si - RW], u[si + 1 + RW], u[si - 1 + RW], u[si + 1 - RW],
+                                                     u[si - 1 - RW]);
                         }
                     }
-                    if (!grid_barrier_group(A.gb, 0, nb, 1, CS_CT, ct == 0, &s_okc)) {
-                        ok = false;
-                        break;
+                    named_barrier(1, CS_CT);
+                    // backward: pressure on the tile; the tile's new state is written out
+                    for (int k = ct; k < ncl; k += CS_CT) {
+                        const int ly = k / tw, lx = k - ly * tw;
+                        const int e = (ly + 1) * HW + lx + 1, si = (ly + LR) * RW + lx + LR;
+                        const double pn = fb_new_p<double>(cc, S[2 * HSZ + e], st[2 * RSZ + si], fu[e + 1], fu[e - 1],
+                                                           fw[e + HW], fw[e - HW]);
+                        const long g = (long)(ty0 + ly) * nx + tx0 + lx;
+                        nxt[g] = fu[e];
+                        nxt[ncell + g] = fw[e];
+                        nxt[2 * ncell + g] = pn;
                     }
-                    // backward: pressure with the new velocities
-                    for (long ca = c0 + ct; ca < c1; ca += 2 * CS_CT) {
-                        const bool two = ca + CS_CT < c1;
-                        const long cb = two ? ca + CS_CT : ca;
-                        const CellNb na = cell_nb(ca, nx, ny), nb2 = cell_nb(cb, nx, ny);
-                        const int ka = (int)(ca - c0), kb = (int)(cb - c0);
-                        const double pa = fb_new_p<double>(cc, S[2 * cmax + ka], ldg2(cur + 2 * ncell + ca),
-                                                           ldg2(nxt + na.xp), ldg2(nxt + na.xm),
-                                                           ldg2(nxt + ncell + na.yp), ldg2(nxt + ncell + na.ym));
-                        const double pb = fb_new_p<double>(cc, S[2 * cmax + kb], ldg2(cur + 2 * ncell + cb),
-                                                           ldg2(nxt + nb2.xp), ldg2(nxt + nb2.xm),
-                                                           ldg2(nxt + ncell + nb2.yp), ldg2(nxt + ncell + nb2.ym));
-                        nxt[2 * ncell + ca] = pa;
-                        if (two) nxt[2 * ncell + cb] = pb;
-                    }
-                    const bool last = st == A.n_g - 1 && m == cc.n_sound - 1;
+                    const bool last = gs == A.n_g - 1 && m == cc.n_sound - 1;
                     if (!last && !grid_barrier_group(A.gb, 0, nb, 1, CS_CT, ct == 0, &s_okc)) {
                         ok = false;
                         break;
@@ -433,18 +468,17 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
                 for (int l = pt; l < ncols; l += CS_PT) cs[l] = __ldcg(A.cvec + l);
                 named_barrier(2, CS_PT);
                 for (int k = pt; k < 3 * ncl; k += CS_PT) {
-                    const int f = k / ncl;
-                    const long row = (long)f * ncell + c0 + (k - f * ncl);
-                    const double* Dr = A.D + row;
+                    const int f = k / ncl, kk = k - f * ncl;
+                    const double* Dr = A.D + tile_row(f, kk);
                     double acc = 0.0;
 #pragma unroll 8
                     for (int l = 0; l < ncols; ++l) acc += __ldg(Dr + (long)l * d) * cs[l];
-                    dc[f * cmax + (k - f * ncl)] = acc;
+                    dc[f * nclx + kk] = acc;
                 }
             }
             if (!ok) s_fail = 1;
         }
-        __syncthreads();   // join: G(delta_i) and D c of the CTA's rows are complete
+        __syncthreads();   // join: G(delta_i) and D c of the tile's rows are complete
         if (s_fail) return;
         const double* qt = A.qt + (long)i * d;
         double* qn = A.q + (long)(i + 1) * d;
@@ -452,10 +486,10 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
         double* ga = A.gacc ? A.gacc + (long)i * d : nullptr;
         double s = 0.0;
         for (int k = tid; k < 3 * ncl; k += CS_NT) {
-            const int f = k / ncl;
-            const long row = (long)f * ncell + c0 + (k - f * ncl);
+            const int f = k / ncl, kk = k - f * ncl;
+            const long row = tile_row(f, kk);
             const double gin = R[row];
-            const double y = qt[row] + (gin + dc[f * cmax + (k - f * ncl)]);
+            const double y = qt[row] + (gin + dc[f * nclx + kk]);
             const double e = y - qn[row];
             s += e * e;
             qn[row] = y;
@@ -514,9 +548,10 @@ long chain_resp_elems(int n_slices) { return (long)(n_slices + 1) * 1024; }
 
 namespace {
 
-size_t split_smem_bytes(long ncell, int nb, int ccap) {
-    const long cmax = (ncell + nb - 1) / nb;
-    return sizeof(double) * (size_t)(6 * cmax + (ccap > 0 ? ccap : 1));
+size_t split_smem_bytes(int nx, int ny, int nb, int order, int ccap) {
+    const SplitTiles t = split_tiles(nx, ny, nb, order);
+    if (t.ntx * t.nty < 1 || t.ntx * t.nty > nb) return 0;
+    return sizeof(double) * (size_t)split_smem_doubles(t, ccap);
 }
 
 // CTAs of the split-group chain (one per SM), or 0 when it does not fit
@@ -550,8 +585,8 @@ cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s) {
         if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int nb = a.max_blocks > 0 && a.max_blocks < sms ? a.max_blocks : sms;
-        const size_t smem = split_smem_bytes(a.d / 3, nb, a.ccap);
-        if (nb >= 1 && smem <= 200 * 1024 && split_grid(smem) >= nb) {
+        const size_t smem = nb >= 1 ? split_smem_bytes(a.nx, a.ny, nb, a.cc.order, a.ccap) : 0;
+        if (smem > 0 && smem <= 200 * 1024 && split_grid(smem) >= nb) {
             cudaError_t e = cudaMemsetAsync(&a.gb->count, 0, sizeof(unsigned), s);
             if (e == cudaSuccess) e = cudaMemsetAsync(a.gb->gcount, 0, sizeof(a.gb->gcount), s);
             if (e != cudaSuccess) return e;
