@@ -196,8 +196,7 @@ cudaError_t fill_int(int* p, int v, int n, cudaStream_t s);
 
 // Grid-barrier state of a cooperative launch (zeroed before each launch).
 struct GridBar {
-    unsigned count;
-    unsigned gen;
+    unsigned count;   // monotonic arrival counter of grid_barrier (zeroed before each launch)
     int err;   // set to 1 when a barrier wait gave up
     unsigned gcount[3];   // monotonic counters of grid_barrier_group (zeroed before a launch using them)
 };

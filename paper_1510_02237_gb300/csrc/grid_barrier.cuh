@@ -5,35 +5,49 @@
 
 namespace pr {
 
-// Sense-reversal barrier over all CTAs of a cooperative launch.  The spin is
-// bounded: after ~2^22 polls (well over a second) it sets the error word and
-// returns false, so a fault elsewhere can never hang the GPU.
+// Poll ctr with acquire loads until it reaches target (counters only grow
+// within a launch).  Gives up -- sets *err to 1 and returns 0 -- after one
+// second by the global timer (or 2^26 polls), and returns 0 at once when
+// another wait has set the error word.
+__device__ __forceinline__ int poll_until(unsigned* ctr, unsigned target, volatile int* verr, int* err) {
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (unsigned long long it = 1;; ++it) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if ((int)(v - target) >= 0) return 1;
+        if ((it & 255) == 0) {
+            if (*verr != 0) return 0;
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t - t0 > 1000000000ull || it > (1ull << 26)) {
+                atomicExch(err, 1);
+                return 0;
+            }
+        }
+    }
+}
+
+// Barrier over all CTAs of a cooperative launch, on the monotonic counter
+// gb->count (zeroed before every launch that uses it): thread 0 of each CTA
+// adds one with release semantics and polls with acquire loads until the
+// counter reaches the next multiple of nblocks.  The spin is bounded
+// (poll_until): after a second it sets the error word and returns false, so
+// a fault elsewhere can never hang the GPU; a set error word makes every
+// later barrier return false at once.
 __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned nblocks) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* vgen = &gb->gen;
         volatile int* verr = &gb->err;
+        int ok = 0;
         if (*verr == 0) {
-            const unsigned g = *vgen;
-            __threadfence();
-            if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
-                atomicExch(&gb->count, 0u);
-                __threadfence();
-                atomicAdd(&gb->gen, 1u);
-            } else {
-                unsigned long long it = 0;
-                while (*vgen == g) {
-                    if (++it > (1ull << 22) || *verr != 0) {
-                        atomicExch(&gb->err, 1);
-                        break;
-                    }
-                    __nanosleep(100);
-                }
-            }
-            __threadfence();
+            unsigned old;
+            asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&gb->count) : "memory");
+            const unsigned target = (old / nblocks + 1) * nblocks;
+            ok = poll_until(&gb->count, target, verr, &gb->err);
         }
-        s_ok = *verr == 0;
+        s_ok = ok && *verr == 0;
     }
     __syncthreads();
     return s_ok != 0;
@@ -45,10 +59,8 @@ __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned nblocks) {
 // the CTA), its first thread (leader) adds one with release semantics and
 // polls with acquire loads until the counter reaches the next multiple of
 // nblocks, the group meets again.  Two groups of a CTA can synchronise with
-// their peers independently.  No reset, no sleep between polls: about 1.7 us
-// per barrier on 152 CTAs, against about 3 us for grid_barrier.  Bounded like
-// grid_barrier, on the same error word; s_ok is a shared-memory word of the
-// group.
+// their peers independently.  Bounded like grid_barrier, on the same error
+// word; s_ok is a shared-memory word of the group.
 __device__ __forceinline__ void named_barrier(int bar_id, int nthr) {
     asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthr) : "memory");
 }
@@ -63,22 +75,7 @@ __device__ __forceinline__ bool grid_barrier_group(GridBar* gb, int slot, unsign
             unsigned old;
             asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(ctr) : "memory");
             const unsigned target = (old / nblocks + 1) * nblocks;
-            unsigned long long it = 0;
-            ok = 1;
-            while (true) {
-                unsigned v;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
-                if ((int)(v - target) >= 0) break;
-                if (++it > (1ull << 22)) {
-                    atomicExch(&gb->err, 1);
-                    ok = 0;
-                    break;
-                }
-                if ((it & 255) == 0 && *verr != 0) {
-                    ok = 0;
-                    break;
-                }
-            }
+            ok = poll_until(ctr, target, verr, &gb->err);
         }
         *s_ok = ok && *verr == 0;
     }

@@ -631,7 +631,7 @@ cudaError_t intra_block(double* wv, double* wz, long d, int m, const double* a2,
     if (nb < 1) return cudaErrorInvalidConfiguration;
     int pstride = 64;
     if ((long)2 * nb * pstride > w.elems) return cudaErrorInvalidValue;
-    // arrival counter to zero; generation and the sticky error word are kept
+    // arrival counter to zero; the sticky error word is kept
     cudaError_t e = cudaMemsetAsync(&gb->count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     double* part = w.partial;
