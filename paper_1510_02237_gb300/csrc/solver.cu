@@ -110,6 +110,12 @@ static int default_cap(int N, int K_max) {
     return (int)(c > 0 ? c : 1);
 }
 
+// Whether the KSE path forms the basis images by linearity (Eq. Genhance)
+// rather than directly: FP64 fine sweep, FP64 correction, not forced direct.
+static bool linear_images(const pr_options& o) {
+    return o.variant == PR_KSE && o.corr_prec != PR_FP32 && o.images != PR_IMAGES_DIRECT && o.fine_prec == PR_FP64;
+}
+
 struct Sizes {
     long d;
     int cap;
@@ -149,7 +155,7 @@ static Sizes compute_sizes(int nx, int ny, int N, int K_max, const pr_options& o
     b += dd * (size_t)s.partial;
     b += dd * (size_t)(N + (N + 1) + PR_MAX_ITERS + 1);
     b += sizeof(int) * (size_t)(3 + N + PR_MAX_ITERS);
-    if (o.proj_prec == PR_PROJ_SPLIT_BF16) b += sg_bytes(s.d, s.cap);
+    if (o.proj_prec == PR_PROJ_SPLIT_BF16) b += sg_bytes(s.d, s.cap, linear_images(o));
     s.bytes = b;
     return s;
 }
@@ -253,7 +259,11 @@ static pr_status block_pass(pr_solver* h, double* v, double* z, int mm) {
     TsWork w{h->partial, h->partial_elems};
     if (h->use_sg) {
         CKC(sg_cgs_pass(&h->sg, v, d, mm, h->r_old, s));
-        if (z) CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->sg.C, h->sg.cap_pad, z, d, z, d, mm, d, -1.0, s));
+        if (z && h->sg.Dr) {
+            CKC(sg_update_images(&h->sg, z, d, mm, h->r_old, s));
+        } else if (z) {
+            CKC(gemm_nn(h->D, d, nullptr, h->r_old, cap, h->sg.C, h->sg.cap_pad, z, d, z, d, mm, d, -1.0, s));
+        }
     } else {
         CKC(gemm_tn(h->Q, d, nullptr, h->r_old, cap, v, d, mm, d, h->C, cap, w, s));
         CKC(gemm_nn(h->Q, d, nullptr, h->r_old, cap, h->C, cap, v, d, v, d, mm, d, -1.0, s));
@@ -306,7 +316,10 @@ static pr_status krylov_block(pr_solver* h, const double* V, const double* FV, c
         CKS(block_pass(h, v, z, mm));
         CKC(cholqr_block(v, z, d, mm, h->nk, h->use_sg ? h->sg.C : h->C, h->use_sg ? h->sg.cap_pad : cap, h->r_old,
                          h->G, h->Rinv, h->Q, h->D, h->r_old, s));
-        if (h->use_sg) CKC(sg_append(&h->sg, h->Q, d, h->r_old, h->r, 0, mm, s));
+        if (h->use_sg) {
+            CKC(sg_append(&h->sg, h->Q, d, h->r_old, h->r, 0, mm, s));
+            if (images && h->sg.Dr) CKC(sg_append_images(&h->sg, h->D, d, h->r_old, h->r, 0, mm, s));
+        }
     }
     CKC(mark());
     return PR_OK;
@@ -818,7 +831,7 @@ pr_status parareal_create(const pr_grid* g, double U, double c_s, double dt_f, d
         chk(cudaEventCreate(&h->ev1));
     }
     if (e == cudaSuccess && o.proj_prec == PR_PROJ_SPLIT_BF16) {
-        chk(sg_init(&h->sg, d, h->cap));
+        chk(sg_init(&h->sg, d, h->cap, linear_images(o)));
         h->use_sg = e == cudaSuccess;
     }
     if (e != cudaSuccess) {

@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(DB_ROWS) k_digits_basis(const double* __restri
                 const int ec = unit_elem(cc & 7, k);
 #pragma unroll
                 for (int s = 0; s < SG_S; ++s) {
-                    Xc[((long)s * nkb * ngl + uc) * 256 + ec] = dg[s];
+                    if (Xc) Xc[((long)s * nkb * ngl + uc) * 256 + ec] = dg[s];
                     tile[s][threadIdx.x][j] = dg[s];
                 }
             }
@@ -670,7 +670,7 @@ inline long cdivl(long a, long b) { return (a + b - 1) / b; }
 
 }  // namespace
 
-size_t sg_bytes(long d, int cap) {
+size_t sg_bytes(long d, int cap, bool images) {
     const long cap_pad = cdivl(cap, SG_KC) * SG_KC;
     const long grid = 1024;   // bound on the SM count
     size_t b = 0;
@@ -680,10 +680,15 @@ size_t sg_bytes(long d, int cap) {
     b += (size_t)SG_S * SG_N * cap_pad * 2;          // Cs
     b += sizeof(int) * ((size_t)cap_pad + 2 * SG_N + 1) + sizeof(unsigned long long) * ((size_t)cap_pad + SG_N);
     b += sizeof(double) * ((size_t)grid * cap_pad * SG_N + (size_t)SG_N * cap_pad);
+    if (images) {
+        b += (size_t)SG_S * cap_pad * dp * 2;        // Dr
+        b += (size_t)SG_S * SG_N * cap_pad * 2;      // CsD
+        b += sizeof(int) * ((size_t)cap_pad + SG_N) + sizeof(unsigned long long) * (size_t)cap_pad;
+    }
     return b;
 }
 
-cudaError_t sg_init(SplitGemm* g, long d, int cap) {
+cudaError_t sg_init(SplitGemm* g, long d, int cap, bool images) {
     *g = SplitGemm();
     if (d < 1 || d % 8 != 0 || cap < 1 || cap > 16384) return cudaErrorInvalidValue;
     g->d = d;
@@ -720,6 +725,13 @@ cudaError_t sg_init(SplitGemm* g, long d, int cap) {
     SG_ALLOC(g->err, sizeof(int));
     SG_ALLOC(g->ws, sizeof(double) * (size_t)g->grid * cp * SG_N);
     SG_ALLOC(g->C, sizeof(double) * (size_t)SG_N * cp);
+    if (images) {
+        SG_ALLOC(g->Dr, uXr * 512);
+        SG_ALLOC(g->CsD, uCs * 512);
+        SG_ALLOC(g->Ed, sizeof(int) * cp);
+        SG_ALLOC(g->GcD, sizeof(int) * SG_N);
+        SG_ALLOC(g->Kd, sizeof(unsigned long long) * cp);
+    }
 #undef SG_ALLOC
     const cudaError_t attr = set_dynamic_smem((const void*)k_finish, 16384 * sizeof(double));
     if (attr != cudaSuccess) {
@@ -730,7 +742,9 @@ cudaError_t sg_init(SplitGemm* g, long d, int cap) {
     for (int i = 0; i < 4; ++i) {
         ok = ok && make_map(&g->mapXc[i], g->Xc, uXc, 16u >> i);
         ok = ok && make_map(&g->mapXr[i], g->Xr, uXr, 16u >> i);
+        if (images) ok = ok && make_map(&g->mapDr[i], g->Dr, uXr, 16u >> i);
     }
+    if (images) ok = ok && make_map(&g->mapCsD2, g->CsD, uCs, 2);
     if (!ok) {
         sg_free(g);
         return cudaErrorNotSupported;
@@ -751,6 +765,11 @@ void sg_free(SplitGemm* g) {
     cudaFree(g->err);
     cudaFree(g->ws);
     cudaFree(g->C);
+    cudaFree(g->Dr);
+    cudaFree(g->CsD);
+    cudaFree(g->Ed);
+    cudaFree(g->GcD);
+    cudaFree(g->Kd);
     *g = SplitGemm();
 }
 
@@ -759,29 +778,43 @@ static int colmax_blocks(long d) {
     return (int)(nb < 1 ? 1 : nb > 128 ? 128 : nb);
 }
 
-cudaError_t sg_append(SplitGemm* g, const double* Q, long ldq, const int* c0_dev, const int* c1_dev, int c0_host,
-                      int maxcols, cudaStream_t s) {
+// Column maxima, exponents and digits of columns of X into the Xr layout
+// (xr) and, when xc is given, the Xc layout.
+static cudaError_t append_digits(SplitGemm* g, const double* X, long ldx, const int* c0_dev, const int* c1_dev,
+                                 int c0_host, int maxcols, unsigned long long* keys, int* exps, __nv_bfloat16* xc,
+                                 __nv_bfloat16* xr, cudaStream_t s) {
     for (int j0 = 0; j0 < maxcols; j0 += SG_N) {
         // columns [c0 + j0, c0 + j0 + SG_N) of the (device-side) range
         const int nc = maxcols - j0 < SG_N ? maxcols - j0 : SG_N;
-        cudaError_t e = cudaMemsetAsync(g->Kq, 0, sizeof(unsigned long long) * g->cap_pad, s);
+        cudaError_t e = cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * g->cap_pad, s);
         if (e != cudaSuccess) return e;
         if (c0_dev) {
             if (j0 > 0) return cudaErrorInvalidValue;   // device ranges: at most SG_N columns per call
-            k_col_max<<<dim3(colmax_blocks(g->d), nc), 256, 0, s>>>(Q, ldq, g->d, c0_dev, c1_dev, 0, g->Kq);
+            k_col_max<<<dim3(colmax_blocks(g->d), nc), 256, 0, s>>>(X, ldx, g->d, c0_dev, c1_dev, 0, keys);
         } else {
-            k_col_max<<<dim3(colmax_blocks(g->d), nc), 256, 0, s>>>(Q, ldq, g->d, nullptr, nullptr, c0_host + j0,
-                                                                   g->Kq);
+            k_col_max<<<dim3(colmax_blocks(g->d), nc), 256, 0, s>>>(X, ldx, g->d, nullptr, nullptr, c0_host + j0,
+                                                                   keys);
         }
         long nb = cdivl(g->d, DB_ROWS);
         if (nb > 8 * 152) nb = 8 * 152;
-        k_digits_basis<<<(int)nb, DB_ROWS, 0, s>>>(Q, ldq, g->d, c0_dev, c1_dev, c0_host + j0, nc, g->Kq, g->Eq, g->Xc,
-                                               g->Xr, g->nkb, g->ngl, g->nlb, g->ngd);
+        k_digits_basis<<<(int)nb, DB_ROWS, 0, s>>>(X, ldx, g->d, c0_dev, c1_dev, c0_host + j0, nc, keys, exps, xc, xr,
+                                               g->nkb, g->ngl, g->nlb, g->ngd);
         count_launches(2);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t sg_append(SplitGemm* g, const double* Q, long ldq, const int* c0_dev, const int* c1_dev, int c0_host,
+                      int maxcols, cudaStream_t s) {
+    return append_digits(g, Q, ldq, c0_dev, c1_dev, c0_host, maxcols, g->Kq, g->Eq, g->Xc, g->Xr, s);
+}
+
+cudaError_t sg_append_images(SplitGemm* g, const double* D, long ldd, const int* c0_dev, const int* c1_dev,
+                             int c0_host, int maxcols, cudaStream_t s) {
+    if (!g->Dr) return cudaErrorInvalidValue;
+    return append_digits(g, D, ldd, c0_dev, c1_dev, c0_host, maxcols, g->Kd, g->Ed, nullptr, g->Dr, s);
 }
 
 cudaError_t sg_project(SplitGemm* g, const double* v, long ldv, int m, const int* r_dev, cudaStream_t s) {
@@ -814,7 +847,10 @@ cudaError_t sg_project(SplitGemm* g, const double* v, long ldv, int m, const int
     return cudaGetLastError();
 }
 
-static cudaError_t sg_apply_update(SplitGemm* g, double* v, long ldv, int m, const int* r_dev, cudaStream_t s) {
+// v <- v - X C on the tensor cores: X's digits (maps mapA, Xr layout) against
+// the folded coefficient digits (map mapB) with their column exponents gc.
+static cudaError_t sg_apply(SplitGemm* g, double* v, long ldv, int m, const int* r_dev, const CUtensorMap* mapA,
+                            const CUtensorMap& mapB, int* gc, cudaStream_t s) {
     SgArgs a{};
     a.mode = 1;
     a.a_slice_units = (long)g->nlb * g->ngd;
@@ -825,11 +861,14 @@ static cudaError_t sg_apply_update(SplitGemm* g, double* v, long ldv, int m, con
     a.k_host = g->cap;
     a.v = v;
     a.ldv = ldv;
-    a.vexp = g->Gc;
+    a.vexp = gc;
     a.ncols = m;
     a.err = g->err;
     long tiles = cdivl(g->d, SG_BM);
-    return launch_mma(g->mapXr, g->mapCs2, a, dim3((unsigned)(tiles < g->grid ? tiles : g->grid)), s);
+    return launch_mma(mapA, mapB, a, dim3((unsigned)(tiles < g->grid ? tiles : g->grid)), s);
+}
+static cudaError_t sg_apply_update(SplitGemm* g, double* v, long ldv, int m, const int* r_dev, cudaStream_t s) {
+    return sg_apply(g, v, ldv, m, r_dev, g->mapXr, g->mapCs2, g->Gc, s);
 }
 
 cudaError_t sg_cgs_pass(SplitGemm* g, double* v, long ldv, int m, const int* r_dev, cudaStream_t s) {
@@ -838,6 +877,16 @@ cudaError_t sg_cgs_pass(SplitGemm* g, double* v, long ldv, int m, const int* r_d
     return sg_apply_update(g, v, ldv, m, r_dev, s);
 }
 
+cudaError_t sg_update_images(SplitGemm* g, double* z, long ldz, int m, const int* r_dev, cudaStream_t s) {
+    if (m < 1 || m > SG_N || !g->Dr) return cudaErrorInvalidValue;
+    // the coefficients of the last projection, folded with D's exponents
+    k_finish<<<SG_N, FIN_T, sizeof(double) * g->cap_pad, s>>>(nullptr, 0, 0, g->d, r_dev, g->Ed, nullptr, m, nullptr,
+                                                            0, g->C, g->cap_pad, g->CsD, g->cap_pad, g->GcD);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return sg_apply(g, z, ldz, m, r_dev, g->mapDr, g->mapCsD2, g->GcD, s);
+}
 cudaError_t sg_update(SplitGemm* g, double* v, long ldv, int m, const double* C, int ldc, const int* r_dev,
                       cudaStream_t s) {
     if (m < 1 || m > SG_N) return cudaErrorInvalidValue;

@@ -55,18 +55,35 @@ struct SplitGemm {
     int* err = nullptr;            // sticky: a pipeline wait gave up
     CUtensorMap mapXc[4], mapXr[4];   // boxes of 16, 8, 4 and 2 units
     CUtensorMap mapVs2, mapCs2;       // boxes of 2 units
+    // With images (sg_init(..., true)): the basis images D = F(Q) - G(Q) in
+    // the Xr layout, their column exponents, and the coefficient digits
+    // folded with those exponents, so that z <- z - D C runs like v <- v - Q C.
+    __nv_bfloat16* Dr = nullptr;
+    __nv_bfloat16* CsD = nullptr;
+    int* Ed = nullptr;             // [cap] column exponents of D
+    int* GcD = nullptr;            // [SG_N] exponents of the folded coefficient columns
+    unsigned long long* Kd = nullptr;   // [cap_pad] column maxima keys of D
+    CUtensorMap mapDr[4], mapCsD2;
 };
 
-// Bytes of device memory sg_init allocates for (d, cap).
-size_t sg_bytes(long d, int cap);
-// Allocate and set up (tensor maps included); d must be a multiple of 8.
-cudaError_t sg_init(SplitGemm* g, long d, int cap);
+// Bytes of device memory sg_init allocates for (d, cap, images).
+size_t sg_bytes(long d, int cap, bool images = false);
+// Allocate and set up (tensor maps included); d must be a multiple of 8;
+// images: also hold the digits of the basis images D.
+cudaError_t sg_init(SplitGemm* g, long d, int cap, bool images = false);
 void sg_free(SplitGemm* g);
 // Digits of columns [c0, c1) of Q in both layouts: a device range (c0_dev,
 // c1_dev; at most maxcols <= SG_N columns) or host columns [c0_host,
 // c0_host + maxcols).
 cudaError_t sg_append(SplitGemm* g, const double* Q, long ldq, const int* c0_dev, const int* c1_dev, int c0_host,
                       int maxcols, cudaStream_t s);
+// Digits of columns of D (the basis images), in the Xr layout, like sg_append.
+cudaError_t sg_append_images(SplitGemm* g, const double* D, long ldd, const int* c0_dev, const int* c1_dev,
+                             int c0_host, int maxcols, cudaStream_t s);
+// z <- z - D C for the m <= SG_N image columns z (ld ldz), with the
+// coefficients C of the last projection (g->C): the image update of a
+// Gram-Schmidt pass.  Needs sg_init(..., true).
+cudaError_t sg_update_images(SplitGemm* g, double* z, long ldz, int m, const int* r_dev, cudaStream_t s);
 // One classical Gram-Schmidt pass of the m <= SG_N columns v (ld ldv) against
 // Q[:, 0:*r_dev):  C = Q^T v (into g->C), then v <- v - Q C.
 cudaError_t sg_cgs_pass(SplitGemm* g, double* v, long ldv, int m, const int* r_dev, cudaStream_t s);
