@@ -743,8 +743,8 @@ def run_ours(args):
     sm.close()
     st_, outs_t, v_t, ph_t = variant({"proj_prec": P.PR_PROJ_SPLIT_BF16})
     fp64_tc = {"value": v_t, "unit": "solves/s", "speedup_vs_fp64": v_t / value,
-               "what": "the FP64 solve with Q^T V, V - Q C and Q^T q on the tensor cores (FP64-accurate split "
-                       "digits)", "phases_ms_per_solve": ph_t}
+               "what": "the FP64 solve with Q^T V, V - Q C, the image update Z - D C and Q^T q on the tensor "
+                       "cores (FP64-accurate split digits)", "phases_ms_per_solve": ph_t}
     if rank == 0:
         fp64_tc["per_ic"] = per_ic_errors(outs_t)
     st_.close()

@@ -118,11 +118,13 @@ typedef struct {
                               (Eq. modifiedCoarse).  PR_PROJ_SPLIT_BF16
                               orthogonalises the new columns in blocks of 16
                               with these products on the tensor cores, to FP64
-                              accuracy (norms, the drop rule, the in-block
-                              Gram-Schmidt and products with D stay FP64); it
-                              needs 3*nx*ny to be a multiple of 8 and adds about
-                              32*cap*3*nx*ny bytes of digit slices to the
-                              footprint (default PR_PROJ_FP64)                  */
+                              accuracy, and with images by linearity also the
+                              image update Z - D C (norms, the drop rule, the
+                              in-block Gram-Schmidt and the serial chain's
+                              products stay FP64); it needs 3*nx*ny to be a
+                              multiple of 8 and adds about 32*cap*3*nx*ny bytes
+                              of digit slices to the footprint (48*cap*3*nx*ny
+                              with images by linearity; default PR_PROJ_FP64) */
     int32_t coarse_scheme; /* PR_COARSE_SPLIT_FE (default): one coarse step is a
                               partially split forward-Euler step with n_sound
                               forward-backward acoustic substeps and damping

@@ -117,8 +117,9 @@ class Server:
         reproduces a served result with a handle of one's own).
 
         mode 'fp64': plain FP64.  'fp64_tc': FP64 fine sweep and correction,
-        the subspace products Q^T V and V - Q C on the BF16 tensor cores with
-        FP32 accumulation and exact split digits (FP64-accurate, so the final
+        the subspace products Q^T V and V - Q C (and the image update
+        Z - D C) on the BF16 tensor cores with FP32 accumulation and exact
+        split digits (FP64-accurate, so the final
         accuracy equals the plain FP64 solve's).  'mixed': additionally FP32
         tendencies in the fine sweep and an FP32 correction (fastest; its
         accuracy depends on the input's conditioning)."""
