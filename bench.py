@@ -72,12 +72,13 @@ def parse():
     ap.add_argument("--serving-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests of the equal-accuracy serving stream (12 requests/s)")
-    ap.add_argument("--case", choices=["fine", "fine32", "fine32x", "solve", "solve_mixed"], default=None,
+    ap.add_argument("--case", choices=["fine", "fine32", "fine32x", "solve", "solve_mixed", "solve_tc"], default=None,
                     help="small isolated case for profiler captures: 'fine' = three fine sweeps over all "
                          "32 slices of the 256x128 workload; 'fine32' = three FP32 fine sweeps over the 64 "
                          "slices of the 512x256 workload ('fine32x': FP32 stages on an FP64 state); 'solve' = "
                          "two solves of the 256x128 workload's "
-                         "first IC; 'solve_mixed' = the same in mixed precision with the tensor-core projections")
+                         "first IC; 'solve_mixed' = the same in mixed precision with the tensor-core projections; "
+                         "'solve_tc' = FP64 with the tensor-core projections")
     return ap.parse_args()
 
 
@@ -823,6 +824,8 @@ def run_case(args):
         opt = {"fine_prec": P.PR_FP32 if args.case == "fine32" else P.PR_FP32X}
     if args.case == "solve_mixed":
         opt = {"fine_prec": P.PR_FP32X, "corr_prec": P.PR_FP32, "proj_prec": P.PR_PROJ_SPLIT_BF16}
+    if args.case == "solve_tc":
+        opt = {"proj_prec": P.PR_PROJ_SPLIT_BF16}
     s = P.Solver(p, stream=torch.cuda.current_stream(), K_max=wl.K, krylov_cap=wl.krylov_cap, **opt)
     q0 = torch.from_numpy(wl.ics[0][1]().ravel()).cuda()
     if args.case in ("fine", "fine32", "fine32x"):
