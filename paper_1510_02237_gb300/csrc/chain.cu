@@ -300,6 +300,7 @@ __device__ __forceinline__ double warp_dot_x_l2(const double* a, const double* x
     return s;
 }
 
+template <bool DELTA>
 __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double red[CS_NT / 32];
@@ -348,29 +349,48 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
 
     // the buffer holding G(delta_i) after the coarse group: every step starts
     // in the buffer other than its input and alternates with each substep
-    const double* R = A.dlt64;
+    const double* R = nullptr;   // the input is neither work state
     for (int st_ = 0; st_ < A.n_g; ++st_) {
         const double* n0 = (R == bufA) ? bufB : bufA;
         R = (cc.n_sound & 1) ? n0 : ((n0 == bufA) ? bufB : bufA);
     }
 
     for (int i = A.i_begin; i < A.i_end; ++i) {
+        // the state K acts on: delta_i, or q_i itself (literal form)
+        const double* xin = DELTA ? A.dlt64 : A.q + (long)i * d;
         if (wid < CS_CW) {
             // ---------------------------------------------------- coarse group
             const int ct = tid;
-            const double* X = A.dlt64;
+            const double* X = xin;
             bool ok = true;
             for (int gs = 0; gs < A.n_g && ok; ++gs) {
                 const double* cur = X;
                 double* nxt = (X == bufA) ? bufB : bufA;
                 for (int m = 0; m < cc.n_sound && ok; ++m) {
-                    // the state on the tile and its ring (periodic)
-                    for (int e = ct; e < RW * RH; e += CS_CT) {
-                        const int ly = e / RW, lx = e - ly * RW;
-                        const long g = (long)pwrap(ty0 - LR + ly, ny) * nx + pwrap(tx0 - LR + lx, nx);
-                        st[e] = ldg2(cur + g);
-                        st[RSZ + e] = ldg2(cur + ncell + g);
-                        st[2 * RSZ + e] = ldg2(cur + 2 * ncell + g);
+                    // the state on the tile and its ring (periodic); four cells
+                    // per thread at a time, their loads in flight together
+                    for (int e0 = ct; e0 < RW * RH; e0 += 4 * CS_CT) {
+                        double vu[4], vw[4], vp[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int e = e0 + q * CS_CT;
+                            if (e < RW * RH) {
+                                const int ly = e / RW, lx = e - ly * RW;
+                                const long g = (long)pwrap(ty0 - LR + ly, ny) * nx + pwrap(tx0 - LR + lx, nx);
+                                vu[q] = ldg2(cur + g);
+                                vw[q] = ldg2(cur + ncell + g);
+                                vp[q] = ldg2(cur + 2 * ncell + g);
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int e = e0 + q * CS_CT;
+                            if (e < RW * RH) {
+                                st[e] = vu[q];
+                                st[RSZ + e] = vw[q];
+                                st[2 * RSZ + e] = vp[q];
+                            }
+                        }
                     }
                     named_barrier(1, CS_CT);
                     if (m == 0) {
@@ -448,7 +468,7 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
         } else {
             // ---------------------------------------------------- product group
             const int pt = tid - CS_CT, pw = pt >> 5;
-            const double* x = A.dlt64;
+            const double* x = xin;
             bool ok = true;
             for (int l = pw; l < ncols; l += CS_PW) {
                 const double s = warp_dot_x_l2(A.Q + (long)l * d, x, r0, r1);
@@ -480,20 +500,27 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
         }
         __syncthreads();   // join: G(delta_i) and D c of the tile's rows are complete
         if (s_fail) return;
-        const double* qt = A.qt + (long)i * d;
+        const double* qt = A.qt ? A.qt + (long)i * d : nullptr;
+        const double* ko = A.kold ? A.kold + (long)i * d : nullptr;
         double* qn = A.q + (long)(i + 1) * d;
         double* dl = A.dlt64;
-        double* ga = A.gacc ? A.gacc + (long)i * d : nullptr;
+        double* ga = (DELTA && A.gacc) ? A.gacc + (long)i * d : nullptr;
         double s = 0.0;
         for (int k = tid; k < 3 * ncl; k += CS_NT) {
             const int f = k / ncl, kk = k - f * ncl;
             const long row = tile_row(f, kk);
             const double gin = R[row];
-            const double y = qt[row] + (gin + dc[f * nclx + kk]);
+            double y;
+            if (DELTA) {
+                y = qt[row] + (gin + dc[f * nclx + kk]);
+            } else {
+                const double knew = gin + dc[f * nclx + kk];
+                y = (qt ? qt[row] : 0.0) + (knew - (ko ? ko[row] : 0.0));
+            }
             const double e = y - qn[row];
             s += e * e;
             qn[row] = y;
-            dl[row] = e;
+            if (DELTA) dl[row] = e;
             if (ga) ga[row] += gin;
         }
 #pragma unroll
@@ -555,6 +582,7 @@ size_t split_smem_bytes(int nx, int ny, int nb, int order, int ccap) {
 }
 
 // CTAs of the split-group chain (one per SM), or 0 when it does not fit
+template <bool DELTA>
 int split_grid(size_t smem) {
     static DevMemo memo;   // [device] -> (shared-memory bytes, blocks)
     int dev = 0;
@@ -565,8 +593,8 @@ int split_grid(size_t smem) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     {
         std::lock_guard<std::mutex> lk(smem_launch_lock());
-        if (set_dynamic_smem((const void*)k_chain_split, smem) != cudaSuccess) return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain_split, CS_NT, smem);
+        if (set_dynamic_smem((const void*)k_chain_split<DELTA>, smem) != cudaSuccess) return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain_split<DELTA>, CS_NT, smem);
     }
     blocks = per >= 1 ? sms : 0;
     memo.put(dev, (int)smem, blocks);
@@ -578,24 +606,27 @@ int split_grid(size_t smem) {
 cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s) {
     if (a.i_end <= a.i_begin) return cudaSuccess;
     if (a.dlt && a.dlt64) return cudaErrorInvalidValue;
-    if (a.dlt64 && a.cc.scheme == 0 && a.cc.n_sound >= 1 && a.n_g >= 1 && a.qt) {
-        // FP64 delta form with the split coarse step: coarse steps and
-        // products side by side in two thread groups (one CTA per SM)
+    const bool split_delta = a.dlt64 && a.qt, split_literal = !a.dlt && !a.dlt64;
+    if ((split_delta || split_literal) && a.cc.scheme == 0 && a.cc.n_sound >= 1 && a.n_g >= 1) {
+        // FP64 with the split coarse step: coarse steps and products side by
+        // side in two thread groups (one CTA per SM)
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int nb = a.max_blocks > 0 && a.max_blocks < sms ? a.max_blocks : sms;
         const size_t smem = nb >= 1 ? split_smem_bytes(a.nx, a.ny, nb, a.cc.order, a.ccap) : 0;
-        if (smem > 0 && smem <= 200 * 1024 && split_grid(smem) >= nb) {
+        const void* fn = split_delta ? (const void*)k_chain_split<true> : (const void*)k_chain_split<false>;
+        const int fit = split_delta ? split_grid<true>(smem) : split_grid<false>(smem);
+        if (smem > 0 && smem <= 200 * 1024 && fit >= nb) {
             cudaError_t e = cudaMemsetAsync(&a.gb->count, 0, sizeof(unsigned), s);
             if (e == cudaSuccess) e = cudaMemsetAsync(a.gb->gcount, 0, sizeof(a.gb->gcount), s);
             if (e != cudaSuccess) return e;
             ChainArgs arg = a;
             void* args[] = {&arg};
             std::lock_guard<std::mutex> lk(smem_launch_lock());
-            e = set_dynamic_smem((const void*)k_chain_split, smem);
+            e = set_dynamic_smem(fn, smem);
             if (e != cudaSuccess) return e;
-            e = cudaLaunchCooperativeKernel((const void*)k_chain_split, dim3(nb), dim3(CS_NT), args, smem, s);
+            e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(CS_NT), args, smem, s);
             count_launches(1);
             return e;
         }

@@ -8,7 +8,10 @@
 // rows of the long operand (basis columns for Q^T V, state rows for V - Q C)
 // against all SG_N = 16 columns of the narrow operand, over a range of the
 // contraction.  Warp 0 streams the 8 digit slices of both operands through a
-// 3-stage TMA pipeline (operand tiles stored pre-swizzled), warp 1 issues 8
+// 3-stage TMA pipeline (operand tiles stored pre-swizzled; one 4-D tensor
+// load per operand and stage brings all 8 slices -- with one 2-D load per
+// slice and tile piece the issue of up to 32 loads per stage, not the
+// memory, set the pace), warp 1 issues 8
 // MMAs per 16 contraction elements -- one per digit slice of the long operand
 // against the stacked slices of the narrow one, 43 digit products in all --
 // into 9 FP32 accumulators (double-buffered across 256-element chunks), and warps
@@ -50,9 +53,6 @@ constexpr int SG_THREADS = 256;
 
 struct SgArgs {
     int mode;               // 0: partial sums of Q^T V;  1: V <- V - Q C
-    long a_slice_units;     // long operand: units between digit slices
-    long a_kb_units;        //   units between contraction blocks (= its row groups)
-    long b_slice_units;     // narrow operand: units between digit slices (2 per block)
     const int* rows_dev;    // mode 0: valid rows (basis columns r)
     int rows_host;          // bound on the rows of the long operand (mode 0: cap, mode 1: d)
     const int* k_dev;       // mode 1: contraction length (basis columns); NULL: k_host
@@ -92,9 +92,11 @@ __device__ __forceinline__ void sg_fail(int* err, volatile int* abort_flag) {
 // pipeline counters run on across items, so loads of the next item overlap
 // the epilogue of the current one.
 __global__ void __launch_bounds__(SG_THREADS, 1)
-    k_split_mma(const __grid_constant__ CUtensorMap mapA16, const __grid_constant__ CUtensorMap mapA8,
-                const __grid_constant__ CUtensorMap mapA4, const __grid_constant__ CUtensorMap mapA2,
-                const __grid_constant__ CUtensorMap mapB2, const SgArgs a) {
+    k_split_mma(const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapA4,
+                const __grid_constant__ CUtensorMap mapA6, const __grid_constant__ CUtensorMap mapA8,
+                const __grid_constant__ CUtensorMap mapA10, const __grid_constant__ CUtensorMap mapA12,
+                const __grid_constant__ CUtensorMap mapA14, const __grid_constant__ CUtensorMap mapA16,
+                const __grid_constant__ CUtensorMap mapB, const SgArgs a) {
     extern __shared__ unsigned char sg_raw[];
     __shared__ __align__(8) uint64_t bars[2 * SG_NST + 5];
     __shared__ uint32_t tmem_slot;
@@ -167,10 +169,7 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
     }
     if (warp == 0 && lane == 0) {
         tc::tma_prefetch_map(&mapA16);
-        tc::tma_prefetch_map(&mapA8);
-        tc::tma_prefetch_map(&mapA4);
-        tc::tma_prefetch_map(&mapA2);
-        tc::tma_prefetch_map(&mapB2);
+        tc::tma_prefetch_map(&mapB);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -201,30 +200,16 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
                         break;
                     }
                     tc::mbar_expect_tx(full(st), bytes);
-                    const long kblk = kb / SG_KC + j;
+                    const int kblk = (int)(kb / SG_KC + j);
                     const uint32_t sa = sbase + st * SG_STAGE;
                     const uint32_t sb = sa + SG_S * SG_A_TILE;
-#pragma unroll 1
-                    for (int s = 0; s < SG_S; ++s) {
-                        const int ua = (int)(s * a.a_slice_units + kblk * a.a_kb_units + row0 / 8);
-                        // the ng row groups as boxes of 16, 8, 4 and 2 units (at most 3 loads)
-                        if (ng == 16) {
-                            tc::tma_load_2d(sa + s * SG_A_TILE, &mapA16, 0, ua, full(st));
-                        } else {
-                            int u = 0;
-                            if (ng & 8) {
-                                tc::tma_load_2d(sa + s * SG_A_TILE, &mapA8, 0, ua, full(st));
-                                u += 8;
-                            }
-                            if (ng & 4) {
-                                tc::tma_load_2d(sa + s * SG_A_TILE + u * 512, &mapA4, 0, ua + u, full(st));
-                                u += 4;
-                            }
-                            if (ng & 2) tc::tma_load_2d(sa + s * SG_A_TILE + u * 512, &mapA2, 0, ua + u, full(st));
-                        }
-                        tc::tma_load_2d(sb + s * SG_B_TILE, &mapB2, 0, (int)(s * a.b_slice_units + kblk * 2),
-                                        full(st));
-                    }
+                    // all 8 digit slices of the long operand's ng row groups
+                    // (slice s at s * ng units) and of the narrow operand's 2
+                    const CUtensorMap* mA = ng == 16 ? &mapA16 : ng == 14 ? &mapA14 : ng == 12 ? &mapA12
+                                          : ng == 10 ? &mapA10 : ng == 8 ? &mapA8 : ng == 6 ? &mapA6
+                                          : ng == 4 ? &mapA4 : &mapA2;
+                    tc::tma_load_4d(sa, mA, 0, row0 / 8, kblk, 0, full(st));
+                    tc::tma_load_4d(sb, &mapB, 0, 0, kblk, 0, full(st));
                     issued[st] += 1;
                 }
             }
@@ -244,6 +229,8 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
                 item(i, row0, kb, ke, split);
                 const int ns = (int)((ke - kb + SG_KC - 1) / SG_KC);
                 const int nch = (ns + SG_SPC - 1) / SG_SPC;
+                // slice s of the long operand's tile starts s * ng units into the stage
+                const uint32_t sl_bytes = (uint32_t)(((min(SG_BM, rows - row0) + 15) / 16) * 2) * 512u;
                 for (int c = 0; c < nch && ok; ++c, ++cg) {
                     const int buf = cg & 1;
                     const uint32_t use = (uint32_t)(cg >> 1);
@@ -270,7 +257,7 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
                             const uint64_t bd = tc::desc_kmajor_sw64(sb + kk * 32);
 #pragma unroll
                             for (int s = 0; s < SG_S; ++s) {
-                                const uint64_t ad = tc::desc_kmajor_sw64(sa + s * SG_A_TILE + kk * 32);
+                                const uint64_t ad = tc::desc_kmajor_sw64(sa + s * sl_bytes + kk * 32);
                                 // slice 0 (groups 0..S) overwrites at the chunk's first step; the
                                 // others then accumulate into groups s..S
                                 tc::mma_bf16(dbase + (uint32_t)(s * SG_N), ad, bd, sg_idesc(s), init | (s > 0));
@@ -309,6 +296,13 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
             uint32_t nanmask = 0;
 #pragma unroll
             for (int n = 0; n < SG_N; ++n) hi[n] = lo[n] = 0;
+            // mode 1: the row's values of v, loaded together before the wait
+            // (one memory round trip instead of one per column)
+            const int vrow = row0 + q * 32 + lane;
+            double vold[SG_N];
+#pragma unroll
+            for (int n = 0; n < SG_N; ++n)
+                vold[n] = (a.mode == 1 && vrow < rows && n < a.ncols) ? a.v[vrow + (long)n * a.ldv] : 0.0;
             for (int c = 0; c < nch; ++c, ++cg) {
                 const int buf = cg & 1;
                 const uint32_t use = (uint32_t)(cg >> 1);
@@ -356,8 +350,7 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
                     if (n < a.ncols) {
                         const double t = (nanmask >> n) & 1u ? __longlong_as_double(0x7FF8000000000000ll)
                                                                : fma((double)hi[n], 0x1p-21, (double)lo[n] * 0x1p-56);
-                        double* o = a.v + row + (long)n * a.ldv;
-                        *o = fma(-t, s_scale[n], *o);
+                        a.v[row + (long)n * a.ldv] = fma(-t, s_scale[n], vold[n]);
                     }
                 }
             }
@@ -638,14 +631,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // BF16 2-D map over `units` operand units of 512 bytes (256 elements each,
 // stored already in the tensor cores' swizzled layout, so no TMA swizzle), box
 // of `box_units` consecutive units, zero fill beyond the end.
-bool make_map(CUtensorMap* m, const void* base, uint64_t units, uint32_t box_units) {
+// A digit-slice operand of units of 512 bytes ordered [slice][contraction
+// block][row group] as a 4-D tensor (256 elements, row groups, blocks,
+// slices); a box covers box_units row groups of one block in all 8 slices.
+// Row groups past the end read as zeros.
+bool make_map(CUtensorMap* m, const void* base, uint64_t groups, uint64_t blocks, uint32_t box_units) {
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[2] = {256, units};
-    cuuint64_t strides[1] = {512};
-    cuuint32_t box[2] = {256, box_units};
-    cuuint32_t es[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+    cuuint64_t dims[4] = {256, groups, blocks, (cuuint64_t)SG_S};
+    cuuint64_t strides[3] = {512, 512 * groups, 512 * groups * blocks};
+    cuuint32_t box[4] = {256, box_units, 1, (cuuint32_t)SG_S};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -661,7 +658,7 @@ cudaError_t launch_mma(const CUtensorMap* A, const CUtensorMap& B2, const SgArgs
     std::lock_guard<std::mutex> lk(smem_launch_lock());
     const cudaError_t attr = set_dynamic_smem((const void*)k_split_mma, SG_DSMEM);
     if (attr != cudaSuccess) return attr;
-    k_split_mma<<<grid, SG_THREADS, SG_DSMEM, s>>>(A[0], A[1], A[2], A[3], B2, a);
+    k_split_mma<<<grid, SG_THREADS, SG_DSMEM, s>>>(A[0], A[1], A[2], A[3], A[4], A[5], A[6], A[7], B2, a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -738,13 +735,14 @@ cudaError_t sg_init(SplitGemm* g, long d, int cap, bool images) {
         sg_free(g);
         return attr;
     }
-    bool ok = make_map(&g->mapVs2, g->Vs, uVs, 2) && make_map(&g->mapCs2, g->Cs, uCs, 2);
-    for (int i = 0; i < 4; ++i) {
-        ok = ok && make_map(&g->mapXc[i], g->Xc, uXc, 16u >> i);
-        ok = ok && make_map(&g->mapXr[i], g->Xr, uXr, 16u >> i);
-        if (images) ok = ok && make_map(&g->mapDr[i], g->Dr, uXr, 16u >> i);
+    bool ok = make_map(&g->mapVs, g->Vs, 2, (uint64_t)g->nkb, 2) && make_map(&g->mapCs, g->Cs, 2, (uint64_t)g->nlb, 2);
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t box = 2u * (uint32_t)(i + 1);
+        ok = ok && make_map(&g->mapXc[i], g->Xc, (uint64_t)g->ngl, (uint64_t)g->nkb, box);
+        ok = ok && make_map(&g->mapXr[i], g->Xr, (uint64_t)g->ngd, (uint64_t)g->nlb, box);
+        if (images) ok = ok && make_map(&g->mapDr[i], g->Dr, (uint64_t)g->ngd, (uint64_t)g->nlb, box);
     }
-    if (images) ok = ok && make_map(&g->mapCsD2, g->CsD, uCs, 2);
+    if (images) ok = ok && make_map(&g->mapCsD, g->CsD, 2, (uint64_t)g->nlb, 2);
     if (!ok) {
         sg_free(g);
         return cudaErrorNotSupported;
@@ -830,16 +828,13 @@ cudaError_t sg_project(SplitGemm* g, const double* v, long ldv, int m, const int
     if (e != cudaSuccess) return e;
     SgArgs a{};
     a.mode = 0;
-    a.a_slice_units = g->nkb * g->ngl;
-    a.a_kb_units = g->ngl;
-    a.b_slice_units = g->nkb * 2;
     a.rows_dev = r_dev;
     a.rows_host = g->cap;
     a.k_host = g->d;
     a.ws = g->ws;
     a.rows_pad = g->cap_pad;
     a.err = g->err;
-    e = launch_mma(g->mapXc, g->mapVs2, a, dim3((unsigned)g->grid), s);
+    e = launch_mma(g->mapXc, g->mapVs, a, dim3((unsigned)g->grid), s);
     if (e != cudaSuccess) return e;
     k_finish<<<SG_N, FIN_T, sizeof(double) * g->cap_pad, s>>>(g->ws, g->cap_pad, g->grid, g->d, r_dev, g->Eq, g->Fv, m,
                                                             g->C, g->cap_pad, nullptr, 0, g->Cs, g->cap_pad, g->Gc);
@@ -853,9 +848,6 @@ static cudaError_t sg_apply(SplitGemm* g, double* v, long ldv, int m, const int*
                             const CUtensorMap& mapB, int* gc, cudaStream_t s) {
     SgArgs a{};
     a.mode = 1;
-    a.a_slice_units = (long)g->nlb * g->ngd;
-    a.a_kb_units = g->ngd;
-    a.b_slice_units = (long)g->nlb * 2;
     a.rows_host = (int)g->d;
     a.k_dev = r_dev;
     a.k_host = g->cap;
@@ -868,7 +860,7 @@ static cudaError_t sg_apply(SplitGemm* g, double* v, long ldv, int m, const int*
     return launch_mma(mapA, mapB, a, dim3((unsigned)(tiles < g->grid ? tiles : g->grid)), s);
 }
 static cudaError_t sg_apply_update(SplitGemm* g, double* v, long ldv, int m, const int* r_dev, cudaStream_t s) {
-    return sg_apply(g, v, ldv, m, r_dev, g->mapXr, g->mapCs2, g->Gc, s);
+    return sg_apply(g, v, ldv, m, r_dev, g->mapXr, g->mapCs, g->Gc, s);
 }
 
 cudaError_t sg_cgs_pass(SplitGemm* g, double* v, long ldv, int m, const int* r_dev, cudaStream_t s) {
@@ -885,7 +877,7 @@ cudaError_t sg_update_images(SplitGemm* g, double* z, long ldz, int m, const int
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return sg_apply(g, z, ldz, m, r_dev, g->mapDr, g->mapCsD2, g->GcD, s);
+    return sg_apply(g, z, ldz, m, r_dev, g->mapDr, g->mapCsD, g->GcD, s);
 }
 cudaError_t sg_update(SplitGemm* g, double* v, long ldv, int m, const double* C, int ldc, const int* r_dev,
                       cudaStream_t s) {

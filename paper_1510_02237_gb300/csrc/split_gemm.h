@@ -53,8 +53,12 @@ struct SplitGemm {
     double* ws = nullptr;          // [grid][SG_N][cap_pad] partial sums of Q^T V
     double* C = nullptr;           // [SG_N][cap_pad] coefficients Q^T V (column-major, ld cap_pad)
     int* err = nullptr;            // sticky: a pipeline wait gave up
-    CUtensorMap mapXc[4], mapXr[4];   // boxes of 16, 8, 4 and 2 units
-    CUtensorMap mapVs2, mapCs2;       // boxes of 2 units
+    // 4-D maps (element, row group, contraction block, digit slice): one load
+    // brings all 8 slices of a stage's operand tile.  mapXc[i] / mapXr[i]
+    // load 2 (i + 1) row groups (16 (i + 1) rows); mapVs / mapCs the 2 row
+    // groups of the narrow operand.
+    CUtensorMap mapXc[8], mapXr[8];
+    CUtensorMap mapVs, mapCs;
     // With images (sg_init(..., true)): the basis images D = F(Q) - G(Q) in
     // the Xr layout, their column exponents, and the coefficient digits
     // folded with those exponents, so that z <- z - D C runs like v <- v - Q C.
@@ -63,7 +67,7 @@ struct SplitGemm {
     int* Ed = nullptr;             // [cap] column exponents of D
     int* GcD = nullptr;            // [SG_N] exponents of the folded coefficient columns
     unsigned long long* Kd = nullptr;   // [cap_pad] column maxima keys of D
-    CUtensorMap mapDr[4], mapCsD2;
+    CUtensorMap mapDr[8], mapCsD;
 };
 
 // Bytes of device memory sg_init allocates for (d, cap, images).
