@@ -72,13 +72,15 @@ def parse():
     ap.add_argument("--serving-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests of the equal-accuracy serving stream (12 requests/s)")
-    ap.add_argument("--case", choices=["fine", "fine32", "fine32x", "solve", "solve_mixed", "solve_tc"], default=None,
+    ap.add_argument("--case", choices=["fine", "fine32", "fine32x", "solve", "solve_mixed", "solve_tc", "split"],
+                    default=None,
                     help="small isolated case for profiler captures: 'fine' = three fine sweeps over all "
                          "32 slices of the 256x128 workload; 'fine32' = three FP32 fine sweeps over the 64 "
                          "slices of the 512x256 workload ('fine32x': FP32 stages on an FP64 state); 'solve' = "
                          "two solves of the 256x128 workload's "
                          "first IC; 'solve_mixed' = the same in mixed precision with the tensor-core projections; "
-                         "'solve_tc' = FP64 with the tensor-core projections")
+                         "'solve_tc' = FP64 with the tensor-core projections; 'split' = the tensor-core products "
+                         "C = A^T B and Y -= A B on A of 98304 x m (m = 128 ... 16) and 16 columns, twice each")
     return ap.parse_args()
 
 
@@ -817,6 +819,22 @@ def run_case(args):
 
     import paper_1510_02237_gb300 as P
     torch.cuda.set_device(0)
+    if args.case == "split":
+        d = W.workload_medium().problem.d
+        g = torch.Generator(device="cuda").manual_seed(1)
+        for m in (128, 112, 96, 64, 56, 32, 16):
+            A = torch.randn(m, d, device="cuda", dtype=torch.float64, generator=g)
+            B = torch.randn(16, d, device="cuda", dtype=torch.float64, generator=g)
+            C = torch.empty(16, m, device="cuda", dtype=torch.float64)
+            for _ in range(2):
+                P.parareal_split_gemm_tn(A, B, C)
+            Y = torch.randn(16, d, device="cuda", dtype=torch.float64, generator=g)
+            Bn = torch.randn(16, m, device="cuda", dtype=torch.float64, generator=g)
+            for _ in range(2):
+                P.parareal_split_gemm_nn(A, Bn, Y)
+        torch.cuda.synchronize()
+        print("case split done")
+        return 0
     wl = W.workload_large() if args.case in ("fine32", "fine32x") else W.workload_medium()
     p = wl.problem
     opt = {}
