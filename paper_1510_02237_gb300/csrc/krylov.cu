@@ -363,13 +363,27 @@ __global__ void __launch_bounds__(IB_NT) k_intra_block(double* wv, double* wz, l
                 __syncthreads();
             }
             if (!grid_barrier(gb, nb)) return;
-            for (int l = wid; l < nn; l += nw) {
-                const double s = warp_sum_strided(P + l, nb, pstride);
-                if (lane == 0) cs[l] = s;
-            }
-            if (last && wid == nw - 1) {
-                const double t = warp_sum_strided(P + 63, nb, pstride);
-                if (lane == 0) s_res2 = t;
+            {
+                // every CTA sums all CTAs' partials of the nn coefficients (and
+                // of ||v||^2 in the last pass) with the loads in flight together:
+                // 16 threads per value, each summing every 16th CTA's partial in
+                // order, then a fixed butterfly over the 16 lanes
+                const int nval = nn + (last ? 1 : 0);
+                for (int v0 = 0; v0 < nval; v0 += IB_NT / 16) {
+                    const int vi = v0 + (int)(threadIdx.x >> 4), sub = threadIdx.x & 15;
+                    double s = 0.0;
+                    if (vi < nval) {
+                        const double* pp = P + (vi < nn ? vi : 63);
+#pragma unroll 8
+                        for (unsigned k = sub; k < nb; k += 16) s += __ldcg(pp + (long)k * pstride);
+                    }
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    if (sub == 0 && vi < nval) {
+                        if (vi < nn) cs[vi] = s;
+                        else s_res2 = s;
+                    }
+                }
             }
             buf ^= 1;
             __syncthreads();
