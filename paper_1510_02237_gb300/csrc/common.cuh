@@ -150,6 +150,11 @@ cudaError_t launch_fine_step_acc64(const double* in, double* out, long stride, i
                                   const FineLaunch& fl = FineLaunch());
 // true when an FP32-input step of this shape runs on the row-streamed kernel
 bool fine_rows_eligible(int nx, bool has_v);
+// FP32 copies of n FP64 states (slice z of the output from slice z, or with
+// map.in_map slice *map.beg + z, of the input; slices z >= *end - *beg of a
+// map are skipped).
+cudaError_t launch_to_fp32_states(const double* in, long instride, float* out, long outstride, int n, long d,
+                                  const SliceMap& map, cudaStream_t s);
 
 // One coarse step (slow tendency + n_sound forward-backward substeps) on n
 // states, FP64 arithmetic or FP32 arithmetic (fp32) on FP64 data.

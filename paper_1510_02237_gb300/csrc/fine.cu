@@ -285,6 +285,33 @@ cudaError_t launch_fine_step(const Tin* in, long instride, Tout* out, long outst
     return launch_tiles<T, Tin, Tout, false>(in, instride, out, outstride, n, nx, ny, has_v, c, s, map, fl);
 }
 
+namespace {
+__global__ void k_to_fp32_states(const double* __restrict__ in, long instride, float* __restrict__ out,
+                                 long outstride, int n, long d, SliceMap map) {
+    long zb = 0;
+    int nact = n;
+    if (map.end) {
+        nact = min(n, *map.end - *map.beg);
+        if (map.in_map) zb = *map.beg;
+    }
+    const long tot = (long)nact * d;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long)gridDim.x * blockDim.x) {
+        const long z = i / d, k = i - z * d;
+        out[z * outstride + k] = (float)in[(zb + z) * instride + k];
+    }
+}
+}  // namespace
+
+cudaError_t launch_to_fp32_states(const double* in, long instride, float* out, long outstride, int n, long d,
+                                  const SliceMap& map, cudaStream_t s) {
+    if (n < 1 || d < 1) return cudaSuccess;
+    long blocks = ((long)n * d + 255) / 256;
+    if (blocks > 152L * 16) blocks = 152L * 16;
+    k_to_fp32_states<<<(unsigned)blocks, 256, 0, s>>>(in, instride, out, outstride, n, d, map);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fine_step_acc64(const double* in, double* out, long stride, int n, int nx, int ny, bool has_v,
                                   const FineCoef<float>& c, cudaStream_t s, const SliceMap& map,
                                   const FineLaunch& fl) {

@@ -185,7 +185,19 @@ static pr_status fine_apply(pr_solver* h, const double* in, double* out, int n, 
             CKC((launch_fine_step<float, double, double>(in, d, out, d, n, h->nx, h->ny, hv, h->fc32, s, m0, h->fl)));
             return PR_OK;
         }
-        CKC((launch_fine_step<float, double, float>(in, d, h->f32a, d, n, h->nx, h->ny, hv, h->fc32, s, m0, h->fl)));
+        if (h->fl.rows && fine_rows_eligible(h->nx, hv)) {
+            // FP32 copies of the input first, so that the first step also runs
+            // on the row-streamed kernel (an FP64 input would be converted at
+            // every read): one conversion pass, then FP32 -> FP32
+            SliceMap mc = m0;
+            mc.in_map = false;
+            CKC(launch_to_fp32_states(in, d, h->f32b, d, n, d, m0, s));
+            CKC((launch_fine_step<float, float, float>(h->f32b, d, h->f32a, d, n, h->nx, h->ny, hv, h->fc32, s, mc,
+                                                       h->fl)));
+        } else {
+            CKC((launch_fine_step<float, double, float>(in, d, h->f32a, d, n, h->nx, h->ny, hv, h->fc32, s, m0,
+                                                        h->fl)));
+        }
         float* a = h->f32a;
         float* b = h->f32b;
         for (int st = 1; st < nf - 1; ++st) {
