@@ -70,14 +70,17 @@ def test_coarse_sweep_chain(nx, ny, N, order, rotation, sm_limit):
         assert _rel(got[i], q) < TOL64, (i, _rel(got[i], q))
 
 
+@pytest.mark.parametrize("nx,ny,N", [(200, 72, 6), (15, 9, 4)], ids=["200x72_N6", "15x9_N4"])
 @pytest.mark.parametrize("sm_limit", [0, 6])
 @pytest.mark.parametrize("order", [1, 3])
 @pytest.mark.parametrize("variant", ["kse", "original"])
-def test_solve_chain_ragged(variant, order, sm_limit):
-    """K = 3 iterations on the ragged 200 x 72 grid: the delta-form chain with
-    the basis products (KSE) and the literal chain with K_old (original)."""
-    p = _problem(200, 72, 6, order, False)
-    q0 = W.ic_gaussian(200, 72, seed=3).ravel()
+def test_solve_chain_ragged(variant, order, sm_limit, nx, ny, N):
+    """K = 3 iterations on ragged grids: the delta-form chain with the basis
+    products (KSE) and the literal chain with K_old (original); 15 x 9 has
+    an odd number of state values (d = 405), so the basis columns start at
+    every 8-byte alignment and the tiles are narrower than one warp."""
+    p = _problem(nx, ny, N, order, False)
+    q0 = W.ic_gaussian(nx, ny, seed=3).ravel()
     K = 3
     with P.Solver(p, stream=torch.cuda.current_stream(), K_max=K, sm_limit=sm_limit,
                   variant=P.PR_KSE if variant == "kse" else P.PR_ORIGINAL) as s:
