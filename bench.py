@@ -518,12 +518,13 @@ def hbm_peak():
 def fine_sweep_fp32(P, torch, stream):
     """The batched FP32 fine sweep on the 512x256 workload: F applied to all
     64 slices at once (the predictor of its first iteration), 20 RK-3 steps:
-    step 1 converts the FP64 states (shared-memory tile kernel), steps 2-20
-    run the row-streamed kernel k_fine_rows (TMA row ring, registers,
-    shuffles), the last writing FP64.  Algorithmic bytes per cell: 36 (first
-    step: FP64 read, FP32 write) + 18 x 24 (FP32 read + write) + 36 (last
-    step: FP32 read, FP64 write) = 504 B; inputs and outputs (201 MB of FP32
-    ping-pong plus 403 MB FP64) exceed the L2."""
+    one pass converts the FP64 states to FP32, then all 20 steps run the
+    row-streamed kernel k_fine_rows (TMA row ring, registers, shuffles), the
+    last writing FP64.  Algorithmic bytes per cell: 36 (first step: FP64
+    read, FP32 write) + 18 x 24 (FP32 read + write) + 36 (last step: FP32
+    read, FP64 write) = 504 B (the separate conversion pass moves 24 B more,
+    not counted); inputs and outputs (201 MB of FP32 ping-pong plus 403 MB
+    FP64) exceed the L2."""
     wl = W.workload_large()
     p = wl.problem
     s = P.Solver(p, stream=stream, K_max=1, fine_prec=P.PR_FP32)
@@ -548,7 +549,7 @@ def fine_sweep_fp32(P, torch, stream):
     peak, src = hbm_peak()
     achieved = bytes_ / (ms / 1e3) / 1e9
     return {"workload": f"{wl.name} predictor: {p.n_slices} slices x {p.nx}x{p.ny}, {p.n_f} RK-3 steps, FP32",
-            "kernels": "k_fine_rows (19 of 20 launches), k_fine_step<float,double,float> (first step)",
+            "kernels": "k_to_fp32_states (FP64 input to FP32), k_fine_rows (all 20 steps)",
             "ms_per_sweep": ms, "launches_per_sweep": launches,
             "cell_steps_per_s": cells * p.n_f / (ms / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
