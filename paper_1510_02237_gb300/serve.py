@@ -96,7 +96,9 @@ class Server:
     """Admit, run and complete requests; see the module docstring."""
 
     def __init__(self, budget_bytes: float = 150e9, max_inflight: int = 16, mode: str = "mixed",
-                 sm_limit=default_sm_limit, autotune: bool = True):
+                 sm_limit=default_sm_limit, autotune: bool = True, sms: int | None = None):
+        """sms: the SM count the admission shares out (default: the current
+        device's)."""
         import torch
         if mode not in self.MODES:
             raise ValueError(f"mode must be one of {self.MODES}")
@@ -106,7 +108,8 @@ class Server:
         self.mode = mode
         self.sm_limit = sm_limit
         self.autotune = autotune
-        self.sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        self.sms = int(sms) if sms else \
+            torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         self.slots = collections.defaultdict(list)
         self.bytes = 0
 
