@@ -237,8 +237,10 @@ __global__ void __launch_bounds__(CH_NT) k_chain(ChainArgs A) {
 // kernel's (the shared fb_new_* helpers; a ring cell's forward values are
 // those its owner computes), and each dot product, coefficient sum and D c
 // row is summed in the tile kernel's order, so the iterates are the same bit
-// for bit; only the order of the residual partial sums differs.
-constexpr int CS_NT = 512, CS_CW = 4, CS_CT = 32 * CS_CW, CS_PT = CS_NT - CS_CT, CS_PW = CS_PT / 32;
+// for bit; only the order of the residual partial sums differs.  The literal
+// form without a basis (the coarse initialisation, the original Parareal, the
+// coarse sweep) has no products: there all 16 warps form the coarse group.
+constexpr int CS_NT = 512, CS_NW = CS_NT / 32, CS_CW = 4;   // threads, warps, coarse warps
 constexpr int CS_TW = 16;   // tile width
 
 // Tiling of an nx x ny grid on nb CTAs: tiles of tw0 x th0 (the last column
@@ -300,8 +302,11 @@ __device__ __forceinline__ double warp_dot_x_l2(const double* a, const double* x
     return s;
 }
 
-template <bool DELTA>
+// CW: warps of the coarse group; CW = CS_NW (no product group) for the literal
+// form without a basis, where D c = 0.
+template <bool DELTA, int CW>
 __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
+    constexpr int CT = 32 * CW, PT = CS_NT - CT, PW = PT / 32 > 0 ? PT / 32 : 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double red[CS_NT / 32];
     __shared__ int s_okc, s_okp, s_okf, s_fail;
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
     for (int i = A.i_begin; i < A.i_end; ++i) {
         // the state K acts on: delta_i, or q_i itself (literal form)
         const double* xin = DELTA ? A.dlt64 : A.q + (long)i * d;
-        if (wid < CS_CW) {
+        if (wid < CW) {
             // ---------------------------------------------------- coarse group
             const int ct = tid;
             const double* X = xin;
@@ -369,11 +374,11 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
                 for (int m = 0; m < cc.n_sound && ok; ++m) {
                     // the state on the tile and its ring (periodic); four cells
                     // per thread at a time, their loads in flight together
-                    for (int e0 = ct; e0 < RW * RH; e0 += 4 * CS_CT) {
+                    for (int e0 = ct; e0 < RW * RH; e0 += 4 * CT) {
                         double vu[4], vw[4], vp[4];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            const int e = e0 + q * CS_CT;
+                            const int e = e0 + q * CT;
                             if (e < RW * RH) {
                                 const int ly = e / RW, lx = e - ly * RW;
                                 const long g = (long)pwrap(ty0 - LR + ly, ny) * nx + pwrap(tx0 - LR + lx, nx);
@@ -384,7 +389,7 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
                         }
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            const int e = e0 + q * CS_CT;
+                            const int e = e0 + q * CT;
                             if (e < RW * RH) {
                                 st[e] = vu[q];
                                 st[RSZ + e] = vw[q];
@@ -392,10 +397,10 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
                             }
                         }
                     }
-                    named_barrier(1, CS_CT);
+                    named_barrier(1, CT);
                     if (m == 0) {
                         // slow tendencies of the step's input (cur == X) on the tile + ring 1
-                        for (int e = ct; e < HW * HH; e += CS_CT) {
+                        for (int e = ct; e < HW * HH; e += CT) {
                             const int hy = e / HW, hx = e - hy * HW;
                             const int si = (hy + LR - 1) * RW + hx + LR - 1;
                             double Ur = cc.U, Vc = cc.V;
@@ -425,14 +430,14 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
                                 S[f * HSZ + e] = v;
                             }
                         }
-                        named_barrier(1, CS_CT);
+                        named_barrier(1, CT);
                     }
                     // forward: velocities on the tile + ring 1
                     {
                         const double* u = st;
                         const double* w = st + RSZ;
                         const double* p = st + 2 * RSZ;
-                        for (int e = ct; e < HW * HH; e += CS_CT) {
+                        for (int e = ct; e < HW * HH; e += CT) {
                             const int hy = e / HW, hx = e - hy * HW;
                             const int si = (hy + LR - 1) * RW + hx + LR - 1;
                             fu[e] = fb_new_u<double>(cc, S[e], u[si], u[si + 1], u[si - 1], p[si + 1], p[si - 1],
@@ -442,9 +447,9 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
                                                      u[si - 1 - RW]);
                         }
                     }
-                    named_barrier(1, CS_CT);
+                    named_barrier(1, CT);
                     // backward: pressure on the tile; the tile's new state is written out
-                    for (int k = ct; k < ncl; k += CS_CT) {
+                    for (int k = ct; k < ncl; k += CT) {
                         const int ly = k / tw, lx = k - ly * tw;
                         const int e = (ly + 1) * HW + lx + 1, si = (ly + LR) * RW + lx + LR;
                         const double pn = fb_new_p<double>(cc, S[2 * HSZ + e], st[2 * RSZ + si], fu[e + 1], fu[e - 1],
@@ -455,7 +460,7 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
                         nxt[2 * ncell + g] = pn;
                     }
                     const bool last = gs == A.n_g - 1 && m == cc.n_sound - 1;
-                    if (!last && !grid_barrier_group(A.gb, 0, nb, 1, CS_CT, ct == 0, &s_okc)) {
+                    if (!last && !grid_barrier_group(A.gb, 0, nb, 1, CT, ct == 0, &s_okc)) {
                         ok = false;
                         break;
                     }
@@ -465,29 +470,29 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
                 X = cur;
             }
             if (!ok) s_fail = 1;
-        } else {
+        } else if constexpr (PT > 0) {
             // ---------------------------------------------------- product group
-            const int pt = tid - CS_CT, pw = pt >> 5;
+            const int pt = tid - CT, pw = pt >> 5;
             const double* x = xin;
             bool ok = true;
-            for (int l = pw; l < ncols; l += CS_PW) {
+            for (int l = pw; l < ncols; l += PW) {
                 const double s = warp_dot_x_l2(A.Q + (long)l * d, x, r0, r1);
                 if (lane == 0) A.part[(long)b * A.ccap + l] = s;
             }
-            ok = grid_barrier_group(A.gb, 1, nb, 2, CS_PT, pt == 0, &s_okp);
+            ok = grid_barrier_group(A.gb, 1, nb, 2, PT, pt == 0, &s_okp);
             if (ok && ncols > 0) {
                 const int cpb = (ncols + (int)nb - 1) / (int)nb;
                 const int l1 = min(ncols, (b + 1) * cpb);
-                for (int l = b * cpb + pw; l < l1; l += CS_PW) {
+                for (int l = b * cpb + pw; l < l1; l += PW) {
                     const double s = warp_sum_strided(A.part + l, nb, A.ccap);
                     if (lane == 0) A.cvec[l] = s;
                 }
             }
-            if (ok) ok = grid_barrier_group(A.gb, 1, nb, 2, CS_PT, pt == 0, &s_okp);
+            if (ok) ok = grid_barrier_group(A.gb, 1, nb, 2, PT, pt == 0, &s_okp);
             if (ok) {
-                for (int l = pt; l < ncols; l += CS_PT) cs[l] = __ldcg(A.cvec + l);
-                named_barrier(2, CS_PT);
-                for (int k = pt; k < 3 * ncl; k += CS_PT) {
+                for (int l = pt; l < ncols; l += PT) cs[l] = __ldcg(A.cvec + l);
+                named_barrier(2, PT);
+                for (int k = pt; k < 3 * ncl; k += PT) {
                     const int f = k / ncl, kk = k - f * ncl;
                     const double* Dr = A.D + tile_row(f, kk);
                     double acc = 0.0;
@@ -510,11 +515,12 @@ __global__ void __launch_bounds__(CS_NT, 1) k_chain_split(ChainArgs A) {
             const int f = k / ncl, kk = k - f * ncl;
             const long row = tile_row(f, kk);
             const double gin = R[row];
+            const double dcv = PT > 0 ? dc[f * nclx + kk] : 0.0;   // (no product group: no basis)
             double y;
             if (DELTA) {
-                y = qt[row] + (gin + dc[f * nclx + kk]);
+                y = qt[row] + (gin + dcv);
             } else {
-                const double knew = gin + dc[f * nclx + kk];
+                const double knew = gin + dcv;
                 y = (qt ? qt[row] : 0.0) + (knew - (ko ? ko[row] : 0.0));
             }
             const double e = y - qn[row];
@@ -582,7 +588,7 @@ size_t split_smem_bytes(int nx, int ny, int nb, int order, int ccap) {
 }
 
 // CTAs of the split-group chain (one per SM), or 0 when it does not fit
-template <bool DELTA>
+template <bool DELTA, int CW>
 int split_grid(size_t smem) {
     static DevMemo memo;   // [device] -> (shared-memory bytes, blocks)
     int dev = 0;
@@ -593,8 +599,8 @@ int split_grid(size_t smem) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     {
         std::lock_guard<std::mutex> lk(smem_launch_lock());
-        if (set_dynamic_smem((const void*)k_chain_split<DELTA>, smem) != cudaSuccess) return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain_split<DELTA>, CS_NT, smem);
+        if (set_dynamic_smem((const void*)k_chain_split<DELTA, CW>, smem) != cudaSuccess) return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain_split<DELTA, CW>, CS_NT, smem);
     }
     blocks = per >= 1 ? sms : 0;
     memo.put(dev, (int)smem, blocks);
@@ -615,8 +621,15 @@ cudaError_t chain_coop(const ChainArgs& a, cudaStream_t s) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int nb = a.max_blocks > 0 && a.max_blocks < sms ? a.max_blocks : sms;
         const size_t smem = nb >= 1 ? split_smem_bytes(a.nx, a.ny, nb, a.cc.order, a.ccap) : 0;
-        const void* fn = split_delta ? (const void*)k_chain_split<true> : (const void*)k_chain_split<false>;
-        const int fit = split_delta ? split_grid<true>(smem) : split_grid<false>(smem);
+        // the literal form without a basis (the coarse initialisation, the
+        // original Parareal, the coarse sweep): all warps in the coarse group
+        const bool coarse_only = split_literal && !a.r_dev;
+        const void* fn = split_delta  ? (const void*)k_chain_split<true, CS_CW>
+                         : coarse_only ? (const void*)k_chain_split<false, CS_NW>
+                                       : (const void*)k_chain_split<false, CS_CW>;
+        const int fit = split_delta  ? split_grid<true, CS_CW>(smem)
+                        : coarse_only ? split_grid<false, CS_NW>(smem)
+                                      : split_grid<false, CS_CW>(smem);
         if (smem > 0 && smem <= 200 * 1024 && fit >= nb) {
             cudaError_t e = cudaMemsetAsync(&a.gb->count, 0, sizeof(unsigned), s);
             if (e == cudaSuccess) e = cudaMemsetAsync(a.gb->gcount, 0, sizeof(a.gb->gcount), s);
